@@ -1,0 +1,200 @@
+/*
+ * geometry.c -- oracle geometry: Kerr metric in Kerr-Schild coordinates
+ * (Section 4.1, Eq. 35), the modified-Kerr-Schild map (Section 4.1, Eq. 36),
+ * the inverse metric, sqrt(-g), the lapse, and the connection used by the
+ * source term of Eq. 7.
+ *
+ * TEST INFRASTRUCTURE ONLY (see orc.h).
+ *
+ * The connection is Gamma^l_{mn} = 1/2 g^{ls} (d_m g_{sn} + d_n g_{sm} - d_s g_{mn});
+ * the paper does not say how it is evaluated.  Here the metric derivatives
+ * are taken by the complex-step method, f'(x) = Im f(x + i h) / h, which is
+ * exact to rounding for analytic f, so no finite-difference truncation enters.
+ */
+#include <math.h>
+#include <string.h>
+#include "orc.h"
+
+/* r(X1) of Eq. 36: exponential inside x_b, hyper-exponential outside. */
+static void mks_r_c(const orc_grid *G, double complex X1, double complex *r,
+                    double complex *drdx)
+{
+    const orc_params *p = &G->p;
+    if (creal(X1) < G->xb) {
+        double complex e = cexp(X1);
+        *r = p->R0 + e;
+        *drdx = e;
+    } else {
+        double complex d = X1 - G->xb;
+        double complex dn = 1.0, dn1 = 1.0;
+        int n = (int)p->n_x;
+        if ((double)n == p->n_x && n >= 1) {
+            for (int m = 0; m < n - 1; m++) dn1 *= d;
+            dn = dn1 * d;
+        } else {
+            dn = cpow(d, p->n_x);
+            dn1 = cpow(d, p->n_x - 1.0);
+        }
+        double complex e = cexp(X1 + dn);
+        *r = p->R0 + e;
+        *drdx = e * (1.0 + p->n_x * dn1);
+    }
+}
+
+/* theta(X2) of Eq. 36, read as pi/2 (1+Y) + (1-h)/2 sin(pi (1+Y)): the
+ * equator-refining map (the printed argument pi(1+Y)/2 is not symmetric
+ * about the equator). */
+static void mks_th_c(const orc_grid *G, double complex X2, double complex *th,
+                     double complex *dthdx)
+{
+    double h = G->p.hslope;
+    double complex y = M_PI * (1.0 + X2);
+    *th = 0.5 * M_PI * (1.0 + X2) + 0.5 * (1.0 - h) * csin(y);
+    *dthdx = 0.5 * M_PI + 0.5 * (1.0 - h) * M_PI * ccos(y);
+}
+
+double orc_r_of_x1(const orc_grid *G, double X1)
+{
+    double complex r, d;
+    mks_r_c(G, X1, &r, &d);
+    return creal(r);
+}
+
+double orc_th_of_x2(const orc_grid *G, double X2)
+{
+    double complex th, d;
+    mks_th_c(G, X2, &th, &d);
+    return creal(th);
+}
+
+/* inverse of r(X1) by bisection (monotone map) */
+double orc_x1_of_r(const orc_grid *G, double r)
+{
+    double lo = -50.0, hi = 50.0;
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (orc_r_of_x1(G, mid) < r) lo = mid; else hi = mid;
+        if (hi - lo <= 1e-15 * fabs(mid)) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Kerr-Schild line element of Eq. 35 (M = 1), written for complex r, theta. */
+static void ks_gcov_c(double complex r, double complex th, double a, double complex g[4][4])
+{
+    double complex s = csin(th), c = ccos(th);
+    double complex s2 = s * s, c2 = c * c;
+    double complex sig = r * r + a * a * c2;
+    double complex z = 2.0 * r / sig;
+    memset(g, 0, sizeof(double complex) * 16);
+    g[0][0] = -(1.0 - z);
+    g[0][1] = g[1][0] = z;
+    g[0][3] = g[3][0] = -a * z * s2;
+    g[1][1] = 1.0 + z;
+    g[1][3] = g[3][1] = -a * (1.0 + z) * s2;
+    g[2][2] = sig;
+    g[3][3] = s2 * (sig + a * a * (1.0 + z) * s2);
+}
+
+void orc_ks_gcov(double r, double th, double a, double g[4][4])
+{
+    double complex gc[4][4];
+    ks_gcov_c(r, th, a, gc);
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) g[m][n] = creal(gc[m][n]);
+}
+
+/* metric in the code coordinates (t, X1, X2, X3) */
+void orc_code_gcov_c(const orc_grid *G, double complex X1, double complex X2,
+                     double complex g[4][4])
+{
+    if (G->p.metric == ORC_MINK_CART) {
+        memset(g, 0, sizeof(double complex) * 16);
+        g[0][0] = -1.0;
+        g[1][1] = g[2][2] = g[3][3] = 1.0;
+        return;
+    }
+    double complex r, drdx, th, dthdx, gks[4][4];
+    mks_r_c(G, X1, &r, &drdx);
+    mks_th_c(G, X2, &th, &dthdx);
+    ks_gcov_c(r, th, G->p.a, gks);
+    double complex J[4] = {1.0, drdx, dthdx, 1.0};
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) g[m][n] = gks[m][n] * J[m] * J[n];
+}
+
+/* Gauss-Jordan inversion with partial pivoting; returns 0 if singular. */
+int orc_invert4(const double m[4][4], double inv[4][4], double *det)
+{
+    double a[4][8];
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+            a[r][c] = m[r][c];
+            a[r][c + 4] = (r == c) ? 1.0 : 0.0;
+        }
+    double d = 1.0;
+    for (int c = 0; c < 4; c++) {
+        int piv = c;
+        for (int r = c + 1; r < 4; r++)
+            if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+        if (a[piv][c] == 0.0) { *det = 0.0; return 0; }
+        if (piv != c) {
+            for (int k = 0; k < 8; k++) { double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t; }
+            d = -d;
+        }
+        double pv = a[c][c];
+        d *= pv;
+        for (int k = 0; k < 8; k++) a[c][k] /= pv;
+        for (int r = 0; r < 4; r++) {
+            if (r == c) continue;
+            double f = a[r][c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < 8; k++) a[r][k] -= f * a[c][k];
+        }
+    }
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) inv[r][c] = a[r][c + 4];
+    *det = d;
+    return 1;
+}
+
+int orc_geom_at(const orc_grid *G, double X1, double X2, orc_geom *out)
+{
+    double complex gc[4][4];
+    orc_code_gcov_c(G, X1, X2, gc);
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) out->gcov[m][n] = creal(gc[m][n]);
+    double det;
+    if (!orc_invert4(out->gcov, out->gcon, &det) || !(det < 0.0)) {
+        memset(out, 0, sizeof(*out));
+        return 0;
+    }
+    out->gdet = sqrt(-det);
+    out->alpha = 1.0 / sqrt(-out->gcon[0][0]);
+    return 1;
+}
+
+/* Connection coefficients conn[l][m][n] = Gamma^l_{mn} at (X1, X2). */
+void orc_conn_at(const orc_grid *G, double X1, double X2, double conn[4][4][4])
+{
+    orc_geom g;
+    orc_geom_at(G, X1, X2, &g);
+    double dg[4][4][4]; /* dg[c][a][b] = d_c g_ab */
+    memset(dg, 0, sizeof(dg));
+    const double h = 1e-30;
+    double complex gp[4][4];
+    orc_code_gcov_c(G, X1 + I * h, X2, gp);
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) dg[1][a][b] = cimag(gp[a][b]) / h;
+    orc_code_gcov_c(G, X1, X2 + I * h, gp);
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) dg[2][a][b] = cimag(gp[a][b]) / h;
+    for (int l = 0; l < 4; l++)
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) {
+                double s = 0.0;
+                for (int sg = 0; sg < 4; sg++)
+                    s += g.gcon[l][sg] * (dg[m][sg][n] + dg[n][sg][m] - dg[sg][m][n]);
+                conn[l][m][n] = 0.5 * s;
+            }
+}

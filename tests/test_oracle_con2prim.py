@@ -1,0 +1,152 @@
+"""Pins of the oracle inversion (Section 2.3, Eqs. 28-32).
+
+The exact answer is known by construction: primitives are drawn first and
+their conserved variables computed, so the inversion must return them.
+Additional pins: homogeneity of Eqs. 29-30 (D, Q scale with lambda and Bf
+with sqrt(lambda) => rho, u scale with lambda, velocities fixed, B with
+sqrt(lambda)), every method on its own reaching the same root, the beta
+switch, and the unphysical-D failure.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+
+GAM = 4.0 / 3.0
+N1 = N2 = 48
+
+
+@pytest.fixture(scope="module")
+def setup():
+    p = oracle.default_params(n1=N1, n2=N2, n3=1, r_out=1000.0, gam=GAM)
+    G = oracle.Grid(p)
+    tab = G.geom_table(0)
+    n = 6000
+    loc = inputs.zone_locations(n, N1, N2, 21, i_h=G.i_h)
+    i, j = loc // N2, loc % N2
+    gsp = tab[i + 2, j + 2, :16].reshape(n, 4, 4)[:, 1:, 1:]
+    pp = inputs.prim_params(n, 22)
+    P = inputs.place_prims(pp, gsp)
+    U = G.prim2cons(P, loc)
+    guess = inputs.perturb_guess(P, 23)
+    return G, loc, pp, P, U, guess
+
+
+def _well_conditioned(pp):
+    return (pp["sigma"] <= 1.0) & (pp["lorentz"] <= 10.0) & (pp["u"] / pp["rho"] >= 1e-3)
+
+
+def _check_forward(pp, P, Pr, tol_const=4e3):
+    """Forward error bounded by the conditioning of Eqs. 29-30: u is fixed
+    by the total energy minus rest mass and kinetic energy, so
+    |du|/u <~ C eps W (1 + sigma) / u; rho and the velocities go through
+    v^2, |d|/|.| <~ C eps Gamma^2 (1 + sigma).  C is a modest constant."""
+    eps = 2.220446049250313e-16
+    W = pp["lorentz"] ** 2 * (pp["rho"] + GAM * pp["u"])
+    cu = eps * W * (1.0 + pp["sigma"]) / pp["u"]
+    cr = eps * pp["lorentz"] ** 2 * (1.0 + pp["sigma"])
+    rel_rho = np.abs(Pr[0] - P[0]) / P[0]
+    rel_u = np.abs(Pr[1] - P[1]) / P[1]
+    du = np.abs(Pr[2:5] - P[2:5]).max(0) / np.maximum(1.0, np.abs(P[2:5]).max(0))
+    assert (rel_rho / cr).max() <= tol_const
+    assert (rel_u / cu).max() <= tol_const
+    assert (du / cr).max() <= tol_const
+    # most zones sit far below the 1e-10 per-step parity target
+    assert np.mean(rel_u < 1e-10) > 0.9 and np.mean(rel_rho < 1e-10) > 0.99
+    assert np.abs(Pr[5:8] - P[5:8]).max() <= 1e-15 * np.abs(P[5:8]).max()
+
+
+@pytest.mark.parametrize("methods,expect", [(1, oracle.C2P_NR), (2, oracle.C2P_BRENT_W),
+                                            (4, oracle.C2P_ENTROPY)])
+def test_each_method_recovers_exact_primitives(setup, methods, expect):
+    G, loc, pp, P, U, guess = setup
+    Pr, fl, it = G.con2prim(U, loc, guess, methods)
+    assert np.all(fl == expect)
+    _check_forward(pp, P, Pr)
+
+
+def test_full_procedure_backward_error_and_conditioning(setup):
+    G, loc, pp, P, U, guess = setup
+    Pr, fl, it = G.con2prim(U, loc, guess, 15)
+    assert not np.any(fl & oracle.C2P_FAIL)
+    # backward error: the recovered primitives reproduce the conserved state
+    U2 = G.prim2cons(Pr, loc)
+    scale = np.abs(U[0]) + np.abs(U[1]) + np.abs(U[2:5]).sum(0)
+    assert (np.abs(U2[:5] - U[:5]).max(0) / scale).max() <= 1e-9
+    # forward error of u is bounded by rounding of the total energy:
+    # |du| <~ C eps (W + b^2 Gamma^2), with W = Gamma^2 (rho + gam u)
+    W = pp["lorentz"] ** 2 * (pp["rho"] + GAM * pp["u"])
+    Es = W * (1.0 + pp["sigma"])
+    assert (np.abs(Pr[1] - P[1]) / (2.2e-16 * Es)).max() < 1e4
+    # Newton in the unmagnetised-to-moderate regime converges in a handful of steps
+    nr = (fl & 7) == oracle.C2P_NR
+    assert it[nr].mean() < 6 and it[nr].max() <= 30
+
+
+def test_beta_switch_selects_entropy(setup):
+    G, loc, pp, P, U, guess = setup
+    Pr, fl, it = G.con2prim(U, loc, guess, 15)
+    # beta of the guess < 1e-2 <=> entropy as first and only method
+    lowbeta = (fl & 7) == oracle.C2P_ENTROPY_BETA
+    assert lowbeta.sum() > 0 and (~lowbeta).sum() > 0
+    Pe, fe, _ = G.con2prim(U, loc, guess, 4)
+    assert np.array_equal(Pr[:, lowbeta], Pe[:, lowbeta])
+
+
+def test_homogeneity(setup):
+    G, loc, pp, P, U, guess = setup
+    m = _well_conditioned(pp)
+    lam = 3.7
+    U2 = U.copy()
+    U2[0:5] *= lam
+    U2[5:8] *= np.sqrt(lam)
+    U2[8] *= lam ** (2.0 - GAM)  # S = p / rho^(gam-1) scales as lam^(2-gam)
+    g2 = guess.copy()
+    g2[0:2] *= lam
+    g2[5:8] *= np.sqrt(lam)
+    P1, f1, _ = G.con2prim(U, loc, guess, 1)
+    P2, f2, _ = G.con2prim(U2, loc, g2, 1)
+    assert np.all(f1 == 0) and np.all(f2 == 0)
+    assert np.abs(P2[0:2, m] / (lam * P1[0:2, m]) - 1).max() < 1e-10
+    assert np.abs(P2[2:5, m] - P1[2:5, m]).max() < 1e-10 * np.abs(P1[2:5, m]).max()
+
+
+def test_unphysical_density_fails(setup):
+    G, loc, pp, P, U, guess = setup
+    Ubad = U[:, :10].copy()
+    Ubad[0] = -np.abs(Ubad[0])
+    Pr, fl, it = G.con2prim(Ubad, loc[:10], guess[:, :10], 15)
+    assert np.all(fl == (oracle.C2P_FAIL | oracle.C2P_FAIL_D))
+    # non-finite input is caught the same way
+    Ubad[0, :] = np.nan
+    Pr, fl, it = G.con2prim(Ubad, loc[:10], guess[:, :10], 15)
+    assert np.all(fl == (oracle.C2P_FAIL | oracle.C2P_FAIL_D))
+
+
+def test_newton_residual_small(setup):
+    """Direct check of Eqs. 29-30 at the converged Newton root (B = 0 subset)."""
+    G, loc, pp, P, U, guess = setup
+    Pr, fl, it = G.con2prim(U, loc, guess, 1)
+    tab = G.geom_table(0)
+    for a in range(0, 200):
+        i, j = divmod(int(loc[a]), N2)
+        row = tab[i + 2, j + 2]
+        gcov, gcon, gdet, alpha = row[:16].reshape(4, 4), row[16:32].reshape(4, 4), row[32], row[33]
+        D = alpha * U[0, a] / gdet
+        Q = alpha * U[1:5, a] / gdet
+        n = np.array([1 / alpha, *(-alpha * gcon[0, 1:])])
+        nQ = n @ Q
+        Qt2 = Q @ gcon @ Q + nQ ** 2
+        Bf = alpha * U[5:8, a] / gdet
+        B2 = Bf @ gcov[1:, 1:] @ Bf
+        QB = Q[1:] @ Bf
+        ut = Pr[2:5, a]
+        lor2 = 1 + ut @ gcov[1:, 1:] @ ut
+        v2 = 1 - 1 / lor2
+        W = lor2 * (Pr[0, a] + GAM * Pr[1, a])
+        p = (GAM - 1) / GAM * (W * (1 - v2) - D * np.sqrt(1 - v2))
+        f1 = v2 * (B2 + W) ** 2 - QB ** 2 * (B2 + 2 * W) / W ** 2 - Qt2
+        f2 = -0.5 * B2 * (1 + v2) + QB ** 2 / (2 * W ** 2) - W + p - nQ
+        assert abs(f1) <= 1e-9 * (B2 + W) ** 2
+        assert abs(f2) <= 1e-9 * (abs(nQ) + B2 + W)
