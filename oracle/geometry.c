@@ -158,18 +158,48 @@ int orc_invert4(const double m[4][4], double inv[4][4], double *det)
     return 1;
 }
 
+/* Inverse metric, sqrt(-g) and lapse.  For Kerr the inverse of Eq. 35 is
+ * written out in closed form (Kerr-Schild: g^tt = -(1+z), g^tr = z,
+ * g^rr = Delta/Sigma, g^r phi = a/Sigma, g^th th = 1/Sigma,
+ * g^phi phi = 1/(Sigma sin^2), z = 2r/Sigma; sqrt(-g) = Sigma |sin theta|)
+ * and mapped to MKS by the diagonal Jacobian of Eq. 36.  A numerical 4x4
+ * inverse loses accuracy with the condition number of the MKS metric, which
+ * grows like (dr/dX1)^2 at large radius. */
 int orc_geom_at(const orc_grid *G, double X1, double X2, orc_geom *out)
 {
     double complex gc[4][4];
     orc_code_gcov_c(G, X1, X2, gc);
     for (int m = 0; m < 4; m++)
         for (int n = 0; n < 4; n++) out->gcov[m][n] = creal(gc[m][n]);
-    double det;
-    if (!orc_invert4(out->gcov, out->gcon, &det) || !(det < 0.0)) {
+    if (G->p.metric == ORC_MINK_CART) {
+        memset(out->gcon, 0, sizeof(out->gcon));
+        out->gcon[0][0] = -1.0;
+        out->gcon[1][1] = out->gcon[2][2] = out->gcon[3][3] = 1.0;
+        out->gdet = 1.0;
+        out->alpha = 1.0;
+        return 1;
+    }
+    double complex rc, drc, thc, dthc;
+    mks_r_c(G, X1, &rc, &drc);
+    mks_th_c(G, X2, &thc, &dthc);
+    double r = creal(rc), th = creal(thc), dr = creal(drc), dth = creal(dthc), a = G->p.a;
+    double s = sin(th), c = cos(th);
+    double sig = r * r + a * a * c * c, del = r * r - 2.0 * r + a * a, z = 2.0 * r / sig;
+    if (s == 0.0) {
         memset(out, 0, sizeof(*out));
         return 0;
     }
-    out->gdet = sqrt(-det);
+    double gi[4][4] = {{0}};
+    gi[0][0] = -(1.0 + z);
+    gi[0][1] = gi[1][0] = z;
+    gi[1][1] = del / sig;
+    gi[1][3] = gi[3][1] = a / sig;
+    gi[2][2] = 1.0 / sig;
+    gi[3][3] = 1.0 / (sig * s * s);
+    double J[4] = {1.0, dr, dth, 1.0};
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) out->gcon[m][n] = gi[m][n] / (J[m] * J[n]);
+    out->gdet = sig * fabs(s) * fabs(dr * dth);
     out->alpha = 1.0 / sqrt(-out->gcon[0][0]);
     return 1;
 }

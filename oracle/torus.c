@@ -14,7 +14,8 @@
  *          - 1/2 sqrt(1 + 4 l^2 Sigma^2 Delta/(A^2 sin^2)) - 2 a l r / A,
  * minus its value at (r_in, pi/2).  l is fixed by d(ln h)/dr = 0 at
  * (r_max, pi/2), found here by root finding.
- * rho = ((h-1)(gam-1)/(kappa gam))^(1/(gam-1)), u = kappa rho^gam/(gam-1),
+ * rho = ((h-1)(gam-1)/(kappa gam))^(1/(gam-1)) with h - 1 = expm1(ln h),
+ * u = kappa rho^gam/(gam-1),
  * then rho and u are divided by max(rho) over the zone centres.
  * Velocity: u^t = sqrt((1+X^2) A/(Sigma Delta)),
  *           u^phi = 2 a r sqrt(1+X^2)/sqrt(A Sigma Delta) + X sqrt(Sigma/A)/sin,
@@ -89,7 +90,7 @@ static double fm_rho(double a, double l, double lnh_in, double r, double th, dou
     double lnh = orc_fm_lnh(a, l, r, th) - lnh_in;
     if (!(lnh > 0.0)) return 0.0;
     *in = 1;
-    double hm1 = exp(lnh) - 1.0;
+    double hm1 = expm1(lnh);
     return pow(hm1 * (gam - 1.0) / (kappa * gam), 1.0 / (gam - 1.0));
 }
 

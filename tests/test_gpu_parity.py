@@ -1,0 +1,232 @@
+"""GPU (libgrmhd.so through the C ABI) against the FP64 CPU oracle.
+
+Sizes are small enough for the oracle to finish in seconds but span several
+thread blocks with ragged tails (grids are not multiples of the block size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import inputs
+from tests.gpu_common import field_err, gpu_mod, make_pair
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10  # per-step parity target of the FP64 path
+
+
+def _sample(og, n, seed, n1, n2):
+    tab = og.geom_table(0)
+    loc = inputs.zone_locations(n, n1, n2, seed, i_h=og.i_h)
+    i, j = loc // n2, loc % n2
+    gsp = tab[i + 2, j + 2, :16].reshape(n, 4, 4)[:, 1:, 1:]
+    pp = inputs.prim_params(n, seed + 1)
+    return loc, pp, inputs.place_prims(pp, gsp)
+
+
+def test_prim2cons_parity():
+    G = gpu_mod()
+    og, ctx = make_pair(40, 36, 1, gam=4.0 / 3.0, r_out=1000.0)
+    loc, pp, P = _sample(og, 5000, 31, 40, 36)
+    Uo = og.prim2cons(P, loc)
+    Ug = G.prim2cons(ctx, P, loc)
+    scale = np.abs(Uo[0]) + np.abs(Uo[1]) + np.abs(Uo[2:5]).sum(0)
+    rel = np.abs(Ug[:5] - Uo[:5]).max(0) / scale
+    # T^t_nu cancels terms of size Gamma^2 (w + b^2): moderate states agree to
+    # rounding, extreme ones (Gamma ~ 50, sigma ~ 100) to rounding x that cancellation
+    moderate = (pp["lorentz"] <= 10.0) & (pp["sigma"] <= 1.0)
+    assert rel[moderate].max() < 1e-13
+    cond = pp["lorentz"] ** 2 * (1.0 + pp["sigma"])
+    assert (rel / (2.2e-16 * cond)).max() < 1e3
+    assert np.abs(Ug[5:8] - Uo[5:8]).max() <= 1e-13 * np.abs(Uo[5:8]).max()
+    assert (np.abs(Ug[8] - Uo[8]) / np.abs(Uo[8])).max() < 1e-12
+
+
+def test_con2prim_parity_and_flags():
+    G = gpu_mod()
+    og, ctx = make_pair(40, 36, 1, gam=4.0 / 3.0, r_out=1000.0)
+    loc, pp, P = _sample(og, 20000, 41, 40, 36)
+    guess = inputs.perturb_guess(P, 43)
+    Uo = og.prim2cons(P, loc)
+    Ug = G.prim2cons(ctx, P, loc)
+    Po, fo, io = og.con2prim(Uo, loc, guess)
+    Pg, fg, ig = G.con2prim(ctx, Ug, loc, guess.copy())
+    assert np.array_equal(fo & ~7 == 0, fg & ~7 == 0)
+    assert np.mean(fo == fg) > 0.999
+    same = fo == fg
+    eps = 2.220446049250313e-16
+    W = pp["lorentz"] ** 2 * (pp["rho"] + 4.0 / 3.0 * pp["u"])
+    cu = eps * W * (1.0 + pp["sigma"]) / pp["u"]
+    cr = eps * pp["lorentz"] ** 2 * (1.0 + pp["sigma"])
+    assert (np.abs(Pg[1] - Po[1]) / Po[1] / cu)[same].max() < 4e3
+    assert (np.abs(Pg[0] - Po[0]) / Po[0] / cr)[same].max() < 4e3
+    # the same root on both sides: typical zones agree far below 1e-10
+    assert np.median(np.abs(Pg[1] - Po[1]) / Po[1]) < 1e-13
+    # same number of Newton iterations almost everywhere
+    nr = (fo == 0) & (fg == 0)
+    assert np.mean(io[nr] == ig[nr]) > 0.99
+
+
+@pytest.fixture(scope="module")
+def c1_pair():
+    og, ctx = make_pair(64, 64, 1, gam=13.0 / 9.0)
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=1)
+    G = gpu_mod()
+    G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=1)
+    return og, ctx
+
+
+def test_torus_init_parity(c1_pair):
+    G = gpu_mod()
+    og, ctx = c1_pair
+    Po, Uo, to, dto = og.get_state()
+    Pg, Ug, tg, dtg = G.get_state(ctx)
+    # near the torus surface rho ~ (h-1)^(1/(gam-1)) with h - 1 = expm1(ln h - ln h_in):
+    # the cancellation in ln h - ln h_in amplifies rounding, so the initial
+    # state agrees to ~1e-10 there and to rounding elsewhere
+    e = field_err(Pg, Po)
+    assert e.max() < 1e-9, e
+    assert field_err(Ug, Uo).max() < 1e-9
+    assert dtg == pytest.approx(dto, rel=1e-12)
+    dg, do = G.diagnostics(ctx), og.diagnostics()
+    assert dg["disk_mass"] == pytest.approx(do["disk_mass"], rel=1e-12)
+    assert dg["disk_eb"] == pytest.approx(do["disk_eb"], rel=1e-12)
+
+
+def test_flux_parity(c1_pair):
+    G = gpu_mod()
+    og, ctx = c1_pair
+    Po, Uo, to, dto = og.get_state()
+    G.set_state(ctx, Po, Uo, to, dto)
+    Fo, dt_o = og.fluxes()
+    Fg, dt_g = G.fluxes(ctx)
+    assert dt_g == pytest.approx(dt_o, rel=1e-13)
+    # the LLF flux is a sum of terms of size |F| and c_w |U| (c_w <= 1): compare
+    # against both scales
+    for d in range(3):
+        for c in range(9):
+            s = np.abs(Fo[d, c]).max() + np.abs(Uo[c]).max()
+            assert np.abs(Fg[d, c] - Fo[d, c]).max() <= 1e-13 * s, (d, c)
+
+
+def test_one_step_parity_from_same_state(c1_pair):
+    G = gpu_mod()
+    og, ctx = c1_pair
+    Po, Uo, to, dto = og.get_state()
+    G.set_state(ctx, Po, Uo, to, dto)
+    og.step()
+    G.step(ctx)
+    Po1, Uo1, to1, dto1 = og.get_state()
+    Pg1, Ug1, tg1, dtg1 = G.get_state(ctx)
+    eP, eU = field_err(Pg1, Po1), field_err(Ug1, Uo1)
+    assert eP.max() < TOL, eP
+    assert eU.max() < TOL, eU
+    assert tg1 == pytest.approx(to1, rel=1e-14)
+    assert dtg1 == pytest.approx(dto1, rel=1e-12)
+
+
+def test_twenty_steps_free_running_and_per_step():
+    """C1: 64x64x1 torus, a = 0.9375, gam = 13/9, beta0 = 100, 4% perturbation,
+    LLF, 20 RK2 steps; each side from its own initial state, plus a per-step
+    check where the GPU restarts from the oracle state."""
+    G = gpu_mod()
+    og, ctx = make_pair(64, 64, 1, gam=13.0 / 9.0)
+    og.init_torus(pert_amp=0.04, seed=1)
+    G.init_torus(ctx, pert_amp=0.04, seed=1)
+    ref, rctx = make_pair(64, 64, 1, gam=13.0 / 9.0)
+    worst = 0.0
+    for s in range(20):
+        Po, Uo, to, dto = og.get_state()
+        G.set_state(rctx, Po, Uo, to, dto)
+        og.step()
+        G.step(rctx)
+        G.step(ctx)
+        e = max(field_err(G.get_state(rctx)[0], og.get_state()[0]).max(),
+                field_err(G.get_state(rctx)[1], og.get_state()[1]).max())
+        worst = max(worst, e)
+    assert worst < TOL, worst
+    Pf, Uf, tf, dtf = G.get_state(ctx)
+    Po, Uo, to, dto = og.get_state()
+    ef = field_err(Pf, Po)
+    assert ef.max() < 1e-8, ef
+    assert tf == pytest.approx(to, rel=1e-12)
+    do, dg = og.diagnostics(), G.diagnostics(ctx)
+    for k in ("n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_ceil", "n_fixed", "n_steps"):
+        assert dg[k] == do[k], k
+    assert abs(dg["nr_iters"] - do["nr_iters"]) <= 1e-4 * do["nr_iters"]
+    assert dg["mdot"] == pytest.approx(do["mdot"], rel=1e-8)
+    assert dg["edot"] == pytest.approx(do["edot"], rel=1e-8)
+    assert dg["divb_max"] < 1e-11
+
+
+def test_3d_ragged_grid_parity():
+    """19 x 14 x 6 zones (no dimension a multiple of a warp), 3 steps."""
+    G = gpu_mod()
+    og, ctx = make_pair(19, 14, 6, gam=4.0 / 3.0, r_out=30.0)
+    og.init_torus(pert_amp=0.02, seed=2)
+    G.init_torus(ctx, pert_amp=0.02, seed=2)
+    e0 = field_err(G.get_state(ctx)[0], og.get_state()[0])
+    assert e0.max() < 1e-9
+    for _ in range(3):
+        Po, Uo, to, dto = og.get_state()
+        G.set_state(ctx, Po, Uo, to, dto)
+        og.step()
+        G.step(ctx)
+        eP = field_err(G.get_state(ctx)[0], og.get_state()[0])
+        eU = field_err(G.get_state(ctx)[1], og.get_state()[1])
+        assert max(eP.max(), eU.max()) < TOL, (eP, eU)
+    assert G.diagnostics(ctx)["divb_max"] == pytest.approx(og.diagnostics()["divb_max"], abs=1e-13)
+
+
+@pytest.mark.parametrize("riemann", [oracle.LLF, oracle.HLL])
+def test_flat_space_step_parity(riemann):
+    """Flat space, periodic box with a smooth random MHD state, LLF and HLL."""
+    G = gpu_mod()
+    box = dict(x1min=0.0, x1max=1.0, x2min=0.0, x2max=1.0, x3min=0.0, x3max=1.0,
+               bc1=oracle.BC_PERIODIC, bc2=oracle.BC_OUTFLOW, bc3=oracle.BC_PERIODIC)
+    og, ctx = make_pair(13, 11, 9, gam=5.0 / 3.0, metric=oracle.MINK_CART, riemann=riemann, **box)
+    n1, n2, n3 = 13, 11, 9
+    x = (np.arange(n1) + 0.5) / n1
+    y = (np.arange(n2) + 0.5) / n2
+    z = (np.arange(n3) + 0.5) / n3
+    X, Y, Z = np.meshgrid(x, y, z, indexing="ij")
+    tp = 2 * np.pi
+    P = np.zeros((8, n1, n2, n3))
+    P[0] = 1.0 + 0.3 * np.sin(tp * X) * np.cos(tp * Y)
+    P[1] = 0.6 + 0.2 * np.cos(tp * (X + Z))
+    P[2] = 0.3 * np.sin(tp * Y)
+    P[3] = -0.2 * np.cos(tp * Z)
+    P[4] = 0.25 * np.sin(tp * (X - Y))
+    P[5] = 0.2 + 0.1 * np.sin(tp * Y)
+    P[6] = 0.1 * np.cos(tp * Z)
+    P[7] = 0.15 * np.sin(tp * X)
+    loc = np.zeros(n1 * n2 * n3, dtype=np.int32)
+    U = og.prim2cons(P.reshape(8, -1), loc).reshape((9, n1, n2, n3))
+    og.set_state(P, U, 0.0, 0.0)
+    dt = og.initial_dt()
+    G.set_state(ctx, P, U, 0.0, dt)
+    for _ in range(3):
+        og.step()
+        G.step(ctx)
+    eP = field_err(G.get_state(ctx)[0], og.get_state()[0])
+    assert eP.max() < 1e-9, eP
+
+
+def test_failed_zone_fixup_parity():
+    """Injected bad conserved states (D < 0) are fixed identically."""
+    G = gpu_mod()
+    og, ctx = make_pair(24, 24, 2, gam=4.0 / 3.0)
+    og.init_torus(pert_amp=0.0)
+    Po, Uo, to, dto = og.get_state()
+    Ub = Uo.copy()
+    for (i, j) in [(10, 12), (11, 12), (15, 8)]:
+        Ub[0, i, j, :] = -1.0
+    og.set_state(Po, Ub, to, dto)
+    G.set_state(ctx, Po, Ub, to, dto)
+    og.step()
+    G.step(ctx)
+    G.sync(ctx)
+    eP = field_err(G.get_state(ctx)[0], og.get_state()[0])
+    assert eP.max() < TOL, eP
+    do, dg = og.diagnostics(), G.diagnostics(ctx)
+    assert dg["n_fail"] == do["n_fail"] > 0
+    assert dg["n_fixed"] == do["n_fixed"]
