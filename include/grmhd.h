@@ -1,0 +1,198 @@
+/*
+ * grmhd.h -- C ABI of the GB300 GR-MHD step library (libgrmhd.so).
+ *
+ * The library advances the ideal GR-MHD equations of cuHARM (Begue et al.,
+ * arXiv 2205.02484) on a modified-Kerr-Schild grid with the HARM-style
+ * conservative scheme of its Section 2: PLM-MC reconstruction (Eqs. 16-17),
+ * LLF or HLL fluxes (Eqs. 18-21), flux-CT (Eqs. 22-24), connection sources
+ * (Eqs. 7, 15), the RK2 predictor-corrector (Eqs. 25-26), the CFL time step
+ * (Eq. 27), Newton/Brent/entropy conserved-to-primitive inversion (Section
+ * 2.3, Eqs. 28-32), failure fixups (Eq. 33), floors and ceilings (Section 2.4,
+ * Eq. 34), and horizon diagnostics (Section 4.2, Eqs. 38-42).  Every step of
+ * the method runs in CUDA kernels compiled for sm_103a.
+ *
+ * Conventions shared by all calls:
+ *  - Every function returns 0 on success or a negative GRMHD_E* code; no C++
+ *    exception crosses the ABI.  grmhd_last_error() returns a message for the
+ *    last failure of a context (or of context creation when ctx is NULL); the
+ *    string is owned by the library and valid until the next call on it.
+ *  - Primitive arrays P hold 8 fields (rho, u, ut^1, ut^2, ut^3, B^1, B^2,
+ *    B^3) in the paper's notation of Eq. 11; conserved arrays U hold 9 fields
+ *    sqrt(-g) (rho u^t, T^t_t, T^t_1, T^t_2, T^t_3, B^1, B^2, B^3, S u^t)
+ *    (Section 2.1 and Eq. 12, S = p / rho^(gam-1)).  Field-major layout:
+ *    element (f, i, j, k) of an active-zone array sits at
+ *    ((f * n1 + i) * n2 + j) * n3 + k, with k (phi) fastest.
+ *  - Pointers are either host or device memory as the on_device argument
+ *    says.  Buffers passed in are always owned by the caller; the library
+ *    copies from and into them and never keeps a pointer past the call.  The
+ *    context owns all of its device memory, streams and CUDA graphs.
+ *  - All device work of a context is issued on its stream (the stream given
+ *    in grmhd_grid_params, or a stream the library creates when that is NULL).
+ *    Calls that return data to the host synchronise that stream first.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRMHD_OK 0
+#define GRMHD_EINVAL (-1)     /* bad argument or parameter */
+#define GRMHD_ECUDA (-2)      /* CUDA runtime error (message in grmhd_last_error) */
+#define GRMHD_ENOMEM (-3)     /* device or host allocation failed */
+#define GRMHD_ENONFINITE (-4) /* non-finite value found in the state */
+#define GRMHD_EFIXUP (-5)     /* some failed zones could not be fixed (Eq. 33) */
+#define GRMHD_EITER (-6)      /* a bounded loop ran out of iterations */
+#define GRMHD_ESTATE (-7)     /* call made in the wrong order (e.g. step before init) */
+
+/* metric kinds for grmhd_set_metric */
+#define GRMHD_KERR_MKS 0   /* Kerr in modified Kerr-Schild coordinates (Section 4.1) */
+#define GRMHD_MINK_CART 1  /* flat space, Cartesian box (tests) */
+
+/* boundary kinds (used for GRMHD_MINK_CART; Kerr grids always use inflow /
+ * polar reflection / periodic in X1 / X2 / X3, Section 4.1) */
+#define GRMHD_BC_INFLOW 0
+#define GRMHD_BC_POLAR 1
+#define GRMHD_BC_PERIODIC 2
+#define GRMHD_BC_OUTFLOW 3
+
+#define GRMHD_LLF 0 /* Eq. 18 */
+#define GRMHD_HLL 1 /* Eq. 21 */
+
+#define GRMHD_FP64 0  /* every stage in FP64 */
+#define GRMHD_MIXED 1 /* reconstruction, fluxes, EMFs in FP32; U and the inversion in FP64 */
+
+/* per-zone inversion flags (grmhd_con2prim): low 3 bits = method */
+#define GRMHD_C2P_NR 0           /* 2D Newton-Raphson on (W, v^2), Eqs. 29-30 */
+#define GRMHD_C2P_BRENT_W 1      /* 1D Brent in W */
+#define GRMHD_C2P_ENTROPY 2      /* entropy inversion (Eq. 32) as fallback */
+#define GRMHD_C2P_ENTROPY_BETA 3 /* entropy inversion chosen because beta < 1e-2 */
+#define GRMHD_C2P_FAIL 8         /* inversion failed: zone needs a fixup */
+#define GRMHD_C2P_FAIL_D 16      /* D <= 0 or non-finite input */
+#define GRMHD_C2P_FAIL_ENT 32    /* entropy inversion impossible */
+
+typedef struct grmhd_ctx grmhd_ctx;
+
+/* Grid of n1 x n2 x n3 active zones (X1 = radius-like, X2 = polar, X3 = phi).
+ * For GRMHD_KERR_MKS: r(X1) = R0 + exp(X1) inside x_b = ln(r_br - R0) and
+ * R0 + exp(X1 + (X1 - x_b)^n_x) outside; theta(X2) = pi/2 (1+X2) +
+ * (1-hslope)/2 sin(pi (1+X2)) with X2 in [-1, 1]; X3 = phi in [0, 2 pi)
+ * (Eq. 36).  X1 spans [ln(r_in - R0), X1(r_out)].  For GRMHD_MINK_CART the
+ * box [x1min, x1max] x [x2min, x2max] x [x3min, x3max] and bc1..bc3 are used. */
+typedef struct {
+    int n1, n2, n3;
+    int metric;
+    double r_in, r_out, hslope, r_br, n_x, R0;
+    double x1min, x1max, x2min, x2max, x3min, x3max;
+    int bc1, bc2, bc3;
+    int riemann;   /* GRMHD_LLF or GRMHD_HLL */
+    int precision; /* GRMHD_FP64 or GRMHD_MIXED */
+    int device;    /* CUDA device ordinal */
+    void *stream;  /* cudaStream_t to issue work on, or NULL */
+} grmhd_grid_params;
+
+/* Physics constants; the paper's values are cfl 0.45 (Eq. 27), nr_tol 1e-10
+ * (Section 2.3), sigma_max 50, bu_max 2500, gamma_max 50 and beta_entropy
+ * 1e-2 (Section 2.4). */
+typedef struct {
+    double gam;
+    double cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_entropy;
+    int nr_maxit, brent_maxit, fix_maxsweep;
+} grmhd_phys_params;
+
+/* Fishbone-Moncrief torus with inner edge r_in and pressure maximum r_max
+ * (Section 5); A_phi = max(rho/rho_max - 0.2, 0) (Eq. 45) normalised so that
+ * max p_g / max p_B = beta0 (beta0 <= 0: no field); internal energy
+ * perturbed by a factor 1 + pert_amp (2 xi - 1) with xi from splitmix64(seed
+ * XOR zone index).  kappa is the polytropic constant (it cancels after the
+ * rho_max normalisation; 1e-3 if <= 0). */
+typedef struct {
+    double r_in, r_max, beta0, pert_amp, kappa;
+    unsigned long long seed;
+} grmhd_torus_params;
+
+/* Diagnostics (Section 4.2): horizon fluxes at the first zone with r >= r_H,
+ * mdot = sum sqrt(-g) rho u^1 dX2 dX3 (Eq. 38), phib = 1/2 sum |sqrt(-g) B^1|
+ * dX2 dX3 (Eq. 39), edot = -sum sqrt(-g) T^1_t (Eq. 41), ldot = sum sqrt(-g)
+ * T^1_3 (Eq. 40), PhiB = phib / sqrt|mdot| (Eq. 42); divb_max is the largest
+ * corner divergence of Eq. 24; disk_mass / disk_eb are the initial disk
+ * integrals of Section 5.  Counters accumulate over all steps since init. */
+typedef struct {
+    double t, dt, mdot, phib, PhiB, edot, ldot, divb_max, disk_mass, disk_eb;
+    long long nr_iters, n_nr, n_brent, n_entropy, n_entropy_beta, n_fail, n_floor, n_ceil,
+        n_gcap, n_fixed, fix_sweeps, n_steps;
+} grmhd_diag;
+
+/* Create a context: validates the parameters, allocates the device state and
+ * builds nothing else.  *out is set only on success.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_params *phys,
+                    grmhd_ctx **out);
+
+/* Build the metric tables (Section 4.1, Eqs. 35-36): g_{mu nu}, g^{mu nu},
+ * sqrt(-g) and the lapse at zone centres and X1/X2 face centres, and the
+ * connection Gamma^l_{mu nu} at centres (exact derivatives by forward-mode
+ * dual numbers).  a is the black-hole spin (ignored for flat space). */
+int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind);
+
+/* Set the torus initial state (needs grmhd_set_metric with GRMHD_KERR_MKS),
+ * fill the ghosts and compute the first time step from a flux sweep. */
+int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *torus);
+
+/* Copy a full active-zone state in (P: 8 fields, U: 9 fields) with the time
+ * t and the next step dt; ghosts are refilled from the boundary conditions.
+ * In GRMHD_MIXED mode P is rounded to FP32. */
+int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt,
+                    int on_device);
+
+/* Copy the active-zone state out (any of P, U, t, dt may be NULL). */
+int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,
+                    int on_device);
+
+/* Advance nsteps full RK2 steps (Eqs. 25-26) with the CFL time step of Eq. 27
+ * (dt of step n+1 from the predictor sweep of step n).  Asynchronous on the
+ * context stream; each step replays one captured CUDA graph.  Inversion
+ * failures that the fixups cannot repair raise GRMHD_EFIXUP at the next
+ * grmhd_sync or grmhd_diagnostics. */
+int grmhd_step(grmhd_ctx *ctx, int nsteps);
+
+/* Batched stand-alone inversion of n conserved states U (9 x n, sqrt(-g)
+ * included) at the centre metric of active zones loc[n] (loc = i*n2 + j),
+ * starting from and overwriting P_inout (8 x n).  flags[n] receives the
+ * GRMHD_C2P_* code, iters[n] (may be NULL) the Newton iterations.  With
+ * use_learned_guess = 1 the Newton start comes from the loaded MLP.  Same
+ * method order and tolerances as the step (Section 2.3). */
+int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P_inout,
+                   int *flags, int *iters, long n, int use_learned_guess, int on_device);
+
+/* Batched conserved variables of n primitive states at zones loc[n]. */
+int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, double *U, long n,
+                    int on_device);
+
+/* Riemann fluxes after flux-CT for the current primitives, active faces only:
+ * out[d][c][n1+1][n2+1][n3+1] (d = direction, c = 9 components, face index
+ * along d; unused slots zero).  *dt_out (may be NULL) receives the CFL step of
+ * Eq. 27.  For tests. */
+int grmhd_fluxes(grmhd_ctx *ctx, double *out, double *dt_out, int on_device);
+
+/* Synchronise the context stream and return the device-side status
+ * (GRMHD_EFIXUP / GRMHD_ENONFINITE if a step hit one) or 0. */
+int grmhd_sync(grmhd_ctx *ctx);
+
+/* Synchronise and compute the diagnostics of the current state. */
+int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out);
+
+/* Release everything the context owns. NULL is allowed. */
+void grmhd_destroy(grmhd_ctx *ctx);
+
+const char *grmhd_last_error(const grmhd_ctx *ctx);
+
+/* Library version string. */
+const char *grmhd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRMHD_H */

@@ -1,0 +1,510 @@
+// abi.cu -- the extern "C" entry points declared in include/grmhd.h.
+//
+// A context owns one grid: its device state, metric tables, scratch, stream
+// and the CUDA graph of one full RK2 step.  The step graph is captured on the
+// first grmhd_step call and replayed afterwards; the time step lives on the
+// device, so replays need no host round trip.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grmhd.h"
+#include "kernels.h"
+
+using namespace grmhd;
+
+struct grmhd_ctx {
+    grmhd_grid_params gp;
+    grmhd_phys_params pp;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Grid g{};
+    GeomBuild gb{};
+    std::vector<void *> allocs;
+    bool metric_set = false, state_set = false;
+    double a = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    double *scratch = nullptr;
+    long long scratch_len = 0;
+    double *staging = nullptr;
+    long long staging_len = 0;
+    unsigned char *intorus = nullptr;
+    double *hpin = nullptr; // pinned host scratch (64 doubles)
+    double disk_mass = 0.0, disk_eb = 0.0;
+    float *mlp = nullptr;
+    bool mlp_loaded = false;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(grmhd_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, GRMHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+template <typename T>
+static int dalloc(grmhd_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return fail(ctx, GRMHD_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cudaMemsetAsync(q, 0, bytes, ctx->stream);
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    return 0;
+}
+
+static long long nact_of(const grmhd_ctx *c) { return (long long)c->g.n1 * c->g.n2 * c->g.n3; }
+
+extern "C" const char *grmhd_version(void) { return "grmhd-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char *grmhd_last_error(const grmhd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+extern "C" void grmhd_destroy(grmhd_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_params *phys, grmhd_ctx **out)
+{
+    grmhd_ctx *ctx = nullptr;
+    if (!grid || !phys || !out) return fail(nullptr, GRMHD_EINVAL, "null argument");
+    if (grid->n1 < 1 || grid->n2 < 1 || grid->n3 < 1) return fail(nullptr, GRMHD_EINVAL, "grid sizes must be >= 1");
+    if (grid->metric == GRMHD_KERR_MKS && grid->n1 < 2)
+        return fail(nullptr, GRMHD_EINVAL, "Kerr grid needs n1 >= 2");
+    if (grid->precision != GRMHD_FP64 && grid->precision != GRMHD_MIXED)
+        return fail(nullptr, GRMHD_EINVAL, "precision must be GRMHD_FP64 or GRMHD_MIXED");
+    if (grid->riemann != GRMHD_LLF && grid->riemann != GRMHD_HLL)
+        return fail(nullptr, GRMHD_EINVAL, "riemann must be GRMHD_LLF or GRMHD_HLL");
+    if (!(phys->gam > 1.0) || !(phys->cfl > 0.0) || phys->nr_maxit < 1 || phys->brent_maxit < 1 ||
+        phys->fix_maxsweep < 1)
+        return fail(nullptr, GRMHD_EINVAL, "bad physics parameters");
+    long long N1 = grid->n1 + 2 * NG, N2 = grid->n2 + 2 * NG, N3 = grid->n3 + 2 * NG;
+    long long nz = N1 * N2 * N3;
+    if (nz > (1LL << 31) - 1) return fail(nullptr, GRMHD_EINVAL, "grid too large for 32-bit zone lists");
+    if (cudaSetDevice(grid->device) != cudaSuccess) return fail(nullptr, GRMHD_ECUDA, "cudaSetDevice failed");
+    ctx = new grmhd_ctx();
+    ctx->gp = *grid;
+    ctx->pp = *phys;
+    if (grid->stream) {
+        ctx->stream = (cudaStream_t)grid->stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamDefault));
+        ctx->own_stream = true;
+    }
+    Grid &g = ctx->g;
+    g.n1 = grid->n1; g.n2 = grid->n2; g.n3 = grid->n3;
+    g.N1 = (int)N1; g.N2 = (int)N2; g.N3 = (int)N3;
+    g.nz = nz;
+    g.metric = grid->metric;
+    g.bc1 = grid->bc1; g.bc2 = grid->bc2; g.bc3 = grid->bc3;
+    g.riemann = grid->riemann;
+    g.mixed = grid->precision == GRMHD_MIXED;
+    g.gam = phys->gam; g.cfl = phys->cfl; g.nr_tol = phys->nr_tol; g.sigma_max = phys->sigma_max;
+    g.bu_max = phys->bu_max; g.gamma_max = phys->gamma_max; g.beta_ent = phys->beta_entropy;
+    g.nr_maxit = phys->nr_maxit; g.brent_maxit = phys->brent_maxit; g.fix_maxsweep = phys->fix_maxsweep;
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    g.nfix_cap = (int)std::min<long long>(nact, 1LL << 20);
+    size_t rs = g.mixed ? sizeof(float) : sizeof(double);
+    int rc = 0;
+    long long nm = N1 * N2;
+    GeomBuild &b = ctx->gb;
+    for (int s = 0; s < 2 && !rc; s++) rc = dalloc(ctx, (char **)&g.P[s], 8 * nz * rs);
+    if (!rc) rc = dalloc(ctx, &g.U, 9 * nz);
+    for (int d = 0; d < 3 && !rc; d++) rc = dalloc(ctx, (char **)&g.F[d], 9 * nz * rs);
+    for (int d = 0; d < 3 && !rc; d++) rc = dalloc(ctx, (char **)&g.E[d], nz * rs);
+    if (!rc) rc = dalloc(ctx, &g.flag, nz);
+    if (!rc) rc = dalloc(ctx, &b.gc, nm);
+    if (!rc) rc = dalloc(ctx, &b.gf1, nm);
+    if (!rc) rc = dalloc(ctx, &b.gf2, nm);
+    if (!rc) rc = dalloc(ctx, &b.gcF, nm);
+    if (!rc) rc = dalloc(ctx, &b.gf1F, nm);
+    if (!rc) rc = dalloc(ctx, &b.gf2F, nm);
+    if (!rc) rc = dalloc(ctx, &b.conn, nm * 40);
+    if (!rc) rc = dalloc(ctx, &b.connF, nm * 40);
+    if (!rc) rc = dalloc(ctx, &b.rc, nm);
+    if (!rc) rc = dalloc(ctx, &b.polar2, nm);
+    if (!rc) rc = dalloc(ctx, &g.scal, 8);
+    if (!rc) rc = dalloc(ctx, &g.dtmin, 4);
+    if (!rc) rc = dalloc(ctx, &g.cnt, C_NCOUNT);
+    if (!rc) rc = dalloc(ctx, &g.status, 4);
+    if (!rc) rc = dalloc(ctx, &g.nfail, 4);
+    if (!rc) rc = dalloc(ctx, &g.faillist, g.nfix_cap);
+    if (!rc) rc = dalloc(ctx, &g.fixbuf, 6LL * g.nfix_cap);
+    if (!rc) rc = dalloc(ctx, &ctx->intorus, (long long)g.n1 * g.n2);
+    long long nbz = (nact + 255) / 256;
+    ctx->scratch_len = 8 * nact + 8 + (long long)(g.n1 + 1) * (g.n2 + 1) + 4 * nbz + 64;
+    if (!rc) rc = dalloc(ctx, &ctx->scratch, ctx->scratch_len);
+    if (!rc && cudaMallocHost(&ctx->hpin, 64 * sizeof(double)) != cudaSuccess) rc = GRMHD_ENOMEM;
+    if (rc) {
+        g_create_err = ctx->err.empty() ? "allocation failed" : ctx->err;
+        grmhd_destroy(ctx);
+        return rc;
+    }
+    g.gc = b.gc; g.gf1 = b.gf1; g.gf2 = b.gf2;
+    g.gcF = b.gcF; g.gf1F = b.gf1F; g.gf2F = b.gf2F;
+    g.conn = b.conn; g.connF = b.connF; g.rc = b.rc; g.polar2 = b.polar2;
+    unsigned long long inf = 0x7FF0000000000000ULL;
+    unsigned long long h[4] = {inf, inf, inf, inf};
+    cudaMemcpyAsync(g.dtmin, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        grmhd_destroy(ctx);
+        return GRMHD_ECUDA;
+    }
+    *out = ctx;
+    return 0;
+}
+
+static double x1_of_r(const CoordParams &cp, double r)
+{
+    double lo = -50.0, hi = 50.0;
+    for (int it = 0; it < 300; it++) {
+        double mid = 0.5 * (lo + hi), rr, dr;
+        mks_radius<double>(cp, mid, rr, dr);
+        if (rr < r) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (kind != GRMHD_KERR_MKS && kind != GRMHD_MINK_CART) return fail(ctx, GRMHD_EINVAL, "unknown metric kind");
+    if (kind == GRMHD_KERR_MKS && !(std::fabs(a) < 1.0)) return fail(ctx, GRMHD_EINVAL, "spin must satisfy |a| < 1");
+    Grid &g = ctx->g;
+    const grmhd_grid_params &p = ctx->gp;
+    g.metric = kind;
+    CoordParams cp{};
+    cp.metric = kind;
+    cp.a = a;
+    cp.hslope = p.hslope;
+    cp.n_x = p.n_x;
+    cp.R0 = p.R0;
+    if (kind == GRMHD_KERR_MKS) {
+        double rh = 1.0 + std::sqrt(1.0 - a * a);
+        if (!(p.r_in > p.R0) || !(p.r_out > p.r_in) || !(p.r_br > p.R0))
+            return fail(ctx, GRMHD_EINVAL, "need R0 < r_in < r_out and r_br > R0");
+        if (g.n2 < 2) return fail(ctx, GRMHD_EINVAL, "Kerr grid needs n2 >= 2");
+        cp.xb = std::log(p.r_br - p.R0);
+        g.x1in = std::log(p.r_in - p.R0);
+        double x1out = p.r_out <= p.r_br ? std::log(p.r_out - p.R0) : x1_of_r(cp, p.r_out);
+        g.x2in = -1.0;
+        g.x3in = 0.0;
+        g.dx[0] = (x1out - g.x1in) / g.n1;
+        g.dx[1] = 2.0 / g.n2;
+        g.dx[2] = 2.0 * M_PI / g.n3;
+        g.i_h = g.n1;
+        for (int i = 0; i < g.n1; i++) {
+            double r, dr;
+            mks_radius<double>(cp, g.x1in + (i + 0.5) * g.dx[0], r, dr);
+            if (r >= rh) { g.i_h = i; break; }
+        }
+    } else {
+        cp.xb = 1e300;
+        g.x1in = p.x1min; g.x2in = p.x2min; g.x3in = p.x3min;
+        g.dx[0] = (p.x1max - p.x1min) / g.n1;
+        g.dx[1] = (p.x2max - p.x2min) / g.n2;
+        g.dx[2] = (p.x3max - p.x3min) / g.n3;
+        g.i_h = 0;
+        if (!(g.dx[0] > 0) || !(g.dx[1] > 0) || !(g.dx[2] > 0)) return fail(ctx, GRMHD_EINVAL, "empty box");
+    }
+    ctx->gb.cp = cp;
+    ctx->a = a;
+    launch_geometry(g, ctx->gb, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->metric_set = true;
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    return 0;
+}
+
+static int reset_counters(grmhd_ctx *ctx)
+{
+    Grid &g = ctx->g;
+    CK(cudaMemsetAsync(g.cnt, 0, C_NCOUNT * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(g.status, 0, 4 * sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(g.nfail, 0, 4 * sizeof(int), ctx->stream));
+    return 0;
+}
+
+static int set_scalars(grmhd_ctx *ctx, double t, double dt)
+{
+    ctx->hpin[0] = dt;
+    ctx->hpin[1] = t;
+    CK(cudaMemcpyAsync(ctx->g.scal, ctx->hpin, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *tp)
+{
+    if (!ctx || !tp) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set || ctx->g.metric != GRMHD_KERR_MKS)
+        return fail(ctx, GRMHD_ESTATE, "init_torus needs grmhd_set_metric(GRMHD_KERR_MKS) first");
+    if (!(tp->r_max > tp->r_in) || !(tp->r_in > 0.0)) return fail(ctx, GRMHD_EINVAL, "need 0 < r_in < r_max");
+    Grid &g = ctx->g;
+    TorusArgs ta{};
+    ta.a = ctx->a;
+    ta.ell = fm_ell_host(ctx->a, tp->r_max);
+    ta.lnh_in = fm_lnh_host(ctx->a, ta.ell, tp->r_in, 0.5 * M_PI);
+    ta.r_in = tp->r_in;
+    ta.kappa = tp->kappa > 0.0 ? tp->kappa : 1e-3;
+    ta.beta0 = tp->beta0;
+    ta.pert_amp = tp->pert_amp;
+    ta.seed = tp->seed;
+    ta.cp = ctx->gb.cp;
+    if (reset_counters(ctx)) return GRMHD_ECUDA;
+    launch_torus(g, ta, ctx->scratch, ctx->intorus, ctx->hpin, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!(ctx->hpin[0] > 0.0)) return fail(ctx, GRMHD_EINVAL, "torus does not intersect the grid");
+    ctx->disk_mass = ctx->hpin[4];
+    ctx->disk_eb = ctx->hpin[5];
+    launch_bc(g, 0, ctx->stream);
+    if (set_scalars(ctx, 0.0, 0.0)) return GRMHD_ECUDA;
+    launch_fluxes_dt(g, 1, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->state_set = true;
+    return 0;
+}
+
+static int ensure_staging(grmhd_ctx *ctx, long long n)
+{
+    if (ctx->staging_len >= n) return 0;
+    double *p;
+    int rc = dalloc(ctx, &p, n);
+    if (rc) return rc;
+    ctx->staging = p;
+    ctx->staging_len = n;
+    return 0;
+}
+
+extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt, int on_device)
+{
+    if (!ctx || !P || !U) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "set_state needs grmhd_set_metric first");
+    long long na = nact_of(ctx);
+    const double *Pd = P, *Ud = U;
+    if (!on_device) {
+        if (ensure_staging(ctx, 17 * na)) return GRMHD_ENOMEM;
+        CK(cudaMemcpyAsync(ctx->staging, P, 8 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->staging + 8 * na, U, 9 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        Pd = ctx->staging;
+        Ud = ctx->staging + 8 * na;
+    }
+    launch_copy_state_in(ctx->g, Pd, Ud, ctx->stream);
+    launch_bc(ctx->g, 0, ctx->stream);
+    CK(cudaGetLastError());
+    if (set_scalars(ctx, t, dt)) return GRMHD_ECUDA;
+    ctx->state_set = true;
+    return 0;
+}
+
+extern "C" int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt, int on_device)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    long long na = nact_of(ctx);
+    if (P || U) {
+        if (on_device) {
+            launch_copy_state_out(ctx->g, P, U, ctx->stream);
+        } else {
+            if (ensure_staging(ctx, 17 * na)) return GRMHD_ENOMEM;
+            launch_copy_state_out(ctx->g, P ? ctx->staging : nullptr, U ? ctx->staging + 8 * na : nullptr, ctx->stream);
+            if (P) CK(cudaMemcpyAsync(P, ctx->staging, 8 * na * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            if (U) CK(cudaMemcpyAsync(U, ctx->staging + 8 * na, 9 * na * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(ctx->hpin, ctx->g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dt) *dt = ctx->hpin[0];
+    if (t) *t = ctx->hpin[1];
+    return 0;
+}
+
+extern "C" int grmhd_step(grmhd_ctx *ctx, int nsteps)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "step needs a state (init_torus or set_state)");
+    if (nsteps < 0) return fail(ctx, GRMHD_EINVAL, "nsteps < 0");
+    if (!ctx->gexec) {
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        launch_step(ctx->g, ctx->stream);
+        cudaError_t le = cudaGetLastError();
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(ctx, GRMHD_ECUDA, std::string("step capture failed: ") +
+                                              cudaGetErrorString(le != cudaSuccess ? le : ee));
+        }
+        ctx->graph = graph;
+        CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+    }
+    for (int s = 0; s < nsteps; s++) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_sync(grmhd_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    int st = 0;
+    CK(cudaMemcpyAsync(&ctx->hpin[8], ctx->g.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(&st, &ctx->hpin[8], sizeof(int));
+    if (st & ST_FIXUP) return fail(ctx, GRMHD_EFIXUP, "some failed zones could not be fixed");
+    if (st & ST_NONFINITE) return fail(ctx, GRMHD_ENONFINITE, "non-finite state");
+    return 0;
+}
+
+extern "C" int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out)
+{
+    if (!ctx || !out) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    Grid &g = ctx->g;
+    double *dout = ctx->scratch + ctx->scratch_len - 16;
+    launch_diagnostics(g, ctx->scratch, ctx->scratch_len - 16, dout, ctx->stream);
+    CK(cudaGetLastError());
+    unsigned long long cnt[C_NCOUNT];
+    CK(cudaMemcpyAsync(ctx->hpin, dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->hpin + 8, g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(cnt, g.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->mdot = ctx->hpin[0];
+    out->phib = ctx->hpin[1];
+    out->edot = ctx->hpin[2];
+    out->ldot = ctx->hpin[3];
+    out->divb_max = ctx->hpin[4];
+    out->PhiB = out->mdot != 0.0 ? out->phib / std::sqrt(std::fabs(out->mdot)) : 0.0;
+    out->dt = ctx->hpin[8];
+    out->t = ctx->hpin[9];
+    out->disk_mass = ctx->disk_mass;
+    out->disk_eb = ctx->disk_eb;
+    out->nr_iters = (long long)cnt[C_NR_ITERS];
+    out->n_nr = (long long)cnt[C_NR];
+    out->n_brent = (long long)cnt[C_BRENT];
+    out->n_entropy = (long long)cnt[C_ENT];
+    out->n_entropy_beta = (long long)cnt[C_ENT_BETA];
+    out->n_fail = (long long)cnt[C_FAIL];
+    out->n_floor = (long long)cnt[C_FLOOR];
+    out->n_ceil = (long long)cnt[C_CEIL];
+    out->n_gcap = (long long)cnt[C_GCAP];
+    out->n_fixed = (long long)cnt[C_FIXED];
+    out->fix_sweeps = (long long)cnt[C_SWEEPS];
+    out->n_steps = (long long)cnt[C_STEPS];
+    return grmhd_sync(ctx);
+}
+
+extern "C" int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, double *U, long n, int on_device)
+{
+    if (!ctx || (n > 0 && (!P || !loc || !U))) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
+    if (n < 0) return fail(ctx, GRMHD_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    const double *Pd = P;
+    const int *ld = loc;
+    double *Ud = U;
+    if (!on_device) {
+        long long need = 17LL * n + (n + 1) / 2 + 1;
+        if (ensure_staging(ctx, need)) return GRMHD_ENOMEM;
+        double *sp = ctx->staging, *su = sp + 8LL * n;
+        int *sl = (int *)(su + 9LL * n);
+        CK(cudaMemcpyAsync(sp, P, 8LL * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(sl, loc, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        Pd = sp; ld = sl; Ud = su;
+    }
+    launch_prim2cons(ctx->g, Pd, ld, Ud, n, ctx->stream);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(U, Ud, 9LL * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P, int *flags, int *iters,
+                              long n, int use_learned_guess, int on_device)
+{
+    if (!ctx || (n > 0 && (!P || !loc || !U || !flags))) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
+    if (n < 0) return fail(ctx, GRMHD_EINVAL, "n < 0");
+    if (use_learned_guess && !ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
+    if (n == 0) return 0;
+    const double *Ud = U;
+    const int *ld = loc;
+    double *Pd = P;
+    int *fd = flags, *id = iters;
+    if (!on_device) {
+        long long need = 17LL * n + 3 * ((n + 1) / 2) + 3;
+        if (ensure_staging(ctx, need)) return GRMHD_ENOMEM;
+        double *su = ctx->staging, *sp = su + 9LL * n;
+        int *sl = (int *)(sp + 8LL * n);
+        int *sf = sl + n, *si = sf + n;
+        CK(cudaMemcpyAsync(su, U, 9LL * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(sp, P, 8LL * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(sl, loc, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        Ud = su; Pd = sp; ld = sl; fd = sf; id = iters ? si : nullptr;
+    }
+    launch_con2prim(ctx->g, Ud, ld, Pd, fd, id, n, use_learned_guess ? ctx->mlp : nullptr, ctx->stream);
+    CK(cudaGetLastError());
+    if (!on_device) {
+        CK(cudaMemcpyAsync(P, Pd, 8LL * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(flags, fd, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        if (iters) CK(cudaMemcpyAsync(iters, id, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_fluxes(grmhd_ctx *ctx, double *out, double *dt_out, int on_device)
+{
+    if (!ctx || !out) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    Grid &g = ctx->g;
+    long long nf = 3LL * NU * (g.n1 + 1) * (g.n2 + 1) * (g.n3 + 1);
+    double *o = out;
+    if (!on_device) {
+        if (ensure_staging(ctx, nf)) return GRMHD_ENOMEM;
+        o = ctx->staging;
+    }
+    // keep the state's dt: save it, sweep, read the sweep's dt, restore
+    CK(cudaMemcpyAsync(ctx->hpin + 16, g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    launch_fluxes_dt(g, 1, ctx->stream);
+    launch_gather_fluxes(g, o, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->hpin + 20, g.scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (dt_out) *dt_out = ctx->hpin[20];
+    CK(cudaMemcpyAsync(g.scal, ctx->hpin + 16, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (!on_device) CK(cudaMemcpyAsync(out, o, nf * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}

@@ -1,0 +1,283 @@
+// con2prim.cuh -- device conserved-to-primitive inversion, Section 2.3 of
+// the paper (Noble et al. 2006 variables), always in FP64.
+//
+// Unknowns W = Gamma^2 h and v^2 solve
+//   (Eq. 29) Qt^2 = v^2 (Bf^2 + W)^2 - (Q.Bf)^2 (Bf^2 + 2W) / W^2
+//   (Eq. 30) Q.n  = -Bf^2/2 (1 + v^2) + (Q.Bf)^2 / (2 W^2) - W + p(W, v^2)
+//   (Eq. 31) p    = (gam-1)/gam [W (1 - v^2) - D sqrt(1 - v^2)]
+// Method order: 2D Newton (tolerance nr_tol, then one more step) -> if not
+// converged, Brent in W with v^2(W) from Eq. 29 -> if that fails, or if
+// Newton gives unphysical values, entropy inversion (W(v^2) of Eq. 32 into
+// Eq. 29, Brent in v^2); entropy alone where the guess has beta < beta_ent.
+// The sign of the Bf^2 term of Eq. 30 is taken as minus (static magnetised
+// fluid), and S of Eq. 32 is the normal-frame entropy density alpha U_S/sqrt(-g).
+#pragma once
+#include "physics.cuh"
+
+namespace grmhd {
+
+constexpr int C2P_NR = 0, C2P_BRENT_W = 1, C2P_ENTROPY = 2, C2P_ENTROPY_BETA = 3;
+constexpr int C2P_FAIL = 8, C2P_FAIL_D = 16, C2P_FAIL_ENT = 32;
+constexpr double V2MAX = 1.0 - 1.0e-16;
+
+struct C2PIn {
+    double D, Qtsq, Bsq, QB, nQ, Sent, gam;
+    double Qt[3], Bf[3];
+};
+
+__device__ __forceinline__ double c2p_pressure(const C2PIn &c, double W, double v2)
+{
+    return (c.gam - 1.0) / c.gam * (W * (1.0 - v2) - c.D * sqrt(1.0 - v2));
+}
+
+__device__ __forceinline__ void c2p_recover(const C2PIn &c, double W, double v2, double p, double *P)
+{
+    double lor = 1.0 / sqrt(1.0 - v2);
+    P[KRHO] = c.D / lor;
+    P[KUU] = p / (c.gam - 1.0);
+    double f = lor / (W + c.Bsq);
+#pragma unroll
+    for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + c.QB * c.Bf[i] / W);
+}
+
+__device__ __forceinline__ bool c2p_physical(const double *P, double v2)
+{
+    bool fin = isfinite(P[0]) && isfinite(P[1]) && isfinite(P[2]) && isfinite(P[3]) && isfinite(P[4]);
+    return fin && P[KRHO] > 0.0 && P[KUU] > 0.0 && v2 >= 0.0 && v2 < 1.0;
+}
+
+// Brent's bracketing root finder (Brent 1973): bisection safeguarded
+// secant / inverse-quadratic steps, stopping at |bracket|/2 <= 2 eps |b| + tol/2.
+template <typename Fn>
+__device__ double brent_root(const Fn &f, double a, double b, double fa, double fb, double tol,
+                             int maxit, bool &ok)
+{
+    const double eps = 2.220446049250313e-16;
+    ok = false;
+    if ((fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return b;
+    if (fa == 0.0) { ok = true; return a; }
+    if (fb == 0.0) { ok = true; return b; }
+    double c = a, fc = fa, d = b - a, e = d;
+    for (int it = 0; it < maxit; it++) {
+        if ((fb > 0.0) == (fc > 0.0) && fb != 0.0 && fc != 0.0) {
+            c = a;
+            fc = fa;
+            d = b - a;
+            e = d;
+        }
+        if (fabs(fc) < fabs(fb)) {
+            a = b; b = c; c = a;
+            fa = fb; fb = fc; fc = fa;
+        }
+        double tol1 = 2.0 * eps * fabs(b) + 0.5 * tol;
+        double xm = 0.5 * (c - b);
+        if (fabs(xm) <= tol1 || fb == 0.0) { ok = true; return b; }
+        bool bisect = true;
+        if (fabs(e) >= tol1 && fabs(fa) > fabs(fb)) {
+            double s = fb / fa, p, q;
+            if (a == c) {
+                p = 2.0 * xm * s;
+                q = 1.0 - s;
+            } else {
+                double qa = fa / fc, r = fb / fc;
+                p = s * (2.0 * xm * qa * (qa - r) - (b - a) * (r - 1.0));
+                q = (qa - 1.0) * (r - 1.0) * (s - 1.0);
+            }
+            if (p > 0.0) q = -q;
+            else p = -p;
+            double lim = fmin(3.0 * xm * q - fabs(tol1 * q), fabs(e * q));
+            if (2.0 * p < lim) {
+                e = d;
+                d = p / q;
+                bisect = false;
+            }
+        }
+        if (bisect) {
+            d = xm;
+            e = d;
+        }
+        a = b;
+        fa = fb;
+        b += (fabs(d) > tol1) ? d : (xm > 0.0 ? tol1 : -tol1);
+        fb = f(b);
+        if (!isfinite(fb)) return b;
+    }
+    return b;
+}
+
+struct ResidW {
+    const C2PIn *c;
+    __device__ double v2(double W) const
+    {
+        double BW = c->Bsq + W;
+        double v = (c->Qtsq + c->QB * c->QB * (c->Bsq + 2.0 * W) / (W * W)) / (BW * BW);
+        return fmin(fmax(v, 0.0), V2MAX);
+    }
+    __device__ double operator()(double W) const
+    {
+        double v = v2(W);
+        return -0.5 * c->Bsq * (1.0 + v) + c->QB * c->QB / (2.0 * W * W) - W + c2p_pressure(*c, W, v) -
+               c->nQ;
+    }
+};
+
+struct ResidS {
+    const C2PIn *c;
+    __device__ double W(double v2) const
+    {
+        double lor = 1.0 / sqrt(1.0 - v2);
+        double rho = c->D / lor;
+        return lor * c->D + lor * c->gam / (c->gam - 1.0) * pow(rho, c->gam - 1.0) * c->Sent;
+    }
+    __device__ double operator()(double v2) const
+    {
+        double w = W(v2);
+        double BW = c->Bsq + w;
+        return v2 * BW * BW - c->QB * c->QB * (c->Bsq + 2.0 * w) / (w * w) - c->Qtsq;
+    }
+};
+
+__device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double tol, int maxit,
+                                  int &iters)
+{
+    const double g1 = (c.gam - 1.0) / c.gam;
+    const double QB2 = c.QB * c.QB;
+    bool extra = false;
+    int n = 0;
+    for (int it = 1; it <= maxit; it++) {
+        n = it;
+        double s = sqrt(1.0 - v2);
+        double p = g1 * (W * (1.0 - v2) - c.D * s);
+        double BW = c.Bsq + W;
+        double W2 = W * W, W3 = W2 * W;
+        double f1 = v2 * BW * BW - QB2 * (c.Bsq + 2.0 * W) / W2 - c.Qtsq;
+        double f2 = -0.5 * c.Bsq * (1.0 + v2) + QB2 / (2.0 * W2) - W + p - c.nQ;
+        double a11 = 2.0 * v2 * BW + 2.0 * QB2 * BW / W3;
+        double a12 = BW * BW;
+        double a21 = -QB2 / W3 - 1.0 + g1 * (1.0 - v2);
+        double a22 = -0.5 * c.Bsq + g1 * (-W + 0.5 * c.D / s);
+        double det = a11 * a22 - a12 * a21;
+        if (!(fabs(det) > 0.0) || !isfinite(det)) break;
+        double dW = -(a22 * f1 - a12 * f2) / det;
+        double dv = -(-a21 * f1 + a11 * f2) / det;
+        double Wn = W + dW;
+        if (!(Wn > 0.0)) Wn = 0.5 * W;
+        double vn = fmin(fmax(v2 + dv, 0.0), V2MAX);
+        double errW = fabs(Wn - W) / fabs(Wn), errv = fabs(vn - v2);
+        W = Wn;
+        v2 = vn;
+        if (!isfinite(W) || !isfinite(v2)) break;
+        if (extra) {
+            iters = n;
+            return true;
+        }
+        if (errW < tol && errv < tol) extra = true;
+    }
+    iters = n;
+    return false;
+}
+
+__device__ inline bool c2p_brent_w(const C2PIn &c, int maxit, double *P)
+{
+    double E = -c.nQ;
+    double lo = c.D, hi = c.gam * fmax(E, c.D) * (1.0 + 1e-10);
+    if (!(lo > 0.0) || !(hi > lo)) return false;
+    ResidW f{&c};
+    bool ok;
+    double W = brent_root(f, lo, hi, f(lo), f(hi), 0.0, maxit, ok);
+    if (!ok) return false;
+    double v2 = f.v2(W);
+    c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
+    return c2p_physical(P, v2);
+}
+
+__device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
+{
+    if (!(c.Sent > 0.0) || !(c.D > 0.0)) return false;
+    ResidS f{&c};
+    double lo = 0.0, hi = 1.0 - 1.0e-12;
+    double flo = f(lo);
+    bool ok = true;
+    double v2 = 0.0;
+    // the residual at v^2 = 0 is <= 0 analytically; > 0 only by rounding => v^2 = 0
+    if (flo < 0.0) v2 = brent_root(f, lo, hi, flo, f(hi), 1.0e-17, maxit, ok);
+    if (!ok) return false;
+    double lor = 1.0 / sqrt(1.0 - v2);
+    double rho = c.D / lor;
+    double p = (c.Sent / lor) * pow(rho, c.gam - 1.0);
+    c2p_recover(c, f.W(v2), v2, p, P);
+    return c2p_physical(P, v2);
+}
+
+// Full inversion of one zone.  U includes sqrt(-g); guess = previous prims.
+// Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g).
+// methods: 1 Newton, 2 Brent-W, 4 entropy, 8 beta switch (15 = paper order).
+// wguess > 0 replaces the Newton starting W (learned guess; v^2 from Eq. 29).
+__device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double guess[NP],
+                               double gam, double beta_ent, double tol, int nr_maxit,
+                               int brent_maxit, int methods, double P[NP], int &iters,
+                               double wguess = 0.0)
+{
+    iters = 0;
+#pragma unroll
+    for (int m = 0; m < NP; m++) P[m] = guess[m];
+    double f = g.alpha / g.gdet;
+    P[KB1] = U[KB1] / g.gdet;
+    P[KB2] = U[KB2] / g.gdet;
+    P[KB3] = U[KB3] / g.gdet;
+    C2PIn c;
+    c.gam = gam;
+    c.D = f * U[KRHO];
+    double Q[4] = {f * U[1], f * U[2], f * U[3], f * U[4]};
+    c.Sent = f * U[KENT];
+    double n[4] = {1.0 / g.alpha, -g.alpha * g.gcon[1], -g.alpha * g.gcon[2], -g.alpha * g.gcon[3]};
+    double Qc[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+        Qc[m] = g.gcon[sym(m, 0)] * Q[0] + g.gcon[sym(m, 1)] * Q[1] + g.gcon[sym(m, 2)] * Q[2] +
+                g.gcon[sym(m, 3)] * Q[3];
+    c.nQ = n[0] * Q[0] + n[1] * Q[1] + n[2] * Q[2] + n[3] * Q[3];
+    double Qsq = Qc[0] * Q[0] + Qc[1] * Q[1] + Qc[2] * Q[2] + Qc[3] * Q[3];
+    c.Qtsq = Qsq + c.nQ * c.nQ;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        c.Qt[i] = Qc[i + 1] + n[i + 1] * c.nQ;
+        c.Bf[i] = g.alpha * P[KB1 + i];
+    }
+    c.QB = Q[1] * c.Bf[0] + Q[2] * c.Bf[1] + Q[3] * c.Bf[2];
+    c.Bsq = spatial_sq(g, c.Bf[0], c.Bf[1], c.Bf[2]);
+    bool fin = isfinite(c.D) && isfinite(c.Qtsq) && isfinite(c.nQ) && isfinite(c.Bsq);
+    if (!fin || !(c.D > 0.0)) return C2P_FAIL | C2P_FAIL_D;
+
+    if (methods & 8) {
+        St<double> s;
+        get_state(guess, g, s);
+        double pg = (gam - 1.0) * guess[KUU];
+        if (s.bsq > 0.0 && pg < beta_ent * 0.5 * s.bsq) {
+            if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY_BETA;
+            return C2P_FAIL | C2P_FAIL_ENT;
+        }
+    }
+    if (methods & 1) {
+        double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
+        double v2 = usq / (1.0 + usq);
+        double W = (1.0 + usq) * (guess[KRHO] + gam * guess[KUU]);
+        if (wguess > 0.0) {
+            W = wguess;
+            v2 = ResidW{&c}.v2(W);
+        }
+        if (!(W > 0.0) || !isfinite(W)) W = c.D;
+        v2 = fmin(v2, V2MAX);
+        if (c2p_newton(c, W, v2, tol, nr_maxit, iters)) {
+            c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
+            if (c2p_physical(P, v2)) return C2P_NR;
+            if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY;
+            return C2P_FAIL | C2P_FAIL_ENT;
+        }
+    }
+    if ((methods & 2) && c2p_brent_w(c, brent_maxit, P)) return C2P_BRENT_W;
+    if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY;
+    return C2P_FAIL | C2P_FAIL_ENT;
+}
+
+} // namespace grmhd

@@ -1,0 +1,232 @@
+// diag.cu -- horizon diagnostics (Section 4.2, Eqs. 38-42), the corner
+// divergence of Eq. 24, batched stand-alone prim2cons / con2prim, and the
+// active-zone state copies.
+//
+// Horizon sums are deterministic: fixed-size blocks write partial sums to
+// scratch and one thread adds them in block order.  The divergence maximum
+// uses an atomic max on the bit pattern of a non-negative double, which is
+// order independent.
+#include "fixes.cuh"
+#include "kernels.h"
+#include "mlp.cuh"
+
+namespace grmhd {
+
+template <typename RS>
+__global__ void k_horizon_partial(Grid g, const RS *P, double *part)
+{
+    int n = g.n2 * g.n3;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[4] = {0, 0, 0, 0};
+    if (t < n && g.metric == KERR_MKS && g.i_h < g.n1) {
+        int j = t / g.n3, k = t % g.n3, i = g.i_h;
+        long long z = zidx(g, i, j, k);
+        double q[NP];
+        for (int c = 0; c < NP; c++) q[c] = (double)P[c * g.nz + z];
+        const Geo<double> geo = g.gc[midx(g, i, j)];
+        St<double> s;
+        get_state(q, geo, s);
+        double T[4];
+        tmunu_row(q, s, g.gam, 1, T);
+        double dA = g.dx[1] * g.dx[2];
+        v[0] = geo.gdet * q[KRHO] * s.ucon[1] * dA;
+        v[1] = 0.5 * geo.gdet * fabs(q[KB1]) * dA;
+        v[2] = -geo.gdet * T[0] * dA;
+        v[3] = geo.gdet * T[3] * dA;
+    }
+    __shared__ double sm[4][256];
+    for (int c = 0; c < 4; c++) sm[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 4; c++) sm[c][threadIdx.x] += sm[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; c++) part[4 * blockIdx.x + c] = sm[c][0];
+}
+
+__global__ void k_horizon_sum(const double *part, int nb, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double a[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nb; b++)
+        for (int c = 0; c < 4; c++) a[c] += part[4 * b + c];
+    for (int c = 0; c < 4; c++) out[c] = a[c];
+}
+
+template <typename RS>
+__global__ void k_divb(Grid g, const RS *P, double *out)
+{
+    bool per3 = g.metric == KERR_MKS || g.bc3 == BC_PERIODIC;
+    int k0 = (per3 || g.n3 == 1) ? 0 : 1;
+    long long n = (long long)(g.n1 - 1) * (g.n2 - 1) * (g.n3 - k0);
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double dv = 0.0;
+    if (t < n && n > 0) {
+        int k = (int)(t % (g.n3 - k0)) + k0;
+        long long r = t / (g.n3 - k0);
+        int j = (int)(r % (g.n2 - 1)) + 1, i = (int)(r / (g.n2 - 1)) + 1;
+        for (int l1 = 0; l1 < 2; l1++)
+            for (int l2 = 0; l2 < 2; l2++)
+                for (int l3 = 0; l3 < 2; l3++) {
+                    int ii = i - 1 + l1, jj = j - 1 + l2, kk = ((k - 1 + l3) % g.n3 + g.n3) % g.n3;
+                    double gd = g.gc[midx(g, ii, jj)].gdet;
+                    long long z = zidx(g, ii, jj, kk);
+                    dv += (2 * l1 - 1) * gd * (double)P[KB1 * g.nz + z] / (4.0 * g.dx[0]) +
+                          (2 * l2 - 1) * gd * (double)P[KB2 * g.nz + z] / (4.0 * g.dx[1]) +
+                          (2 * l3 - 1) * gd * (double)P[KB3 * g.nz + z] / (4.0 * g.dx[2]);
+                }
+    }
+    dv = fabs(dv);
+    for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
+    if ((threadIdx.x & 31) == 0 && dv > 0.0)
+        atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong(dv));
+}
+
+// out_dev[0..3] = mdot, phib, edot, ldot; out_dev[4] = max corner divergence
+void launch_diagnostics(const Grid &g, double *scratch, long scratch_len, double *out_dev, cudaStream_t s)
+{
+    int n = g.n2 * g.n3;
+    int nb = (n + 255) / 256;
+    (void)scratch_len;
+    cudaMemsetAsync(out_dev, 0, 8 * sizeof(double), s);
+    long long nc = (long long)(g.n1 - 1) * (g.n2 - 1) * g.n3;
+    unsigned nbc = (unsigned)((nc + 255) / 256);
+    if (g.mixed) {
+        k_horizon_partial<float><<<nb, 256, 0, s>>>(g, (const float *)g.P[0], scratch);
+        if (nc > 0) k_divb<float><<<nbc, 256, 0, s>>>(g, (const float *)g.P[0], out_dev + 4);
+    } else {
+        k_horizon_partial<double><<<nb, 256, 0, s>>>(g, (const double *)g.P[0], scratch);
+        if (nc > 0) k_divb<double><<<nbc, 256, 0, s>>>(g, (const double *)g.P[0], out_dev + 4);
+    }
+    k_horizon_sum<<<1, 32, 0, s>>>(scratch, nb, out_dev);
+}
+
+// ------------------------------------------------------------ point batches
+
+__global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, long n)
+{
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int l = loc[t];
+    if (l < 0 || l >= g.n1 * g.n2) {
+        for (int c = 0; c < NU; c++) U[c * n + t] = NAN;
+        return;
+    }
+    const Geo<double> geo = g.gc[midx(g, l / g.n2, l % g.n2)];
+    double q[NP], Uz[NU];
+    for (int c = 0; c < NP; c++) q[c] = P[c * n + t];
+    St<double> s;
+    get_state(q, geo, s);
+    prim_to_UF<double, false>(q, geo, s, g.gam, 0, Uz);
+    for (int c = 0; c < NU; c++) U[c * n + t] = Uz[c];
+}
+
+__global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, int *flags, int *iters,
+                           long n, const float *mlp)
+{
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int l = loc[t];
+    if (l < 0 || l >= g.n1 * g.n2) {
+        flags[t] = C2P_FAIL | C2P_FAIL_D;
+        if (iters) iters[t] = 0;
+        return;
+    }
+    const Geo<double> geo = g.gc[midx(g, l / g.n2, l % g.n2)];
+    double Uz[NU], q0[NP], q[NP];
+    for (int c = 0; c < NU; c++) Uz[c] = U[c * n + t];
+    for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
+    double wg = 0.0;
+    if (mlp) {
+        // features of the learned Newton start (log-normalised, Section 2.3 variables)
+        double f = geo.alpha / geo.gdet;
+        double D = f * Uz[KRHO];
+        if (D > 0.0) {
+            double Q[4] = {f * Uz[1], f * Uz[2], f * Uz[3], f * Uz[4]};
+            double nq = Q[0] / geo.alpha;
+            for (int i = 1; i <= 3; i++) nq += -geo.alpha * geo.gcon[i] * Q[i];
+            double Qc[4];
+            for (int m = 0; m < 4; m++)
+                Qc[m] = geo.gcon[sym(m, 0)] * Q[0] + geo.gcon[sym(m, 1)] * Q[1] + geo.gcon[sym(m, 2)] * Q[2] +
+                        geo.gcon[sym(m, 3)] * Q[3];
+            double Qt2 = Qc[0] * Q[0] + Qc[1] * Q[1] + Qc[2] * Q[2] + Qc[3] * Q[3] + nq * nq;
+            double Bf[3] = {geo.alpha * Uz[KB1] / geo.gdet, geo.alpha * Uz[KB2] / geo.gdet,
+                            geo.alpha * Uz[KB3] / geo.gdet};
+            double B2 = spatial_sq(geo, Bf[0], Bf[1], Bf[2]);
+            double QB = Q[1] * Bf[0] + Q[2] * Bf[1] + Q[3] * Bf[2];
+            double tau = -nq - D;
+            double feat[5] = {log(fmax(tau / D, 1e-30)), log(fmax(Qt2 / (D * D), 1e-30)),
+                              log(fmax(B2 / D, 1e-30)), log(fmax(QB * QB / (D * D * D), 1e-30)), log(D)};
+            wg = D * exp((double)mlp_log_w_guess(mlp, feat));
+        }
+    }
+    int it;
+    flags[t] = con2prim(Uz, geo, q0, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, q, it, wg);
+    if (iters) iters[t] = it;
+    for (int c = 0; c < NP; c++) P[c * n + t] = q[c];
+}
+
+void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U, long n, cudaStream_t s)
+{
+    if (n > 0) k_prim2cons<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, P, loc, U, n);
+}
+
+void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
+                     long n, const float *mlp, cudaStream_t s)
+{
+    if (n > 0) k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp);
+}
+
+// ------------------------------------------------------------ state copies
+
+template <typename RS>
+__global__ void k_state_in(Grid g, const double *Pa, const double *Ua)
+{
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nact) return;
+    int k = (int)(t % g.n3);
+    long long r = t / g.n3;
+    int j = (int)(r % g.n2), i = (int)(r / g.n2);
+    long long z = zidx(g, i, j, k);
+    RS *P = (RS *)g.P[0];
+    for (int c = 0; c < NP; c++) P[c * g.nz + z] = (RS)Pa[c * nact + t];
+    for (int c = 0; c < NU; c++) g.U[c * g.nz + z] = Ua[c * nact + t];
+}
+
+template <typename RS>
+__global__ void k_state_out(Grid g, double *Pa, double *Ua)
+{
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nact) return;
+    int k = (int)(t % g.n3);
+    long long r = t / g.n3;
+    int j = (int)(r % g.n2), i = (int)(r / g.n2);
+    long long z = zidx(g, i, j, k);
+    const RS *P = (const RS *)g.P[0];
+    if (Pa)
+        for (int c = 0; c < NP; c++) Pa[c * nact + t] = (double)P[c * g.nz + z];
+    if (Ua)
+        for (int c = 0; c < NU; c++) Ua[c * nact + t] = g.U[c * g.nz + z];
+}
+
+void launch_copy_state_in(const Grid &g, const double *P, const double *U, cudaStream_t s)
+{
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    unsigned nb = (unsigned)((nact + 255) / 256);
+    if (g.mixed) k_state_in<float><<<nb, 256, 0, s>>>(g, P, U);
+    else k_state_in<double><<<nb, 256, 0, s>>>(g, P, U);
+}
+
+void launch_copy_state_out(const Grid &g, double *P, double *U, cudaStream_t s)
+{
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    unsigned nb = (unsigned)((nact + 255) / 256);
+    if (g.mixed) k_state_out<float><<<nb, 256, 0, s>>>(g, P, U);
+    else k_state_out<double><<<nb, 256, 0, s>>>(g, P, U);
+}
+
+} // namespace grmhd

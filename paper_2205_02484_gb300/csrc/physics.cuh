@@ -1,0 +1,177 @@
+// physics.cuh -- pointwise GR-MHD physics of Sections 2.1-2.2, templated on
+// the arithmetic type (double for the FP64 path, float for the mixed path).
+//
+//   u^mu from the modified velocity ut^i (Eq. 11): u^t = Gamma/alpha,
+//   u^i = ut^i - Gamma alpha g^{ti}; b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t;
+//   T^mu_nu = (w + b^2) u^mu u_nu + (p + b^2/2) delta - b^mu b_nu (Eq. 5);
+//   U = sqrt(-g)(rho u^t, T^t_nu, B^i, S u^t), F^d likewise (Eqs. 6-8, 12);
+//   wave speeds: roots of the quadratic form of Eq. 19 along direction d.
+//
+// In the mixed path the energy component of U and F is carried rest-mass
+// subtracted (T^t_t + rho u^t, T^d_t + rho u^d), with 1 + u_t evaluated as
+// (1 - alpha) - alpha (Gamma - 1) + g_{ti} ut^i so that no FP32 cancellation
+// between the rest mass and the energy occurs; the update adds the mass flux
+// back in FP64, so the stored energy is still sqrt(-g) T^t_t.
+#pragma once
+#include "common.cuh"
+
+namespace grmhd {
+
+template <typename R>
+struct St {
+    R ucon[4], ucov[4], bcon[4], bcov[4], bsq, gamma, usq;
+};
+
+template <typename R>
+__device__ __forceinline__ R spatial_sq(const Geo<R> &g, R x, R y, R z)
+{
+    return g.gcov[4] * x * x + g.gcov[7] * y * y + g.gcov[9] * z * z +
+           R(2) * (g.gcov[5] * x * y + g.gcov[6] * x * z + g.gcov[8] * y * z);
+}
+
+template <typename R>
+__device__ __forceinline__ void lower4(const Geo<R> &g, const R v[4], R w[4])
+{
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+        w[m] = g.gcov[sym(m, 0)] * v[0] + g.gcov[sym(m, 1)] * v[1] + g.gcov[sym(m, 2)] * v[2] +
+               g.gcov[sym(m, 3)] * v[3];
+}
+
+template <typename R>
+__device__ __forceinline__ void get_state(const R q[NP], const Geo<R> &g, St<R> &s)
+{
+    R usq = spatial_sq(g, q[KU1], q[KU2], q[KU3]);
+    R gm = sqrt(R(1) + usq);
+    s.usq = usq;
+    s.gamma = gm;
+    s.ucon[0] = gm / g.alpha;
+#pragma unroll
+    for (int i = 1; i <= 3; i++) s.ucon[i] = q[KU1 + i - 1] - gm * g.alpha * g.gcon[sym(0, i)];
+    lower4(g, s.ucon, s.ucov);
+    s.bcon[0] = q[KB1] * s.ucov[1] + q[KB2] * s.ucov[2] + q[KB3] * s.ucov[3];
+#pragma unroll
+    for (int i = 1; i <= 3; i++) s.bcon[i] = (q[KB1 + i - 1] + s.bcon[0] * s.ucon[i]) / s.ucon[0];
+    lower4(g, s.bcon, s.bcov);
+    s.bsq = s.bcon[0] * s.bcov[0] + s.bcon[1] * s.bcov[1] + s.bcon[2] * s.bcov[2] +
+            s.bcon[3] * s.bcov[3];
+}
+
+template <typename R>
+__device__ __forceinline__ R powr(R x, R y);
+template <>
+__device__ __forceinline__ double powr<double>(double x, double y) { return pow(x, y); }
+template <>
+__device__ __forceinline__ float powr<float>(float x, float y) { return powf(x, y); }
+
+// Row mu of T^mu_nu.
+template <typename R>
+__device__ __forceinline__ void tmunu_row(const R q[NP], const St<R> &s, R gam, int mu, R T[4])
+{
+    R p = (gam - R(1)) * q[KUU];
+    R w = q[KRHO] + q[KUU] + p;
+    R wb = w + s.bsq;
+#pragma unroll
+    for (int n = 0; n < 4; n++) T[n] = wb * s.ucon[mu] * s.ucov[n] - s.bcon[mu] * s.bcov[n];
+    T[mu] += p + R(0.5) * s.bsq;
+}
+
+// Conserved vector (d = 0) or flux along d (1..3), Eqs. 6-8 plus the entropy
+// density of Eq. 12.  RMS: rest-mass-subtracted energy (mixed path).
+template <typename R, bool RMS>
+__device__ __forceinline__ void prim_to_UF(const R q[NP], const Geo<R> &g, const St<R> &s, R gam,
+                                           int d, R out[NU])
+{
+    R T[4];
+    tmunu_row(q, s, gam, d, T);
+    R gd = g.gdet;
+    R p = (gam - R(1)) * q[KUU];
+    R ent = p / powr(q[KRHO], gam - R(1));
+    out[KRHO] = gd * q[KRHO] * s.ucon[d];
+    if (RMS) {
+        // T^d_t + rho u^d = rho u^d (1 + u_t) + (u + p + b^2) u^d u_t - b^d b_t (+ p + b^2/2 if d = t)
+        R opu = g.oma - g.alpha * (s.usq / (s.gamma + R(1))) +
+                (g.gcov[1] * q[KU1] + g.gcov[2] * q[KU2] + g.gcov[3] * q[KU3]);
+        R e = q[KRHO] * s.ucon[d] * opu + (q[KUU] + p + s.bsq) * s.ucon[d] * s.ucov[0] -
+              s.bcon[d] * s.bcov[0];
+        if (d == 0) e += p + R(0.5) * s.bsq;
+        out[1] = gd * e;
+    } else {
+        out[1] = gd * T[0];
+    }
+    out[2] = gd * T[1];
+    out[3] = gd * T[2];
+    out[4] = gd * T[3];
+    if (d == 0) {
+        out[KB1] = gd * q[KB1];
+        out[KB2] = gd * q[KB2];
+        out[KB3] = gd * q[KB3];
+    } else {
+#pragma unroll
+        for (int i = 1; i <= 3; i++) out[KB1 + i - 1] = gd * (s.bcon[d] * s.ucon[i] - s.bcon[i] * s.ucon[d]);
+    }
+    out[KENT] = gd * ent * s.ucon[d];
+}
+
+// c1 >= c2: roots of (1 - cms2)(u^d - v u^t)^2 = cms2 (g^tt v^2 - 2 g^td v + g^dd)
+template <typename R>
+__device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, const St<R> &s, R gam,
+                                            int d, R &c1, R &c2)
+{
+    R p = (gam - R(1)) * q[KUU];
+    R ef = q[KRHO] + q[KUU] + p;
+    R va2 = s.bsq / (s.bsq + ef);
+    R cs2 = gam * p / ef;
+    R cms2 = va2 + cs2 * (R(1) - va2);
+    R A1 = R(1) - cms2;
+    R ut = s.ucon[0], ud = s.ucon[d];
+    R A = A1 * ut * ut - cms2 * g.gcon[0];
+    R B = R(-2) * (A1 * ut * ud - cms2 * g.gcon[sym(0, d)]);
+    R C = A1 * ud * ud - cms2 * g.gcon[sym(d, d)];
+    R disc = B * B - R(4) * A * C;
+    disc = disc < R(0) ? R(0) : disc;
+    R sq = sqrt(disc);
+    R vp = (-B + sq) / (R(2) * A);
+    R vm = (-B - sq) / (R(2) * A);
+    c1 = vp > vm ? vp : vm;
+    c2 = vp > vm ? vm : vp;
+}
+
+// MC-limited slope (Eq. 16, signed central branch)
+template <typename R>
+__device__ __forceinline__ R mc_slope(R qm, R q0, R qp)
+{
+    R dm = q0 - qm, dp = qp - q0, dc = qp - qm;
+    if (dm * dp < R(0)) return R(0);
+    if (fabs(dm) < fabs(dp) && R(2) * fabs(dm) < R(0.5) * fabs(dc)) return R(2) * dm;
+    if (R(2) * fabs(dp) < R(0.5) * fabs(dc)) return R(2) * dp;
+    return R(0.5) * dc;
+}
+
+// Source of Eq. 7 at the cell centre: S_nu = sqrt(-g) T^k_l Gamma^l_{nu k};
+// conn holds Gamma^l_{mn} as conn[l*10 + sym(m,n)].
+template <typename R>
+__device__ __forceinline__ void source_terms(const R q[NP], const Geo<R> &g, const R *conn,
+                                             const St<R> &s, R gam, R S[4])
+{
+    R T[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) tmunu_row(q, s, gam, k, T[k]);
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) {
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int l = 0; l < 4; l++) acc += T[k][l] * conn[l * 10 + sym(nu, k)];
+        S[nu] = g.gdet * acc;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_geo(const Geo<R> *tab, int m, Geo<R> &g)
+{
+    g = tab[m];
+}
+
+} // namespace grmhd

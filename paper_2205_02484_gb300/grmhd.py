@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libgrmhd.so (include/grmhd.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host memory, on_device=0) or torch
+CUDA tensors (device memory, on_device=1); shapes follow the header's
+field-major active-zone layout.  Errors raise GrmhdError with the library's
+message.  If the shared library is missing the import fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KERR_MKS, MINK_CART = 0, 1
+BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW = 0, 1, 2, 3
+LLF, HLL = 0, 1
+FP64, MIXED = 0, 1
+C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
+C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT = 8, 16, 32
+NP, NU = 8, 9
+
+ERRORS = {-1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENONFINITE", -5: "EFIXUP", -6: "EITER",
+          -7: "ESTATE"}
+
+
+class GrmhdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"grmhd {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridParams(C.Structure):
+    _fields_ = [
+        ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("metric", C.c_int),
+        ("r_in", C.c_double), ("r_out", C.c_double), ("hslope", C.c_double), ("r_br", C.c_double),
+        ("n_x", C.c_double), ("R0", C.c_double),
+        ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double), ("x2max", C.c_double),
+        ("x3min", C.c_double), ("x3max", C.c_double),
+        ("bc1", C.c_int), ("bc2", C.c_int), ("bc3", C.c_int), ("riemann", C.c_int),
+        ("precision", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
+class PhysParams(C.Structure):
+    _fields_ = [("gam", C.c_double), ("cfl", C.c_double), ("nr_tol", C.c_double),
+                ("sigma_max", C.c_double), ("bu_max", C.c_double), ("gamma_max", C.c_double),
+                ("beta_entropy", C.c_double), ("nr_maxit", C.c_int), ("brent_maxit", C.c_int),
+                ("fix_maxsweep", C.c_int)]
+
+
+class TorusParams(C.Structure):
+    _fields_ = [("r_in", C.c_double), ("r_max", C.c_double), ("beta0", C.c_double),
+                ("pert_amp", C.c_double), ("kappa", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class Diag(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb")] + \
+               [(n, C.c_longlong) for n in
+                ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_floor",
+                 "n_ceil", "n_gcap", "n_fixed", "fix_sweeps", "n_steps")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+# every symbol include/grmhd.h declares, with its ctypes signature
+_V = C.c_void_p
+SIGNATURES = {
+    "grmhd_init_grid": (C.c_int, [C.POINTER(GridParams), C.POINTER(PhysParams), C.POINTER(_V)]),
+    "grmhd_set_metric": (C.c_int, [_V, C.c_double, C.c_int]),
+    "grmhd_init_torus": (C.c_int, [_V, C.POINTER(TorusParams)]),
+    "grmhd_set_state": (C.c_int, [_V, _V, _V, C.c_double, C.c_double, C.c_int]),
+    "grmhd_get_state": (C.c_int, [_V, _V, _V, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
+    "grmhd_step": (C.c_int, [_V, C.c_int]),
+    "grmhd_con2prim": (C.c_int, [_V, _V, _V, _V, _V, _V, C.c_long, C.c_int, C.c_int]),
+    "grmhd_prim2cons": (C.c_int, [_V, _V, _V, _V, C.c_long, C.c_int]),
+    "grmhd_fluxes": (C.c_int, [_V, _V, C.POINTER(C.c_double), C.c_int]),
+    "grmhd_sync": (C.c_int, [_V]),
+    "grmhd_diagnostics": (C.c_int, [_V, C.POINTER(Diag)]),
+    "grmhd_destroy": (None, [_V]),
+    "grmhd_last_error": (C.c_char_p, [_V]),
+    "grmhd_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libgrmhd.so (raises if it is missing and building is not allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"{path} not built: run __graft_entry__.build() or "
+                              f"python -m paper_2205_02484_gb300.build")
+        _build.build()
+    L = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    # torch tensor
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+class Context:
+    """Owning handle of one grmhd_ctx."""
+
+    def __init__(self, handle, grid: GridParams, phys: PhysParams):
+        self.h = handle
+        self.grid = grid
+        self.phys = phys
+        self.L = load()
+
+    @property
+    def shape(self):
+        return (self.grid.n1, self.grid.n2, self.grid.n3)
+
+    @property
+    def nact(self):
+        return self.grid.n1 * self.grid.n2 * self.grid.n3
+
+    def check(self, rc):
+        if rc != 0:
+            msg = self.L.grmhd_last_error(self.h)
+            raise GrmhdError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if self.h:
+            self.L.grmhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_phys(gam=13.0 / 9.0, **kw) -> PhysParams:
+    d = dict(gam=gam, cfl=0.45, nr_tol=1e-10, sigma_max=50.0, bu_max=2500.0, gamma_max=50.0,
+             beta_entropy=1e-2, nr_maxit=30, brent_maxit=100, fix_maxsweep=16)
+    d.update(kw)
+    return PhysParams(**d)
+
+
+def default_grid(n1, n2, n3, a=0.9375, r_out=40.0, precision=FP64, **kw) -> GridParams:
+    d = dict(n1=n1, n2=n2, n3=n3, metric=KERR_MKS, r_in=0.98 * (1.0 + (1.0 - a * a) ** 0.5),
+             r_out=r_out, hslope=0.3, r_br=400.0, n_x=4.0, R0=0.0, x1min=0.0, x1max=1.0, x2min=0.0,
+             x2max=1.0, x3min=0.0, x3max=1.0, bc1=BC_OUTFLOW, bc2=BC_OUTFLOW, bc3=BC_PERIODIC,
+             riemann=LLF, precision=precision, device=0, stream=None)
+    d.update(kw)
+    return GridParams(**d)
+
+
+# ------------------------------------------------------------ ABI functions
+
+def init_grid(grid: GridParams, phys: PhysParams) -> Context:
+    L = load()
+    h = C.c_void_p()
+    rc = L.grmhd_init_grid(C.byref(grid), C.byref(phys), C.byref(h))
+    if rc != 0:
+        raise GrmhdError(rc, L.grmhd_last_error(None).decode())
+    return Context(h.value, grid, phys)
+
+
+def set_metric(ctx: Context, a: float, kind: int = KERR_MKS):
+    ctx.check(ctx.L.grmhd_set_metric(ctx.h, a, kind))
+
+
+def init_torus(ctx: Context, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=1, kappa=1e-3):
+    tp = TorusParams(r_in, r_max, beta0, pert_amp, kappa, seed)
+    ctx.check(ctx.L.grmhd_init_torus(ctx.h, C.byref(tp)))
+
+
+def set_state(ctx: Context, P, U, t: float, dt: float):
+    pp, dev = _ptr(P)
+    up, dev2 = _ptr(U)
+    if dev != dev2:
+        raise ValueError("P and U must both be host or both be device")
+    ctx.check(ctx.L.grmhd_set_state(ctx.h, pp, up, t, dt, dev))
+
+
+def get_state(ctx: Context, P=None, U=None):
+    """Fills P (8, n1, n2, n3) and U (9, ...) (numpy or CUDA tensors; new numpy
+    arrays if None) and returns (P, U, t, dt)."""
+    if P is None:
+        P = np.zeros((NP,) + ctx.shape)
+    if U is None:
+        U = np.zeros((NU,) + ctx.shape)
+    pp, dev = _ptr(P)
+    up, dev2 = _ptr(U)
+    if dev != dev2:
+        raise ValueError("P and U must both be host or both be device")
+    t, dt = C.c_double(), C.c_double()
+    ctx.check(ctx.L.grmhd_get_state(ctx.h, pp, up, C.byref(t), C.byref(dt), dev))
+    return P, U, t.value, dt.value
+
+
+def step(ctx: Context, nsteps: int = 1):
+    ctx.check(ctx.L.grmhd_step(ctx.h, nsteps))
+
+
+def sync(ctx: Context):
+    ctx.check(ctx.L.grmhd_sync(ctx.h))
+
+
+def diagnostics(ctx: Context) -> dict:
+    d = Diag()
+    ctx.check(ctx.L.grmhd_diagnostics(ctx.h, C.byref(d)))
+    return d.as_dict()
+
+
+def prim2cons(ctx: Context, P, loc, U=None):
+    n = loc.shape[0]
+    if U is None:
+        U = np.zeros((NU, n))
+    pp, dev = _ptr(P)
+    lp, _ = _ptr(loc)
+    up, _ = _ptr(U)
+    ctx.check(ctx.L.grmhd_prim2cons(ctx.h, pp, lp, up, n, dev))
+    return U
+
+
+def con2prim(ctx: Context, U, loc, P_inout, flags=None, iters=None, use_learned_guess=False):
+    n = loc.shape[0]
+    if flags is None:
+        flags = np.zeros(n, dtype=np.int32)
+    if iters is None:
+        iters = np.zeros(n, dtype=np.int32)
+    up, dev = _ptr(U)
+    lp, _ = _ptr(loc)
+    pp, _ = _ptr(P_inout)
+    fp, _ = _ptr(flags)
+    ip, _ = _ptr(iters)
+    ctx.check(ctx.L.grmhd_con2prim(ctx.h, up, lp, pp, fp, ip, n, int(use_learned_guess), dev))
+    return P_inout, flags, iters
+
+
+def fluxes(ctx: Context, out=None):
+    n1, n2, n3 = ctx.shape
+    if out is None:
+        out = np.zeros((3, NU, n1 + 1, n2 + 1, n3 + 1))
+    op, dev = _ptr(out)
+    dt = C.c_double()
+    ctx.check(ctx.L.grmhd_fluxes(ctx.h, op, C.byref(dt), dev))
+    return out, dt.value
+
+
+def version() -> str:
+    return load().grmhd_version().decode()
