@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark: zone-cycles/s of the GR-MHD step on the 256^3 Fishbone-Moncrief
+torus (MKS, r_out = 1000 M, a = 0.9375, gamma = 4/3, beta_0 = 100), mixed
+precision (FP32 fluxes, FP64 conserved variables and inversion), with the
+plain FP64 step timed beside it on the same GPU.
+
+One JSON line on stdout (rank 0).  A "step" is one full RK2 step (both
+stages, inversion, floors, fixups, boundaries and the CFL time step) of the
+whole grid, replayed from a captured CUDA graph; inputs are resident in HBM.
+The state (4.5 GB mixed, 7.7 GB FP64) is far larger than the 129 MB L2, so
+no L2 flush is needed between steps.
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own torus
+(independent replicas, different perturbation seeds, weak scaling); the
+time is the max over ranks and the value the zone-cycles of all ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+HBM_BYTES_PER_ZONE_CYCLE = {"mixed": 344.0, "fp64": 472.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="zones per direction (default 256)")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="FP64 steps (0: steps // 4, >= 3)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n):
+    return {"workload": f"3D Fishbone-Moncrief torus {n}^3 MKS, r_out=1000 M, a=0.9375, gamma=4/3, "
+                        f"beta_min=100, 4% perturbation, mixed FP32-flux/FP64-inversion, PLM-MC+LLF+flux-CT",
+            "grid": [n, n, n], "r_out": 1000.0, "spin": 0.9375, "gamma": 4.0 / 3.0, "beta0": 100.0,
+            "r_in": 6.0, "r_max": 12.0, "precision": "mixed", "riemann": "LLF",
+            "l2": "state (4.5 GB) exceeds L2 (129 MB); no flush needed",
+            "graph": "one CUDA graph per RK2 step"}
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample_run(n, n3s, steps, warmup):
+    """The FP64 CPU oracle, as it stands, on an n x n x n3s slab of the
+    workload (same r, theta grid; n3s phi zones).  Returns (zone-cycles/s,
+    seconds, description)."""
+    import oracle
+    p = oracle.default_params(n1=n, n2=n, n3=n3s, gam=4.0 / 3.0, r_out=1000.0, a=0.9375)
+    og = oracle.Grid(p)
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
+    if warmup:
+        og.step(warmup)
+    t0 = time.perf_counter()
+    og.step(steps)
+    dt = time.perf_counter() - t0
+    zc = n * n * n3s * steps / dt
+    desc = (f"{n}x{n}x{n3s} phi-slab of the {n}^3 torus (same r, theta grid), {steps} RK2 steps "
+            f"after {warmup} warm-up, single-threaded plain C -O2")
+    return zc, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.n
+    # per-step work bounded so that warmup + steps finish in about a minute
+    n3s = 1 if args.steps + args.warmup > 10 else 2
+    zc, dt, desc = oracle_sample_run(n, n3s, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": "zone-cycles/s at 256^3 (FP64 vs mixed, same GB300); % of HBM roofline",
+            "value": zc, "unit": "zone-cycles/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(n),
+            "cpu_baseline": {"value": zc, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": zc, "unit": "zone-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2205_02484_gb300 import grmhd as G
+    G.load(build_if_missing=True)
+    n = args.n
+    stream = torch.cuda.current_stream()
+
+    def make_ctx(precision):
+        gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=precision, device=local)
+        gp.stream = stream.cuda_stream
+        ctx = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+        G.set_metric(ctx, 0.9375, G.KERR_MKS)
+        G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3 + rank)
+        return ctx
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(ctx, steps, warmup, sample_clocks):
+        G.step(ctx, warmup)
+        G.sync(ctx)
+        clk = ClockSampler(local if world > 1 else None) if sample_clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.step(ctx, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clocks = clk.stop() if clk else None
+        G.sync(ctx)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clocks
+
+    zones = n * n * n
+    # ---- headline: mixed precision
+    ctx = make_ctx(G.MIXED)
+    ms, clocks = timed(ctx, args.steps, args.warmup, True)
+    value = zones * args.steps * world / (ms * 1e-3)
+    ms_step = ms / args.steps
+    diag = G.diagnostics(ctx)
+    # per-kernel breakdown (events between kernel groups, no graph)
+    prof = G.step_profiled(ctx, 3)
+    parts = {k: v / 3.0 for k, v in prof.items()}
+    upd = (parts["update_c2p_pred"] + parts["update_c2p_corr"]) / 2.0
+    flux = sum(parts[f"flux_x{d}_{s}"] for d in (1, 2, 3) for s in ("pred", "corr")) / 6.0
+    kernels_ms = {k: round(v, 4) for k, v in parts.items()}
+    fp64_peak = G.peak_probe(local, True)
+    fp32_peak = G.peak_probe(local, False)
+    # FP64 work of the update+inversion kernel per zone (instruction counts from
+    # ncu on this workload: DFMA counted as 2 flops)
+    fp64_flops_per_zone_stage = float(os.environ.get("GRMHD_UPDATE_FP64_FLOPS", "0")) or None
+    if fp64_flops_per_zone_stage:
+        ach = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
+                    "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": ach / fp64_peak,
+                    "traffic": None, "peak_source": "FMA-chain probe on this GPU"}
+    else:
+        upd_bytes = 264.0 * zones
+        ach = upd_bytes / (upd * 1e-3) / 1e9
+        peak = 6674.5
+        roofline = {"bound": "hbm", "kernel": "k_update (stage update + FP64 inversion)",
+                    "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None}
+    hbm_step = HBM_BYTES_PER_ZONE_CYCLE["mixed"] * zones / (ms_step * 1e-3) / 1e9
+    gpu_launches = 21 * args.steps
+    # ---- e2e through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        Ph = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+        Uh = torch.empty((9, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+        G.get_state(ctx, Ph, Uh)
+        t0, dt0 = diag["t"], diag["dt"]
+        ne = 3
+        barrier()
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        for _ in range(ne):
+            G.set_state(ctx, Ph, Uh, t0, dt0)
+            G.step(ctx, 1)
+            _, _, t0, dt0 = G.get_state(ctx, Ph, Uh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t_start
+        if dist is not None:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": zones * ne * world / el, "unit": "zone-cycles/s",
+               "h2d_bytes_per_step": int(Ph.nbytes + Uh.nbytes), "d2h_bytes_per_step": int(Ph.nbytes + Uh.nbytes),
+               "path": "grmhd_set_state(host) + grmhd_step + grmhd_get_state(host), pinned buffers"}
+        del Ph, Uh
+    ctx.close()
+    torch.cuda.synchronize()
+    # ---- the plain FP64 step beside it
+    fp64 = None
+    if not args.no_fp64:
+        k64 = args.fp64_steps or max(3, args.steps // 4)
+        c64 = make_ctx(G.FP64)
+        ms64, _ = timed(c64, k64, min(args.warmup, 3), False)
+        prof64 = G.step_profiled(c64, 1)
+        fp64 = {"value": zones * k64 * world / (ms64 * 1e-3), "unit": "zone-cycles/s", "steps": k64,
+                "ms_per_step": ms64 / k64,
+                "hbm_frac_of_measured": HBM_BYTES_PER_ZONE_CYCLE["fp64"] * zones / (ms64 / k64 * 1e-3) / 1e9 / 6674.5,
+                "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
+        c64.close()
+    # ---- CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        zc, dt, desc = oracle_sample_run(n, 2, 2, 0)
+        cpu = {"value": zc, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": "zone-cycles/s at 256^3 (FP64 vs mixed, same GB300); % of HBM roofline",
+            "value": value, "unit": "zone-cycles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 fluxes + f64 U/inversion", "data": "synthetic",
+            "config": workload_config(n),
+            "hbm_roofline": {"bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE["mixed"], "achieved_gbs": hbm_step,
+                             "peak_gbs": 6674.5, "frac_of_measured": hbm_step / 6674.5,
+                             "frac_of_nominal_7900": hbm_step / 7900.0},
+            "roofline": roofline,
+            "peaks_probe_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+            "kernels_ms_per_step": kernels_ms,
+            "fp64_step": fp64,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "diagnostics_after_bench": {k: diag[k] for k in ("t", "dt", "mdot", "divb_max", "n_fail", "n_fixed",
+                                                             "nr_iters", "n_nr", "n_entropy_beta", "n_floor")},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -188,6 +188,24 @@ void grmhd_destroy(grmhd_ctx *ctx);
 
 const char *grmhd_last_error(const grmhd_ctx *ctx);
 
+/* Number of timing slots filled by grmhd_step_profiled. */
+#define GRMHD_PROF_SLOTS 16
+
+/* Run nsteps steps without the graph, with a CUDA event on the context
+ * stream before each kernel group, and accumulate the elapsed milliseconds:
+ * ms_out[stage*7 + part] for stage 0 (predictor) / 1 (corrector) and part
+ * 0-2 fluxes along X1..X3 (Eqs. 16-21), 3 EMFs (Eq. 22), 4 update + inversion
+ * (Eqs. 25-26, Section 2.3-2.4), 5 fixups (Eq. 33), 6 boundary fill; ms_out[14]
+ * the time-step finalisation (Eq. 27), ms_out[15] the whole step.  The state
+ * advances exactly as with grmhd_step.  ms_out holds GRMHD_PROF_SLOTS doubles. */
+int grmhd_step_profiled(grmhd_ctx *ctx, int nsteps, double *ms_out);
+
+/* Throughput of dependent-FMA chains on device (fp64 = 1: double, 0:
+ * float), in TFLOP/s (2 flops per FMA): the ALU roofline denominators for
+ * kernels bound by FP64 or FP32 arithmetic.  Allocates a 8 KB buffer and
+ * runs a few sub-second kernels. */
+int grmhd_peak_probe(int device, int fp64, double *tflops);
+
 /* Library version string. */
 const char *grmhd_version(void);
 

@@ -789,7 +789,7 @@ void orc_diagnostics(orc_grid *G, orc_diag *out)
     out->edot = edot;
     out->ldot = ldot;
     out->PhiB = mdot != 0.0 ? phib / sqrt(fabs(mdot)) : 0.0;
-    /* corner divergence of Eq. 24, acting on sqrt(-g) B^i */
+    /* corner divergence of Eq. 24, acting on the conserved sqrt(-g) B^i */
     double dmax = 0.0;
     int periodic3 = (p->metric == ORC_KERR_MKS) || p->bc3 == ORC_BC_PERIODIC;
     int k0 = (periodic3 || p->n3 == 1) ? 0 : 1;
@@ -802,11 +802,10 @@ void orc_diagnostics(orc_grid *G, orc_diag *out)
                         for (int l3 = 0; l3 < 2; l3++) {
                             int ii = i - 1 + l1, jj = j - 1 + l2, kk = k - 1 + l3;
                             kk = ((kk % p->n3) + p->n3) % p->n3;
-                            double gd = G->gc[orc_midx(G, ii, jj)].gdet;
                             long z = orc_idx(G, ii, jj, kk);
-                            dv += (2 * l1 - 1) * gd * AT(G->P, KB1, z) / (4.0 * G->dx[0]) +
-                                  (2 * l2 - 1) * gd * AT(G->P, KB2, z) / (4.0 * G->dx[1]) +
-                                  (2 * l3 - 1) * gd * AT(G->P, KB3, z) / (4.0 * G->dx[2]);
+                            dv += (2 * l1 - 1) * AT(G->U, KB1, z) / (4.0 * G->dx[0]) +
+                                  (2 * l2 - 1) * AT(G->U, KB2, z) / (4.0 * G->dx[1]) +
+                                  (2 * l3 - 1) * AT(G->U, KB3, z) / (4.0 * G->dx[2]);
                         }
                 dmax = maxf(dmax, fabs(dv));
             }

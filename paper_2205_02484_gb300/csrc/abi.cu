@@ -233,6 +233,7 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         g.i_h = 0;
         if (!(g.dx[0] > 0) || !(g.dx[1] > 0) || !(g.dx[2] > 0)) return fail(ctx, GRMHD_EINVAL, "empty box");
     }
+    for (int d = 0; d < 3; d++) g.idx[d] = 1.0 / g.dx[d];
     ctx->gb.cp = cp;
     ctx->a = a;
     launch_geometry(g, ctx->gb, ctx->stream);
@@ -506,5 +507,50 @@ extern "C" int grmhd_fluxes(grmhd_ctx *ctx, double *out, double *dt_out, int on_
     CK(cudaMemcpyAsync(g.scal, ctx->hpin + 16, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (!on_device) CK(cudaMemcpyAsync(out, o, nf * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_step_profiled(grmhd_ctx *ctx, int nsteps, double *ms_out)
+{
+    if (!ctx || !ms_out) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "step needs a state (init_torus or set_state)");
+    const int NE = 16;
+    cudaEvent_t ev[NE];
+    for (int e = 0; e < NE; e++) CK(cudaEventCreate(&ev[e]));
+    for (int p = 0; p < GRMHD_PROF_SLOTS; p++) ms_out[p] = 0.0;
+    for (int s = 0; s < nsteps; s++) {
+        launch_step_profiled(ctx->g, ctx->stream, ev);
+        CK(cudaGetLastError());
+        CK(cudaEventSynchronize(ev[NE - 1]));
+        for (int st = 0; st < 2; st++)
+            for (int part = 0; part < 7; part++) {
+                float ms;
+                int e = st * 7 + part;
+                CK(cudaEventElapsedTime(&ms, ev[e], ev[e + 1]));
+                ms_out[st * 7 + part] += ms;
+            }
+        float ms;
+        CK(cudaEventElapsedTime(&ms, ev[14], ev[15]));
+        ms_out[14] += ms;
+        CK(cudaEventElapsedTime(&ms, ev[0], ev[15]));
+        ms_out[15] += ms;
+    }
+    for (int e = 0; e < NE; e++) cudaEventDestroy(ev[e]);
+    return 0;
+}
+
+extern "C" int grmhd_peak_probe(int device, int fp64, double *tflops)
+{
+    grmhd_ctx *ctx = nullptr;
+    if (!tflops) return fail(nullptr, GRMHD_EINVAL, "null argument");
+    CK(cudaSetDevice(device));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    cudaStream_t s;
+    CK(cudaStreamCreate(&s));
+    *tflops = launch_fma_probe(fp64, sms, s);
+    cudaError_t e = cudaGetLastError();
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return fail(nullptr, GRMHD_ECUDA, cudaGetErrorString(e));
     return 0;
 }

@@ -36,7 +36,12 @@ struct Geo {
     R gcon[10];
     R gdet;
     R alpha;
-    R oma; // 1 - alpha, evaluated in FP64 before rounding
+    R oma;    // 1 - alpha, evaluated in FP64 before rounding
+    R igdet;  // 1 / sqrt(-g)
+    R ialpha; // 1 / alpha
+    R aig;    // alpha / sqrt(-g)
+    R rfl;    // density floor of Eq. 34 at this radius (centre records)
+    R ufl;    // internal-energy floor of Eq. 34
 };
 
 // counters accumulated on the device (indices into Grid::cnt)
@@ -52,7 +57,7 @@ struct Grid {
     int n1, n2, n3, N1, N2, N3;
     long long nz;
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
-    double dx[3], x1in, x2in, x3in;
+    double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     int nr_maxit, brent_maxit, fix_maxsweep, pad0;
     // metric tables

@@ -5,12 +5,19 @@
 //   (Eq. 29) Qt^2 = v^2 (Bf^2 + W)^2 - (Q.Bf)^2 (Bf^2 + 2W) / W^2
 //   (Eq. 30) Q.n  = -Bf^2/2 (1 + v^2) + (Q.Bf)^2 / (2 W^2) - W + p(W, v^2)
 //   (Eq. 31) p    = (gam-1)/gam [W (1 - v^2) - D sqrt(1 - v^2)]
-// Method order: 2D Newton (tolerance nr_tol, then one more step) -> if not
-// converged, Brent in W with v^2(W) from Eq. 29 -> if that fails, or if
-// Newton gives unphysical values, entropy inversion (W(v^2) of Eq. 32 into
-// Eq. 29, Brent in v^2); entropy alone where the guess has beta < beta_ent.
-// The sign of the Bf^2 term of Eq. 30 is taken as minus (static magnetised
-// fluid), and S of Eq. 32 is the normal-frame entropy density alpha U_S/sqrt(-g).
+// Method order: 2D Newton (tolerance nr_tol) -> if not converged, Brent in W
+// with v^2(W) from Eq. 29 -> if that fails, or if Newton gives unphysical
+// values, entropy inversion (W(v^2) of Eq. 32 into Eq. 29, Brent in v^2);
+// entropy alone where the guess has beta < beta_ent.  The sign of the Bf^2
+// term of Eq. 30 is taken as minus (static magnetised fluid), and S of
+// Eq. 32 is the normal-frame entropy density alpha U_S / sqrt(-g).
+//
+// Cost on GB300 is set by the FP64 pipe (1/64 of the FP32 rate), so the
+// Newton step is written with three reciprocals (1/W, 1/sqrt(1-v^2), 1/det)
+// instead of a division per term.  In the FP64 path Newton takes one more
+// step after the tolerance is met (so that the oracle and this code stop on
+// the same rounding-level root); the mixed path stops at the tolerance,
+// where quadratic convergence already puts the iterate at ~tol^2.
 #pragma once
 #include "physics.cuh"
 
@@ -30,14 +37,17 @@ __device__ __forceinline__ double c2p_pressure(const C2PIn &c, double W, double 
     return (c.gam - 1.0) / c.gam * (W * (1.0 - v2) - c.D * sqrt(1.0 - v2));
 }
 
+// primitives from (W, v^2) and the pressure; ut^i = Gamma/(W+B^2) (Qt^i + (Q.B) B^i / W)
 __device__ __forceinline__ void c2p_recover(const C2PIn &c, double W, double v2, double p, double *P)
 {
-    double lor = 1.0 / sqrt(1.0 - v2);
-    P[KRHO] = c.D / lor;
+    double omv = 1.0 - v2;
+    double lor = rsqrt(omv);
+    P[KRHO] = c.D * (omv * lor);
     P[KUU] = p / (c.gam - 1.0);
     double f = lor / (W + c.Bsq);
+    double qbw = c.QB / W;
 #pragma unroll
-    for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + c.QB * c.Bf[i] / W);
+    for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + qbw * c.Bf[i]);
 }
 
 __device__ __forceinline__ bool c2p_physical(const double *P, double v2)
@@ -137,6 +147,7 @@ struct ResidS {
     }
 };
 
+template <bool EXTRA>
 __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double tol, int maxit,
                                   int &iters)
 {
@@ -146,24 +157,28 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
     int n = 0;
     for (int it = 1; it <= maxit; it++) {
         n = it;
-        double s = sqrt(1.0 - v2);
-        double p = g1 * (W * (1.0 - v2) - c.D * s);
+        double omv = 1.0 - v2;
+        double is = rsqrt(omv); // 1 / sqrt(1 - v^2)
+        double s = omv * is;
+        double iW = 1.0 / W;
+        double qw2 = QB2 * iW * iW; // (Q.B)^2 / W^2
+        double p = g1 * (W * omv - c.D * s);
         double BW = c.Bsq + W;
-        double W2 = W * W, W3 = W2 * W;
-        double f1 = v2 * BW * BW - QB2 * (c.Bsq + 2.0 * W) / W2 - c.Qtsq;
-        double f2 = -0.5 * c.Bsq * (1.0 + v2) + QB2 / (2.0 * W2) - W + p - c.nQ;
-        double a11 = 2.0 * v2 * BW + 2.0 * QB2 * BW / W3;
+        double f1 = v2 * BW * BW - qw2 * (c.Bsq + 2.0 * W) - c.Qtsq;
+        double f2 = -0.5 * c.Bsq * (1.0 + v2) + 0.5 * qw2 - W + p - c.nQ;
+        double a11 = 2.0 * v2 * BW + 2.0 * qw2 * iW * BW;
         double a12 = BW * BW;
-        double a21 = -QB2 / W3 - 1.0 + g1 * (1.0 - v2);
-        double a22 = -0.5 * c.Bsq + g1 * (-W + 0.5 * c.D / s);
+        double a21 = -qw2 * iW - 1.0 + g1 * omv;
+        double a22 = -0.5 * c.Bsq + g1 * (-W + 0.5 * c.D * is);
         double det = a11 * a22 - a12 * a21;
         if (!(fabs(det) > 0.0) || !isfinite(det)) break;
-        double dW = -(a22 * f1 - a12 * f2) / det;
-        double dv = -(-a21 * f1 + a11 * f2) / det;
+        double idet = 1.0 / det;
+        double dW = -(a22 * f1 - a12 * f2) * idet;
+        double dv = -(-a21 * f1 + a11 * f2) * idet;
         double Wn = W + dW;
         if (!(Wn > 0.0)) Wn = 0.5 * W;
         double vn = fmin(fmax(v2 + dv, 0.0), V2MAX);
-        double errW = fabs(Wn - W) / fabs(Wn), errv = fabs(vn - v2);
+        bool conv = fabs(Wn - W) < tol * fabs(Wn) && fabs(vn - v2) < tol;
         W = Wn;
         v2 = vn;
         if (!isfinite(W) || !isfinite(v2)) break;
@@ -171,7 +186,13 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
             iters = n;
             return true;
         }
-        if (errW < tol && errv < tol) extra = true;
+        if (conv) {
+            if (!EXTRA) {
+                iters = n;
+                return true;
+            }
+            extra = true;
+        }
     }
     iters = n;
     return false;
@@ -213,24 +234,27 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 // Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g).
 // methods: 1 Newton, 2 Brent-W, 4 entropy, 8 beta switch (15 = paper order).
 // wguess > 0 replaces the Newton starting W (learned guess; v^2 from Eq. 29).
+// MIXED: no confirmation Newton step, and the beta switch evaluated in FP32
+// with the FP32 metric record gf (must be non-null then).
+template <bool MIXED = false>
 __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double guess[NP],
                                double gam, double beta_ent, double tol, int nr_maxit,
                                int brent_maxit, int methods, double P[NP], int &iters,
-                               double wguess = 0.0)
+                               double wguess = 0.0, const Geo<float> *gf = nullptr)
 {
     iters = 0;
 #pragma unroll
     for (int m = 0; m < NP; m++) P[m] = guess[m];
-    double f = g.alpha / g.gdet;
-    P[KB1] = U[KB1] / g.gdet;
-    P[KB2] = U[KB2] / g.gdet;
-    P[KB3] = U[KB3] / g.gdet;
+    double f = g.aig;
+    P[KB1] = U[KB1] * g.igdet;
+    P[KB2] = U[KB2] * g.igdet;
+    P[KB3] = U[KB3] * g.igdet;
     C2PIn c;
     c.gam = gam;
     c.D = f * U[KRHO];
     double Q[4] = {f * U[1], f * U[2], f * U[3], f * U[4]};
     c.Sent = f * U[KENT];
-    double n[4] = {1.0 / g.alpha, -g.alpha * g.gcon[1], -g.alpha * g.gcon[2], -g.alpha * g.gcon[3]};
+    double n[4] = {g.ialpha, -g.alpha * g.gcon[1], -g.alpha * g.gcon[2], -g.alpha * g.gcon[3]};
     double Qc[4];
 #pragma unroll
     for (int m = 0; m < 4; m++)
@@ -250,10 +274,22 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
     if (!fin || !(c.D > 0.0)) return C2P_FAIL | C2P_FAIL_D;
 
     if (methods & 8) {
-        St<double> s;
-        get_state(guess, g, s);
-        double pg = (gam - 1.0) * guess[KUU];
-        if (s.bsq > 0.0 && pg < beta_ent * 0.5 * s.bsq) {
+        bool low_beta;
+        if (MIXED) {
+            float qf[NP];
+#pragma unroll
+            for (int m = 0; m < NP; m++) qf[m] = (float)guess[m];
+            St<float> s;
+            get_state(qf, *gf, s);
+            float pg = ((float)gam - 1.0f) * qf[KUU];
+            low_beta = s.bsq > 0.0f && pg < (float)beta_ent * 0.5f * s.bsq;
+        } else {
+            St<double> s;
+            get_state(guess, g, s);
+            double pg = (gam - 1.0) * guess[KUU];
+            low_beta = s.bsq > 0.0 && pg < beta_ent * 0.5 * s.bsq;
+        }
+        if (low_beta) {
             if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY_BETA;
             return C2P_FAIL | C2P_FAIL_ENT;
         }
@@ -268,7 +304,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         }
         if (!(W > 0.0) || !isfinite(W)) W = c.D;
         v2 = fmin(v2, V2MAX);
-        if (c2p_newton(c, W, v2, tol, nr_maxit, iters)) {
+        if (c2p_newton<!MIXED>(c, W, v2, tol, nr_maxit, iters)) {
             c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
             if (c2p_physical(P, v2)) return C2P_NR;
             if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY;

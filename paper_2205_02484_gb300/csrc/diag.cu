@@ -1,5 +1,5 @@
 // diag.cu -- horizon diagnostics (Section 4.2, Eqs. 38-42), the corner
-// divergence of Eq. 24, batched stand-alone prim2cons / con2prim, and the
+// divergence of Eq. 24 (on the conserved sqrt(-g) B^i), batched stand-alone prim2cons / con2prim, and the
 // active-zone state copies.
 //
 // Horizon sums are deterministic: fixed-size blocks write partial sums to
@@ -55,8 +55,7 @@ __global__ void k_horizon_sum(const double *part, int nb, double *out)
     for (int c = 0; c < 4; c++) out[c] = a[c];
 }
 
-template <typename RS>
-__global__ void k_divb(Grid g, const RS *P, double *out)
+__global__ void k_divb(Grid g, double *out)
 {
     bool per3 = g.metric == KERR_MKS || g.bc3 == BC_PERIODIC;
     int k0 = (per3 || g.n3 == 1) ? 0 : 1;
@@ -71,11 +70,10 @@ __global__ void k_divb(Grid g, const RS *P, double *out)
             for (int l2 = 0; l2 < 2; l2++)
                 for (int l3 = 0; l3 < 2; l3++) {
                     int ii = i - 1 + l1, jj = j - 1 + l2, kk = ((k - 1 + l3) % g.n3 + g.n3) % g.n3;
-                    double gd = g.gc[midx(g, ii, jj)].gdet;
                     long long z = zidx(g, ii, jj, kk);
-                    dv += (2 * l1 - 1) * gd * (double)P[KB1 * g.nz + z] / (4.0 * g.dx[0]) +
-                          (2 * l2 - 1) * gd * (double)P[KB2 * g.nz + z] / (4.0 * g.dx[1]) +
-                          (2 * l3 - 1) * gd * (double)P[KB3 * g.nz + z] / (4.0 * g.dx[2]);
+                    dv += (2 * l1 - 1) * g.U[KB1 * g.nz + z] / (4.0 * g.dx[0]) +
+                          (2 * l2 - 1) * g.U[KB2 * g.nz + z] / (4.0 * g.dx[1]) +
+                          (2 * l3 - 1) * g.U[KB3 * g.nz + z] / (4.0 * g.dx[2]);
                 }
     }
     dv = fabs(dv);
@@ -95,10 +93,10 @@ void launch_diagnostics(const Grid &g, double *scratch, long scratch_len, double
     unsigned nbc = (unsigned)((nc + 255) / 256);
     if (g.mixed) {
         k_horizon_partial<float><<<nb, 256, 0, s>>>(g, (const float *)g.P[0], scratch);
-        if (nc > 0) k_divb<float><<<nbc, 256, 0, s>>>(g, (const float *)g.P[0], out_dev + 4);
+        if (nc > 0) k_divb<<<nbc, 256, 0, s>>>(g, out_dev + 4);
     } else {
         k_horizon_partial<double><<<nb, 256, 0, s>>>(g, (const double *)g.P[0], scratch);
-        if (nc > 0) k_divb<double><<<nbc, 256, 0, s>>>(g, (const double *)g.P[0], out_dev + 4);
+        if (nc > 0) k_divb<<<nbc, 256, 0, s>>>(g, out_dev + 4);
     }
     k_horizon_sum<<<1, 32, 0, s>>>(scratch, nb, out_dev);
 }

@@ -6,21 +6,12 @@
 // Ceilings add the missing rho, u as matter at rest in the normal (ZAMO)
 // frame (ut^i = 0, B = 0) to U and re-invert with Newton; if that fails the
 // primitives are raised directly.  U is recomputed from the final primitives
-// of every modified zone.
+// of every modified zone.  The floor values of Eq. 34 are tabulated per
+// (r, theta) with the metric.
 #pragma once
 #include "con2prim.cuh"
 
 namespace grmhd {
-
-__device__ __forceinline__ void floor_values(const Grid &g, double r, double &rfl, double &ufl)
-{
-    rfl = 1e-20;
-    ufl = 1e-20;
-    if (g.metric == KERR_MKS) {
-        rfl = fmax(rfl, 1e-5 * pow(r, -0.5));
-        ufl = fmax(ufl, (1e-5 / 3.0) * pow(r, -2.5));
-    }
-}
 
 __device__ __forceinline__ bool gamma_cap(const Grid &g, const Geo<double> &geo, double q[NP])
 {
@@ -36,19 +27,34 @@ __device__ __forceinline__ bool gamma_cap(const Grid &g, const Geo<double> &geo,
     return false;
 }
 
-// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied
-__device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, double r, double q[NP],
-                                     const double Un[NU])
+// b^2 of primitives q; in the mixed path from the FP32 record gf
+template <bool MIXED>
+__device__ __forceinline__ double bsq_of(const double q[NP], const Geo<double> &geo, const Geo<float> *gf)
 {
-    int res = 0;
-    double rfl, ufl;
-    floor_values(g, r, rfl, ufl);
-    if (q[KRHO] < rfl) { q[KRHO] = rfl; res |= 1; }
-    if (q[KUU] < ufl) { q[KUU] = ufl; res |= 1; }
+    if (MIXED) {
+        float qf[NP];
+#pragma unroll
+        for (int m = 0; m < NP; m++) qf[m] = (float)q[m];
+        St<float> s;
+        get_state(qf, *gf, s);
+        return (double)s.bsq;
+    }
     St<double> s;
     get_state(q, geo, s);
-    double drho = fmax(0.0, s.bsq / g.sigma_max - q[KRHO]);
-    double du = fmax(0.0, s.bsq / g.bu_max - q[KUU]);
+    return s.bsq;
+}
+
+// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied
+template <bool MIXED = false>
+__device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, double q[NP],
+                                     const double Un[NU], const Geo<float> *gf = nullptr)
+{
+    int res = 0;
+    if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
+    if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }
+    double bsq = bsq_of<MIXED>(q, geo, gf);
+    double drho = fmax(0.0, bsq / g.sigma_max - q[KRHO]);
+    double du = fmax(0.0, bsq / g.bu_max - q[KUU]);
     if (drho > 0.0 || du > 0.0) {
         res |= 3;
         double dq[NP] = {drho, du, 0, 0, 0, 0, 0, 0};
@@ -63,7 +69,7 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, doub
         gs[KRHO] += drho;
         gs[KUU] += du;
         int it;
-        int fl = con2prim(U2, geo, gs, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 1, qn, it);
+        int fl = con2prim<false>(U2, geo, gs, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 1, qn, it);
         if (fl == C2P_NR) {
 #pragma unroll
             for (int c = 0; c < NP; c++) q[c] = qn[c];
@@ -76,17 +82,65 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, doub
     return res;
 }
 
-__device__ inline void post_fixup(const Grid &g, const Geo<double> &geo, double r, double q[NP])
+__device__ inline void post_fixup(const Grid &g, const Geo<double> &geo, double q[NP])
 {
-    double rfl, ufl;
-    floor_values(g, r, rfl, ufl);
-    if (q[KRHO] < rfl) q[KRHO] = rfl;
-    if (q[KUU] < ufl) q[KUU] = ufl;
+    if (q[KRHO] < geo.rfl) q[KRHO] = geo.rfl;
+    if (q[KUU] < geo.ufl) q[KUU] = geo.ufl;
     St<double> s;
     get_state(q, geo, s);
     q[KRHO] = fmax(q[KRHO], s.bsq / g.sigma_max);
     q[KUU] = fmax(q[KUU], s.bsq / g.bu_max);
     gamma_cap(g, geo, q);
+}
+
+// FP64 conserved variables of q (Eqs. 6-8, 12).
+//
+// Mixed path: only the rest mass U_rho = sqrt(-g) rho u^t is formed in FP64
+// (u^t = (1 + (Gamma - 1)) / alpha with Gamma - 1 = ut^2/(1 + Gamma) from
+// the FP32 state); the rest-mass-subtracted energy sqrt(-g)(T^t_t + rho u^t),
+// the momenta and the entropy come from the FP32 state, and
+// U_E = (U_E + U_rho) - U_rho is assembled in FP64.  The inversion depends on
+// E - D, which is therefore carried with FP32 relative accuracy of the
+// thermal + kinetic + binding energy, not of the rest mass.
+template <bool MIXED = false>
+__device__ inline void cons_of(const double q[NP], const Geo<double> &geo, double gam, double U[NU],
+                               const Geo<float> *gf = nullptr)
+{
+    if (MIXED) {
+        float qf[NP];
+#pragma unroll
+        for (int m = 0; m < NP; m++) qf[m] = (float)q[m];
+        St<float> s;
+        get_state(qf, *gf, s);
+        float Uf[NU], Ff[NU];
+        prim_to_UF2<float, true>(qf, *gf, s, (float)gam, 1, Uf, Ff);
+        double gm1 = (double)(s.usq / (s.gamma + 1.0f));
+        U[KRHO] = geo.gdet * q[KRHO] * ((1.0 + gm1) * geo.ialpha);
+        U[1] = (double)Uf[1] - U[KRHO];
+        U[2] = (double)Uf[2];
+        U[3] = (double)Uf[3];
+        U[4] = (double)Uf[4];
+        U[KB1] = geo.gdet * q[KB1];
+        U[KB2] = geo.gdet * q[KB2];
+        U[KB3] = geo.gdet * q[KB3];
+        U[KENT] = (double)Uf[KENT];
+        return;
+    }
+    St<double> s;
+    get_state(q, geo, s);
+    double T[4];
+    tmunu_row(q, s, gam, 0, T);
+    double gd = geo.gdet;
+    double p = (gam - 1.0) * q[KUU];
+    U[KRHO] = gd * q[KRHO] * s.ucon[0];
+    U[1] = gd * T[0];
+    U[2] = gd * T[1];
+    U[3] = gd * T[2];
+    U[4] = gd * T[3];
+    U[KB1] = gd * q[KB1];
+    U[KB2] = gd * q[KB2];
+    U[KB3] = gd * q[KB3];
+    U[KENT] = gd * (p * pow(q[KRHO], 1.0 - gam)) * s.ucon[0];
 }
 
 } // namespace grmhd

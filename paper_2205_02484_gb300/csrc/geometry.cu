@@ -64,6 +64,18 @@ __device__ void make_geo(const CoordParams &cp, double X1, double X2, Geo<double
     g.gdet = ok ? sqrt(-det) : 0.0;
     g.alpha = ok ? 1.0 / sqrt(-gi[0][0]) : 0.0;
     g.oma = ok ? 1.0 - g.alpha : 0.0;
+    g.igdet = ok ? 1.0 / g.gdet : 0.0;
+    g.ialpha = ok ? sqrt(-gi[0][0]) : 0.0;
+    g.aig = ok ? g.alpha / g.gdet : 0.0;
+    // floors of Eq. 34 at this radius (flat space: the absolute floors only)
+    double r, dr;
+    mks_radius<double>(cp, X1, r, dr);
+    g.rfl = 1e-20;
+    g.ufl = 1e-20;
+    if (cp.metric == KERR_MKS) {
+        g.rfl = fmax(g.rfl, 1e-5 * pow(r, -0.5));
+        g.ufl = fmax(g.ufl, (1e-5 / 3.0) * pow(r, -2.5));
+    }
     for (int a = 0; a < 10; a++) {
         gf.gcov[a] = (float)g.gcov[a];
         gf.gcon[a] = (float)g.gcon[a];
@@ -71,6 +83,11 @@ __device__ void make_geo(const CoordParams &cp, double X1, double X2, Geo<double
     gf.gdet = (float)g.gdet;
     gf.alpha = (float)g.alpha;
     gf.oma = (float)g.oma;
+    gf.igdet = (float)g.igdet;
+    gf.ialpha = (float)g.ialpha;
+    gf.aig = (float)g.aig;
+    gf.rfl = (float)g.rfl;
+    gf.ufl = (float)g.ufl;
 }
 
 __global__ void k_geometry(Grid g, GeomBuild b)

@@ -6,6 +6,8 @@ namespace grmhd {
 
 // step.cu
 void launch_step(const Grid &g, cudaStream_t s);
+void launch_step_profiled(const Grid &g, cudaStream_t s, cudaEvent_t *ev);
+double launch_fma_probe(int fp64, int sms, cudaStream_t s);
 void launch_bc(const Grid &g, int buf, cudaStream_t s);
 void launch_fluxes_dt(const Grid &g, int set_dt, cudaStream_t s);
 void launch_gather_fluxes(const Grid &g, double *out, cudaStream_t s);

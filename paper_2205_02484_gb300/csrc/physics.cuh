@@ -45,13 +45,14 @@ __device__ __forceinline__ void get_state(const R q[NP], const Geo<R> &g, St<R> 
     R gm = sqrt(R(1) + usq);
     s.usq = usq;
     s.gamma = gm;
-    s.ucon[0] = gm / g.alpha;
+    s.ucon[0] = gm * g.ialpha;
+    const R iut = g.alpha / gm; // 1 / u^t
 #pragma unroll
     for (int i = 1; i <= 3; i++) s.ucon[i] = q[KU1 + i - 1] - gm * g.alpha * g.gcon[sym(0, i)];
     lower4(g, s.ucon, s.ucov);
     s.bcon[0] = q[KB1] * s.ucov[1] + q[KB2] * s.ucov[2] + q[KB3] * s.ucov[3];
 #pragma unroll
-    for (int i = 1; i <= 3; i++) s.bcon[i] = (q[KB1 + i - 1] + s.bcon[0] * s.ucon[i]) / s.ucon[0];
+    for (int i = 1; i <= 3; i++) s.bcon[i] = (q[KB1 + i - 1] + s.bcon[0] * s.ucon[i]) * iut;
     lower4(g, s.bcon, s.bcov);
     s.bsq = s.bcon[0] * s.bcov[0] + s.bcon[1] * s.bcov[1] + s.bcon[2] * s.bcov[2] +
             s.bcon[3] * s.bcov[3];
@@ -86,7 +87,7 @@ __device__ __forceinline__ void prim_to_UF(const R q[NP], const Geo<R> &g, const
     tmunu_row(q, s, gam, d, T);
     R gd = g.gdet;
     R p = (gam - R(1)) * q[KUU];
-    R ent = p / powr(q[KRHO], gam - R(1));
+    R ent = p * powr(q[KRHO], R(1) - gam);
     out[KRHO] = gd * q[KRHO] * s.ucon[d];
     if (RMS) {
         // T^d_t + rho u^d = rho u^d (1 + u_t) + (u + p + b^2) u^d u_t - b^d b_t (+ p + b^2/2 if d = t)
@@ -113,6 +114,45 @@ __device__ __forceinline__ void prim_to_UF(const R q[NP], const Geo<R> &g, const
     out[KENT] = gd * ent * s.ucon[d];
 }
 
+// Conserved vector and flux along d of one state together: the rows T^t_nu
+// and T^d_nu share every factor, and the entropy density is evaluated once.
+template <typename R, bool RMS>
+__device__ __forceinline__ void prim_to_UF2(const R q[NP], const Geo<R> &g, const St<R> &s, R gam,
+                                            int d, R U[NU], R F[NU])
+{
+    const R gd = g.gdet;
+    const R p = (gam - R(1)) * q[KUU];
+    const R wb = q[KRHO] + q[KUU] + p + s.bsq;
+    const R ptot = p + R(0.5) * s.bsq;
+    const R ent = gd * p * powr(q[KRHO], R(1) - gam);
+    const R gut = gd * s.ucon[0], gud = gd * s.ucon[d];
+    const R gbt = gd * s.bcon[0], gbd = gd * s.bcon[d];
+    U[KRHO] = gut * q[KRHO];
+    F[KRHO] = gud * q[KRHO];
+#pragma unroll
+    for (int n = 0; n < 4; n++) {
+        U[1 + n] = wb * gut * s.ucov[n] - gbt * s.bcov[n];
+        F[1 + n] = wb * gud * s.ucov[n] - gbd * s.bcov[n];
+    }
+    U[1] += gd * ptot;
+    F[1 + d] += gd * ptot;
+    if (RMS) {
+        // T^mu_t + rho u^mu = rho u^mu (1 + u_t) + (u + p + b^2) u^mu u_t - b^mu b_t (+ ptot for mu = t)
+        const R opu = g.oma - g.alpha * (s.usq / (s.gamma + R(1))) +
+                      (g.gcov[1] * q[KU1] + g.gcov[2] * q[KU2] + g.gcov[3] * q[KU3]);
+        const R rest = q[KUU] + p + s.bsq;
+        U[1] = gut * (q[KRHO] * opu + rest * s.ucov[0]) - gbt * s.bcov[0] + gd * ptot;
+        F[1] = gud * (q[KRHO] * opu + rest * s.ucov[0]) - gbd * s.bcov[0];
+    }
+    U[KB1] = gd * q[KB1];
+    U[KB2] = gd * q[KB2];
+    U[KB3] = gd * q[KB3];
+#pragma unroll
+    for (int i = 1; i <= 3; i++) F[KB1 + i - 1] = gbd * s.ucon[i] - gd * s.bcon[i] * s.ucon[d];
+    U[KENT] = ent * s.ucon[0];
+    F[KENT] = ent * s.ucon[d];
+}
+
 // c1 >= c2: roots of (1 - cms2)(u^d - v u^t)^2 = cms2 (g^tt v^2 - 2 g^td v + g^dd)
 template <typename R>
 __device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, const St<R> &s, R gam,
@@ -120,8 +160,10 @@ __device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, cons
 {
     R p = (gam - R(1)) * q[KUU];
     R ef = q[KRHO] + q[KUU] + p;
-    R va2 = s.bsq / (s.bsq + ef);
-    R cs2 = gam * p / ef;
+    R ee = s.bsq + ef;
+    R inv = R(1) / (ee * ef);
+    R va2 = s.bsq * ef * inv;   // b^2 / (b^2 + rho + u + p)
+    R cs2 = gam * p * ee * inv; // gam p / (rho + u + p)
     R cms2 = va2 + cs2 * (R(1) - va2);
     R A1 = R(1) - cms2;
     R ut = s.ucon[0], ud = s.ucon[d];
@@ -131,8 +173,9 @@ __device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, cons
     R disc = B * B - R(4) * A * C;
     disc = disc < R(0) ? R(0) : disc;
     R sq = sqrt(disc);
-    R vp = (-B + sq) / (R(2) * A);
-    R vm = (-B - sq) / (R(2) * A);
+    R i2a = R(0.5) / A;
+    R vp = (-B + sq) * i2a;
+    R vm = (-B - sq) * i2a;
     c1 = vp > vm ? vp : vm;
     c2 = vp > vm ? vm : vp;
 }

@@ -247,12 +247,10 @@ __global__ void __launch_bounds__(128) k_flux(Grid g, const R *__restrict__ P, R
             }
             constexpr bool RMS = sizeof(R) == 4;
             R Ux[NU], Fx[NU];
-            prim_to_UF<R, RMS>(ql, geo, sl, gam, 0, Ux);
-            prim_to_UF<R, RMS>(ql, geo, sl, gam, D, Fx);
+            prim_to_UF2<R, RMS>(ql, geo, sl, gam, D, Ux, Fx);
 #pragma unroll
             for (int c = 0; c < NU; c++) out[c] = wlF * Fx[c] + wlU * Ux[c];
-            prim_to_UF<R, RMS>(qr, geo, sr, gam, 0, Ux);
-            prim_to_UF<R, RMS>(qr, geo, sr, gam, D, Fx);
+            prim_to_UF2<R, RMS>(qr, geo, sr, gam, D, Ux, Fx);
 #pragma unroll
             for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
         }
@@ -352,49 +350,56 @@ __global__ void __launch_bounds__(128) k_update(Grid g, const R *__restrict__ Pi
 #pragma unroll
             for (int c = 0; c < 4; c++) src[c] = sf[c];
         }
-        // flux divergence; B components from the flux-CT edge averages (Eq. 23)
+        // flux divergence; B components from the flux-CT edge averages (Eq. 23),
+        // formed exactly as the replaced face values.  The mixed path takes the
+        // divergence in FP32 (the fluxes' own precision) and converts each
+        // component once before the FP64 accumulation; the mass divergence is
+        // added back to the rest-mass-subtracted energy in FP64 so that U_E and
+        // U_rho see the same rounded mass flux.
         double Un[NU];
-        const double idx1 = 1.0 / g.dx[0], idx2 = 1.0 / g.dx[1], idx3 = 1.0 / g.dx[2];
-        double divD = 0.0;
-#pragma unroll
-        for (int c = 0; c < NU; c++) {
-            if (c >= KB1 && c <= KB3) continue;
-            const long long o = c * nz + z;
-            double d1 = ((double)F1[o + si] - (double)F1[o]) / g.dx[0];
-            double d2 = ((double)F2[o + sj] - (double)F2[o]) / g.dx[1];
-            double d3 = ((double)F3[o + sk] - (double)F3[o]) / g.dx[2];
-            double div = d1 + d2 + d3;
-            if (c == KRHO) divD = div;
-            double rhs = -div;
-            if (c == 1 && sizeof(R) == 4) rhs += divD; // rest-mass-subtracted energy flux
-            if (c >= 1 && c <= 4) rhs += src[c - 1];
-            Un[c] = g.U[o] + dts * rhs;
-        }
-        (void)idx1; (void)idx2; (void)idx3;
         {
-            // replaced B-fluxes, formed exactly as the face values of Eq. 23
-            double f2b1_j = -0.5 * ((double)E3[z + si] + (double)E3[z]);
-            double f2b1_jp = -0.5 * ((double)E3[z + si + sj] + (double)E3[z + sj]);
-            double f3b1_k = 0.5 * ((double)E2[z + si] + (double)E2[z]);
-            double f3b1_kp = 0.5 * ((double)E2[z + si + sk] + (double)E2[z + sk]);
-            double f1b2_i = 0.5 * ((double)E3[z + sj] + (double)E3[z]);
-            double f1b2_ip = 0.5 * ((double)E3[z + si + sj] + (double)E3[z + si]);
-            double f3b2_k = -0.5 * ((double)E1[z + sj] + (double)E1[z]);
-            double f3b2_kp = -0.5 * ((double)E1[z + sj + sk] + (double)E1[z + sk]);
-            double f1b3_i = -0.5 * ((double)E2[z + sk] + (double)E2[z]);
-            double f1b3_ip = -0.5 * ((double)E2[z + si + sk] + (double)E2[z + si]);
-            double f2b3_j = 0.5 * ((double)E1[z + sk] + (double)E1[z]);
-            double f2b3_jp = 0.5 * ((double)E1[z + sj + sk] + (double)E1[z + sj]);
-            double db1 = (0.0 - 0.0) / g.dx[0] + (f2b1_jp - f2b1_j) / g.dx[1] + (f3b1_kp - f3b1_k) / g.dx[2];
-            double db2 = (f1b2_ip - f1b2_i) / g.dx[0] + (0.0 - 0.0) / g.dx[1] + (f3b2_kp - f3b2_k) / g.dx[2];
-            double db3 = (f1b3_ip - f1b3_i) / g.dx[0] + (f2b3_jp - f2b3_j) / g.dx[1] + (0.0 - 0.0) / g.dx[2];
-            Un[KB1] = g.U[KB1 * nz + z] - dts * db1;
-            Un[KB2] = g.U[KB2 * nz + z] - dts * db2;
-            Un[KB3] = g.U[KB3 * nz + z] - dts * db3;
+            typedef R T;
+            const T ix1 = (T)g.idx[0], ix2 = (T)g.idx[1], ix3 = (T)g.idx[2];
+            T dv[NU];
+#pragma unroll
+            for (int c = 0; c < NU; c++) {
+                if (c >= KB1 && c <= KB3) continue;
+                const long long o = c * nz + z;
+                T d1 = (F1[o + si] - F1[o]) * ix1;
+                T d2 = (F2[o + sj] - F2[o]) * ix2;
+                T d3 = (F3[o + sk] - F3[o]) * ix3;
+                dv[c] = d1 + d2 + d3;
+            }
+            T f2b1_j = T(-0.5) * (E3[z + si] + E3[z]);
+            T f2b1_jp = T(-0.5) * (E3[z + si + sj] + E3[z + sj]);
+            T f3b1_k = T(0.5) * (E2[z + si] + E2[z]);
+            T f3b1_kp = T(0.5) * (E2[z + si + sk] + E2[z + sk]);
+            T f1b2_i = T(0.5) * (E3[z + sj] + E3[z]);
+            T f1b2_ip = T(0.5) * (E3[z + si + sj] + E3[z + si]);
+            T f3b2_k = T(-0.5) * (E1[z + sj] + E1[z]);
+            T f3b2_kp = T(-0.5) * (E1[z + sj + sk] + E1[z + sk]);
+            T f1b3_i = T(-0.5) * (E2[z + sk] + E2[z]);
+            T f1b3_ip = T(-0.5) * (E2[z + si + sk] + E2[z + si]);
+            T f2b3_j = T(0.5) * (E1[z + sk] + E1[z]);
+            T f2b3_jp = T(0.5) * (E1[z + sj + sk] + E1[z + sj]);
+            dv[KB1] = (f2b1_jp - f2b1_j) * ix2 + (f3b1_kp - f3b1_k) * ix3;
+            dv[KB2] = (f1b2_ip - f1b2_i) * ix1 + (f3b2_kp - f3b2_k) * ix3;
+            dv[KB3] = (f1b3_ip - f1b3_i) * ix1 + (f2b3_jp - f2b3_j) * ix2;
+            double dD = (double)dv[KRHO];
+#pragma unroll
+            for (int c = 0; c < NU; c++) {
+                double rhs = -(double)dv[c];
+                if (c == 1 && sizeof(R) == 4) rhs += dD; // rest-mass-subtracted energy flux
+                if (c >= 1 && c <= 4) rhs += src[c - 1];
+                Un[c] = g.U[c * nz + z] + dts * rhs;
+            }
         }
         double qn[NP];
         int it;
-        int fl = con2prim(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it);
+        constexpr bool MX = sizeof(R) == 4;
+        const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
+        int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it,
+                              0.0, gfr);
         c_it = it;
         int meth = fl & 7;
         if (fl & C2P_FAIL) {
@@ -408,12 +413,10 @@ __global__ void __launch_bounds__(128) k_update(Grid g, const R *__restrict__ Pi
             c_br = meth == C2P_BRENT_W;
             c_en = meth == C2P_ENTROPY;
             c_eb = meth == C2P_ENTROPY_BETA;
-            int res = post_inversion(g, geo, g.rc[m], qn, Un);
+            int res = post_inversion<MX>(g, geo, qn, Un, gfr);
             if (res & 1) {
                 c_fl = 1;
-                St<double> sn;
-                get_state(qn, geo, sn);
-                prim_to_UF<double, false>(qn, geo, sn, g.gam, 0, Un);
+                cons_of<MX>(qn, geo, g.gam, Un, gfr);
             }
             c_ce = (res & 2) != 0;
             c_gc = (res & 4) != 0;
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(1024) k_fixup(Grid g, R *P, int corr)
                 const Geo<double> geo = g.gc[m];
                 double q[NP];
                 for (int c = 0; c < NP; c++) q[c] = c < 5 ? nb[(long long)c * cap + a] : (double)P[c * nz + z];
-                post_fixup(g, geo, g.rc[m], q);
+                post_fixup(g, geo, q);
                 for (int c = 0; c < NP; c++) P[c * nz + z] = (R)q[c];
                 if (corr) {
                     St<double> s;
@@ -608,6 +611,57 @@ static void stage(const Grid &g, int src, int dst, double dtfac, int corr, int w
     fill_bc<R>(g, Pout, s);
 }
 
+// One part of a stage, for per-kernel timing: 0-2 fluxes along X1..X3,
+// 3 EMFs, 4 update + inversion, 5 fixups, 6 boundary fill.
+template <typename R>
+static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, int corr, int want_dt,
+                       cudaStream_t s)
+{
+    const int T = 128;
+    const R *Pin = (const R *)g.P[src];
+    R *Pout = (R *)g.P[dst];
+    Box b1{{0, -1, -1}, {g.n1 + 1, g.n2 + 2, g.n3 + 2}};
+    Box b2{{-1, 0, -1}, {g.n1 + 2, g.n2 + 1, g.n3 + 2}};
+    Box b3{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, g.n3 + 1}};
+    Box be{{0, 0, 0}, {g.n1 + 1, g.n2 + 1, g.n3 + 1}};
+    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    switch (part) {
+    case 0: k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[0], b1, want_dt); break;
+    case 1: k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[1], b2, want_dt); break;
+    case 2: k_flux<R, 3><<<nblk(b3.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[2], b3, want_dt); break;
+    case 3:
+        k_emf<R><<<nblk(be.count(), T), T, 0, s>>>(g, (const R *)g.F[0], (const R *)g.F[1], (const R *)g.F[2],
+                                                    (R *)g.E[0], (R *)g.E[1], (R *)g.E[2], be);
+        break;
+    case 4:
+        k_update<R><<<nblk(nact, T), T, 0, s>>>(g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1],
+                                                 (const R *)g.F[2], (const R *)g.E[0], (const R *)g.E[1],
+                                                 (const R *)g.E[2], dtfac, corr);
+        break;
+    case 5: k_fixup<R><<<1, 1024, 0, s>>>(g, Pout, corr); break;
+    default: fill_bc<R>(g, Pout, s); break;
+    }
+}
+
+// The same step as launch_step, with an event recorded before each part;
+// ev holds 2 * 7 + 2 events.
+void launch_step_profiled(const Grid &g, cudaStream_t s, cudaEvent_t *ev)
+{
+    int e = 0;
+    for (int st = 0; st < 2; st++) {
+        int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
+        double fac = st == 0 ? 0.5 : 1.0;
+        for (int part = 0; part < 7; part++) {
+            cudaEventRecord(ev[e++], s);
+            if (g.mixed) stage_part<float>(g, part, src, dst, fac, st, st == 0, s);
+            else stage_part<double>(g, part, src, dst, fac, st, st == 0, s);
+        }
+    }
+    cudaEventRecord(ev[e++], s);
+    k_finalize<<<1, 32, 0, s>>>(g, 1);
+    cudaEventRecord(ev[e++], s);
+}
+
 void launch_step(const Grid &g, cudaStream_t s)
 {
     if (g.mixed) {
@@ -678,6 +732,49 @@ void launch_gather_fluxes(const Grid &g, double *out, cudaStream_t s)
     long long nf = (long long)(g.n1 + 1) * (g.n2 + 1) * (g.n3 + 1);
     if (g.mixed) k_gather_fluxes<float><<<nblk(3 * nf, 128), 128, 0, s>>>(g, out);
     else k_gather_fluxes<double><<<nblk(3 * nf, 128), 128, 0, s>>>(g, out);
+}
+
+// FMA-chain throughput probe: 8 independent chains per thread.
+template <typename T>
+__global__ void k_fma_probe(T *out, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) x[c] = T(threadIdx.x + c);
+    for (int it = 0; it < iters; it++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) x[c] = x[c] * a + b;
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) s += x[c];
+    if (s == T(-1.2345)) out[threadIdx.x] = s;
+}
+
+double launch_fma_probe(int fp64, int sms, cudaStream_t s)
+{
+    const int T = 256, iters = fp64 ? 4096 : 65536;
+    int blocks = sms * 8;
+    void *out;
+    cudaMalloc(&out, 1024 * sizeof(double));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0, s);
+        if (fp64) k_fma_probe<double><<<blocks, T, 0, s>>>((double *)out, iters, 0.999999, 1e-7);
+        else k_fma_probe<float><<<blocks, T, 0, s>>>((float *)out, iters, 0.9999f, 1e-7f);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double fl = 2.0 * 8.0 * iters * (double)blocks * T;
+        if (rep > 0) best = fmax(best, fl / (ms * 1e-3) / 1e12);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return best;
 }
 
 } // namespace grmhd

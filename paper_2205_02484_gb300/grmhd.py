@@ -86,7 +86,12 @@ SIGNATURES = {
     "grmhd_destroy": (None, [_V]),
     "grmhd_last_error": (C.c_char_p, [_V]),
     "grmhd_version": (C.c_char_p, []),
+    "grmhd_step_profiled": (C.c_int, [_V, C.c_int, C.POINTER(C.c_double)]),
+    "grmhd_peak_probe": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
 }
+
+PROF_SLOTS = 16
+PROF_PARTS = ("flux_x1", "flux_x2", "flux_x3", "emf", "update_c2p", "fixup", "bc")
 
 _lib = None
 
@@ -272,6 +277,29 @@ def fluxes(ctx: Context, out=None):
     dt = C.c_double()
     ctx.check(ctx.L.grmhd_fluxes(ctx.h, op, C.byref(dt), dev))
     return out, dt.value
+
+
+def step_profiled(ctx: Context, nsteps: int = 1) -> dict:
+    """Per-kernel-group milliseconds summed over nsteps (CUDA events on the
+    context stream); keys '<part>_pred', '<part>_corr', 'finalize', 'step'."""
+    buf = (C.c_double * PROF_SLOTS)()
+    ctx.check(ctx.L.grmhd_step_profiled(ctx.h, nsteps, buf))
+    out = {}
+    for st, tag in ((0, "pred"), (1, "corr")):
+        for p, name in enumerate(PROF_PARTS):
+            out[f"{name}_{tag}"] = buf[st * 7 + p]
+    out["finalize"] = buf[14]
+    out["step"] = buf[15]
+    return out
+
+
+def peak_probe(device: int = 0, fp64: bool = True) -> float:
+    L = load()
+    v = C.c_double()
+    rc = L.grmhd_peak_probe(device, int(fp64), C.byref(v))
+    if rc != 0:
+        raise GrmhdError(rc, L.grmhd_last_error(None).decode())
+    return v.value
 
 
 def version() -> str:

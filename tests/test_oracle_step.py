@@ -158,3 +158,24 @@ def test_floors_exact():
     Pn = G.get_state()[0]
     assert Pn[0, i, j, 0] == pytest.approx(1e-5 * r ** -0.5, rel=1e-14)
     assert Pn[1, i, j, 0] == pytest.approx((1e-5 / 3) * r ** -2.5, rel=1e-14)
+
+
+def test_horizon_flux_of_split_monopole_closed_form():
+    """phi_B = 1/2 sum |sqrt(-g) B^1| dX2 dX3 (Eq. 39) of a split monopole
+    sqrt(-g) B^1 = +-B0 is 2 pi B0 exactly, and its corner divergence is 0."""
+    p = oracle.default_params(n1=24, n2=24, n3=3, gam=GAM)
+    G = oracle.Grid(p)
+    G.init_torus(pert_amp=0.0, beta0=0.0)
+    P, U, t, dt = G.get_state()
+    tab = G.geom_table(0)
+    gdet = tab[2:26, 2:26, 32][:, :, None]
+    sgn = np.where(np.arange(24) < 12, 1.0, -1.0)[None, :, None]
+    B0 = 3e-3
+    P[5] = B0 * sgn / gdet
+    loc = np.repeat((np.arange(24)[:, None] * 24 + np.arange(24)[None, :]).astype(np.int32), 3, axis=1)
+    U = G.prim2cons(P.reshape(8, -1), loc.reshape(-1)).reshape(U.shape)
+    G.set_state(P, U, t, dt)
+    d = G.diagnostics()
+    assert d["phib"] == pytest.approx(2 * np.pi * B0, rel=1e-12)
+    assert d["divb_max"] <= 1e-14 * B0 / G.dx[0]
+    assert d["PhiB"] == pytest.approx(d["phib"] / np.sqrt(abs(d["mdot"])), rel=1e-12)
