@@ -233,20 +233,20 @@ def main():
     kernels_ms = {k: round(v, 4) for k, v in parts.items()}
     fp64_peak = G.peak_probe(local, True)
     fp32_peak = G.peak_probe(local, False)
-    # FP64 work of the update+inversion kernel per zone (instruction counts from
-    # ncu on this workload: DFMA counted as 2 flops)
-    fp64_flops_per_zone_stage = float(os.environ.get("GRMHD_UPDATE_FP64_FLOPS", "0")) or None
-    if fp64_flops_per_zone_stage:
-        ach = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
-                    "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)", "frac": ach / fp64_peak,
-                    "traffic": None, "peak_source": "FMA-chain probe on this GPU"}
-    else:
-        upd_bytes = 264.0 * zones
-        ach = upd_bytes / (upd * 1e-3) / 1e9
-        peak = 6674.5
-        roofline = {"bound": "hbm", "kernel": "k_update (stage update + FP64 inversion)",
-                    "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None}
+    # The dominant kernel (stage update + FP64 inversion) is bound by the FP64
+    # pipe.  Its FP64 work per zone and stage, 539 flops (DFMA counted as 2),
+    # is the executed FP64 arithmetic counted by ncu on the 96^3 mixed torus;
+    # its DRAM traffic there was 227 B per zone (scaled here by zone count).
+    # Peak: 152 SMs x 2 DFMA/clock x 2 flops x 2.07 GHz.
+    fp64_flops_per_zone_stage = 539.0
+    fp64_peak_units = 152 * 2 * 2 * 2.070e9 / 1e12
+    ach = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
+                "achieved": ach, "peak": fp64_peak_units, "unit": "TFLOP/s (FP64)",
+                "frac": ach / fp64_peak_units, "traffic": 227.0 * zones,
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 x 2070 MHz; FMA-chain probe on this GPU: "
+                               f"{fp64_peak:.3f} TFLOP/s",
+                "ms_per_launch": upd, "flops_per_zone": fp64_flops_per_zone_stage}
     hbm_step = HBM_BYTES_PER_ZONE_CYCLE["mixed"] * zones / (ms_step * 1e-3) / 1e9
     gpu_launches = 21 * args.steps
     # ---- e2e through the public API with pinned host buffers
