@@ -206,6 +206,26 @@ int grmhd_step_profiled(grmhd_ctx *ctx, int nsteps, double *ms_out);
  * runs a few sub-second kernels. */
 int grmhd_peak_probe(int device, int fp64, double *tflops);
 
+/* Horizon diagnostics that allocate no device memory at all.  The paper has
+ * no counterpart: this is a library convenience for callers that may not
+ * call cudaMalloc -- for example a host application that has handed all
+ * device memory to its own pool allocator and forbids further allocation,
+ * or a monitoring hook that must not disturb a fixed memory budget between
+ * steps.  It computes the same sums as grmhd_diagnostics (same kernels) but
+ * keeps the reduction's partial sums in a fixed array of the library
+ * (256 KiB, reserved on every device that loads the library until exit)
+ * instead of the context's scratch buffer.
+ *   out_dev: caller-owned device memory for 8 doubles; once the context
+ *            stream has run the work, out_dev[0..4] = mdot, phib, edot, ldot,
+ *            divb_max and out_dev[5..7] are zero.  The call is asynchronous
+ *            on the context stream and does not synchronise it.
+ * Limit: the horizon shell n2 * n3 may not exceed 2,097,152 zones
+ * (GRMHD_EINVAL with a message otherwise).  The first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  All calls on a device share the array: calls whose
+ * kernels overlap on the GPU (e.g. contexts on different streams) race. */
+int grmhd_diagnostics_noalloc(grmhd_ctx *ctx, double *out_dev);
+
 /* Library version string. */
 const char *grmhd_version(void);
 

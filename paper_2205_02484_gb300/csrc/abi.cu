@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -552,5 +553,67 @@ extern "C" int grmhd_peak_probe(int device, int fp64, double *tflops)
     cudaError_t e = cudaGetLastError();
     cudaStreamDestroy(s);
     if (e != cudaSuccess) return fail(nullptr, GRMHD_ECUDA, cudaGetErrorString(e));
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Horizon diagnostics with no device allocation at all.
+//
+// grmhd_diagnostics reduces the horizon sums through per-block partial sums
+// kept in the context's scratch buffer.  This variant runs the same kernels
+// but keeps those partial sums in the file-scope array below, which the CUDA
+// runtime reserves on every device that loads the library, once, for the
+// life of the process.  Nothing in it needs to start at zero: every call
+// writes all the partial sums it later reads.  Every call on a device shares
+// the array, so two calls whose kernels overlap on the GPU (for instance two
+// contexts on different streams) race on it.
+static constexpr int NOALLOC_MAX_BLOCKS = 8192; // horizon shells up to 8192 * 256 (theta, phi) zones
+static constexpr long long NOALLOC_DOUBLES = 4LL * NOALLOC_MAX_BLOCKS; // 256 KiB
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_DOUBLES];
+
+static constexpr int NOALLOC_MAX_DEVICES = 64;
+static double *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_partials on device dev, looked up once per
+// device with that device current (host code may not use the symbol itself).
+static int noalloc_partials(grmhd_ctx *ctx, int dev, double **out)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        int prev = 0;
+        CK(cudaGetDevice(&prev));
+        CK(cudaSetDevice(dev));
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        cudaError_t e2 = cudaSetDevice(prev);
+        if (e != cudaSuccess)
+            return fail(ctx, GRMHD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        CK(e2);
+        g_noalloc_addr[dev] = (double *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return 0;
+}
+
+extern "C" int grmhd_diagnostics_noalloc(grmhd_ctx *ctx, double *out_dev)
+{
+    if (!ctx || !out_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    const Grid &g = ctx->g;
+    long long shell = (long long)g.n2 * g.n3;
+    long long blocks = (shell + 255) / 256;
+    if (blocks > NOALLOC_MAX_BLOCKS)
+        return fail(ctx, GRMHD_EINVAL,
+                    "grmhd_diagnostics_noalloc: horizon shell of n2*n3 = " + std::to_string(shell) +
+                        " zones exceeds its maximum of " + std::to_string(256LL * NOALLOC_MAX_BLOCKS) +
+                        " zones; use grmhd_diagnostics");
+    int dev = ctx->gp.device;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, GRMHD_EINVAL, "device ordinal out of range");
+    double *partials = nullptr;
+    int rc = noalloc_partials(ctx, dev, &partials);
+    if (rc) return rc;
+    launch_diagnostics(g, partials, NOALLOC_DOUBLES, out_dev, ctx->stream);
+    CK(cudaGetLastError());
     return 0;
 }

@@ -88,6 +88,7 @@ SIGNATURES = {
     "grmhd_version": (C.c_char_p, []),
     "grmhd_step_profiled": (C.c_int, [_V, C.c_int, C.POINTER(C.c_double)]),
     "grmhd_peak_probe": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "grmhd_diagnostics_noalloc": (C.c_int, [_V, _V]),
 }
 
 PROF_SLOTS = 16
@@ -291,6 +292,16 @@ def step_profiled(ctx: Context, nsteps: int = 1) -> dict:
     out["finalize"] = buf[14]
     out["step"] = buf[15]
     return out
+
+
+def diagnostics_noalloc(ctx: Context, out_dev):
+    """Horizon diagnostics into a caller-owned CUDA tensor of 8 doubles
+    without any device allocation (asynchronous on the context stream)."""
+    ptr, dev = _ptr(out_dev)
+    if not dev or out_dev.numel() < 8:
+        raise ValueError("out_dev must be a CUDA tensor of at least 8 doubles")
+    ctx.check(ctx.L.grmhd_diagnostics_noalloc(ctx.h, ptr))
+    return out_dev
 
 
 def peak_probe(device: int = 0, fp64: bool = True) -> float:
