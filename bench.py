@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -116,6 +117,93 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- multi-rank
+
+def max_over_ranks(x, dist=None, device=None):
+    """Largest x over all ranks (the job's time is that of its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(zones_per_rank, steps, world, ms_max):
+    """Whole-job zone-cycles/s: every rank advances its own grid."""
+    return zones_per_rank * steps * world / (ms_max * 1e-3)
+
+
+# -------------------------------------------------------------- ensemble
+
+ENSEMBLE_SHAPES = [(64, 64, 1), (96, 64, 1), (128, 64, 32), (128, 96, 64), (192, 128, 64)]
+
+
+def ensemble_specs(n=24, master_seed=2024):
+    """Batched-ensemble workload: n tori with shapes drawn from 64x64x1 up to
+    192x128x64, spin U[0, 0.98], gamma in {4/3, 13/9, 5/3}, beta_0 U[30, 300],
+    perturbation seeds 100.. (one master seed)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(master_seed))
+    out = []
+    for m in range(n):
+        shape = ENSEMBLE_SHAPES[int(rng.integers(len(ENSEMBLE_SHAPES)))]
+        a = float(rng.uniform(0.0, 0.98))
+        gam = [4.0 / 3.0, 13.0 / 9.0, 5.0 / 3.0][int(rng.integers(3))]
+        b0 = float(rng.uniform(30.0, 300.0))
+        out.append((shape, a, gam, b0, 100 + m))
+    return out
+
+
+def run_ensemble(G, torch, stream, device, steps=10):
+    from paper_2205_02484_gb300 import tuning
+    members = []
+    for shape, a, gam, b0, seed in ensemble_specs():
+        gp = G.default_grid(*shape, a=a, r_out=100.0, precision=G.MIXED, device=device)
+        gp.stream = stream.cuda_stream
+        c = G.init_grid(gp, G.default_phys(gam=gam))
+        G.set_metric(c, a, G.KERR_MKS)
+        G.init_torus(c, r_in=6.0, r_max=12.0, beta0=b0, pert_amp=0.04, seed=seed)
+        members.append(c)
+    zones = sum(c.nact for c in members)
+    ens = G.ensemble_create(members)
+    tiling, cached = tuning.tune_or_load(ens, torch.cuda.get_device_name(device), trial_steps=2)
+
+    def time_it(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    G.ensemble_step(ens, 2)
+    ms_ens = time_it(lambda k: G.ensemble_step(ens, k), steps)
+    G.ensemble_sync(ens)
+
+    def loop(k):
+        for _ in range(k):
+            for c in members:
+                G.step(c, 1)
+    loop(1)
+    ms_loop = time_it(loop, steps)
+    for c in members:
+        G.sync(c)
+    ens.close()
+    for c in members:
+        c.close()
+    return {"workload": "24 FM tori, shapes 64x64x1..192x128x64, a U[0,0.98], gamma {4/3,13/9,5/3}, "
+                        "beta_0 U[30,300], r_out 100 M, mixed precision, one persistent launch per kernel "
+                        "class and one CUDA graph per ensemble step",
+            "members": len(members), "zones": zones, "steps": steps,
+            "value": zones * steps / (ms_ens * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms_ens / steps,
+            "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
+            "loop_ms_per_step": ms_loop / steps, "speedup_vs_loop": ms_loop / ms_ens,
+            "tiling": tiling, "tiling_from_cache": cached}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -212,17 +300,14 @@ def main():
         ms = e0.elapsed_time(e1)
         clocks = clk.stop() if clk else None
         G.sync(ctx)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         return ms, clocks
 
     zones = n * n * n
     # ---- headline: mixed precision
     ctx = make_ctx(G.MIXED)
     ms, clocks = timed(ctx, args.steps, args.warmup, True)
-    value = zones * args.steps * world / (ms * 1e-3)
+    value = aggregate_value(zones, args.steps, world, ms)
     ms_step = ms / args.steps
     diag = G.diagnostics(ctx)
     # per-kernel breakdown (events between kernel groups, no graph)
@@ -266,12 +351,8 @@ def main():
             G.step(ctx, 1)
             _, _, t0, dt0 = G.get_state(ctx, Ph, Uh)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t_start
-        if dist is not None:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": zones * ne * world / el, "unit": "zone-cycles/s",
+        el = max_over_ranks(time.perf_counter() - t_start, dist, "cuda")
+        e2e = {"value": aggregate_value(zones, ne, world, el * 1e3), "unit": "zone-cycles/s",
                "h2d_bytes_per_step": int(Ph.nbytes + Uh.nbytes), "d2h_bytes_per_step": int(Ph.nbytes + Uh.nbytes),
                "path": "grmhd_set_state(host) + grmhd_step + grmhd_get_state(host), pinned buffers"}
         del Ph, Uh
@@ -284,11 +365,15 @@ def main():
         c64 = make_ctx(G.FP64)
         ms64, _ = timed(c64, k64, min(args.warmup, 3), False)
         prof64 = G.step_profiled(c64, 1)
-        fp64 = {"value": zones * k64 * world / (ms64 * 1e-3), "unit": "zone-cycles/s", "steps": k64,
+        fp64 = {"value": aggregate_value(zones, k64, world, ms64), "unit": "zone-cycles/s", "steps": k64,
                 "ms_per_step": ms64 / k64,
                 "hbm_frac_of_measured": HBM_BYTES_PER_ZONE_CYCLE["fp64"] * zones / (ms64 / k64 * 1e-3) / 1e9 / 6674.5,
                 "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
         c64.close()
+    # ---- batched ensemble (independent tori, one launch per kernel class)
+    ensemble = None
+    if world == 1 and not args.no_ensemble:
+        ensemble = run_ensemble(G, torch, stream, local)
     # ---- CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -308,6 +393,7 @@ def main():
             "peaks_probe_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
             "kernels_ms_per_step": kernels_ms,
             "fp64_step": fp64,
+            "ensemble": ensemble,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,

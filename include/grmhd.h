@@ -206,6 +206,49 @@ int grmhd_step_profiled(grmhd_ctx *ctx, int nsteps, double *ms_out);
  * runs a few sub-second kernels. */
 int grmhd_peak_probe(int device, int fp64, double *tflops);
 
+/* ----------------------------------------------------------------------
+ * Ensemble: many independent grids advanced together.  Every kernel class
+ * of the RK2 step (face sweeps, EMFs, update + inversion, fixups, boundary
+ * fill, dt) is one persistent launch that walks a ragged tile list over all
+ * members, and one ensemble step is one captured CUDA graph.  Members are
+ * contexts made with grmhd_init_grid / grmhd_set_metric / grmhd_init_torus
+ * (or grmhd_set_state); they may differ in size, spin, adiabatic index and
+ * field, but must share the device and the precision.  They keep their own
+ * state, time step, counters and diagnostics (read them with the member
+ * calls), must outlive the ensemble, and are stepped on the first member's
+ * stream.  Each member evolves exactly as it would alone.
+ * ---------------------------------------------------------------------- */
+typedef struct grmhd_ens grmhd_ens;
+
+/* Tiling of the persistent launches: elements per thread per tile and
+ * persistent blocks per SM, for the face sweeps and for the update kernel. */
+typedef struct {
+    int items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update;
+} grmhd_ens_tiling;
+
+/* Build an ensemble of n member contexts (each with metric and state).
+ * Errors: EINVAL (mixed devices or precisions), ESTATE (member not ready),
+ * ENOMEM. */
+int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens **out);
+
+/* Advance every member by nsteps RK2 steps (asynchronous; graph replay). */
+int grmhd_ensemble_step(grmhd_ens *ens, int nsteps);
+
+/* Set / read the tiling (1-16 elements per thread, 1-64 blocks per SM). */
+int grmhd_ensemble_set_tiling(grmhd_ens *ens, const grmhd_ens_tiling *t);
+int grmhd_ensemble_get_tiling(const grmhd_ens *ens, grmhd_ens_tiling *t);
+
+/* Time trial steps over a grid of tilings (face sweeps and update timed
+ * separately with CUDA events), keep the fastest, and restore every member's
+ * state, counters and time step afterwards.  best / best_ms may be NULL. */
+int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_ens_tiling *best, double *best_ms);
+
+/* Synchronise and return the first member status error (GRMHD_EFIXUP ...). */
+int grmhd_ensemble_sync(grmhd_ens *ens);
+
+void grmhd_ensemble_destroy(grmhd_ens *ens);
+const char *grmhd_ensemble_last_error(const grmhd_ens *ens);
+
 /* Horizon diagnostics that allocate no device memory at all.  The paper has
  * no counterpart: this is a library convenience for callers that may not
  * call cudaMalloc -- for example a host application that has handed all

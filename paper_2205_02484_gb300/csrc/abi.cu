@@ -72,6 +72,11 @@ static int dalloc(grmhd_ctx *ctx, T **p, size_t count)
 
 static long long nact_of(const grmhd_ctx *c) { return (long long)c->g.n1 * c->g.n2 * c->g.n3; }
 
+const Grid *ctx_grid(const grmhd_ctx *ctx) { return ctx ? &ctx->g : nullptr; }
+bool ctx_ready(const grmhd_ctx *ctx) { return ctx && ctx->metric_set && ctx->state_set; }
+int ctx_device(const grmhd_ctx *ctx) { return ctx->gp.device; }
+cudaStream_t ctx_stream(const grmhd_ctx *ctx) { return ctx->stream; }
+
 extern "C" const char *grmhd_version(void) { return "grmhd-gb300 0.1 (sm_103a)"; }
 
 extern "C" const char *grmhd_last_error(const grmhd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -237,6 +242,7 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
     for (int d = 0; d < 3; d++) g.idx[d] = 1.0 / g.dx[d];
     ctx->gb.cp = cp;
     ctx->a = a;
+    (void)cudaGetLastError(); // a stale error of an unrelated earlier call is not ours
     launch_geometry(g, ctx->gb, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -282,6 +288,7 @@ extern "C" int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *tp)
     ta.seed = tp->seed;
     ta.cp = ctx->gb.cp;
     if (reset_counters(ctx)) return GRMHD_ECUDA;
+    (void)cudaGetLastError();
     launch_torus(g, ta, ctx->scratch, ctx->intorus, ctx->hpin, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
@@ -321,6 +328,7 @@ extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U,
         Pd = ctx->staging;
         Ud = ctx->staging + 8 * na;
     }
+    (void)cudaGetLastError();
     launch_copy_state_in(ctx->g, Pd, Ud, ctx->stream);
     launch_bc(ctx->g, 0, ctx->stream);
     CK(cudaGetLastError());
@@ -334,6 +342,7 @@ extern "C" int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, 
     if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
     if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
     long long na = nact_of(ctx);
+    (void)cudaGetLastError();
     if (P || U) {
         if (on_device) {
             launch_copy_state_out(ctx->g, P, U, ctx->stream);
@@ -357,6 +366,7 @@ extern "C" int grmhd_step(grmhd_ctx *ctx, int nsteps)
     if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
     if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "step needs a state (init_torus or set_state)");
     if (nsteps < 0) return fail(ctx, GRMHD_EINVAL, "nsteps < 0");
+    (void)cudaGetLastError();
     if (!ctx->gexec) {
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         launch_step(ctx->g, ctx->stream);
@@ -393,6 +403,7 @@ extern "C" int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out)
     if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
     Grid &g = ctx->g;
     double *dout = ctx->scratch + ctx->scratch_len - 16;
+    (void)cudaGetLastError();
     launch_diagnostics(g, ctx->scratch, ctx->scratch_len - 16, dout, ctx->stream);
     CK(cudaGetLastError());
     unsigned long long cnt[C_NCOUNT];
@@ -444,6 +455,7 @@ extern "C" int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, 
         CK(cudaMemcpyAsync(sl, loc, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
         Pd = sp; ld = sl; Ud = su;
     }
+    (void)cudaGetLastError();
     launch_prim2cons(ctx->g, Pd, ld, Ud, n, ctx->stream);
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(U, Ud, 9LL * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -474,6 +486,7 @@ extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, d
         CK(cudaMemcpyAsync(sl, loc, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
         Ud = su; Pd = sp; ld = sl; fd = sf; id = iters ? si : nullptr;
     }
+    (void)cudaGetLastError();
     launch_con2prim(ctx->g, Ud, ld, Pd, fd, id, n, use_learned_guess ? ctx->mlp : nullptr, ctx->stream);
     CK(cudaGetLastError());
     if (!on_device) {
@@ -499,6 +512,7 @@ extern "C" int grmhd_fluxes(grmhd_ctx *ctx, double *out, double *dt_out, int on_
     // keep the state's dt: save it, sweep, read the sweep's dt, restore
     CK(cudaMemcpyAsync(ctx->hpin + 16, g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    (void)cudaGetLastError();
     launch_fluxes_dt(g, 1, ctx->stream);
     launch_gather_fluxes(g, o, ctx->stream);
     CK(cudaGetLastError());
@@ -519,6 +533,7 @@ extern "C" int grmhd_step_profiled(grmhd_ctx *ctx, int nsteps, double *ms_out)
     cudaEvent_t ev[NE];
     for (int e = 0; e < NE; e++) CK(cudaEventCreate(&ev[e]));
     for (int p = 0; p < GRMHD_PROF_SLOTS; p++) ms_out[p] = 0.0;
+    (void)cudaGetLastError();
     for (int s = 0; s < nsteps; s++) {
         launch_step_profiled(ctx->g, ctx->stream, ev);
         CK(cudaGetLastError());

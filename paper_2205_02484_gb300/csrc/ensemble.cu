@@ -1,0 +1,448 @@
+// ensemble.cu -- a batch of independent tori (different sizes, spins,
+// adiabatic indices, field strengths) advanced together: every kernel class
+// of the RK2 step is one persistent launch over a ragged work list that
+// spans all members, and the whole ensemble step is one captured CUDA graph.
+//
+// Work list: for kernel class c and member m the elements (faces, edges,
+// zones, ghost zones) are cut into tiles of blockDim * items elements;
+// prefix[c][m] counts the tiles of members < m.  A persistent grid of
+// (SM count x blocks per SM) blocks walks the tiles; a block finds its
+// member by binary search on the prefix, stages that member's descriptor in
+// shared memory and runs the same item functions as the single-grid kernels,
+// so every member evolves bit-for-bit as it would alone.  Fixups run one
+// block per member, the CFL step and counters stay per member.
+//
+// Tunables (tile length in elements per thread, persistent blocks per SM)
+// are picked by grmhd_ensemble_autotune from timed trial steps.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grmhd.h"
+#include "kernels.h"
+#include "stage_items.cuh"
+
+namespace grmhd {
+
+enum { W_F1 = 0, W_F2, W_F3, W_EMF, W_UPD, W_POL, W_BC1, W_BC2, W_BC3, W_NCLASS };
+constexpr int ENS_THREADS = 128;
+
+struct EnsDev {
+    const Grid *grids;       // [n]
+    const long long *prefix; // [W_NCLASS][n + 1]
+    int n;
+    int items[W_NCLASS];
+};
+
+__host__ __device__ inline long long class_count(const Grid &g, int cls)
+{
+    switch (cls) {
+    case W_F1: return flux_box(g, 1).count();
+    case W_F2: return flux_box(g, 2).count();
+    case W_F3: return flux_box(g, 3).count();
+    case W_EMF: return edge_box(g).count();
+    case W_UPD: return nact_of(g);
+    case W_POL: return polar_count(g);
+    case W_BC1: return bc1_count(g);
+    case W_BC2: return bc2_count(g);
+    default: return bc3_count(g);
+    }
+}
+
+__device__ __forceinline__ int find_member(const long long *pre, int n, long long w)
+{
+    int lo = 0, hi = n; // pre[lo] <= w < pre[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (pre[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename R, int CLS>
+__global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int dst, double dtfac, int corr,
+                                                       int want_dt)
+{
+    __shared__ Grid sg;
+    const long long *pre = E.prefix + (long long)CLS * (E.n + 1);
+    const long long total = pre[E.n];
+    const int items = E.items[CLS];
+    const long long tile = (long long)blockDim.x * items;
+    int cur = -1;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+        int m = find_member(pre, E.n, w);
+        if (m != cur) {
+            __syncthreads();
+            if (threadIdx.x == 0) sg = E.grids[m];
+            __syncthreads();
+            cur = m;
+        }
+        const long long base = (w - pre[m]) * tile;
+        const R *Pin = (const R *)sg.P[src];
+        R *Pout = (R *)sg.P[dst];
+        double dtc = INFINITY;
+        UpdCount cn{};
+        for (int it = 0; it < items; it++) {
+            long long t = base + (long long)it * blockDim.x + threadIdx.x;
+            if (CLS == W_F1) dtc = fmin(dtc, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_box(sg, 1), want_dt, t));
+            if (CLS == W_F2) dtc = fmin(dtc, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_box(sg, 2), want_dt, t));
+            if (CLS == W_F3) dtc = fmin(dtc, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_box(sg, 3), want_dt, t));
+            if (CLS == W_EMF)
+                emf_item(sg, (const R *)sg.F[0], (const R *)sg.F[1], (const R *)sg.F[2], (R *)sg.E[0], (R *)sg.E[1],
+                         (R *)sg.E[2], edge_box(sg), t);
+            if (CLS == W_UPD)
+                update_call<R>(sg, Pin, Pout, (const R *)sg.F[0], (const R *)sg.F[1], (const R *)sg.F[2],
+                            (const R *)sg.E[0], (const R *)sg.E[1], (const R *)sg.E[2], dtfac, corr, t, cn);
+            if (CLS == W_POL) polar_item(sg, Pout, t);
+            if (CLS == W_BC1) bc1_call(sg, Pout, t);
+            if (CLS == W_BC2) bc2_item(sg, Pout, t);
+            if (CLS == W_BC3) bc3_item(sg, Pout, t);
+        }
+        if ((CLS == W_F1 || CLS == W_F2 || CLS == W_F3) && want_dt) block_min_into(&sg.dtmin[CLS - W_F1], dtc);
+        if (CLS == W_UPD) flush_counts(sg, cn);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) ek_fixup(EnsDev E, int dst, int corr)
+{
+    const Grid &g = E.grids[blockIdx.x];
+    fixup_call(g, (R *)g.P[dst], corr);
+}
+
+__global__ void ek_finalize(EnsDev E)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < E.n) finalize_one(E.grids[m], 1);
+}
+
+} // namespace grmhd
+
+using namespace grmhd;
+
+struct grmhd_ens {
+    std::vector<grmhd_ctx *> members;
+    std::vector<Grid> hgrids;
+    Grid *dgrids = nullptr;
+    long long *dprefix = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0, mixed = 0, sms = 0;
+    grmhd_ens_tiling tiling{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long tiles[W_NCLASS] = {0};
+    std::string err;
+};
+
+static int efail(grmhd_ens *e, int code, const std::string &m)
+{
+    if (e) e->err = m;
+    return code;
+}
+
+#define ECK(call)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return efail(ens, GRMHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void drop_graph(grmhd_ens *ens)
+{
+    if (ens->gexec) cudaGraphExecDestroy(ens->gexec);
+    if (ens->graph) cudaGraphDestroy(ens->graph);
+    ens->gexec = nullptr;
+    ens->graph = nullptr;
+}
+
+// tile prefix tables for the current tiling
+static int build_tables(grmhd_ens *ens)
+{
+    int n = (int)ens->members.size();
+    int items[W_NCLASS];
+    for (int c = 0; c < W_NCLASS; c++) items[c] = 4;
+    items[W_F1] = items[W_F2] = items[W_F3] = ens->tiling.items_flux;
+    items[W_UPD] = ens->tiling.items_update;
+    std::vector<long long> pre((size_t)W_NCLASS * (n + 1));
+    for (int c = 0; c < W_NCLASS; c++) {
+        long long acc = 0;
+        long long tile = (long long)ENS_THREADS * items[c];
+        for (int m = 0; m < n; m++) {
+            pre[(size_t)c * (n + 1) + m] = acc;
+            acc += (class_count(ens->hgrids[m], c) + tile - 1) / tile;
+        }
+        pre[(size_t)c * (n + 1) + n] = acc;
+        ens->tiles[c] = acc;
+    }
+    ECK(cudaMemcpyAsync(ens->dprefix, pre.data(), pre.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                        ens->stream));
+    ECK(cudaStreamSynchronize(ens->stream));
+    return 0;
+}
+
+static EnsDev ens_dev(const grmhd_ens *ens)
+{
+    EnsDev E{};
+    E.grids = ens->dgrids;
+    E.prefix = ens->dprefix;
+    E.n = (int)ens->members.size();
+    for (int c = 0; c < W_NCLASS; c++) E.items[c] = 4;
+    E.items[W_F1] = E.items[W_F2] = E.items[W_F3] = ens->tiling.items_flux;
+    E.items[W_UPD] = ens->tiling.items_update;
+    return E;
+}
+
+// Launch one ensemble step; with ev != nullptr an event is recorded before
+// each launch (2 stages x 10 launches + finalize + end = 22 events).
+template <typename R>
+static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *ev)
+{
+    EnsDev E = ens_dev(ens);
+    const int n = E.n;
+    auto grid_of = [&](int cls) {
+        int bps = (cls == W_UPD) ? ens->tiling.blocks_per_sm_update
+                                 : (cls <= W_F3 ? ens->tiling.blocks_per_sm_flux : 8);
+        long long b = std::min<long long>((long long)ens->sms * bps, ens->tiles[cls]);
+        return (unsigned)std::max<long long>(b, 1);
+    };
+    int e = 0;
+    for (int st = 0; st < 2; st++) {
+        int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
+        double fac = st == 0 ? 0.5 : 1.0;
+        int corr = st, wdt = st == 0;
+#define REC() do { if (ev) cudaEventRecord(ev[e++], s); } while (0)
+        REC(); ek_sweep<R, W_F1><<<grid_of(W_F1), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_F2><<<grid_of(W_F2), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_F3><<<grid_of(W_F3), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_EMF><<<grid_of(W_EMF), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_UPD><<<grid_of(W_UPD), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_fixup<R><<<n, 1024, 0, s>>>(E, dst, corr);
+        REC(); ek_sweep<R, W_POL><<<grid_of(W_POL), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC1><<<grid_of(W_BC1), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC2><<<grid_of(W_BC2), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC3><<<grid_of(W_BC3), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+    }
+    REC();
+    ek_finalize<<<(n + 127) / 128, 128, 0, s>>>(E);
+    REC();
+#undef REC
+}
+
+static void ens_step_launch(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *ev)
+{
+    if (ens->mixed) launch_ens_step<float>(ens, s, ev);
+    else launch_ens_step<double>(ens, s, ev);
+}
+
+extern "C" int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens **out)
+{
+    grmhd_ens *ens = nullptr;
+    if (!members || n < 1 || !out) return GRMHD_EINVAL;
+    ens = new grmhd_ens();
+    for (int m = 0; m < n; m++) {
+        const Grid *g = ctx_grid(members[m]);
+        if (!g || !ctx_ready(members[m])) {
+            delete ens;
+            return GRMHD_ESTATE;
+        }
+        if (m > 0 && (g->mixed != ens->hgrids[0].mixed || ctx_device(members[m]) != ctx_device(members[0]))) {
+            delete ens;
+            return GRMHD_EINVAL;
+        }
+        ens->members.push_back(members[m]);
+        ens->hgrids.push_back(*g);
+    }
+    ens->mixed = ens->hgrids[0].mixed;
+    ens->device = ctx_device(members[0]);
+    ens->stream = ctx_stream(members[0]);
+    cudaDeviceGetAttribute(&ens->sms, cudaDevAttrMultiProcessorCount, ens->device);
+    ens->tiling = grmhd_ens_tiling{2, 2, 8, 4};
+    if (cudaMalloc(&ens->dgrids, sizeof(Grid) * n) != cudaSuccess ||
+        cudaMalloc(&ens->dprefix, sizeof(long long) * W_NCLASS * (n + 1)) != cudaSuccess) {
+        grmhd_ensemble_destroy(ens);
+        return GRMHD_ENOMEM;
+    }
+    cudaMemcpyAsync(ens->dgrids, ens->hgrids.data(), sizeof(Grid) * n, cudaMemcpyHostToDevice, ens->stream);
+    if (build_tables(ens) != 0) {
+        grmhd_ensemble_destroy(ens);
+        return GRMHD_ECUDA;
+    }
+    *out = ens;
+    return 0;
+}
+
+extern "C" void grmhd_ensemble_destroy(grmhd_ens *ens)
+{
+    if (!ens) return;
+    // The stream belongs to the first member, which may already be gone;
+    // cudaFree below waits for all device work anyway.
+    drop_graph(ens);
+    if (ens->dgrids) cudaFree(ens->dgrids);
+    if (ens->dprefix) cudaFree(ens->dprefix);
+    delete ens;
+}
+
+extern "C" const char *grmhd_ensemble_last_error(const grmhd_ens *ens) { return ens ? ens->err.c_str() : ""; }
+
+extern "C" int grmhd_ensemble_set_tiling(grmhd_ens *ens, const grmhd_ens_tiling *t)
+{
+    if (!ens || !t) return GRMHD_EINVAL;
+    if (t->items_flux < 1 || t->items_flux > 16 || t->items_update < 1 || t->items_update > 16 ||
+        t->blocks_per_sm_flux < 1 || t->blocks_per_sm_flux > 64 || t->blocks_per_sm_update < 1 ||
+        t->blocks_per_sm_update > 64)
+        return efail(ens, GRMHD_EINVAL, "tiling out of range (items 1-16, blocks per SM 1-64)");
+    ECK(cudaStreamSynchronize(ens->stream));
+    ens->tiling = *t;
+    drop_graph(ens);
+    return build_tables(ens);
+}
+
+extern "C" int grmhd_ensemble_get_tiling(const grmhd_ens *ens, grmhd_ens_tiling *t)
+{
+    if (!ens || !t) return GRMHD_EINVAL;
+    *t = ens->tiling;
+    return 0;
+}
+
+extern "C" int grmhd_ensemble_step(grmhd_ens *ens, int nsteps)
+{
+    if (!ens) return GRMHD_EINVAL;
+    if (nsteps < 0) return efail(ens, GRMHD_EINVAL, "nsteps < 0");
+    (void)cudaGetLastError(); // a stale error of an unrelated earlier call is not ours
+    if (!ens->gexec) {
+        ECK(cudaStreamBeginCapture(ens->stream, cudaStreamCaptureModeThreadLocal));
+        ens_step_launch(ens, ens->stream, nullptr);
+        cudaError_t le = cudaGetLastError();
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(ens->stream, &graph);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return efail(ens, GRMHD_ECUDA, std::string("ensemble capture failed: ") +
+                                               cudaGetErrorString(le != cudaSuccess ? le : ee));
+        }
+        ens->graph = graph;
+        ECK(cudaGraphInstantiate(&ens->gexec, ens->graph, 0));
+    }
+    for (int s = 0; s < nsteps; s++) ECK(cudaGraphLaunch(ens->gexec, ens->stream));
+    return 0;
+}
+
+extern "C" int grmhd_ensemble_sync(grmhd_ens *ens)
+{
+    if (!ens) return GRMHD_EINVAL;
+    ECK(cudaStreamSynchronize(ens->stream));
+    for (grmhd_ctx *c : ens->members) {
+        int rc = grmhd_sync(c);
+        if (rc) return efail(ens, rc, grmhd_last_error(c));
+    }
+    return 0;
+}
+
+// Snapshot of one member's evolving state (P^n, U, dt/t, counters, CFL minima).
+struct Snap {
+    void *P = nullptr, *U = nullptr;
+    size_t pbytes = 0, ubytes = 0;
+    double scal[8];
+    unsigned long long cnt[C_NCOUNT], dtmin[4];
+};
+
+extern "C" int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_ens_tiling *best, double *best_ms)
+{
+    if (!ens) return GRMHD_EINVAL;
+    if (trial_steps < 1) return efail(ens, GRMHD_EINVAL, "trial_steps < 1");
+    cudaStream_t s = ens->stream;
+    ECK(cudaStreamSynchronize(s));
+    // save every member so that the trials leave the state unchanged
+    std::vector<Snap> snaps(ens->members.size());
+    size_t rs = ens->mixed ? sizeof(float) : sizeof(double);
+    for (size_t m = 0; m < snaps.size(); m++) {
+        const Grid &g = ens->hgrids[m];
+        Snap &sn = snaps[m];
+        sn.pbytes = 8 * (size_t)g.nz * rs;
+        sn.ubytes = 9 * (size_t)g.nz * sizeof(double);
+        ECK(cudaMalloc(&sn.P, sn.pbytes));
+        ECK(cudaMalloc(&sn.U, sn.ubytes));
+        ECK(cudaMemcpyAsync(sn.P, g.P[0], sn.pbytes, cudaMemcpyDeviceToDevice, s));
+        ECK(cudaMemcpyAsync(sn.U, g.U, sn.ubytes, cudaMemcpyDeviceToDevice, s));
+        ECK(cudaMemcpyAsync(sn.scal, g.scal, sizeof(sn.scal), cudaMemcpyDeviceToHost, s));
+        ECK(cudaMemcpyAsync(sn.cnt, g.cnt, sizeof(sn.cnt), cudaMemcpyDeviceToHost, s));
+        ECK(cudaMemcpyAsync(sn.dtmin, g.dtmin, sizeof(sn.dtmin), cudaMemcpyDeviceToHost, s));
+    }
+    ECK(cudaStreamSynchronize(s));
+    const int NE = 22;
+    cudaEvent_t ev[NE];
+    for (int e = 0; e < NE; e++) ECK(cudaEventCreate(&ev[e]));
+    // flux sweeps and the update are timed separately; each picks its own
+    // (items per thread, blocks per SM) from a small grid of candidates
+    const int items_c[3] = {1, 2, 4};
+    const int bps_c[4] = {2, 4, 8, 16};
+    grmhd_ens_tiling keep = ens->tiling, cur = keep;
+    double best_flux = 1e300, best_upd = 1e300;
+    grmhd_ens_tiling bt = keep;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 4; b++) {
+            cur.items_flux = items_c[a];
+            cur.blocks_per_sm_flux = bps_c[b];
+            cur.items_update = items_c[a];
+            cur.blocks_per_sm_update = std::min(bps_c[b], 4);
+            ens->tiling = cur;
+            if (build_tables(ens)) goto done;
+            double tf = 0.0, tu = 0.0;
+            for (int it = 0; it <= trial_steps; it++) {
+                ens_step_launch(ens, s, ev);
+                ECK(cudaEventSynchronize(ev[NE - 1]));
+                if (it == 0) continue; // first run of a configuration warms up
+                for (int st = 0; st < 2; st++) {
+                    float ms;
+                    for (int k = 0; k < 3; k++) {
+                        ECK(cudaEventElapsedTime(&ms, ev[st * 10 + k], ev[st * 10 + k + 1]));
+                        tf += ms;
+                    }
+                    ECK(cudaEventElapsedTime(&ms, ev[st * 10 + 4], ev[st * 10 + 5]));
+                    tu += ms;
+                }
+            }
+            if (tf < best_flux) {
+                best_flux = tf;
+                bt.items_flux = cur.items_flux;
+                bt.blocks_per_sm_flux = cur.blocks_per_sm_flux;
+            }
+            if (tu < best_upd) {
+                best_upd = tu;
+                bt.items_update = cur.items_update;
+                bt.blocks_per_sm_update = cur.blocks_per_sm_update;
+            }
+        }
+done:
+    for (int e = 0; e < NE; e++) cudaEventDestroy(ev[e]);
+    cudaError_t err = cudaGetLastError();
+    // restore the members
+    for (size_t m = 0; m < snaps.size(); m++) {
+        const Grid &g = ens->hgrids[m];
+        Snap &sn = snaps[m];
+        cudaMemcpyAsync(g.P[0], sn.P, sn.pbytes, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(g.U, sn.U, sn.ubytes, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(g.scal, sn.scal, sizeof(sn.scal), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g.cnt, sn.cnt, sizeof(sn.cnt), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g.dtmin, sn.dtmin, sizeof(sn.dtmin), cudaMemcpyHostToDevice, s);
+    }
+    cudaStreamSynchronize(s);
+    for (Snap &sn : snaps) {
+        cudaFree(sn.P);
+        cudaFree(sn.U);
+    }
+    for (size_t m = 0; m < snaps.size(); m++) launch_bc(ens->hgrids[m], 0, s);
+    if (err != cudaSuccess) {
+        ens->tiling = keep;
+        build_tables(ens);
+        return efail(ens, GRMHD_ECUDA, cudaGetErrorString(err));
+    }
+    ens->tiling = bt;
+    drop_graph(ens);
+    int rc = build_tables(ens);
+    if (rc) return rc;
+    if (best) *best = bt;
+    if (best_ms) *best_ms = (best_flux + best_upd) / trial_steps;
+    return 0;
+}

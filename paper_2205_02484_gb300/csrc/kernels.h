@@ -47,3 +47,10 @@ void launch_copy_state_in(const Grid &g, const double *P, const double *U, cudaS
 void launch_copy_state_out(const Grid &g, double *P, double *U, cudaStream_t s);
 
 } // namespace grmhd
+
+// context accessors for the ensemble (abi.cu)
+struct grmhd_ctx;
+const grmhd::Grid *ctx_grid(const grmhd_ctx *ctx);
+bool ctx_ready(const grmhd_ctx *ctx);
+int ctx_device(const grmhd_ctx *ctx);
+cudaStream_t ctx_stream(const grmhd_ctx *ctx);

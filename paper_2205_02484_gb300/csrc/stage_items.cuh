@@ -1,0 +1,658 @@
+// stage_items.cuh -- the per-element bodies of one RK2 stage, shared by the
+// single-grid kernels (step.cu) and the persistent ensemble kernels
+// (ensemble.cu).  Each item function processes one element (a face, an edge,
+// a zone or a ghost zone) of one grid and returns what the caller reduces.
+//
+//   boundary fill (Section 4.1)  -> polar_item, bc1_item, bc2_item, bc3_item
+//   face fluxes (Eqs. 16-21)     -> flux_item<D>: PLM-MC face states, U and F of
+//                                   both states, LLF/HLL, c_w, CFL candidate (Eq. 27)
+//   flux-CT EMFs (Eq. 22)        -> emf_item
+//   update + inversion           -> update_item: flux divergence with the flux-CT
+//                                   B-fluxes of Eq. 23 formed from the EMFs,
+//                                   connection source (Eq. 15), RK2 stage update
+//                                   (Eqs. 25-26) with FP64 accumulation, FP64
+//                                   inversion (Section 2.3), floors/ceilings/cap
+//                                   (Section 2.4); failed zones are compacted
+//   fixups (Eq. 33)              -> fixup_block: Jacobi sweeps over the list (one block)
+//   dt                           -> finalize_one
+//
+// R is the flux arithmetic type (double, or float in the mixed path), which is
+// also the primitive storage type.
+#pragma once
+#include "fixes.cuh"
+
+namespace grmhd {
+
+struct Box {
+    int lo[3], n[3];
+    __host__ __device__ long long count() const { return (long long)n[0] * n[1] * n[2]; }
+};
+
+// element boxes of one grid: faces along X1..X3 (with the ring flux-CT
+// needs), edges, active zones
+__host__ __device__ inline Box flux_box(const Grid &g, int d)
+{
+    if (d == 1) return Box{{0, -1, -1}, {g.n1 + 1, g.n2 + 2, g.n3 + 2}};
+    if (d == 2) return Box{{-1, 0, -1}, {g.n1 + 2, g.n2 + 1, g.n3 + 2}};
+    return Box{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, g.n3 + 1}};
+}
+__host__ __device__ inline Box edge_box(const Grid &g) { return Box{{0, 0, 0}, {g.n1 + 1, g.n2 + 1, g.n3 + 1}}; }
+__host__ __device__ inline long long nact_of(const Grid &g) { return (long long)g.n1 * g.n2 * g.n3; }
+__host__ __device__ inline long long polar_count(const Grid &g)
+{
+    return (g.metric == KERR_MKS && g.n2 >= 6) ? (long long)g.n1 * g.n3 : 0;
+}
+__host__ __device__ inline long long bc1_count(const Grid &g) { return (long long)g.n2 * g.n3 * NG * 2; }
+__host__ __device__ inline long long bc2_count(const Grid &g) { return (long long)(g.n1 + 2 * NG) * g.n3 * NG * 2; }
+__host__ __device__ inline long long bc3_count(const Grid &g)
+{
+    return (long long)(g.n1 + 2 * NG) * (g.n2 + 2 * NG) * NG * 2;
+}
+
+__device__ __forceinline__ void box_decode(const Box &b, long long t, int &i, int &j, int &k)
+{
+    k = (int)(t % b.n[2]);
+    long long r = t / b.n[2];
+    j = (int)(r % b.n[1]);
+    i = (int)(r / b.n[1]);
+    i += b.lo[0];
+    j += b.lo[1];
+    k += b.lo[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide minimum of v, combined into *dst (bits of a positive double);
+// every thread of the block must call it
+__device__ __forceinline__ void block_min_into(unsigned long long *dst, double v)
+{
+    __shared__ double sm[32];
+    v = warp_min(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < (int)(blockDim.x >> 5) ? sm[lane] : INFINITY;
+        x = warp_min(x);
+        if (lane == 0 && x < INFINITY) atomicMin(dst, dbits(x));
+    }
+}
+
+__device__ __forceinline__ void block_count(unsigned long long *dst, unsigned v)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
+}
+
+// ------------------------------------------------------------ boundary fill
+
+__device__ __forceinline__ int wrapi(int k, int n) { return ((k % n) + n) % n; }
+
+template <typename RS>
+__device__ __forceinline__ void polar_item(const Grid &g, RS *P, long long t)
+{
+    if (t >= polar_count(g)) return;
+    int i = (int)(t / g.n3), k = (int)(t % g.n3);
+    const long long f = (long long)KU2 * g.nz;
+    RS a = P[f + zidx(g, i, 2, k)], b = P[f + zidx(g, i, g.n2 - 3, k)];
+    P[f + zidx(g, i, 0, k)] = a * RS(0.5 / 2.5);
+    P[f + zidx(g, i, 1, k)] = a * RS(1.5 / 2.5);
+    P[f + zidx(g, i, g.n2 - 1, k)] = b * RS(0.5 / 2.5);
+    P[f + zidx(g, i, g.n2 - 2, k)] = b * RS(1.5 / 2.5);
+}
+
+// u^1 = 0 at fixed ut^2, ut^3: ut^1 = Gamma alpha g^{t1}, Gamma from its quadratic
+__device__ inline void zero_radial_velocity(const Geo<double> &geo, double q[NP])
+{
+    double c = geo.alpha * geo.gcon[1];
+    double a2 = 1.0 - geo.gcov[4] * c * c;
+    if (!(a2 > 0.0)) return;
+    double b = -2.0 * c * (geo.gcov[5] * q[KU2] + geo.gcov[6] * q[KU3]);
+    double rest = geo.gcov[7] * q[KU2] * q[KU2] + 2.0 * geo.gcov[8] * q[KU2] * q[KU3] +
+                  geo.gcov[9] * q[KU3] * q[KU3];
+    double cc = -(1.0 + rest);
+    double disc = b * b - 4.0 * a2 * cc;
+    double gm = (-b + sqrt(disc)) / (2.0 * a2);
+    q[KU1] = gm * c;
+}
+
+template <typename RS>
+__device__ inline void bc1_item(const Grid &g, RS *P, long long t)
+{
+    if (t >= bc1_count(g)) return;
+    int side = (int)(t % 2);
+    long long r = t / 2;
+    int gh = 1 + (int)(r % NG);
+    r /= NG;
+    int k = (int)(r % g.n3), j = (int)(r / g.n3);
+    int bc = g.metric == KERR_MKS ? BC_INFLOW : g.bc1;
+    int id = side == 0 ? -gh : g.n1 - 1 + gh;
+    int is;
+    if (bc == BC_PERIODIC) is = wrapi(id, g.n1);
+    else is = side == 0 ? 0 : g.n1 - 1;
+    long long zs = zidx(g, is, j, k), zd = zidx(g, id, j, k);
+    if (bc != BC_INFLOW) {
+#pragma unroll
+        for (int c = 0; c < NP; c++) P[c * g.nz + zd] = P[c * g.nz + zs];
+        return;
+    }
+    double q[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) q[c] = (double)P[c * g.nz + zs];
+    Geo<double> geo = g.gc[midx(g, id, j)];
+    St<double> s;
+    get_state(q, geo, s);
+    if ((side == 0 && s.ucon[1] > 0.0) || (side == 1 && s.ucon[1] < 0.0)) zero_radial_velocity(geo, q);
+#pragma unroll
+    for (int c = 0; c < NP; c++) P[c * g.nz + zd] = (RS)q[c];
+}
+
+template <typename RS>
+__device__ __forceinline__ void bc2_item(const Grid &g, RS *P, long long t)
+{
+    if (t >= bc2_count(g)) return;
+    int side = (int)(t % 2);
+    long long r = t / 2;
+    int gh = 1 + (int)(r % NG);
+    r /= NG;
+    int k = (int)(r % g.n3), i = (int)(r / g.n3) - NG;
+    int bc = g.metric == KERR_MKS ? BC_POLAR : g.bc2;
+    int jd = side == 0 ? -gh : g.n2 - 1 + gh;
+    int js;
+    bool flip = false;
+    if (bc == BC_POLAR) {
+        js = side == 0 ? gh - 1 : g.n2 - gh;
+        flip = true;
+    } else if (bc == BC_PERIODIC) {
+        js = wrapi(jd, g.n2);
+    } else {
+        js = side == 0 ? 0 : g.n2 - 1;
+    }
+    long long zs = zidx(g, i, js, k), zd = zidx(g, i, jd, k);
+#pragma unroll
+    for (int c = 0; c < NP; c++) {
+        RS v = P[c * g.nz + zs];
+        if (flip && (c == KU2 || c == KB2)) v = -v;
+        P[c * g.nz + zd] = v;
+    }
+}
+
+template <typename RS>
+__device__ __forceinline__ void bc3_item(const Grid &g, RS *P, long long t)
+{
+    if (t >= bc3_count(g)) return;
+    int side = (int)(t % 2);
+    long long r = t / 2;
+    int gh = 1 + (int)(r % NG);
+    r /= NG;
+    int j = (int)(r % (g.n2 + 2 * NG)) - NG, i = (int)(r / (g.n2 + 2 * NG)) - NG;
+    int bc = g.metric == KERR_MKS ? BC_PERIODIC : g.bc3;
+    int kd = side == 0 ? -gh : g.n3 - 1 + gh;
+    int ks = bc == BC_PERIODIC ? wrapi(kd, g.n3) : (side == 0 ? 0 : g.n3 - 1);
+    long long zs = zidx(g, i, j, ks), zd = zidx(g, i, j, kd);
+#pragma unroll
+    for (int c = 0; c < NP; c++) P[c * g.nz + zd] = P[c * g.nz + zs];
+}
+
+// ------------------------------------------------------------- face fluxes
+
+template <typename R>
+__device__ __forceinline__ const Geo<R> *face_table(const Grid &g, int d);
+template <>
+__device__ __forceinline__ const Geo<double> *face_table<double>(const Grid &g, int d)
+{
+    return d == 1 ? g.gf1 : (d == 2 ? g.gf2 : g.gc);
+}
+template <>
+__device__ __forceinline__ const Geo<float> *face_table<float>(const Grid &g, int d)
+{
+    return d == 1 ? g.gf1F : (d == 2 ? g.gf2F : g.gcF);
+}
+
+// Face (i,j,k) of direction D lies between zone index-1 and index along D.
+// Returns the CFL candidate cfl dX^D / c_w of an active face (else +inf).
+template <typename R, int D>
+__device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                            const Box &box, int want_dt, long long t)
+{
+    double dtc = INFINITY;
+    if (t >= box.count()) return dtc;
+    int i, j, k;
+    box_decode(box, t, i, j, k);
+    long long z = zidx(g, i, j, k);
+    R out[NU];
+    R cw = R(0);
+    bool polar = (D == 2) && g.polar2[midx(g, i, j)];
+    if (polar) {
+#pragma unroll
+        for (int c = 0; c < NU; c++) out[c] = R(0);
+    } else {
+        const long long st = D == 1 ? (long long)g.N2 * g.N3 : (D == 2 ? g.N3 : 1);
+        R ql[NP], qr[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const R *pc = P + c * g.nz + z;
+            R qm2 = ldg(pc - 2 * st), qm1 = ldg(pc - st), q0 = ldg(pc), qp1 = ldg(pc + st);
+            ql[c] = qm1 + R(0.5) * mc_slope(qm2, qm1, q0);
+            qr[c] = q0 - R(0.5) * mc_slope(qm1, q0, qp1);
+        }
+        const Geo<R> geo = face_table<R>(g, D)[midx(g, i, j)];
+        St<R> sl, sr;
+        get_state(ql, geo, sl);
+        get_state(qr, geo, sr);
+        R gam = (R)g.gam;
+        R c1l, c2l, c1r, c2r;
+        wave_speeds(ql, geo, sl, gam, D, c1l, c2l);
+        wave_speeds(qr, geo, sr, gam, D, c1r, c2r);
+        R cmax = fabs(fmax(R(0), fmax(c1r, c1l)));
+        R cmin = fabs(fmax(R(0), fmax(-c2r, -c2l)));
+        cw = fmax(cmax, cmin);
+        R wlF, wlU, wrF, wrU;
+        if (g.riemann == 1 && cmax + cmin > R(0)) {
+            R inv = R(1) / (cmax + cmin);
+            wlF = cmax * inv;
+            wrF = cmin * inv;
+            wlU = cmax * cmin * inv;
+            wrU = -wlU;
+        } else if (g.riemann == 1) {
+            wlF = wrF = R(0.5);
+            wlU = wrU = R(0);
+        } else {
+            wlF = wrF = R(0.5);
+            wlU = R(0.5) * cw;
+            wrU = -wlU;
+        }
+        constexpr bool RMS = sizeof(R) == 4;
+        R Ux[NU], Fx[NU];
+        prim_to_UF2<R, RMS>(ql, geo, sl, gam, D, Ux, Fx);
+#pragma unroll
+        for (int c = 0; c < NU; c++) out[c] = wlF * Fx[c] + wlU * Ux[c];
+        prim_to_UF2<R, RMS>(qr, geo, sr, gam, D, Ux, Fx);
+#pragma unroll
+        for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NU; c++) F[c * g.nz + z] = out[c];
+    if (want_dt) {
+        int ix[3] = {i, j, k}, nn[3] = {g.n1, g.n2, g.n3};
+        bool act = true;
+#pragma unroll
+        for (int e = 0; e < 3; e++) act = act && ix[e] >= 0 && ix[e] < nn[e] + (e == D - 1 ? 1 : 0);
+        if (act && cw > R(0)) dtc = g.cfl * g.dx[D - 1] / (double)cw;
+    }
+    return dtc;
+}
+
+// -------------------------------------------------------------------- EMFs
+
+// E3 at (i-1/2, j-1/2, k), E1 at (i, j-1/2, k-1/2), E2 at (i-1/2, j, k-1/2) (Eq. 22)
+template <typename R>
+__device__ __forceinline__ void emf_item(const Grid &g, const R *__restrict__ F1, const R *__restrict__ F2,
+                                         const R *__restrict__ F3, R *E1, R *E2, R *E3, const Box &box,
+                                         long long t)
+{
+    if (t >= box.count()) return;
+    int i, j, k;
+    box_decode(box, t, i, j, k);
+    const long long nz = g.nz;
+    long long z = zidx(g, i, j, k);
+    long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
+    if (k < g.n3)
+        E3[z] = R(0.25) * (F1[KB2 * nz + z] + F1[KB2 * nz + z - sj] - F2[KB1 * nz + z] - F2[KB1 * nz + z - si]);
+    if (i < g.n1)
+        E1[z] = R(0.25) * (F2[KB3 * nz + z] + F2[KB3 * nz + z - sk] - F3[KB2 * nz + z] - F3[KB2 * nz + z - sj]);
+    if (j < g.n2)
+        E2[z] = R(0.25) * (F3[KB1 * nz + z] + F3[KB1 * nz + z - si] - F1[KB3 * nz + z] - F1[KB3 * nz + z - sk]);
+}
+
+// --------------------------------------------------------- update + invert
+
+constexpr int NHZ = 4; // zones next to the horizon that keep the FP64 source in the mixed path
+
+// per-thread counters of update_item: Newton iterations, methods, failures,
+// floor/ceiling/cap hits
+struct UpdCount {
+    unsigned it, nr, br, en, eb, fail, fl, ce, gc;
+};
+
+template <typename R>
+__device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *__restrict__ Pout,
+                                   const R *__restrict__ F1, const R *__restrict__ F2,
+                                   const R *__restrict__ F3, const R *__restrict__ E1,
+                                   const R *__restrict__ E2, const R *__restrict__ E3, double dtfac, int corr,
+                                   long long t, UpdCount &cn)
+{
+    long long nact = nact_of(g);
+    if (t >= nact) return;
+    int k = (int)(t % g.n3);
+    long long r = t / g.n3;
+    int j = (int)(r % g.n2), i = (int)(r / g.n2);
+    const long long nz = g.nz;
+    long long z = zidx(g, i, j, k);
+    int m = midx(g, i, j);
+    const long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
+    const double dts = dtfac * g.scal[0];
+    double q[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) q[c] = (double)Pin[c * nz + z];
+    const Geo<double> geo = g.gc[m];
+    // source (Eq. 15)
+    double src[4];
+    if (sizeof(R) == 8 || i < g.i_h + NHZ) {
+        St<double> s;
+        get_state(q, geo, s);
+        source_terms(q, geo, g.conn + (long long)m * 40, s, g.gam, src);
+    } else {
+        const Geo<float> gf = g.gcF[m];
+        float qf[NP], sf[4];
+#pragma unroll
+        for (int c = 0; c < NP; c++) qf[c] = (float)Pin[c * nz + z];
+        St<float> s;
+        get_state(qf, gf, s);
+        source_terms(qf, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
+#pragma unroll
+        for (int c = 0; c < 4; c++) src[c] = sf[c];
+    }
+    // flux divergence; B components from the flux-CT edge averages (Eq. 23),
+    // formed exactly as the replaced face values.  The mixed path takes the
+    // divergence in FP32 (the fluxes' own precision) and converts each
+    // component once before the FP64 accumulation; the mass divergence is
+    // added back to the rest-mass-subtracted energy in FP64 so that U_E and
+    // U_rho see the same rounded mass flux.
+    double Un[NU];
+    {
+        typedef R T;
+        const T ix1 = (T)g.idx[0], ix2 = (T)g.idx[1], ix3 = (T)g.idx[2];
+        T dv[NU];
+#pragma unroll
+        for (int c = 0; c < NU; c++) {
+            if (c >= KB1 && c <= KB3) continue;
+            const long long o = c * nz + z;
+            T d1 = (F1[o + si] - F1[o]) * ix1;
+            T d2 = (F2[o + sj] - F2[o]) * ix2;
+            T d3 = (F3[o + sk] - F3[o]) * ix3;
+            dv[c] = d1 + d2 + d3;
+        }
+        T f2b1_j = T(-0.5) * (E3[z + si] + E3[z]);
+        T f2b1_jp = T(-0.5) * (E3[z + si + sj] + E3[z + sj]);
+        T f3b1_k = T(0.5) * (E2[z + si] + E2[z]);
+        T f3b1_kp = T(0.5) * (E2[z + si + sk] + E2[z + sk]);
+        T f1b2_i = T(0.5) * (E3[z + sj] + E3[z]);
+        T f1b2_ip = T(0.5) * (E3[z + si + sj] + E3[z + si]);
+        T f3b2_k = T(-0.5) * (E1[z + sj] + E1[z]);
+        T f3b2_kp = T(-0.5) * (E1[z + sj + sk] + E1[z + sk]);
+        T f1b3_i = T(-0.5) * (E2[z + sk] + E2[z]);
+        T f1b3_ip = T(-0.5) * (E2[z + si + sk] + E2[z + si]);
+        T f2b3_j = T(0.5) * (E1[z + sk] + E1[z]);
+        T f2b3_jp = T(0.5) * (E1[z + sj + sk] + E1[z + sj]);
+        dv[KB1] = (f2b1_jp - f2b1_j) * ix2 + (f3b1_kp - f3b1_k) * ix3;
+        dv[KB2] = (f1b2_ip - f1b2_i) * ix1 + (f3b2_kp - f3b2_k) * ix3;
+        dv[KB3] = (f1b3_ip - f1b3_i) * ix1 + (f2b3_jp - f2b3_j) * ix2;
+        double dD = (double)dv[KRHO];
+#pragma unroll
+        for (int c = 0; c < NU; c++) {
+            double rhs = -(double)dv[c];
+            if (c == 1 && sizeof(R) == 4) rhs += dD; // rest-mass-subtracted energy flux
+            if (c >= 1 && c <= 4) rhs += src[c - 1];
+            Un[c] = g.U[c * nz + z] + dts * rhs;
+        }
+    }
+    double qn[NP];
+    int it;
+    constexpr bool MX = sizeof(R) == 4;
+    const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
+    int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it, 0.0,
+                          gfr);
+    cn.it += it;
+    int meth = fl & 7;
+    if (fl & C2P_FAIL) {
+        cn.fail += 1;
+        g.flag[z] = 1;
+        int slot = atomicAdd(g.nfail, 1);
+        if (slot < g.nfix_cap) g.faillist[slot] = (int)t;
+    } else {
+        g.flag[z] = 0;
+        cn.nr += meth == C2P_NR;
+        cn.br += meth == C2P_BRENT_W;
+        cn.en += meth == C2P_ENTROPY;
+        cn.eb += meth == C2P_ENTROPY_BETA;
+        int res = post_inversion<MX>(g, geo, qn, Un, gfr);
+        if (res & 1) {
+            cn.fl += 1;
+            cons_of<MX>(qn, geo, g.gam, Un, gfr);
+        }
+        cn.ce += (res & 2) != 0;
+        cn.gc += (res & 4) != 0;
+    }
+#pragma unroll
+    for (int c = 0; c < NP; c++) Pout[c * nz + z] = (R)qn[c];
+    if (corr) {
+#pragma unroll
+        for (int c = 0; c < NU; c++) g.U[c * nz + z] = Un[c];
+    }
+}
+
+__device__ __forceinline__ void flush_counts(const Grid &g, const UpdCount &cn)
+{
+    block_count(&g.cnt[C_NR_ITERS], cn.it);
+    block_count(&g.cnt[C_NR], cn.nr);
+    block_count(&g.cnt[C_BRENT], cn.br);
+    block_count(&g.cnt[C_ENT], cn.en);
+    block_count(&g.cnt[C_ENT_BETA], cn.eb);
+    block_count(&g.cnt[C_FAIL], cn.fail);
+    block_count(&g.cnt[C_FLOOR], cn.fl);
+    block_count(&g.cnt[C_CEIL], cn.ce);
+    block_count(&g.cnt[C_GCAP], cn.gc);
+}
+
+// ------------------------------------------------------------------ fixups
+
+// One block walks the compacted list of failed zones of one grid.  Each
+// sweep first computes every repairable zone's average from neighbours that
+// were good at the start of the sweep, then writes them (Jacobi), so the
+// result does not depend on the list order.  Every thread of the block calls it.
+template <typename R>
+__device__ inline void fixup_block(const Grid &g, R *P, int corr)
+{
+    __shared__ int s_left;
+    const int nlist = min(*g.nfail, g.nfix_cap);
+    if (nlist == 0) return;
+    const long long nz = g.nz;
+    const int cap = g.nfix_cap;
+    double *nb = g.fixbuf;            // [5][cap]
+    double *found = g.fixbuf + 5LL * cap;
+    int sweep = 0;
+    for (; sweep < g.fix_maxsweep; sweep++) {
+        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+            int t = g.faillist[a];
+            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
+            found[a] = 0.0;
+            if (!g.flag[zidx(g, i, j, k)]) continue;
+            const int fo[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+            const int dg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
+            bool done = false;
+            for (int s = 0; s < 2 && !done; s++) {
+                const int(*set)[2] = s == 0 ? fo : dg;
+                bool all = true;
+                for (int mm = 0; mm < 4; mm++) {
+                    int ii = i + set[mm][0], jj = j + set[mm][1];
+                    if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2 || g.flag[zidx(g, ii, jj, k)]) all = false;
+                }
+                if (all) {
+                    for (int c = 0; c < 5; c++) {
+                        double acc = 0.0;
+                        for (int mm = 0; mm < 4; mm++)
+                            acc += (double)P[c * nz + zidx(g, i + set[mm][0], j + set[mm][1], k)];
+                        nb[(long long)c * cap + a] = 0.25 * acc;
+                    }
+                    done = true;
+                }
+            }
+            if (!done) {
+                int cnt = 0;
+                double acc[5] = {0, 0, 0, 0, 0};
+                for (int s = 0; s < 2; s++)
+                    for (int mm = 0; mm < 4; mm++) {
+                        int ii = i + (s ? dg : fo)[mm][0], jj = j + (s ? dg : fo)[mm][1];
+                        if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2) continue;
+                        long long zz = zidx(g, ii, jj, k);
+                        if (g.flag[zz]) continue;
+                        for (int c = 0; c < 5; c++) acc[c] += (double)P[c * nz + zz];
+                        cnt++;
+                    }
+                if (cnt > 0) {
+                    for (int c = 0; c < 5; c++) nb[(long long)c * cap + a] = acc[c] / cnt;
+                    done = true;
+                }
+            }
+            if (done) found[a] = 1.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_left = 0;
+        __syncthreads();
+        int left = 0;
+        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+            int t = g.faillist[a];
+            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
+            long long z = zidx(g, i, j, k);
+            if (found[a] != 0.0) {
+                int m = midx(g, i, j);
+                const Geo<double> geo = g.gc[m];
+                double q[NP];
+                for (int c = 0; c < NP; c++) q[c] = c < 5 ? nb[(long long)c * cap + a] : (double)P[c * nz + z];
+                post_fixup(g, geo, q);
+                for (int c = 0; c < NP; c++) P[c * nz + z] = (R)q[c];
+                if (corr) {
+                    St<double> s;
+                    get_state(q, geo, s);
+                    double Uz[NU];
+                    prim_to_UF<double, false>(q, geo, s, g.gam, 0, Uz);
+                    for (int c = 0; c < NU; c++) g.U[c * nz + z] = Uz[c];
+                }
+                g.flag[z] = 0;
+                atomicAdd(&g.cnt[C_FIXED], 1ULL);
+            } else if (g.flag[z]) {
+                left++;
+            }
+        }
+        __syncthreads(); // all flag writes of this sweep done before the next reads
+        if (left) atomicAdd(&s_left, left);
+        __syncthreads();
+        if (s_left == 0) {
+            sweep++;
+            break;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&g.cnt[C_SWEEPS], (unsigned long long)sweep);
+        if (s_left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
+        *g.nfail = 0;
+    }
+}
+
+// ----------------------------------------------------- FP64 out-of-line calls
+// The FP64 items are compiled out of line and called from both the
+// single-grid and the ensemble kernels, so both run the same machine code:
+// inlined into different kernels the compiler may contract or schedule the
+// FP64 arithmetic differently and the two paths would differ in the last
+// bit.  The FP32-flux path is inlined (its two instantiations already agree).
+
+static __device__ __noinline__ double flux_item_d1(const Grid &g, const double *P, double *F, const Box &box, int w,
+                                            long long t)
+{
+    return flux_item<double, 1>(g, P, F, box, w, t);
+}
+static __device__ __noinline__ double flux_item_d2(const Grid &g, const double *P, double *F, const Box &box, int w,
+                                            long long t)
+{
+    return flux_item<double, 2>(g, P, F, box, w, t);
+}
+static __device__ __noinline__ double flux_item_d3(const Grid &g, const double *P, double *F, const Box &box, int w,
+                                            long long t)
+{
+    return flux_item<double, 3>(g, P, F, box, w, t);
+}
+static __device__ __noinline__ void update_item_d(const Grid &g, const double *Pin, double *Pout, const double *F1,
+                                           const double *F2, const double *F3, const double *E1,
+                                           const double *E2, const double *E3, double dtfac, int corr,
+                                           long long t, UpdCount &cn)
+{
+    update_item<double>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+}
+static __device__ __noinline__ void bc1_item_d(const Grid &g, double *P, long long t) { bc1_item<double>(g, P, t); }
+static __device__ __noinline__ void fixup_block_d(const Grid &g, double *P, int corr) { fixup_block<double>(g, P, corr); }
+
+template <typename R, int D>
+__device__ __forceinline__ double flux_call(const Grid &g, const R *P, R *F, const Box &box, int w, long long t)
+{
+    if constexpr (sizeof(R) == 8) {
+        if constexpr (D == 1) return flux_item_d1(g, P, F, box, w, t);
+        else if constexpr (D == 2) return flux_item_d2(g, P, F, box, w, t);
+        else return flux_item_d3(g, P, F, box, w, t);
+    } else {
+        return flux_item<R, D>(g, P, F, box, w, t);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void update_call(const Grid &g, const R *Pin, R *Pout, const R *F1, const R *F2,
+                                            const R *F3, const R *E1, const R *E2, const R *E3, double dtfac,
+                                            int corr, long long t, UpdCount &cn)
+{
+    if constexpr (sizeof(R) == 8) update_item_d(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+    else update_item<R>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+}
+
+template <typename R>
+__device__ __forceinline__ void bc1_call(const Grid &g, R *P, long long t)
+{
+    if constexpr (sizeof(R) == 8) bc1_item_d(g, P, t);
+    else bc1_item<R>(g, P, t);
+}
+
+template <typename R>
+__device__ __forceinline__ void fixup_call(const Grid &g, R *P, int corr)
+{
+    if constexpr (sizeof(R) == 8) fixup_block_d(g, P, corr);
+    else fixup_block<R>(g, P, corr);
+}
+
+// --------------------------------------------------------------------- dt
+
+// 1/dt = sum_l 1/dt^l (Eq. 27); t += dt for a finished step; minima reset.
+__device__ inline void finalize_one(const Grid &g, int advance)
+{
+    double inv = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double v = __longlong_as_double((long long)g.dtmin[d]);
+        if (v < INFINITY) inv += 1.0 / v;
+        g.dtmin[d] = dbits(INFINITY);
+    }
+    if (advance) {
+        g.scal[1] += g.scal[0];
+        g.cnt[C_STEPS] += 1;
+    }
+    g.scal[0] = inv > 0.0 ? 1.0 / inv : INFINITY;
+}
+
+} // namespace grmhd

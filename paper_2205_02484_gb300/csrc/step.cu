@@ -1,314 +1,54 @@
-// step.cu -- kernels of one RK2 stage of the conservative GR-MHD scheme.
+// step.cu -- single-grid kernels of the RK2 step and their launch sequence.
 //
-//   boundary fill (Section 4.1)  -> k_polar, k_bc1, k_bc2, k_bc3
-//   face fluxes (Eqs. 16-21)     -> k_flux<D>: PLM-MC face states, U and F of
-//                                   both states, LLF/HLL, c_w, and the CFL
-//                                   minimum of Eq. 27 (warp-shuffle reduction)
-//   flux-CT EMFs (Eq. 22)        -> k_emf
-//   update + inversion           -> k_update: flux divergence with the flux-CT
-//                                   B-fluxes of Eq. 23 formed from the EMFs,
-//                                   connection source (Eq. 15), RK2 stage update
-//                                   (Eqs. 25-26) with FP64 accumulation, FP64
-//                                   inversion (Section 2.3), floors/ceilings/cap
-//                                   (Section 2.4); failed zones are compacted
-//   fixups (Eq. 33)              -> k_fixup: Jacobi sweeps over the compacted list
-//   dt                           -> k_finalize
-//
-// R is the flux arithmetic type (double, or float in the mixed path); RS the
-// primitive storage type (the same as R).
-#include "fixes.cuh"
+// Each kernel maps one thread to one element of one grid and runs the item
+// function of stage_items.cuh; the fluxes reduce the CFL candidates of a
+// block with warp shuffles and one atomic, the update reduces its counters
+// the same way.  A step is 21 launches: per stage three face sweeps, EMFs,
+// update + inversion, fixups, four boundary kernels; then the dt kernel.
 #include "kernels.h"
+#include "stage_items.cuh"
 
 namespace grmhd {
-
-// ----------------------------------------------------------------- helpers
-
-struct Box {
-    int lo[3], n[3];
-    __host__ __device__ long long count() const { return (long long)n[0] * n[1] * n[2]; }
-};
-
-__device__ __forceinline__ void box_decode(const Box &b, long long t, int &i, int &j, int &k)
-{
-    k = (int)(t % b.n[2]);
-    long long r = t / b.n[2];
-    j = (int)(r % b.n[1]);
-    i = (int)(r / b.n[1]);
-    i += b.lo[0];
-    j += b.lo[1];
-    k += b.lo[2];
-}
-
-template <typename T>
-__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
-
-__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
-
-__device__ __forceinline__ double warp_min(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// ------------------------------------------------------------ boundary fill
 
 template <typename RS>
 __global__ void k_polar(Grid g, RS *P)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)g.n1 * g.n3;
-    if (t >= n) return;
-    int i = (int)(t / g.n3), k = (int)(t % g.n3);
-    const long long f = (long long)KU2 * g.nz;
-    RS a = P[f + zidx(g, i, 2, k)], b = P[f + zidx(g, i, g.n2 - 3, k)];
-    P[f + zidx(g, i, 0, k)] = a * RS(0.5 / 2.5);
-    P[f + zidx(g, i, 1, k)] = a * RS(1.5 / 2.5);
-    P[f + zidx(g, i, g.n2 - 1, k)] = b * RS(0.5 / 2.5);
-    P[f + zidx(g, i, g.n2 - 2, k)] = b * RS(1.5 / 2.5);
-}
-
-__device__ __forceinline__ int wrapi(int k, int n) { return ((k % n) + n) % n; }
-
-// u^1 = 0 at fixed ut^2, ut^3: ut^1 = Gamma alpha g^{t1}, Gamma from its quadratic
-__device__ void zero_radial_velocity(const Geo<double> &geo, double q[NP])
-{
-    double c = geo.alpha * geo.gcon[1];
-    double a2 = 1.0 - geo.gcov[4] * c * c;
-    if (!(a2 > 0.0)) return;
-    double b = -2.0 * c * (geo.gcov[5] * q[KU2] + geo.gcov[6] * q[KU3]);
-    double rest = geo.gcov[7] * q[KU2] * q[KU2] + 2.0 * geo.gcov[8] * q[KU2] * q[KU3] +
-                  geo.gcov[9] * q[KU3] * q[KU3];
-    double cc = -(1.0 + rest);
-    double disc = b * b - 4.0 * a2 * cc;
-    double gm = (-b + sqrt(disc)) / (2.0 * a2);
-    q[KU1] = gm * c;
+    polar_item(g, P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 template <typename RS>
 __global__ void k_bc1(Grid g, RS *P)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)g.n2 * g.n3 * NG * 2;
-    if (t >= n) return;
-    int side = (int)(t % 2);
-    long long r = t / 2;
-    int gh = 1 + (int)(r % NG);
-    r /= NG;
-    int k = (int)(r % g.n3), j = (int)(r / g.n3);
-    int bc = g.metric == KERR_MKS ? BC_INFLOW : g.bc1;
-    int id = side == 0 ? -gh : g.n1 - 1 + gh;
-    int is;
-    if (bc == BC_PERIODIC) is = wrapi(id, g.n1);
-    else is = side == 0 ? 0 : g.n1 - 1;
-    long long zs = zidx(g, is, j, k), zd = zidx(g, id, j, k);
-    if (bc != BC_INFLOW) {
-#pragma unroll
-        for (int c = 0; c < NP; c++) P[c * g.nz + zd] = P[c * g.nz + zs];
-        return;
-    }
-    double q[NP];
-#pragma unroll
-    for (int c = 0; c < NP; c++) q[c] = (double)P[c * g.nz + zs];
-    Geo<double> geo = g.gc[midx(g, id, j)];
-    St<double> s;
-    get_state(q, geo, s);
-    if ((side == 0 && s.ucon[1] > 0.0) || (side == 1 && s.ucon[1] < 0.0)) zero_radial_velocity(geo, q);
-#pragma unroll
-    for (int c = 0; c < NP; c++) P[c * g.nz + zd] = (RS)q[c];
+    bc1_call(g, P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 template <typename RS>
 __global__ void k_bc2(Grid g, RS *P)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)(g.n1 + 2 * NG) * g.n3 * NG * 2;
-    if (t >= n) return;
-    int side = (int)(t % 2);
-    long long r = t / 2;
-    int gh = 1 + (int)(r % NG);
-    r /= NG;
-    int k = (int)(r % g.n3), i = (int)(r / g.n3) - NG;
-    int bc = g.metric == KERR_MKS ? BC_POLAR : g.bc2;
-    int jd = side == 0 ? -gh : g.n2 - 1 + gh;
-    int js;
-    bool flip = false;
-    if (bc == BC_POLAR) {
-        js = side == 0 ? gh - 1 : g.n2 - gh;
-        flip = true;
-    } else if (bc == BC_PERIODIC) {
-        js = wrapi(jd, g.n2);
-    } else {
-        js = side == 0 ? 0 : g.n2 - 1;
-    }
-    long long zs = zidx(g, i, js, k), zd = zidx(g, i, jd, k);
-#pragma unroll
-    for (int c = 0; c < NP; c++) {
-        RS v = P[c * g.nz + zs];
-        if (flip && (c == KU2 || c == KB2)) v = -v;
-        P[c * g.nz + zd] = v;
-    }
+    bc2_item(g, P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 template <typename RS>
 __global__ void k_bc3(Grid g, RS *P)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long n = (long long)(g.n1 + 2 * NG) * (g.n2 + 2 * NG) * NG * 2;
-    if (t >= n) return;
-    int side = (int)(t % 2);
-    long long r = t / 2;
-    int gh = 1 + (int)(r % NG);
-    r /= NG;
-    int j = (int)(r % (g.n2 + 2 * NG)) - NG, i = (int)(r / (g.n2 + 2 * NG)) - NG;
-    int bc = g.metric == KERR_MKS ? BC_PERIODIC : g.bc3;
-    int kd = side == 0 ? -gh : g.n3 - 1 + gh;
-    int ks = bc == BC_PERIODIC ? wrapi(kd, g.n3) : (side == 0 ? 0 : g.n3 - 1);
-    long long zs = zidx(g, i, j, ks), zd = zidx(g, i, j, kd);
-#pragma unroll
-    for (int c = 0; c < NP; c++) P[c * g.nz + zd] = P[c * g.nz + zs];
+    bc3_item(g, P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
-// ------------------------------------------------------------- face fluxes
-
-template <typename R>
-__device__ __forceinline__ const Geo<R> *face_table(const Grid &g, int d);
-template <>
-__device__ __forceinline__ const Geo<double> *face_table<double>(const Grid &g, int d)
-{
-    return d == 1 ? g.gf1 : (d == 2 ? g.gf2 : g.gc);
-}
-template <>
-__device__ __forceinline__ const Geo<float> *face_table<float>(const Grid &g, int d)
-{
-    return d == 1 ? g.gf1F : (d == 2 ? g.gf2F : g.gcF);
-}
-
-// Face (i,j,k) of direction D lies between zone index-1 and index along D.
 template <typename R, int D>
 __global__ void __launch_bounds__(128) k_flux(Grid g, const R *__restrict__ P, R *__restrict__ F,
                                               Box box, int want_dt)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double dtc = INFINITY;
-    if (t < box.count()) {
-        int i, j, k;
-        box_decode(box, t, i, j, k);
-        long long z = zidx(g, i, j, k);
-        R out[NU];
-        R cw = R(0);
-        bool polar = (D == 2) && g.polar2[midx(g, i, j)];
-        if (polar) {
-#pragma unroll
-            for (int c = 0; c < NU; c++) out[c] = R(0);
-        } else {
-            const long long st = D == 1 ? (long long)g.N2 * g.N3 : (D == 2 ? g.N3 : 1);
-            R ql[NP], qr[NP];
-#pragma unroll
-            for (int c = 0; c < NP; c++) {
-                const R *pc = P + c * g.nz + z;
-                R qm2 = ldg(pc - 2 * st), qm1 = ldg(pc - st), q0 = ldg(pc), qp1 = ldg(pc + st);
-                ql[c] = qm1 + R(0.5) * mc_slope(qm2, qm1, q0);
-                qr[c] = q0 - R(0.5) * mc_slope(qm1, q0, qp1);
-            }
-            const Geo<R> geo = face_table<R>(g, D)[midx(g, i, j)];
-            St<R> sl, sr;
-            get_state(ql, geo, sl);
-            get_state(qr, geo, sr);
-            R gam = (R)g.gam;
-            R c1l, c2l, c1r, c2r;
-            wave_speeds(ql, geo, sl, gam, D, c1l, c2l);
-            wave_speeds(qr, geo, sr, gam, D, c1r, c2r);
-            R cmax = fabs(fmax(R(0), fmax(c1r, c1l)));
-            R cmin = fabs(fmax(R(0), fmax(-c2r, -c2l)));
-            cw = fmax(cmax, cmin);
-            R wlF, wlU, wrF, wrU;
-            if (g.riemann == 1 && cmax + cmin > R(0)) {
-                R inv = R(1) / (cmax + cmin);
-                wlF = cmax * inv;
-                wrF = cmin * inv;
-                wlU = cmax * cmin * inv;
-                wrU = -wlU;
-            } else if (g.riemann == 1) {
-                wlF = wrF = R(0.5);
-                wlU = wrU = R(0);
-            } else {
-                wlF = wrF = R(0.5);
-                wlU = R(0.5) * cw;
-                wrU = -wlU;
-            }
-            constexpr bool RMS = sizeof(R) == 4;
-            R Ux[NU], Fx[NU];
-            prim_to_UF2<R, RMS>(ql, geo, sl, gam, D, Ux, Fx);
-#pragma unroll
-            for (int c = 0; c < NU; c++) out[c] = wlF * Fx[c] + wlU * Ux[c];
-            prim_to_UF2<R, RMS>(qr, geo, sr, gam, D, Ux, Fx);
-#pragma unroll
-            for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
-        }
-#pragma unroll
-        for (int c = 0; c < NU; c++) F[c * g.nz + z] = out[c];
-        if (want_dt) {
-            int ix[3] = {i, j, k}, nn[3] = {g.n1, g.n2, g.n3};
-            bool act = true;
-#pragma unroll
-            for (int e = 0; e < 3; e++) act = act && ix[e] >= 0 && ix[e] < nn[e] + (e == D - 1 ? 1 : 0);
-            if (act && cw > R(0)) dtc = g.cfl * g.dx[D - 1] / (double)cw;
-        }
-    }
-    if (want_dt) {
-        dtc = warp_min(dtc);
-        __shared__ double sm[32];
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (lane == 0) sm[w] = dtc;
-        __syncthreads();
-        if (w == 0) {
-            double v = lane < (blockDim.x >> 5) ? sm[lane] : INFINITY;
-            v = warp_min(v);
-            if (lane == 0 && v < INFINITY) atomicMin(&g.dtmin[D - 1], dbits(v));
-        }
-    }
+    double dtc = flux_call<R, D>(g, P, F, box, want_dt, t);
+    if (want_dt) block_min_into(&g.dtmin[D - 1], dtc);
 }
 
-// -------------------------------------------------------------------- EMFs
-
-// E3 at (i-1/2, j-1/2, k), E1 at (i, j-1/2, k-1/2), E2 at (i-1/2, j, k-1/2) (Eq. 22)
 template <typename R>
 __global__ void k_emf(Grid g, const R *__restrict__ F1, const R *__restrict__ F2,
                       const R *__restrict__ F3, R *E1, R *E2, R *E3, Box box)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= box.count()) return;
-    int i, j, k;
-    box_decode(box, t, i, j, k);
-    const long long nz = g.nz;
-    long long z = zidx(g, i, j, k);
-    long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
-    if (k < g.n3)
-        E3[z] = R(0.25) * (F1[KB2 * nz + z] + F1[KB2 * nz + z - sj] - F2[KB1 * nz + z] - F2[KB1 * nz + z - si]);
-    if (i < g.n1)
-        E1[z] = R(0.25) * (F2[KB3 * nz + z] + F2[KB3 * nz + z - sk] - F3[KB2 * nz + z] - F3[KB2 * nz + z - sj]);
-    if (j < g.n2)
-        E2[z] = R(0.25) * (F3[KB1 * nz + z] + F3[KB1 * nz + z - si] - F1[KB3 * nz + z] - F1[KB3 * nz + z - sk]);
+    emf_item(g, F1, F2, F3, E1, E2, E3, box, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
-
-// --------------------------------------------------------- update + invert
-
-__device__ __forceinline__ void block_count(unsigned long long *dst, unsigned v)
-{
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, (unsigned long long)v);
-}
-
-constexpr int NHZ = 4; // zones next to the horizon that keep the FP64 source in the mixed path
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_update(Grid g, const R *__restrict__ Pin, R *__restrict__ Pout,
@@ -317,251 +57,22 @@ __global__ void __launch_bounds__(128) k_update(Grid g, const R *__restrict__ Pi
                                                 const R *__restrict__ E2, const R *__restrict__ E3,
                                                 double dtfac, int corr)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long nact = (long long)g.n1 * g.n2 * g.n3;
-    unsigned c_it = 0, c_nr = 0, c_br = 0, c_en = 0, c_eb = 0, c_fail = 0, c_fl = 0, c_ce = 0, c_gc = 0;
-    if (t < nact) {
-        int k = (int)(t % g.n3);
-        long long r = t / g.n3;
-        int j = (int)(r % g.n2), i = (int)(r / g.n2);
-        const long long nz = g.nz;
-        long long z = zidx(g, i, j, k);
-        int m = midx(g, i, j);
-        const long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
-        const double dts = dtfac * g.scal[0];
-        double q[NP];
-#pragma unroll
-        for (int c = 0; c < NP; c++) q[c] = (double)Pin[c * nz + z];
-        const Geo<double> geo = g.gc[m];
-        // source (Eq. 15)
-        double src[4];
-        if (sizeof(R) == 8 || i < g.i_h + NHZ) {
-            St<double> s;
-            get_state(q, geo, s);
-            source_terms(q, geo, g.conn + (long long)m * 40, s, g.gam, src);
-        } else {
-            const Geo<float> gf = g.gcF[m];
-            float qf[NP], sf[4];
-#pragma unroll
-            for (int c = 0; c < NP; c++) qf[c] = (float)Pin[c * nz + z];
-            St<float> s;
-            get_state(qf, gf, s);
-            source_terms(qf, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
-#pragma unroll
-            for (int c = 0; c < 4; c++) src[c] = sf[c];
-        }
-        // flux divergence; B components from the flux-CT edge averages (Eq. 23),
-        // formed exactly as the replaced face values.  The mixed path takes the
-        // divergence in FP32 (the fluxes' own precision) and converts each
-        // component once before the FP64 accumulation; the mass divergence is
-        // added back to the rest-mass-subtracted energy in FP64 so that U_E and
-        // U_rho see the same rounded mass flux.
-        double Un[NU];
-        {
-            typedef R T;
-            const T ix1 = (T)g.idx[0], ix2 = (T)g.idx[1], ix3 = (T)g.idx[2];
-            T dv[NU];
-#pragma unroll
-            for (int c = 0; c < NU; c++) {
-                if (c >= KB1 && c <= KB3) continue;
-                const long long o = c * nz + z;
-                T d1 = (F1[o + si] - F1[o]) * ix1;
-                T d2 = (F2[o + sj] - F2[o]) * ix2;
-                T d3 = (F3[o + sk] - F3[o]) * ix3;
-                dv[c] = d1 + d2 + d3;
-            }
-            T f2b1_j = T(-0.5) * (E3[z + si] + E3[z]);
-            T f2b1_jp = T(-0.5) * (E3[z + si + sj] + E3[z + sj]);
-            T f3b1_k = T(0.5) * (E2[z + si] + E2[z]);
-            T f3b1_kp = T(0.5) * (E2[z + si + sk] + E2[z + sk]);
-            T f1b2_i = T(0.5) * (E3[z + sj] + E3[z]);
-            T f1b2_ip = T(0.5) * (E3[z + si + sj] + E3[z + si]);
-            T f3b2_k = T(-0.5) * (E1[z + sj] + E1[z]);
-            T f3b2_kp = T(-0.5) * (E1[z + sj + sk] + E1[z + sk]);
-            T f1b3_i = T(-0.5) * (E2[z + sk] + E2[z]);
-            T f1b3_ip = T(-0.5) * (E2[z + si + sk] + E2[z + si]);
-            T f2b3_j = T(0.5) * (E1[z + sk] + E1[z]);
-            T f2b3_jp = T(0.5) * (E1[z + sj + sk] + E1[z + sj]);
-            dv[KB1] = (f2b1_jp - f2b1_j) * ix2 + (f3b1_kp - f3b1_k) * ix3;
-            dv[KB2] = (f1b2_ip - f1b2_i) * ix1 + (f3b2_kp - f3b2_k) * ix3;
-            dv[KB3] = (f1b3_ip - f1b3_i) * ix1 + (f2b3_jp - f2b3_j) * ix2;
-            double dD = (double)dv[KRHO];
-#pragma unroll
-            for (int c = 0; c < NU; c++) {
-                double rhs = -(double)dv[c];
-                if (c == 1 && sizeof(R) == 4) rhs += dD; // rest-mass-subtracted energy flux
-                if (c >= 1 && c <= 4) rhs += src[c - 1];
-                Un[c] = g.U[c * nz + z] + dts * rhs;
-            }
-        }
-        double qn[NP];
-        int it;
-        constexpr bool MX = sizeof(R) == 4;
-        const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
-        int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it,
-                              0.0, gfr);
-        c_it = it;
-        int meth = fl & 7;
-        if (fl & C2P_FAIL) {
-            c_fail = 1;
-            g.flag[z] = 1;
-            int slot = atomicAdd(g.nfail, 1);
-            if (slot < g.nfix_cap) g.faillist[slot] = (int)t;
-        } else {
-            g.flag[z] = 0;
-            c_nr = meth == C2P_NR;
-            c_br = meth == C2P_BRENT_W;
-            c_en = meth == C2P_ENTROPY;
-            c_eb = meth == C2P_ENTROPY_BETA;
-            int res = post_inversion<MX>(g, geo, qn, Un, gfr);
-            if (res & 1) {
-                c_fl = 1;
-                cons_of<MX>(qn, geo, g.gam, Un, gfr);
-            }
-            c_ce = (res & 2) != 0;
-            c_gc = (res & 4) != 0;
-        }
-#pragma unroll
-        for (int c = 0; c < NP; c++) Pout[c * nz + z] = (R)qn[c];
-        if (corr) {
-#pragma unroll
-            for (int c = 0; c < NU; c++) g.U[c * nz + z] = Un[c];
-        }
-    }
-    block_count(&g.cnt[C_NR_ITERS], c_it);
-    block_count(&g.cnt[C_NR], c_nr);
-    block_count(&g.cnt[C_BRENT], c_br);
-    block_count(&g.cnt[C_ENT], c_en);
-    block_count(&g.cnt[C_ENT_BETA], c_eb);
-    block_count(&g.cnt[C_FAIL], c_fail);
-    block_count(&g.cnt[C_FLOOR], c_fl);
-    block_count(&g.cnt[C_CEIL], c_ce);
-    block_count(&g.cnt[C_GCAP], c_gc);
+    UpdCount cn{};
+    update_call<R>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr,
+                blockIdx.x * (long long)blockDim.x + threadIdx.x, cn);
+    flush_counts(g, cn);
 }
 
-// ------------------------------------------------------------------ fixups
-
-// One block walks the compacted list of failed zones.  Each sweep first
-// computes every repairable zone's average from neighbours that were good at
-// the start of the sweep, then writes them (Jacobi), so the result does not
-// depend on the list order.
 template <typename R>
 __global__ void __launch_bounds__(1024) k_fixup(Grid g, R *P, int corr)
 {
-    __shared__ int s_left;
-    const int nlist = min(*g.nfail, g.nfix_cap);
-    if (nlist == 0) return;
-    const long long nz = g.nz;
-    const int cap = g.nfix_cap;
-    double *nb = g.fixbuf;            // [5][cap]
-    double *found = g.fixbuf + 5LL * cap;
-    int sweep = 0;
-    for (; sweep < g.fix_maxsweep; sweep++) {
-        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
-            int t = g.faillist[a];
-            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
-            found[a] = 0.0;
-            if (!g.flag[zidx(g, i, j, k)]) continue;
-            const int fo[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
-            const int dg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
-            bool done = false;
-            for (int s = 0; s < 2 && !done; s++) {
-                const int(*set)[2] = s == 0 ? fo : dg;
-                bool all = true;
-                for (int mm = 0; mm < 4; mm++) {
-                    int ii = i + set[mm][0], jj = j + set[mm][1];
-                    if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2 || g.flag[zidx(g, ii, jj, k)]) all = false;
-                }
-                if (all) {
-                    for (int c = 0; c < 5; c++) {
-                        double acc = 0.0;
-                        for (int mm = 0; mm < 4; mm++)
-                            acc += (double)P[c * nz + zidx(g, i + set[mm][0], j + set[mm][1], k)];
-                        nb[(long long)c * cap + a] = 0.25 * acc;
-                    }
-                    done = true;
-                }
-            }
-            if (!done) {
-                int cnt = 0;
-                double acc[5] = {0, 0, 0, 0, 0};
-                for (int s = 0; s < 2; s++)
-                    for (int mm = 0; mm < 4; mm++) {
-                        int ii = i + (s ? dg : fo)[mm][0], jj = j + (s ? dg : fo)[mm][1];
-                        if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2) continue;
-                        long long zz = zidx(g, ii, jj, k);
-                        if (g.flag[zz]) continue;
-                        for (int c = 0; c < 5; c++) acc[c] += (double)P[c * nz + zz];
-                        cnt++;
-                    }
-                if (cnt > 0) {
-                    for (int c = 0; c < 5; c++) nb[(long long)c * cap + a] = acc[c] / cnt;
-                    done = true;
-                }
-            }
-            if (done) found[a] = 1.0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_left = 0;
-        __syncthreads();
-        int left = 0;
-        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
-            int t = g.faillist[a];
-            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
-            long long z = zidx(g, i, j, k);
-            if (found[a] != 0.0) {
-                int m = midx(g, i, j);
-                const Geo<double> geo = g.gc[m];
-                double q[NP];
-                for (int c = 0; c < NP; c++) q[c] = c < 5 ? nb[(long long)c * cap + a] : (double)P[c * nz + z];
-                post_fixup(g, geo, q);
-                for (int c = 0; c < NP; c++) P[c * nz + z] = (R)q[c];
-                if (corr) {
-                    St<double> s;
-                    get_state(q, geo, s);
-                    double Uz[NU];
-                    prim_to_UF<double, false>(q, geo, s, g.gam, 0, Uz);
-                    for (int c = 0; c < NU; c++) g.U[c * nz + z] = Uz[c];
-                }
-                g.flag[z] = 0;
-                atomicAdd(&g.cnt[C_FIXED], 1ULL);
-            } else if (g.flag[z]) {
-                left++;
-            }
-        }
-        __syncthreads(); // all flag writes of this sweep done before the next reads
-        if (left) atomicAdd(&s_left, left);
-        __syncthreads();
-        if (s_left == 0) {
-            sweep++;
-            break;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        atomicAdd(&g.cnt[C_SWEEPS], (unsigned long long)sweep);
-        if (s_left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
-        *g.nfail = 0;
-    }
+    fixup_call(g, P, corr);
 }
 
-// --------------------------------------------------------------------- dt
-
-// 1/dt = sum_l 1/dt^l (Eq. 27); t += dt for a finished step; minima reset.
 __global__ void k_finalize(Grid g, int advance)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double inv = 0.0;
-    for (int d = 0; d < 3; d++) {
-        double v = __longlong_as_double((long long)g.dtmin[d]);
-        if (v < INFINITY) inv += 1.0 / v;
-        g.dtmin[d] = dbits(INFINITY);
-    }
-    if (advance) {
-        g.scal[1] += g.scal[0];
-        g.cnt[C_STEPS] += 1;
-    }
-    g.scal[0] = inv > 0.0 ? 1.0 / inv : INFINITY;
+    finalize_one(g, advance);
 }
 
 // ------------------------------------------------------------------ launch
@@ -572,47 +83,14 @@ template <typename R>
 static void fill_bc(const Grid &g, R *P, cudaStream_t s)
 {
     const int T = 128;
-    if (g.metric == KERR_MKS && g.n2 >= 6) {
-        long long n = (long long)g.n1 * g.n3;
-        k_polar<R><<<nblk(n, T), T, 0, s>>>(g, P);
-    }
-    k_bc1<R><<<nblk((long long)g.n2 * g.n3 * NG * 2, T), T, 0, s>>>(g, P);
-    k_bc2<R><<<nblk((long long)(g.n1 + 2 * NG) * g.n3 * NG * 2, T), T, 0, s>>>(g, P);
-    k_bc3<R><<<nblk((long long)(g.n1 + 2 * NG) * (g.n2 + 2 * NG) * NG * 2, T), T, 0, s>>>(g, P);
+    if (polar_count(g) > 0) k_polar<R><<<nblk(polar_count(g), T), T, 0, s>>>(g, P);
+    k_bc1<R><<<nblk(bc1_count(g), T), T, 0, s>>>(g, P);
+    k_bc2<R><<<nblk(bc2_count(g), T), T, 0, s>>>(g, P);
+    k_bc3<R><<<nblk(bc3_count(g), T), T, 0, s>>>(g, P);
 }
 
-template <typename R>
-static void fluxes(const Grid &g, const R *P, int want_dt, cudaStream_t s)
-{
-    const int T = 128;
-    Box b1{{0, -1, -1}, {g.n1 + 1, g.n2 + 2, g.n3 + 2}};
-    Box b2{{-1, 0, -1}, {g.n1 + 2, g.n2 + 1, g.n3 + 2}};
-    Box b3{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, g.n3 + 1}};
-    k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, P, (R *)g.F[0], b1, want_dt);
-    k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, P, (R *)g.F[1], b2, want_dt);
-    k_flux<R, 3><<<nblk(b3.count(), T), T, 0, s>>>(g, P, (R *)g.F[2], b3, want_dt);
-    Box be{{0, 0, 0}, {g.n1 + 1, g.n2 + 1, g.n3 + 1}};
-    k_emf<R><<<nblk(be.count(), T), T, 0, s>>>(g, (const R *)g.F[0], (const R *)g.F[1], (const R *)g.F[2],
-                                                (R *)g.E[0], (R *)g.E[1], (R *)g.E[2], be);
-}
-
-template <typename R>
-static void stage(const Grid &g, int src, int dst, double dtfac, int corr, int want_dt, cudaStream_t s)
-{
-    const R *Pin = (const R *)g.P[src];
-    R *Pout = (R *)g.P[dst];
-    fluxes<R>(g, Pin, want_dt, s);
-    long long nact = (long long)g.n1 * g.n2 * g.n3;
-    const int T = 128;
-    k_update<R><<<nblk(nact, T), T, 0, s>>>(g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1],
-                                             (const R *)g.F[2], (const R *)g.E[0], (const R *)g.E[1],
-                                             (const R *)g.E[2], dtfac, corr);
-    k_fixup<R><<<1, 1024, 0, s>>>(g, Pout, corr);
-    fill_bc<R>(g, Pout, s);
-}
-
-// One part of a stage, for per-kernel timing: 0-2 fluxes along X1..X3,
-// 3 EMFs, 4 update + inversion, 5 fixups, 6 boundary fill.
+// One part of a stage: 0-2 fluxes along X1..X3, 3 EMFs, 4 update + inversion,
+// 5 fixups, 6 boundary fill.
 template <typename R>
 static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, int corr, int want_dt,
                        cudaStream_t s)
@@ -620,11 +98,7 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     const int T = 128;
     const R *Pin = (const R *)g.P[src];
     R *Pout = (R *)g.P[dst];
-    Box b1{{0, -1, -1}, {g.n1 + 1, g.n2 + 2, g.n3 + 2}};
-    Box b2{{-1, 0, -1}, {g.n1 + 2, g.n2 + 1, g.n3 + 2}};
-    Box b3{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, g.n3 + 1}};
-    Box be{{0, 0, 0}, {g.n1 + 1, g.n2 + 1, g.n3 + 1}};
-    long long nact = (long long)g.n1 * g.n2 * g.n3;
+    Box b1 = flux_box(g, 1), b2 = flux_box(g, 2), b3 = flux_box(g, 3), be = edge_box(g);
     switch (part) {
     case 0: k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[0], b1, want_dt); break;
     case 1: k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[1], b2, want_dt); break;
@@ -634,13 +108,19 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
                                                     (R *)g.E[0], (R *)g.E[1], (R *)g.E[2], be);
         break;
     case 4:
-        k_update<R><<<nblk(nact, T), T, 0, s>>>(g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1],
-                                                 (const R *)g.F[2], (const R *)g.E[0], (const R *)g.E[1],
-                                                 (const R *)g.E[2], dtfac, corr);
+        k_update<R><<<nblk(nact_of(g), T), T, 0, s>>>(g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1],
+                                                       (const R *)g.F[2], (const R *)g.E[0], (const R *)g.E[1],
+                                                       (const R *)g.E[2], dtfac, corr);
         break;
     case 5: k_fixup<R><<<1, 1024, 0, s>>>(g, Pout, corr); break;
     default: fill_bc<R>(g, Pout, s); break;
     }
+}
+
+template <typename R>
+static void stage(const Grid &g, int src, int dst, double dtfac, int corr, int want_dt, cudaStream_t s)
+{
+    for (int part = 0; part < 7; part++) stage_part<R>(g, part, src, dst, dtfac, corr, want_dt, s);
 }
 
 // The same step as launch_step, with an event recorded before each part;
@@ -683,8 +163,10 @@ void launch_bc(const Grid &g, int buf, cudaStream_t s)
 // flux sweep of buffer 0 only (CFL step of Eq. 27 at init, and the flux test entry)
 void launch_fluxes_dt(const Grid &g, int set_dt, cudaStream_t s)
 {
-    if (g.mixed) fluxes<float>(g, (const float *)g.P[0], 1, s);
-    else fluxes<double>(g, (const double *)g.P[0], 1, s);
+    for (int part = 0; part < 4; part++) {
+        if (g.mixed) stage_part<float>(g, part, 0, 1, 0.0, 0, 1, s);
+        else stage_part<double>(g, part, 0, 1, 0.0, 0, 1, s);
+    }
     if (set_dt) k_finalize<<<1, 32, 0, s>>>(g, 0);
 }
 

@@ -69,6 +69,14 @@ class Diag(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class EnsTiling(C.Structure):
+    _fields_ = [("items_flux", C.c_int), ("items_update", C.c_int), ("blocks_per_sm_flux", C.c_int),
+                ("blocks_per_sm_update", C.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 # every symbol include/grmhd.h declares, with its ctypes signature
 _V = C.c_void_p
 SIGNATURES = {
@@ -89,6 +97,14 @@ SIGNATURES = {
     "grmhd_step_profiled": (C.c_int, [_V, C.c_int, C.POINTER(C.c_double)]),
     "grmhd_peak_probe": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "grmhd_diagnostics_noalloc": (C.c_int, [_V, _V]),
+    "grmhd_ensemble_create": (C.c_int, [C.POINTER(_V), C.c_int, C.POINTER(_V)]),
+    "grmhd_ensemble_step": (C.c_int, [_V, C.c_int]),
+    "grmhd_ensemble_set_tiling": (C.c_int, [_V, C.POINTER(EnsTiling)]),
+    "grmhd_ensemble_get_tiling": (C.c_int, [_V, C.POINTER(EnsTiling)]),
+    "grmhd_ensemble_autotune": (C.c_int, [_V, C.c_int, C.POINTER(EnsTiling), C.POINTER(C.c_double)]),
+    "grmhd_ensemble_sync": (C.c_int, [_V]),
+    "grmhd_ensemble_destroy": (None, [_V]),
+    "grmhd_ensemble_last_error": (C.c_char_p, [_V]),
 }
 
 PROF_SLOTS = 16
@@ -302,6 +318,70 @@ def diagnostics_noalloc(ctx: Context, out_dev):
         raise ValueError("out_dev must be a CUDA tensor of at least 8 doubles")
     ctx.check(ctx.L.grmhd_diagnostics_noalloc(ctx.h, ptr))
     return out_dev
+
+
+# ------------------------------------------------------------------ ensemble
+
+class Ensemble:
+    """Owning handle of a grmhd_ens; keeps its member contexts alive."""
+
+    def __init__(self, handle, members):
+        self.h = handle
+        self.members = list(members)
+        self.L = load()
+
+    def check(self, rc):
+        if rc != 0:
+            msg = self.L.grmhd_ensemble_last_error(self.h) if self.h else b""
+            raise GrmhdError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if self.h:
+            self.L.grmhd_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ensemble_create(members) -> Ensemble:
+    L = load()
+    arr = (C.c_void_p * len(members))(*[m.h for m in members])
+    h = C.c_void_p()
+    rc = L.grmhd_ensemble_create(arr, len(members), C.byref(h))
+    if rc != 0:
+        raise GrmhdError(rc, "ensemble_create failed (members must share device and precision and have a state)")
+    return Ensemble(h.value, members)
+
+
+def ensemble_step(ens: Ensemble, nsteps: int = 1):
+    ens.check(ens.L.grmhd_ensemble_step(ens.h, nsteps))
+
+
+def ensemble_sync(ens: Ensemble):
+    ens.check(ens.L.grmhd_ensemble_sync(ens.h))
+
+
+def ensemble_set_tiling(ens: Ensemble, items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update):
+    t = EnsTiling(items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update)
+    ens.check(ens.L.grmhd_ensemble_set_tiling(ens.h, C.byref(t)))
+
+
+def ensemble_get_tiling(ens: Ensemble) -> dict:
+    t = EnsTiling()
+    ens.check(ens.L.grmhd_ensemble_get_tiling(ens.h, C.byref(t)))
+    return t.as_dict()
+
+
+def ensemble_autotune(ens: Ensemble, trial_steps: int = 2):
+    t = EnsTiling()
+    ms = C.c_double()
+    ens.check(ens.L.grmhd_ensemble_autotune(ens.h, trial_steps, C.byref(t), C.byref(ms)))
+    return t.as_dict(), ms.value
 
 
 def peak_probe(device: int = 0, fp64: bool = True) -> float:
