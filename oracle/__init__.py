@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["geometry.c", "physics.c", "con2prim.c", "grid.c", "torus.c"]
+_SRCS = ["geometry.c", "physics.c", "con2prim.c", "grid.c", "torus.c", "mlp.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -85,6 +85,7 @@ class Diag(C.Structure):
 
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
+_F = C.POINTER(C.c_float)
 
 
 def _p(a: np.ndarray, t=_D):
@@ -132,6 +133,19 @@ def lib():
                 "orc_fm_ucon_bl": (None, [C.c_double, C.c_double, C.c_double, C.c_double, _D]),
                 "orc_uniform": (C.c_double, [C.c_uint64, C.c_uint64]),
                 "orc_x1_of_r": (C.c_double, [V, C.c_double]),
+                "orc_mlp_nparam": (C.c_int, []),
+                "orc_bf16_round": (C.c_float, [C.c_float]),
+                "orc_mlp_features": (C.c_int, [_D, C.POINTER(Geom), _D]),
+                "orc_mlp_samples": (None, [V, C.c_uint64, C.c_long, C.c_long, _D, _I, _D, _D, _D]),
+                "orc_mlp_forward": (None, [_F, _F, _F, C.c_long, _D]),
+                "orc_mlp_loss_grad": (C.c_double, [_F, _F, _F, _F, C.c_long, _D]),
+                "orc_mlp_loss_grad_d": (C.c_double, [_D, _F, _F, _F, C.c_long, _D]),
+                "orc_mlp_adamw": (None, [_D, _D, _D, _D, C.c_long, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double]),
+                "orc_mlp_train_steps": (C.c_double, [_F, _F, _F, _F, C.c_long, C.c_long, C.c_long,
+                                                     C.c_double, C.c_double, C.c_double, C.c_double,
+                                                     C.c_double, _F, _F, _D]),
+                "orc_c2p_batch_w": (None, [V, _D, _I, _D, _D, _D, _I, _I, C.c_long, C.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -281,6 +295,105 @@ class Grid:
         self.L.orc_c2p_batch(self.h, _p(U), _p(loc, _I), _p(guess), _p(P), _p(flags, _I),
                              _p(iters, _I), n, methods)
         return P, flags, iters
+
+    def con2prim_w(self, U, loc, guess, wguess, methods=15):
+        """Inversion with an explicit Newton starting W per zone (<= 0: plain start)."""
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(NU, -1)
+        guess = np.ascontiguousarray(guess, dtype=np.float64).reshape(NP, -1)
+        wguess = np.ascontiguousarray(wguess, dtype=np.float64)
+        loc = np.ascontiguousarray(loc, dtype=np.int32)
+        n = U.shape[1]
+        P = np.zeros((NP, n))
+        flags = np.zeros(n, dtype=np.int32)
+        iters = np.zeros(n, dtype=np.int32)
+        self.L.orc_c2p_batch_w(self.h, _p(U), _p(loc, _I), _p(guess), _p(wguess), _p(P), _p(flags, _I),
+                               _p(iters, _I), n, methods)
+        return P, flags, iters
+
+    def mlp_samples(self, seed, first, n):
+        """Samples first..first+n-1 of the seeded MLP training distribution:
+        P (8, n), loc (n), U (9, n), features (5, n), labels log(W/D) (n)."""
+        P = np.zeros((NP, n))
+        loc = np.zeros(n, dtype=np.int32)
+        U = np.zeros((NU, n))
+        feat = np.zeros((5, n))
+        lab = np.zeros(n)
+        self.L.orc_mlp_samples(self.h, seed, first, n, _p(P), _p(loc, _I), _p(U), _p(feat), _p(lab))
+        return P, loc, U, feat, lab
+
+
+# ------------------------------------------------------------------ MLP helpers
+
+MLP_NPARAM = 4609
+MLP_SLICES = {"W1": (0, 320), "b1": (320, 384), "W2": (384, 4480), "b2": (4480, 4544),
+              "W3": (4544, 4608), "b3": (4608, 4609)}
+
+
+def bf16_round(x):
+    """Round FP32 values to the nearest BF16 value (ties to even)."""
+    L = lib()
+    x = np.asarray(x, dtype=np.float32)
+    return np.array([L.orc_bf16_round(float(v)) for v in x.ravel()], dtype=np.float32).reshape(x.shape)
+
+
+def mlp_features(U, g: Geom):
+    L = lib()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    f = np.zeros(5)
+    rc = L.orc_mlp_features(_p(U), C.byref(g), _p(f))
+    return f, rc
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def mlp_forward(theta, norm, feat):
+    """Predictions log(W/D) of features (5, n) with FP32 parameters theta."""
+    theta, norm, feat = _f32(theta), _f32(norm), _f32(feat).reshape(5, -1)
+    n = feat.shape[1]
+    y = np.zeros(n)
+    lib().orc_mlp_forward(_p(theta, _F), _p(norm, _F), _p(feat, _F), n, _p(y))
+    return y
+
+
+def mlp_loss_grad(theta, norm, feat, label):
+    theta, norm, feat, label = _f32(theta), _f32(norm), _f32(feat).reshape(5, -1), _f32(label)
+    n = feat.shape[1]
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().orc_mlp_loss_grad(_p(theta, _F), _p(norm, _F), _p(feat, _F), _p(label, _F), n, _p(g))
+    return loss, g
+
+
+def mlp_loss_grad_exact(w, norm, feat, label):
+    """Loss and gradient with FP64 weights w used unrounded."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    norm, feat, label = _f32(norm), _f32(feat).reshape(5, -1), _f32(label)
+    n = feat.shape[1]
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().orc_mlp_loss_grad_d(_p(w), _p(norm, _F), _p(feat, _F), _p(label, _F), n, _p(g))
+    return loss, g
+
+
+def mlp_adamw(theta, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """One AdamW step in place on FP64 arrays theta, m, v."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    lib().orc_mlp_adamw(_p(theta), _p(m), _p(v), _p(grad), step, lr, beta1, beta2, eps, wd)
+
+
+def mlp_train_steps(theta, norm, feat, label, batch, nsteps, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """nsteps of minibatch AdamW from theta (FP32); returns (theta, last loss)."""
+    th = _f32(theta).copy()
+    norm, feat, label = _f32(norm), _f32(feat).reshape(5, -1), _f32(label)
+    n = feat.shape[1]
+    fb = np.zeros((5, batch), dtype=np.float32)
+    lb = np.zeros(batch, dtype=np.float32)
+    work = np.zeros(4 * MLP_NPARAM)
+    loss = lib().orc_mlp_train_steps(_p(th, _F), _p(norm, _F), _p(feat, _F), _p(label, _F), n, batch, nsteps,
+                                     lr, beta1, beta2, eps, wd, _p(fb, _F), _p(lb, _F), _p(work))
+    return th, loss
 
 
 # ----------------------------------------------------------- pointwise helpers

@@ -219,8 +219,11 @@ static int entropy_inv(const c2p_in *c, const orc_params *prm, double *P)
  * bit mask of allowed methods (1 Newton, 2 Brent-W, 4 entropy, 8 beta switch),
  * 15 for the full procedure.  Returns the C2P_* flag.
  */
-int orc_con2prim(const double U[ORC_NU], const orc_geom *g, const double *guess,
-                 const orc_params *prm, double P[ORC_NP], int *iters, int methods)
+/* Inversion of one zone.  wguess > 0 replaces the Newton starting W taken
+ * from the guess primitives, and v^2 then follows from Eq. 29 at that W (the
+ * learned starting point); wguess <= 0 is the plain start from the guess. */
+int orc_con2prim_w(const double U[ORC_NU], const orc_geom *g, const double *guess,
+                   const orc_params *prm, double P[ORC_NP], int *iters, int methods, double wguess)
 {
     *iters = 0;
     for (int m = 0; m < ORC_NP; m++) P[m] = guess[m];
@@ -278,6 +281,10 @@ int orc_con2prim(const double U[ORC_NU], const orc_geom *g, const double *guess,
             for (int j = 0; j < 3; j++) usq += g->gcov[i + 1][j + 1] * ut[i] * ut[j];
         double v2 = usq / (1.0 + usq);
         double W = (1.0 + usq) * (guess[KRHO] + prm->gam * guess[KUU]);
+        if (wguess > 0.0) {
+            W = wguess;
+            v2 = v2_of_W(&c, W);
+        }
         if (!(W > 0.0) || !isfinite(W)) W = c.D;
         if (v2 > V2MAX) v2 = V2MAX;
         if (newton2d(&c, &W, &v2, prm, iters)) {
@@ -291,4 +298,10 @@ int orc_con2prim(const double U[ORC_NU], const orc_geom *g, const double *guess,
     if ((methods & 2) && brent_w(&c, prm, P)) return C2P_BRENT_W;
     if ((methods & 4) && entropy_inv(&c, prm, P)) return C2P_ENTROPY;
     return C2P_FAIL | C2P_FAIL_ENT;
+}
+
+int orc_con2prim(const double U[ORC_NU], const orc_geom *g, const double *guess,
+                 const orc_params *prm, double P[ORC_NP], int *iters, int methods)
+{
+    return orc_con2prim_w(U, g, guess, prm, P, iters, methods, 0.0);
 }

@@ -112,8 +112,16 @@ void orc_source(const double *q, const orc_geom *g, const double conn[4][4][4],
 /* con2prim.c */
 int orc_con2prim(const double U[ORC_NU], const orc_geom *g, const double *guess,
                  const orc_params *p, double P[ORC_NP], int *iters, int methods);
+int orc_con2prim_w(const double U[ORC_NU], const orc_geom *g, const double *guess,
+                   const orc_params *p, double P[ORC_NP], int *iters, int methods, double wguess);
 double orc_brent(double (*f)(double, void *), void *ctx, double a, double b, double fa,
                  double fb, double tol, int maxit, int *ok);
+
+/* torus.c */
+double orc_uniform(uint64_t seed, uint64_t idx);
+
+/* mlp.c */
+int orc_mlp_features(const double U[ORC_NU], const orc_geom *g, double feat[5]);
 
 /* grid.c */
 long orc_idx(const orc_grid *G, int i, int j, int k);
