@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-mlp", action="store_true")
     return ap.parse_args()
 
 
@@ -204,6 +205,95 @@ def run_ensemble(G, torch, stream, device, steps=10):
             "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
             "loop_ms_per_step": ms_loop / steps, "speedup_vs_loop": ms_loop / ms_ens,
             "tiling": tiling, "tiling_from_cache": cached}
+
+
+# ------------------------------------------------------- learned Newton start
+
+# FP32 flops per training sample of the 5-64-64-1 network: forward
+# 2 (5*64 + 64*64 + 64); backward dh1 = W2^T dh2 (2*64*64), dW2 (2*64*64),
+# dW1 (2*64*5), dW3, db (3*2*64)
+MLP_TRAIN_FLOPS = 2 * (5 * 64 + 64 * 64 + 64) + 2 * 64 * 64 * 2 + 2 * 64 * 5 + 3 * 2 * 64
+
+
+def counters(G, ctx):
+    d = G.diagnostics(ctx)
+    return {k: d[k] for k in ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_fixed")}
+
+
+def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4, steps=10):
+    """Train the learned Newton start on the GPU, compare inversions from a
+    poor start with and without it, and time the 256x192x192 mixed step with
+    the plain and the learned start."""
+    gp = G.default_grid(256, 192, 192, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
+    gp.stream = stream.cuda_stream
+    ctx = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+    G.set_metric(ctx, 0.9375, G.KERR_MKS)
+    rep = G.mlp_train(ctx, n_samples=n_samples, n_val=100_000, seed=7, init_seed=1, epochs=epochs, batch=4096,
+                      lr=2e-3, lr_min=2e-5, weight_decay=1e-4)
+    train = dict(rep)
+    train["tflops_fp32"] = rep["samples_per_s"] * MLP_TRAIN_FLOPS / 1e12
+    train["frac_of_fp32_probe"] = train["tflops_fp32"] / fp32_peak if fp32_peak else None
+    train["flops_per_sample"] = MLP_TRAIN_FLOPS
+
+    def ev_time(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # held-out states; the poor start knows rho, u and B but not the flow (no velocity)
+    n = 1_000_000
+    P, loc, U, f, y = G.mlp_samples(ctx, 7, 50_000_000, n, device=True)
+    inv = {}
+    for name, learned in (("plain_static_start", False), ("learned_start", True)):
+        g0 = P.clone()
+        g0[2:5] = 0.0
+        flags = torch.zeros(n, dtype=torch.int32, device=P.device)
+        iters = torch.zeros(n, dtype=torch.int32, device=P.device)
+        G.con2prim(ctx, U, loc, g0.clone(), flags, iters, use_learned_guess=learned)   # warm
+        ms = ev_time(lambda: G.con2prim(ctx, U, loc, g0, flags, iters, use_learned_guess=learned))
+        fl = flags.cpu().numpy()
+        it = iters.cpu().numpy()
+        nr = fl == 0
+        inv[name] = {"ms": ms, "inversions_per_s": n / (ms * 1e-3), "newton_iters_mean": float(it[nr].mean()),
+                     "frac_newton": float(nr.mean()), "frac_brent": float((fl == 1).mean()),
+                     "frac_entropy": float((fl == 2).mean()), "frac_entropy_beta": float((fl == 3).mean()),
+                     "frac_fail": float(((fl & 8) != 0).mean())}
+    g0 = P.clone()
+    flags = torch.zeros(n, dtype=torch.int32, device=P.device)
+    iters = torch.zeros(n, dtype=torch.int32, device=P.device)
+    G.con2prim(ctx, U, loc, g0, flags, iters)
+    fl, it = flags.cpu().numpy(), iters.cpu().numpy()
+    inv["exact_prims_start"] = {"newton_iters_mean": float(it[fl == 0].mean()), "frac_newton": float((fl == 0).mean())}
+
+    # the 256x192x192 step: plain start (previous-stage primitives) vs learned
+    G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+    zones = ctx.nact
+    step = {}
+    for name, learned in (("plain_start", False), ("learned_start", True)):
+        G.set_learned_guess(ctx, learned)
+        G.step(ctx, 2)
+        c0 = counters(G, ctx)
+        ms = ev_time(lambda: G.step(ctx, steps))
+        c1 = counters(G, ctx)
+        d = {k: c1[k] - c0[k] for k in c0}
+        inversions = 2 * zones * steps
+        step[name] = {"value": zones * steps / (ms * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms / steps,
+                      "newton_iters_per_newton_zone": d["nr_iters"] / max(d["n_nr"], 1),
+                      "fallback_per_inversion": (d["n_brent"] + d["n_entropy"]) / inversions,
+                      "entropy_beta_per_inversion": d["n_entropy_beta"] / inversions,
+                      "fail_per_inversion": d["n_fail"] / inversions}
+    G.set_learned_guess(ctx, False)
+    ctx.close()
+    return {"workload": "learned Newton start: 5-64-64-1 MLP, BF16 weights, FP32 accumulate; trained on the GPU "
+                        f"on {n_samples} seeded samples x {epochs} epochs (log-uniform rho in [1e-6,1], u/rho in "
+                        "[1e-4,10], Gamma in [1,50], b^2/rho in [1e-3,100]) at the 256x192x192 MKS grid's metric; "
+                        "step: 256x192x192 FM torus, mixed precision",
+            "train": train, "inversion_1e6_heldout": inv, "step_256x192x192": step}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -374,6 +464,10 @@ def main():
     ensemble = None
     if world == 1 and not args.no_ensemble:
         ensemble = run_ensemble(G, torch, stream, local)
+    # ---- learned Newton start: training, inversions, the 256x192x192 step
+    mlp = None
+    if world == 1 and not args.no_mlp:
+        mlp = run_mlp(G, torch, stream, local, fp32_peak)
     # ---- CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -394,6 +488,7 @@ def main():
             "kernels_ms_per_step": kernels_ms,
             "fp64_step": fp64,
             "ensemble": ensemble,
+            "learned_start": mlp,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,

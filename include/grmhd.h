@@ -269,6 +269,113 @@ const char *grmhd_ensemble_last_error(const grmhd_ens *ens);
  * kernels overlap on the GPU (e.g. contexts on different streams) race. */
 int grmhd_diagnostics_noalloc(grmhd_ctx *ctx, double *out_dev);
 
+/* ---------------------------------------------------------------------
+ * Learned Newton start of the inversion (Section 2.3 names the Newton
+ * starting point; the learned guess is this library's extension).  A 5-64-64-1
+ * ReLU network maps five invariants of a conserved state to log(W/D), where
+ * W = Gamma^2 (rho + u + p) and D = Gamma rho.  Newton then starts from that W,
+ * with v^2 from Eq. 29.
+ *
+ * Features, from the Section 2.3 variables with tau = -n.Q - D, each argument
+ * clamped below at 1e-30:
+ *   log(tau/D), log(Qt^2/D^2), log(Bf^2/D), log((Q.Bf)^2/D^3), log(D)
+ *
+ * Parameter vector theta: FP32, GRMHD_MLP_NPARAM entries, in this order:
+ *   W1[64][5], b1[64], W2[64][64], b2[64], W3[64], b3   (rows = output units)
+ * The forward pass uses the weight matrices rounded to BF16 (ties to even)
+ * and keeps inputs, biases, activations and accumulation in FP32.
+ *
+ * norm[GRMHD_MLP_NNORM] standardises inputs and output:
+ *   feature mean[5], feature std[5], output mean, output std.
+ *   x = (f - mean)/std, and prediction = s*std_y + mean_y.
+ *
+ * Training loss over a batch of n samples: (1/n) sum (s - t)^2, with
+ * t = (y - mean_y)/std_y.  The gradient of each weight is taken at its BF16
+ * value and applied to the FP32 master copy.  The optimiser is AdamW with
+ * bias-corrected moments and decoupled weight decay on W1, W2, W3.
+ * ------------------------------------------------------------------- */
+#define GRMHD_MLP_NPARAM 4609
+#define GRMHD_MLP_NNORM 12
+
+/* Load parameters (host arrays) as the context's network; the inversion
+ * entry points may then use it (use_learned_guess). */
+int grmhd_mlp_load(grmhd_ctx *ctx, const float *theta, const float *norm);
+
+/* Copy the context's network (FP32 master and norm) to host arrays. */
+int grmhd_mlp_get(grmhd_ctx *ctx, float *theta, float *norm);
+
+/* Samples first .. first+n-1 of the seeded training distribution, at
+ * zone-centre metrics of this grid; needs grmhd_set_metric.  Any output may
+ * be NULL.  Outputs, field-major:
+ *   P (8 x n), loc (n, = i*n2 + j), U (9 x n, sqrt(-g) included),
+ *   feat (5 x n, FP32), label (n, FP32 log(W/D)).
+ * Sample i draws xi_k = top 53 bits of splitmix64(seed ^ (16 i + k)),
+ * k = 0..9, and sets:
+ *   - the zone (floor(xi_0 n1), floor(xi_1 n2));
+ *   - rho = 1e-6^(1-xi_2);
+ *   - u/rho = 1e-4 * 1e5^xi_3;
+ *   - Gamma = 50^xi_4;
+ *   - b^2/rho = 1e-3 * 1e5^xi_5;
+ *   - directions (cos th, ph) = (2 xi_6 - 1, 2 pi xi_7) for the velocity and
+ *     (2 xi_8 - 1, 2 pi xi_9) for the field, with components e^i/sqrt(g_ii). */
+int grmhd_mlp_samples(grmhd_ctx *ctx, unsigned long long seed, long first, long n, double *P, int *loc,
+                      double *U, float *feat, float *label, int on_device);
+
+/* Predicted log(W/D) of n feature vectors (5 x n) with the loaded network. */
+int grmhd_mlp_forward(grmhd_ctx *ctx, const float *feat, long n, float *y, int on_device);
+
+/* Loss and its gradient (GRMHD_MLP_NPARAM FP32 values) over one batch of n
+ * samples (n <= 1048576), for the given parameters and norm. The context's
+ * loaded network is left unchanged.  feat, label, grad follow on_device;
+ * theta and norm are host arrays; loss (may be NULL) is a host double. */
+int grmhd_mlp_loss_grad(grmhd_ctx *ctx, const float *theta, const float *norm, const float *feat,
+                        const float *label, long n, float *grad, double *loss, int on_device);
+
+/* nsteps of minibatch AdamW at a constant learning rate, from theta_inout
+ * (host, FP32) with zero moments.  Step s uses samples (s*batch + b) mod n,
+ * for b < batch.  theta_inout receives the result.  loss_last (may be NULL)
+ * receives the mean loss of the last step, taken before its update.  The
+ * loaded network is left unchanged.  batch <= 1048576. */
+int grmhd_mlp_train_steps(grmhd_ctx *ctx, float *theta_inout, const float *norm, const float *feat,
+                          const float *label, long n, long batch, long nsteps, double lr, double beta1,
+                          double beta2, double eps, double weight_decay, double *loss_last, int on_device);
+
+typedef struct {
+    long n_samples;          /* training set size (samples 0 .. n-1 of seed) */
+    long n_val;              /* held-out samples n .. n+n_val-1 of the same seed */
+    unsigned long long seed; /* sample seed */
+    unsigned long long init_seed; /* weight initialisation seed */
+    int epochs;
+    int batch;               /* <= 1048576 */
+    double lr, lr_min;       /* cosine schedule from lr to lr_min over all steps */
+    double beta1, beta2, eps, weight_decay;
+} grmhd_mlp_train_params;
+
+typedef struct {
+    double loss_first, loss_last; /* mean batch loss of the first and last step */
+    double val_rmse, val_maxerr;  /* error of log(W/D) on the held-out samples */
+    double train_ms;              /* device time of the training steps (CUDA events) */
+    double samples_per_s;         /* steps * batch / train time */
+    long steps;
+} grmhd_mlp_train_report;
+
+/* Train the network on the GPU and load it as the context's network:
+ *   1. generate the training and held-out samples;
+ *   2. set norm from the training set's mean and std;
+ *   3. initialise the weights He-uniform from init_seed;
+ *   4. run epochs * n_samples / batch AdamW steps, replayed as CUDA graphs;
+ *   5. evaluate the held-out error.
+ * The training epochs take the set in a fresh permutation each. */
+int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp, grmhd_mlp_train_report *rep);
+
+/* on = 1: every inversion of grmhd_step starts Newton from the loaded
+ * network's W (and v^2 of Eq. 29) instead of the stage's primitives; on = 0
+ * restores the plain start.  The method order, tolerances and fallbacks are
+ * unchanged.  Needs a loaded network for on = 1; later loads or training
+ * runs replace the network in place.  Ensemble steps always use the plain
+ * start. */
+int grmhd_set_learned_guess(grmhd_ctx *ctx, int on);
+
 /* Library version string. */
 const char *grmhd_version(void);
 

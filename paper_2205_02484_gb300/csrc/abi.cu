@@ -8,11 +8,13 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "../../include/grmhd.h"
 #include "kernels.h"
+#include "mlp.cuh"
 
 using namespace grmhd;
 
@@ -35,7 +37,8 @@ struct grmhd_ctx {
     unsigned char *intorus = nullptr;
     double *hpin = nullptr; // pinned host scratch (64 doubles)
     double disk_mass = 0.0, disk_eb = 0.0;
-    float *mlp = nullptr;
+    float *mlp = nullptr;       // packed forward buffer of the learned Newton start
+    float *mlp_theta = nullptr; // its FP32 parameters
     bool mlp_loaded = false;
     std::string err;
 };
@@ -630,5 +633,405 @@ extern "C" int grmhd_diagnostics_noalloc(grmhd_ctx *ctx, double *out_dev)
     if (rc) return rc;
     launch_diagnostics(g, partials, NOALLOC_DOUBLES, out_dev, ctx->stream);
     CK(cudaGetLastError());
+    return 0;
+}
+
+// ---------------------------------------------------------------- learned start
+
+static_assert(GRMHD_MLP_NPARAM == MLP_NPARAM, "parameter count of the header and the kernels differ");
+
+namespace {
+
+// device buffers of one call, freed when the call returns
+struct DevTmp {
+    std::vector<void *> p;
+    bool bad = false;
+    ~DevTmp()
+    {
+        for (void *q : p) cudaFree(q);
+    }
+    template <typename T>
+    T *get(size_t count)
+    {
+        void *q = nullptr;
+        if (cudaMalloc(&q, count * sizeof(T) > 16 ? count * sizeof(T) : 16) != cudaSuccess) {
+            bad = true;
+            return nullptr;
+        }
+        p.push_back(q);
+        return (T *)q;
+    }
+};
+
+int make_trainer(grmhd_ctx *ctx, DevTmp &tmp, int batch, long long hist, MlpTrainer &T)
+{
+    int nb = mlp_grad_blocks(batch);
+    T.theta = tmp.get<float>(MLP_NPARAM);
+    T.m = tmp.get<float>(MLP_NPARAM);
+    T.v = tmp.get<float>(MLP_NPARAM);
+    T.fwd = tmp.get<float>(MLP_FLOATS);
+    T.part = tmp.get<float>((size_t)nb * MLP_NPARAM);
+    T.lpart = tmp.get<double>(nb);
+    T.step = tmp.get<long long>(1);
+    T.ticket = tmp.get<unsigned int>(1);
+    T.loss_hist = tmp.get<double>(hist);
+    T.hist_len = hist;
+    if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc of the training buffers failed");
+    CK(cudaMemsetAsync(T.m, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(T.v, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(T.fwd, 0, MLP_FLOATS * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(T.step, 0, sizeof(long long), ctx->stream));
+    CK(cudaMemsetAsync(T.ticket, 0, sizeof(unsigned int), ctx->stream));
+    CK(cudaMemsetAsync(T.loss_hist, 0, hist * sizeof(double), ctx->stream));
+    CK(mlp_grad_setup());
+    return 0;
+}
+
+int check_norm(grmhd_ctx *ctx, const float *norm)
+{
+    for (int k = 0; k < GRMHD_MLP_NNORM; k++)
+        if (!std::isfinite(norm[k])) return fail(ctx, GRMHD_EINVAL, "norm has a non-finite entry");
+    for (int k = 5; k < 10; k++)
+        if (!(norm[k] > 0.0f)) return fail(ctx, GRMHD_EINVAL, "feature std must be positive");
+    if (!(norm[11] > 0.0f)) return fail(ctx, GRMHD_EINVAL, "output std must be positive");
+    return 0;
+}
+
+// the trainer's forward view of host parameters theta and norm
+int trainer_load(grmhd_ctx *ctx, const MlpTrainer &T, const float *theta, const float *norm)
+{
+    CK(cudaMemcpyAsync(T.theta, theta, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(T.fwd, norm, GRMHD_MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    (void)cudaGetLastError();
+    launch_mlp_pack(T.theta, T.fwd, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+int ensure_mlp_bufs(grmhd_ctx *ctx)
+{
+    if (!ctx->mlp) {
+        int rc = dalloc(ctx, &ctx->mlp, MLP_FLOATS);
+        if (rc) return rc;
+    }
+    if (!ctx->mlp_theta) {
+        int rc = dalloc(ctx, &ctx->mlp_theta, MLP_NPARAM);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+// device copies of host inputs (or the caller's device pointers)
+template <typename T>
+const T *dev_in(grmhd_ctx *ctx, DevTmp &tmp, const T *p, size_t count, int on_device)
+{
+    if (on_device || !p) return p;
+    T *d = tmp.get<T>(count);
+    if (!d) return nullptr;
+    if (cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) {
+        tmp.bad = true;
+        return nullptr;
+    }
+    return d;
+}
+
+} // namespace
+
+extern "C" int grmhd_mlp_load(grmhd_ctx *ctx, const float *theta, const float *norm)
+{
+    if (!ctx || !theta || !norm) return fail(ctx, GRMHD_EINVAL, "null argument");
+    for (int k = 0; k < MLP_NPARAM; k++)
+        if (!std::isfinite(theta[k])) return fail(ctx, GRMHD_EINVAL, "theta has a non-finite entry");
+    if (int rc = check_norm(ctx, norm)) return rc;
+    if (int rc = ensure_mlp_bufs(ctx)) return rc;
+    CK(cudaMemcpyAsync(ctx->mlp_theta, theta, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mlp, norm, GRMHD_MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    (void)cudaGetLastError();
+    launch_mlp_pack(ctx->mlp_theta, ctx->mlp, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_loaded = true;
+    return 0;
+}
+
+extern "C" int grmhd_mlp_get(grmhd_ctx *ctx, float *theta, float *norm)
+{
+    if (!ctx || (!theta && !norm)) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
+    if (theta)
+        CK(cudaMemcpyAsync(theta, ctx->mlp_theta, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    if (norm)
+        CK(cudaMemcpyAsync(norm, ctx->mlp, GRMHD_MLP_NNORM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_mlp_samples(grmhd_ctx *ctx, unsigned long long seed, long first, long n, double *P, int *loc,
+                                 double *U, float *feat, float *label, int on_device)
+{
+    if (!ctx) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
+    if (n < 0 || first < 0) return fail(ctx, GRMHD_EINVAL, "first and n must be >= 0");
+    if (n == 0) return 0;
+    DevTmp tmp;
+    double *Pd = P, *Ud = U;
+    int *ld = loc;
+    float *fd = feat, *yd = label;
+    if (!on_device) {
+        if (P) Pd = tmp.get<double>((size_t)NP * n);
+        if (U) Ud = tmp.get<double>((size_t)NU * n);
+        if (loc) ld = tmp.get<int>(n);
+        if (feat) fd = tmp.get<float>((size_t)MLP_IN * n);
+        if (label) yd = tmp.get<float>(n);
+        if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc of the sample buffers failed");
+    }
+    (void)cudaGetLastError();
+    launch_mlp_samples(ctx->g, seed, first, n, Pd, ld, Ud, fd, yd, ctx->stream);
+    CK(cudaGetLastError());
+    if (!on_device) {
+        if (P) CK(cudaMemcpyAsync(P, Pd, (size_t)NP * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (U) CK(cudaMemcpyAsync(U, Ud, (size_t)NU * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (loc) CK(cudaMemcpyAsync(loc, ld, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        if (feat)
+            CK(cudaMemcpyAsync(feat, fd, (size_t)MLP_IN * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        if (label) CK(cudaMemcpyAsync(label, yd, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+extern "C" int grmhd_mlp_forward(grmhd_ctx *ctx, const float *feat, long n, float *y, int on_device)
+{
+    if (!ctx || (n > 0 && (!feat || !y))) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
+    if (n < 0) return fail(ctx, GRMHD_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    DevTmp tmp;
+    const float *fd = dev_in(ctx, tmp, feat, (size_t)MLP_IN * n, on_device);
+    float *yd = on_device ? y : tmp.get<float>(n);
+    if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc or copy of the forward buffers failed");
+    (void)cudaGetLastError();
+    launch_mlp_forward(ctx->mlp, fd, n, yd, ctx->stream);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(y, yd, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+static const long MLP_MAX_BATCH = 1L << 20;
+
+extern "C" int grmhd_mlp_loss_grad(grmhd_ctx *ctx, const float *theta, const float *norm, const float *feat,
+                                   const float *label, long n, float *grad, double *loss, int on_device)
+{
+    if (!ctx || !theta || !norm || !feat || !label || !grad) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (n < 1 || n > MLP_MAX_BATCH) return fail(ctx, GRMHD_EINVAL, "n must be in [1, 1048576]");
+    if (int rc = check_norm(ctx, norm)) return rc;
+    DevTmp tmp;
+    MlpTrainer T{};
+    if (int rc = make_trainer(ctx, tmp, (int)n, 1, T)) return rc;
+    if (int rc = trainer_load(ctx, T, theta, norm)) return rc;
+    const float *fd = dev_in(ctx, tmp, feat, (size_t)MLP_IN * n, on_device);
+    const float *ld = dev_in(ctx, tmp, label, (size_t)n, on_device);
+    float *gd = on_device ? grad : tmp.get<float>(MLP_NPARAM);
+    if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc or copy of the gradient buffers failed");
+    (void)cudaGetLastError();
+    launch_mlp_grad(T, fd, ld, n, (int)n, 1ull, ctx->stream);
+    launch_mlp_reduce_grad(T, (int)n, gd, ctx->stream);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(grad, gd, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    int nb = mlp_grad_blocks((int)n);
+    std::vector<double> lp(nb);
+    CK(cudaMemcpyAsync(lp.data(), T.lpart, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss) {
+        double l = 0.0;
+        for (double v : lp) l += v;
+        *loss = l / (double)n;
+    }
+    return 0;
+}
+
+extern "C" int grmhd_mlp_train_steps(grmhd_ctx *ctx, float *theta, const float *norm, const float *feat,
+                                     const float *label, long n, long batch, long nsteps, double lr, double beta1,
+                                     double beta2, double eps, double wd, double *loss_last, int on_device)
+{
+    if (!ctx || !theta || !norm || !feat || !label) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (n < 1 || batch < 1 || batch > MLP_MAX_BATCH || nsteps < 1)
+        return fail(ctx, GRMHD_EINVAL, "need n >= 1, 1 <= batch <= 1048576, nsteps >= 1");
+    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+        return fail(ctx, GRMHD_EINVAL, "bad optimiser parameters");
+    if (int rc = check_norm(ctx, norm)) return rc;
+    DevTmp tmp;
+    MlpTrainer T{};
+    if (int rc = make_trainer(ctx, tmp, (int)batch, nsteps, T)) return rc;
+    if (int rc = trainer_load(ctx, T, theta, norm)) return rc;
+    const float *fd = dev_in(ctx, tmp, feat, (size_t)MLP_IN * n, on_device);
+    const float *ld = dev_in(ctx, tmp, label, (size_t)n, on_device);
+    if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc or copy of the training data failed");
+    MlpHyper h{lr, lr, beta1, beta2, eps, wd, 0};
+    (void)cudaGetLastError();
+    for (long s = 0; s < nsteps; s++) {
+        launch_mlp_grad(T, fd, ld, n, (int)batch, 1ull, ctx->stream);
+        launch_mlp_adam(T, (int)batch, h, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(theta, T.theta, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    double ll = 0.0;
+    CK(cudaMemcpyAsync(&ll, T.loss_hist + (nsteps - 1), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (loss_last) *loss_last = ll;
+    return 0;
+}
+
+static unsigned long long coprime_multiplier(long long n)
+{
+    unsigned long long c = ((unsigned long long)(0.6180339887498949 * (double)n)) | 1ull;
+    while (std::gcd(c, (unsigned long long)n) != 1ull) c += 2;
+    return c;
+}
+
+extern "C" int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp, grmhd_mlp_train_report *rep)
+{
+    if (!ctx || !tp) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
+    const long long N = tp->n_samples, V = tp->n_val;
+    if (N < 1 || N > (1LL << 31) - 1 || V < 0 || tp->epochs < 1 || tp->batch < 1 || tp->batch > MLP_MAX_BATCH)
+        return fail(ctx, GRMHD_EINVAL, "need 1 <= n_samples < 2^31, n_val >= 0, epochs >= 1, 1 <= batch <= 1048576");
+    if (!(tp->lr >= 0.0) || !(tp->lr_min >= 0.0) || !(tp->beta1 >= 0.0 && tp->beta1 < 1.0) ||
+        !(tp->beta2 >= 0.0 && tp->beta2 < 1.0) || !(tp->eps > 0.0))
+        return fail(ctx, GRMHD_EINVAL, "bad optimiser parameters");
+    const long long steps = ((long long)tp->epochs * N + tp->batch - 1) / tp->batch;
+    DevTmp tmp;
+    float *feat = tmp.get<float>((size_t)MLP_IN * N), *lab = tmp.get<float>((size_t)N);
+    float *vfeat = tmp.get<float>((size_t)MLP_IN * (V > 0 ? V : 1)), *vlab = tmp.get<float>((size_t)(V > 0 ? V : 1));
+    const int mblk = 1024;
+    double *mpart = tmp.get<double>((size_t)12 * mblk);
+    const int nbv = V > 0 ? mlp_eval_blocks(V) : 1;
+    double *vpart = tmp.get<double>((size_t)2 * nbv);
+    if (tmp.bad) return fail(ctx, GRMHD_ENOMEM, "cudaMalloc of the training set failed");
+    (void)cudaGetLastError();
+    launch_mlp_samples(ctx->g, tp->seed, 0, N, nullptr, nullptr, nullptr, feat, lab, ctx->stream);
+    if (V > 0) launch_mlp_samples(ctx->g, tp->seed, N, V, nullptr, nullptr, nullptr, vfeat, vlab, ctx->stream);
+    launch_mlp_moments(feat, lab, N, mpart, mblk, ctx->stream);
+    CK(cudaGetLastError());
+    std::vector<double> mp((size_t)12 * mblk);
+    CK(cudaMemcpyAsync(mp.data(), mpart, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float norm[GRMHD_MLP_NNORM];
+    for (int c = 0; c < 6; c++) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int b = 0; b < mblk; b++) {
+            s1 += mp[(size_t)b * 12 + 2 * c];
+            s2 += mp[(size_t)b * 12 + 2 * c + 1];
+        }
+        double mean = s1 / (double)N, var = s2 / (double)N - mean * mean;
+        double sd = var > 1e-24 ? std::sqrt(var) : 1.0;
+        if (c < 5) {
+            norm[c] = (float)mean;
+            norm[5 + c] = (float)sd;
+        } else {
+            norm[10] = (float)mean;
+            norm[11] = (float)sd;
+        }
+    }
+    MlpTrainer T{};
+    if (int rc = make_trainer(ctx, tmp, tp->batch, steps, T)) return rc;
+    (void)cudaGetLastError();
+    launch_mlp_init(T.theta, tp->init_seed, ctx->stream);
+    CK(cudaMemcpyAsync(T.fwd, norm, sizeof(norm), cudaMemcpyHostToDevice, ctx->stream));
+    launch_mlp_pack(T.theta, T.fwd, ctx->stream);
+    CK(cudaGetLastError());
+    const unsigned long long mul = coprime_multiplier(N);
+    MlpHyper h{tp->lr, tp->lr_min, tp->beta1, tp->beta2, tp->eps, tp->weight_decay, steps};
+
+    // the steps as CUDA graphs of up to 32 steps each
+    const long long chunk = steps < 32 ? steps : 32;
+    cudaGraph_t gr[2] = {nullptr, nullptr};
+    cudaGraphExec_t ge[2] = {nullptr, nullptr};
+    long long lens[2] = {chunk, steps % chunk};
+    int err = 0;
+    for (int q = 0; q < 2 && !err; q++) {
+        if (lens[q] == 0) continue;
+        if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            err = 1;
+            break;
+        }
+        for (long long s = 0; s < lens[q]; s++) {
+            launch_mlp_grad(T, feat, lab, N, tp->batch, mul, ctx->stream);
+            launch_mlp_adam(T, tp->batch, h, ctx->stream);
+        }
+        if (cudaStreamEndCapture(ctx->stream, &gr[q]) != cudaSuccess ||
+            cudaGraphInstantiate(&ge[q], gr[q], 0) != cudaSuccess)
+            err = 1;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    if (!err && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        cudaEventRecord(e0, ctx->stream);
+        for (long long r = 0; r < steps / chunk; r++) cudaGraphLaunch(ge[0], ctx->stream);
+        if (ge[1]) cudaGraphLaunch(ge[1], ctx->stream);
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) err = 1;
+    } else {
+        err = 1;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (int q = 0; q < 2; q++) {
+        if (ge[q]) cudaGraphExecDestroy(ge[q]);
+        if (gr[q]) cudaGraphDestroy(gr[q]);
+    }
+    if (err) {
+        cudaError_t e = cudaGetLastError();
+        return fail(ctx, GRMHD_ECUDA, std::string("training graph failed: ") + cudaGetErrorString(e));
+    }
+
+    double vr = 0.0, vm = 0.0;
+    if (V > 0) {
+        launch_mlp_eval(T.fwd, vfeat, vlab, V, vpart, ctx->stream);
+        CK(cudaGetLastError());
+        std::vector<double> ev((size_t)2 * nbv);
+        CK(cudaMemcpyAsync(ev.data(), vpart, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        double se = 0.0;
+        for (int b = 0; b < nbv; b++) {
+            se += ev[2 * b];
+            vm = std::max(vm, ev[2 * b + 1]);
+        }
+        vr = std::sqrt(se / (double)V);
+    }
+    double lf = 0.0, ll = 0.0;
+    CK(cudaMemcpyAsync(&lf, T.loss_hist, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ll, T.loss_hist + (steps - 1), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (int rc = ensure_mlp_bufs(ctx)) return rc;
+    CK(cudaMemcpyAsync(ctx->mlp, T.fwd, MLP_FLOATS * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mlp_theta, T.theta, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_loaded = true;
+    if (rep) {
+        rep->loss_first = lf;
+        rep->loss_last = ll;
+        rep->val_rmse = vr;
+        rep->val_maxerr = vm;
+        rep->train_ms = ms;
+        rep->samples_per_s = ms > 0.0f ? (double)steps * tp->batch / (ms * 1e-3) : 0.0;
+        rep->steps = (long)steps;
+    }
+    return 0;
+}
+
+extern "C" int grmhd_set_learned_guess(grmhd_ctx *ctx, int on)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (on && !ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
+    const float *want = on ? ctx->mlp : nullptr;
+    if (ctx->g.mlp == want) return 0;
+    // the captured step holds the grid record by value: capture again
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->g.mlp = want;
     return 0;
 }

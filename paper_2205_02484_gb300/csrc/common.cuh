@@ -30,6 +30,22 @@ __host__ __device__ constexpr int sym(int m, int n)
                   : (n == 0 ? m : (n == 1 ? 3 + m : (n == 2 ? 5 + m : 9)));
 }
 
+// splitmix64 (Steele, Lea & Flood 2014): one output of the generator whose
+// state before the call is x
+__host__ __device__ inline unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// counter-based uniform in [0, 1): the top 53 bits of splitmix64(seed ^ idx)
+__host__ __device__ inline double counter_uniform(unsigned long long seed, unsigned long long idx)
+{
+    return (double)(splitmix64(seed ^ idx) >> 11) * (1.0 / 9007199254740992.0);
+}
+
 template <typename R>
 struct Geo {
     R gcov[10];
@@ -80,6 +96,7 @@ struct Grid {
     int *faillist;              // compacted failed zones of a stage
     int *nfail;
     double *fixbuf;             // [5][nfix_cap] new primitives of a fixup sweep
+    const float *mlp;           // learned Newton start of the inversion (null: start from the stage's primitives)
 };
 
 __host__ __device__ __forceinline__ long long zidx(const Grid &g, int i, int j, int k)

@@ -136,30 +136,7 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     double Uz[NU], q0[NP], q[NP];
     for (int c = 0; c < NU; c++) Uz[c] = U[c * n + t];
     for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
-    double wg = 0.0;
-    if (mlp) {
-        // features of the learned Newton start (log-normalised, Section 2.3 variables)
-        double f = geo.alpha / geo.gdet;
-        double D = f * Uz[KRHO];
-        if (D > 0.0) {
-            double Q[4] = {f * Uz[1], f * Uz[2], f * Uz[3], f * Uz[4]};
-            double nq = Q[0] / geo.alpha;
-            for (int i = 1; i <= 3; i++) nq += -geo.alpha * geo.gcon[i] * Q[i];
-            double Qc[4];
-            for (int m = 0; m < 4; m++)
-                Qc[m] = geo.gcon[sym(m, 0)] * Q[0] + geo.gcon[sym(m, 1)] * Q[1] + geo.gcon[sym(m, 2)] * Q[2] +
-                        geo.gcon[sym(m, 3)] * Q[3];
-            double Qt2 = Qc[0] * Q[0] + Qc[1] * Q[1] + Qc[2] * Q[2] + Qc[3] * Q[3] + nq * nq;
-            double Bf[3] = {geo.alpha * Uz[KB1] / geo.gdet, geo.alpha * Uz[KB2] / geo.gdet,
-                            geo.alpha * Uz[KB3] / geo.gdet};
-            double B2 = spatial_sq(geo, Bf[0], Bf[1], Bf[2]);
-            double QB = Q[1] * Bf[0] + Q[2] * Bf[1] + Q[3] * Bf[2];
-            double tau = -nq - D;
-            double feat[5] = {log(fmax(tau / D, 1e-30)), log(fmax(Qt2 / (D * D), 1e-30)),
-                              log(fmax(B2 / D, 1e-30)), log(fmax(QB * QB / (D * D * D), 1e-30)), log(D)};
-            wg = D * exp((double)mlp_log_w_guess(mlp, feat));
-        }
-    }
+    double wg = mlp ? mlp_w_start(mlp, Uz, geo) : 0.0;
     int it;
     flags[t] = con2prim(Uz, geo, q0, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, q, it, wg);
     if (iters) iters[t] = it;

@@ -41,6 +41,39 @@ void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U,
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
                      long n, const float *mlp, cudaStream_t s);
 
+// mlp.cu (learned Newton start)
+struct MlpHyper {
+    double lr0, lr_min, b1, b2, eps, wd;
+    long long total_steps; // > 0: cosine from lr0 to lr_min over total_steps; else constant lr0
+};
+struct MlpTrainer {
+    float *theta, *m, *v; // FP32 master parameters and AdamW moments [MLP_NPARAM]
+    float *fwd;           // packed forward buffer (norm, biases, BF16 weights)
+    float *part;          // per-block gradient rows [blocks][MLP_NPARAM]
+    double *lpart;        // per-block loss sums [blocks]
+    long long *step;      // steps taken (device)
+    unsigned int *ticket; // last-block detection of the AdamW kernel
+    double *loss_hist;    // mean loss of step s at [s % hist_len]
+    long long hist_len;
+};
+void launch_mlp_samples(const Grid &g, unsigned long long seed, long long first, long long n, double *P, int *loc,
+                        double *U, float *feat, float *label, cudaStream_t s);
+void launch_mlp_forward(const float *fwd, const float *feat, long long n, float *y, cudaStream_t s);
+void launch_mlp_moments(const float *feat, const float *label, long long n, double *part, int nblk, cudaStream_t s);
+void launch_mlp_init(float *theta, unsigned long long seed, cudaStream_t s);
+void launch_mlp_pack(const float *theta, float *fwd, cudaStream_t s);
+size_t mlp_grad_smem();
+int mlp_grad_blocks(int batch);
+cudaError_t mlp_grad_setup();
+void launch_mlp_grad(const MlpTrainer &T, const float *feat, const float *label, long long n, int batch,
+                     unsigned long long mul, cudaStream_t s);
+void launch_mlp_adam(const MlpTrainer &T, int batch, const MlpHyper &h, cudaStream_t s);
+void launch_mlp_reduce_grad(const MlpTrainer &T, int batch, float *grad, cudaStream_t s);
+int mlp_eval_blocks(long long n);
+// part: 2 * mlp_eval_blocks(n) doubles
+void launch_mlp_eval(const float *fwd, const float *feat, const float *label, long long n, double *part,
+                     cudaStream_t s);
+
 // diag.cu
 void launch_diagnostics(const Grid &g, double *scratch, long scratch_len, double *out_dev, cudaStream_t s);
 void launch_copy_state_in(const Grid &g, const double *P, const double *U, cudaStream_t s);

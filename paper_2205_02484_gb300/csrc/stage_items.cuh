@@ -20,6 +20,7 @@
 // also the primitive storage type.
 #pragma once
 #include "fixes.cuh"
+#include "mlp.cuh"
 
 namespace grmhd {
 
@@ -334,7 +335,9 @@ struct UpdCount {
     unsigned it, nr, br, en, eb, fail, fl, ce, gc;
 };
 
-template <typename R>
+// LEARN: Newton starts from the learned W of the grid's network (g.mlp)
+// instead of the stage's guess primitives
+template <typename R, bool LEARN = false>
 __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *__restrict__ Pout,
                                    const R *__restrict__ F1, const R *__restrict__ F2,
                                    const R *__restrict__ F3, const R *__restrict__ E1,
@@ -420,7 +423,9 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     int it;
     constexpr bool MX = sizeof(R) == 4;
     const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
-    int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it, 0.0,
+    double wg = 0.0;
+    if constexpr (LEARN) wg = mlp_w_start(g.mlp, Un, geo);
+    int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it, wg,
                           gfr);
     cn.it += it;
     int meth = fl & 7;
@@ -614,13 +619,13 @@ __device__ __forceinline__ double flux_call(const Grid &g, const R *P, R *F, con
     }
 }
 
-template <typename R>
+template <typename R, bool LEARN = false>
 __device__ __forceinline__ void update_call(const Grid &g, const R *Pin, R *Pout, const R *F1, const R *F2,
                                             const R *F3, const R *E1, const R *E2, const R *E3, double dtfac,
                                             int corr, long long t, UpdCount &cn)
 {
-    if constexpr (sizeof(R) == 8) update_item_d(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
-    else update_item<R>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+    if constexpr (sizeof(R) == 8 && !LEARN) update_item_d(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+    else update_item<R, LEARN>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
 }
 
 template <typename R>

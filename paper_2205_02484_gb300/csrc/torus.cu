@@ -211,14 +211,6 @@ __global__ void k_sum_pairs(const double *part, int n, double *out)
     out[1] = b;
 }
 
-__device__ inline unsigned long long splitmix64(unsigned long long x)
-{
-    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 // perturbation, floors, conserved variables, write into the ghosted state
 template <typename RS>
 __global__ void k_torus_finish(Grid g, TorusArgs ta, const double *Pd, const unsigned char *intorus)
@@ -232,7 +224,7 @@ __global__ void k_torus_finish(Grid g, TorusArgs ta, const double *Pd, const uns
     double q[NP];
     for (int c = 0; c < NP; c++) q[c] = Pd[c * nact + t];
     if (intorus[i * g.n2 + j] && ta.pert_amp != 0.0) {
-        double xi = (double)(splitmix64(ta.seed ^ (unsigned long long)t) >> 11) * (1.0 / 9007199254740992.0);
+        double xi = counter_uniform(ta.seed, (unsigned long long)t);
         q[KUU] *= 1.0 + ta.pert_amp * (2.0 * xi - 1.0);
     }
     int m = midx(g, i, j);

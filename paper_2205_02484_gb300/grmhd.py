@@ -79,6 +79,26 @@ class EnsTiling(C.Structure):
 
 # every symbol include/grmhd.h declares, with its ctypes signature
 _V = C.c_void_p
+MLP_NPARAM = 4609
+MLP_NNORM = 12
+
+
+class MlpTrainParams(C.Structure):
+    _fields_ = [("n_samples", C.c_long), ("n_val", C.c_long), ("seed", C.c_ulonglong),
+                ("init_seed", C.c_ulonglong), ("epochs", C.c_int), ("batch", C.c_int),
+                ("lr", C.c_double), ("lr_min", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double), ("weight_decay", C.c_double)]
+
+
+class MlpTrainReport(C.Structure):
+    _fields_ = [("loss_first", C.c_double), ("loss_last", C.c_double), ("val_rmse", C.c_double),
+                ("val_maxerr", C.c_double), ("train_ms", C.c_double), ("samples_per_s", C.c_double),
+                ("steps", C.c_long)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 SIGNATURES = {
     "grmhd_init_grid": (C.c_int, [C.POINTER(GridParams), C.POINTER(PhysParams), C.POINTER(_V)]),
     "grmhd_set_metric": (C.c_int, [_V, C.c_double, C.c_int]),
@@ -105,6 +125,16 @@ SIGNATURES = {
     "grmhd_ensemble_sync": (C.c_int, [_V]),
     "grmhd_ensemble_destroy": (None, [_V]),
     "grmhd_ensemble_last_error": (C.c_char_p, [_V]),
+    "grmhd_mlp_load": (C.c_int, [_V, _V, _V]),
+    "grmhd_mlp_get": (C.c_int, [_V, _V, _V]),
+    "grmhd_mlp_samples": (C.c_int, [_V, C.c_ulonglong, C.c_long, C.c_long, _V, _V, _V, _V, _V, C.c_int]),
+    "grmhd_mlp_forward": (C.c_int, [_V, _V, C.c_long, _V, C.c_int]),
+    "grmhd_mlp_loss_grad": (C.c_int, [_V, _V, _V, _V, _V, C.c_long, _V, C.POINTER(C.c_double), C.c_int]),
+    "grmhd_mlp_train_steps": (C.c_int, [_V, _V, _V, _V, _V, C.c_long, C.c_long, C.c_long, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.POINTER(C.c_double), C.c_int]),
+    "grmhd_mlp_train": (C.c_int, [_V, C.POINTER(MlpTrainParams), C.POINTER(MlpTrainReport)]),
+    "grmhd_set_learned_guess": (C.c_int, [_V, C.c_int]),
 }
 
 PROF_SLOTS = 16
@@ -395,3 +425,97 @@ def peak_probe(device: int = 0, fp64: bool = True) -> float:
 
 def version() -> str:
     return load().grmhd_version().decode()
+
+
+# ------------------------------------------------------------ learned start
+
+def _f32_host(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def mlp_load(ctx: Context, theta, norm):
+    th = _f32_host(theta, MLP_NPARAM)
+    nm = _f32_host(norm, MLP_NNORM)
+    ctx.check(ctx.L.grmhd_mlp_load(ctx.h, th.ctypes.data, nm.ctypes.data))
+
+
+def mlp_get(ctx: Context):
+    th = np.zeros(MLP_NPARAM, dtype=np.float32)
+    nm = np.zeros(MLP_NNORM, dtype=np.float32)
+    ctx.check(ctx.L.grmhd_mlp_get(ctx.h, th.ctypes.data, nm.ctypes.data))
+    return th, nm
+
+
+def mlp_samples(ctx: Context, seed: int, first: int, n: int, device=False):
+    """Samples first..first+n-1 of the seeded training distribution:
+    P (8, n), loc (n), U (9, n), feat (5, n) FP32, label (n) FP32."""
+    if device:
+        import torch
+        dev = torch.device("cuda", ctx.grid.device)
+        P = torch.zeros((NP, n), dtype=torch.float64, device=dev)
+        loc = torch.zeros(n, dtype=torch.int32, device=dev)
+        U = torch.zeros((NU, n), dtype=torch.float64, device=dev)
+        feat = torch.zeros((5, n), dtype=torch.float32, device=dev)
+        lab = torch.zeros(n, dtype=torch.float32, device=dev)
+    else:
+        P, loc, U = np.zeros((NP, n)), np.zeros(n, dtype=np.int32), np.zeros((NU, n))
+        feat, lab = np.zeros((5, n), dtype=np.float32), np.zeros(n, dtype=np.float32)
+    ptrs = [_ptr(a)[0] for a in (P, loc, U, feat, lab)]
+    ctx.check(ctx.L.grmhd_mlp_samples(ctx.h, seed, first, n, *ptrs, int(device)))
+    return P, loc, U, feat, lab
+
+
+def mlp_forward(ctx: Context, feat, y=None):
+    n = feat.shape[-1]
+    if y is None:
+        y = np.zeros(n, dtype=np.float32)
+    fp, dev = _ptr(feat)
+    yp, _ = _ptr(y)
+    ctx.check(ctx.L.grmhd_mlp_forward(ctx.h, fp, n, yp, dev))
+    return y
+
+
+def mlp_loss_grad(ctx: Context, theta, norm, feat, label):
+    th = _f32_host(theta, MLP_NPARAM)
+    nm = _f32_host(norm, MLP_NNORM)
+    n = feat.shape[-1]
+    fp, dev = _ptr(feat)
+    lp, _ = _ptr(label)
+    if dev:
+        import torch
+        grad = torch.zeros(MLP_NPARAM, dtype=torch.float32, device=feat.device)
+    else:
+        grad = np.zeros(MLP_NPARAM, dtype=np.float32)
+    gp, _ = _ptr(grad)
+    loss = C.c_double()
+    ctx.check(ctx.L.grmhd_mlp_loss_grad(ctx.h, th.ctypes.data, nm.ctypes.data, fp, lp, n, gp, C.byref(loss), dev))
+    return loss.value, grad
+
+
+def mlp_train_steps(ctx: Context, theta, norm, feat, label, batch, nsteps, lr, beta1=0.9, beta2=0.999,
+                    eps=1e-8, weight_decay=0.0):
+    th = _f32_host(theta, MLP_NPARAM).copy()
+    nm = _f32_host(norm, MLP_NNORM)
+    n = feat.shape[-1]
+    fp, dev = _ptr(feat)
+    lp, _ = _ptr(label)
+    loss = C.c_double()
+    ctx.check(ctx.L.grmhd_mlp_train_steps(ctx.h, th.ctypes.data, nm.ctypes.data, fp, lp, n, batch, nsteps, lr,
+                                          beta1, beta2, eps, weight_decay, C.byref(loss), dev))
+    return th, loss.value
+
+
+def mlp_train(ctx: Context, n_samples=10_000_000, n_val=100_000, seed=7, init_seed=1, epochs=4, batch=4096,
+              lr=2e-3, lr_min=2e-5, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-4) -> dict:
+    tp = MlpTrainParams(n_samples, n_val, seed, init_seed, epochs, batch, lr, lr_min, beta1, beta2, eps,
+                        weight_decay)
+    rep = MlpTrainReport()
+    ctx.check(ctx.L.grmhd_mlp_train(ctx.h, C.byref(tp), C.byref(rep)))
+    return rep.as_dict()
+
+
+def set_learned_guess(ctx: Context, on: bool = True):
+    ctx.check(ctx.L.grmhd_set_learned_guess(ctx.h, int(on)))
