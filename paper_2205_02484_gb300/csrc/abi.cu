@@ -108,7 +108,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     if (grid->riemann != GRMHD_LLF && grid->riemann != GRMHD_HLL)
         return fail(nullptr, GRMHD_EINVAL, "riemann must be GRMHD_LLF or GRMHD_HLL");
     if (!(phys->gam > 1.0) || !(phys->cfl > 0.0) || phys->nr_maxit < 1 || phys->brent_maxit < 1 ||
-        phys->fix_maxsweep < 1)
+        phys->fix_maxsweep < 1 || !(phys->sigma_max > 0.0) || !(phys->bu_max > 0.0) || !(phys->gamma_max >= 1.0))
         return fail(nullptr, GRMHD_EINVAL, "bad physics parameters");
     long long N1 = grid->n1 + 2 * NG, N2 = grid->n2 + 2 * NG, N3 = grid->n3 + 2 * NG;
     long long nz = N1 * N2 * N3;
@@ -133,6 +133,11 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.mixed = grid->precision == GRMHD_MIXED;
     g.gam = phys->gam; g.cfl = phys->cfl; g.nr_tol = phys->nr_tol; g.sigma_max = phys->sigma_max;
     g.bu_max = phys->bu_max; g.gamma_max = phys->gamma_max; g.beta_ent = phys->beta_entropy;
+    g.g1 = (g.gam - 1.0) / g.gam;
+    g.igm1 = 1.0 / (g.gam - 1.0);
+    g.isig = 1.0 / g.sigma_max;
+    g.ibu = 1.0 / g.bu_max;
+    g.nr_tol_mixed = std::sqrt(g.nr_tol);
     g.nr_maxit = phys->nr_maxit; g.brent_maxit = phys->brent_maxit; g.fix_maxsweep = phys->fix_maxsweep;
     long long nact = (long long)g.n1 * g.n2 * g.n3;
     g.nfix_cap = (int)std::min<long long>(nact, 1LL << 20);
@@ -154,6 +159,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     if (!rc) rc = dalloc(ctx, &b.conn, nm * 40);
     if (!rc) rc = dalloc(ctx, &b.connF, nm * 40);
     if (!rc) rc = dalloc(ctx, &b.rc, nm);
+    if (!rc) rc = dalloc(ctx, &b.gsp, nm * 6);
     if (!rc) rc = dalloc(ctx, &b.polar2, nm);
     if (!rc) rc = dalloc(ctx, &g.scal, 8);
     if (!rc) rc = dalloc(ctx, &g.dtmin, 4);
@@ -174,7 +180,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     }
     g.gc = b.gc; g.gf1 = b.gf1; g.gf2 = b.gf2;
     g.gcF = b.gcF; g.gf1F = b.gf1F; g.gf2F = b.gf2F;
-    g.conn = b.conn; g.connF = b.connF; g.rc = b.rc; g.polar2 = b.polar2;
+    g.conn = b.conn; g.connF = b.connF; g.rc = b.rc; g.polar2 = b.polar2; g.gsp = b.gsp;
     unsigned long long inf = 0x7FF0000000000000ULL;
     unsigned long long h[4] = {inf, inf, inf, inf};
     cudaMemcpyAsync(g.dtmin, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream);

@@ -75,6 +75,8 @@ struct Grid {
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
     double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
+    double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max
+    double nr_tol_mixed;        // sqrt(nr_tol): Newton acceptance of the mixed path
     int nr_maxit, brent_maxit, fix_maxsweep, pad0;
     // metric tables
     const Geo<double> *gc, *gf1, *gf2;
@@ -82,6 +84,8 @@ struct Grid {
     const double *conn; // [N1*N2][40]: conn[l*10 + sym(m,n)]
     const float *connF;
     const double *rc;   // r of zone centres (1 for flat space)
+    const double *gsp;  // [N1*N2][6] spatial inverse metric at centres, g^{ij} - g^{ti} g^{tj} / g^{tt}
+                        // (packed 11 12 13 22 23 33)
     const unsigned char *polar2; // X2 face on a pole
     // state
     void *P[2];

@@ -28,13 +28,31 @@ constexpr int C2P_FAIL = 8, C2P_FAIL_D = 16, C2P_FAIL_ENT = 32;
 constexpr double V2MAX = 1.0 - 1.0e-16;
 
 struct C2PIn {
-    double D, Qtsq, Bsq, QB, nQ, Sent, gam;
+    double D, Qtsq, Bsq, QB, nQ, Sent, gam, g1, igm1; // g1 = (gam-1)/gam, igm1 = 1/(gam-1)
     double Qt[3], Bf[3];
 };
 
+// solver parameters of a grid; the EOS ratios and the mixed path's Newton
+// acceptance sqrt(tol) are formed once on the host
+struct C2PPar {
+    double gam, g1, igm1, beta_ent, tol, tol_mixed;
+    int nr_maxit, brent_maxit;
+};
+
+__device__ __forceinline__ C2PPar c2p_par(const Grid &g)
+{
+    return C2PPar{g.gam, g.g1, g.igm1, g.beta_ent, g.nr_tol, g.nr_tol_mixed, g.nr_maxit, g.brent_maxit};
+}
+
+// finite test on the high word: integer pipe instead of an FP64 compare
+__device__ __forceinline__ bool finite64(double x)
+{
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 __device__ __forceinline__ double c2p_pressure(const C2PIn &c, double W, double v2)
 {
-    return (c.gam - 1.0) / c.gam * (W * (1.0 - v2) - c.D * sqrt(1.0 - v2));
+    return c.g1 * (W * (1.0 - v2) - c.D * sqrt(1.0 - v2));
 }
 
 // primitives from (W, v^2) and the pressure; ut^i = Gamma/(W+B^2) (Qt^i + (Q.B) B^i / W)
@@ -43,17 +61,22 @@ __device__ __forceinline__ void c2p_recover(const C2PIn &c, double W, double v2,
     double omv = 1.0 - v2;
     double lor = rsqrt(omv);
     P[KRHO] = c.D * (omv * lor);
-    P[KUU] = p / (c.gam - 1.0);
-    double f = lor / (W + c.Bsq);
-    double qbw = c.QB / W;
+    P[KUU] = p * c.igm1;
+    // 1/(W + B^2) and 1/W from one reciprocal
+    double WB = W + c.Bsq;
+    double r = 1.0 / (W * WB);
+    double f = lor * (W * r);
+    double qbw = c.QB * (WB * r);
 #pragma unroll
     for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + qbw * c.Bf[i]);
 }
 
 __device__ __forceinline__ bool c2p_physical(const double *P, double v2)
 {
-    bool fin = isfinite(P[0]) && isfinite(P[1]) && isfinite(P[2]) && isfinite(P[3]) && isfinite(P[4]);
-    return fin && P[KRHO] > 0.0 && P[KUU] > 0.0 && v2 >= 0.0 && v2 < 1.0;
+    bool fin = finite64(P[0]) && finite64(P[1]) && finite64(P[2]) && finite64(P[3]) && finite64(P[4]);
+    // finite doubles: x > 0 exactly when the signed 64-bit pattern is > 0
+    return fin && __double_as_longlong(P[KRHO]) > 0 && __double_as_longlong(P[KUU]) > 0 && v2 >= 0.0 &&
+           v2 < 1.0;
 }
 
 // Brent's bracketing root finder (Brent 1973): bisection safeguarded
@@ -137,7 +160,7 @@ struct ResidS {
     {
         double lor = 1.0 / sqrt(1.0 - v2);
         double rho = c->D / lor;
-        return lor * c->D + lor * c->gam / (c->gam - 1.0) * pow(rho, c->gam - 1.0) * c->Sent;
+        return lor * c->D + lor * c->gam * c->igm1 * pow(rho, c->gam - 1.0) * c->Sent;
     }
     __device__ double operator()(double v2) const
     {
@@ -151,7 +174,7 @@ template <bool EXTRA>
 __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double tol, int maxit,
                                   int &iters)
 {
-    const double g1 = (c.gam - 1.0) / c.gam;
+    const double g1 = c.g1;
     const double QB2 = c.QB * c.QB;
     bool extra = false;
     int n = 0;
@@ -171,7 +194,7 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
         double a21 = -qw2 * iW - 1.0 + g1 * omv;
         double a22 = -0.5 * c.Bsq + g1 * (-W + 0.5 * c.D * is);
         double det = a11 * a22 - a12 * a21;
-        if (!(fabs(det) > 0.0) || !isfinite(det)) break;
+        if (!finite64(det) || (__double_as_longlong(det) << 1) == 0) break; // non-finite or +-0
         double idet = 1.0 / det;
         double dW = -(a22 * f1 - a12 * f2) * idet;
         double dv = -(-a21 * f1 + a11 * f2) * idet;
@@ -181,7 +204,7 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
         bool conv = fabs(Wn - W) < tol * fabs(Wn) && fabs(vn - v2) < tol;
         W = Wn;
         v2 = vn;
-        if (!isfinite(W) || !isfinite(v2)) break;
+        if (!finite64(W) || !finite64(v2)) break;
         if (extra) {
             iters = n;
             return true;
@@ -230,90 +253,105 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
     return c2p_physical(P, v2);
 }
 
-// Full inversion of one zone.  U includes sqrt(-g); guess = previous prims.
-// Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g).
+// Full inversion of one zone.  U includes sqrt(-g); gsp = the spatial
+// inverse metric gamma^{ij} of the zone (packed 11 12 13 22 23 33).
+// Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g), and on
+// failure P[0..4] keep the guess (the fixups repair the zone).
 // methods: 1 Newton, 2 Brent-W, 4 entropy, 8 beta switch (15 = paper order).
 // wguess > 0 replaces the Newton starting W (learned guess; v^2 from Eq. 29).
-// MIXED: no confirmation Newton step, and the beta switch evaluated in FP32
-// with the FP32 metric record gf (must be non-null then).
+// FP64 path: guess = the previous FP64 primitives, Newton takes one more step
+// after the tolerance.  MIXED: guessf = the previous FP32 primitives (guess
+// unused); the starting (W, v^2) and the beta switch are formed in FP32 with
+// the FP32 metric record gf, and Newton stops once its step is below
+// sqrt(tol) -- quadratic convergence then leaves an error of order tol.
 template <bool MIXED = false>
-__device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double guess[NP],
-                               double gam, double beta_ent, double tol, int nr_maxit,
-                               int brent_maxit, int methods, double P[NP], int &iters,
-                               double wguess = 0.0, const Geo<float> *gf = nullptr)
+__device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double gsp[6],
+                               const double *guess, const float *guessf, const C2PPar &par, int methods,
+                               double P[NP], int &iters, double wguess = 0.0, const Geo<float> *gf = nullptr)
 {
     iters = 0;
+    if (!MIXED) {
 #pragma unroll
-    for (int m = 0; m < NP; m++) P[m] = guess[m];
-    double f = g.aig;
+        for (int m = 0; m < 5; m++) P[m] = guess[m];
+    }
+    auto fail = [&](int code) {
+        if (MIXED) {
+#pragma unroll
+            for (int m = 0; m < 5; m++) P[m] = (double)guessf[m];
+        }
+        return code;
+    };
+    const double f = g.aig;
     P[KB1] = U[KB1] * g.igdet;
     P[KB2] = U[KB2] * g.igdet;
     P[KB3] = U[KB3] * g.igdet;
     C2PIn c;
-    c.gam = gam;
+    c.gam = par.gam;
+    c.g1 = par.g1;
+    c.igm1 = par.igm1;
     c.D = f * U[KRHO];
-    double Q[4] = {f * U[1], f * U[2], f * U[3], f * U[4]};
+    const double Q0 = f * U[1], Q1 = f * U[2], Q2 = f * U[3], Q3 = f * U[4];
     c.Sent = f * U[KENT];
-    double n[4] = {g.ialpha, -g.alpha * g.gcon[1], -g.alpha * g.gcon[2], -g.alpha * g.gcon[3]};
-    double Qc[4];
+    // n^mu = (1/alpha, -alpha g^{ti}); the projection j^{mu nu} = g^{mu nu} +
+    // n^mu n^nu has j^{t mu} = 0 and j^{ij} = gamma^{ij}, so Qt^i = gamma^{ij} Q_j
+    // and Qt^2 = Qt^i Q_i (no cancellation against the energy)
+    c.nQ = g.ialpha * Q0 - g.alpha * (g.gcon[1] * Q1 + g.gcon[2] * Q2 + g.gcon[3] * Q3);
+    c.Qt[0] = gsp[0] * Q1 + gsp[1] * Q2 + gsp[2] * Q3;
+    c.Qt[1] = gsp[1] * Q1 + gsp[3] * Q2 + gsp[4] * Q3;
+    c.Qt[2] = gsp[2] * Q1 + gsp[4] * Q2 + gsp[5] * Q3;
+    c.Qtsq = c.Qt[0] * Q1 + c.Qt[1] * Q2 + c.Qt[2] * Q3;
 #pragma unroll
-    for (int m = 0; m < 4; m++)
-        Qc[m] = g.gcon[sym(m, 0)] * Q[0] + g.gcon[sym(m, 1)] * Q[1] + g.gcon[sym(m, 2)] * Q[2] +
-                g.gcon[sym(m, 3)] * Q[3];
-    c.nQ = n[0] * Q[0] + n[1] * Q[1] + n[2] * Q[2] + n[3] * Q[3];
-    double Qsq = Qc[0] * Q[0] + Qc[1] * Q[1] + Qc[2] * Q[2] + Qc[3] * Q[3];
-    c.Qtsq = Qsq + c.nQ * c.nQ;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        c.Qt[i] = Qc[i + 1] + n[i + 1] * c.nQ;
-        c.Bf[i] = g.alpha * P[KB1 + i];
-    }
-    c.QB = Q[1] * c.Bf[0] + Q[2] * c.Bf[1] + Q[3] * c.Bf[2];
+    for (int i = 0; i < 3; i++) c.Bf[i] = g.alpha * P[KB1 + i];
+    c.QB = Q1 * c.Bf[0] + Q2 * c.Bf[1] + Q3 * c.Bf[2];
     c.Bsq = spatial_sq(g, c.Bf[0], c.Bf[1], c.Bf[2]);
-    bool fin = isfinite(c.D) && isfinite(c.Qtsq) && isfinite(c.nQ) && isfinite(c.Bsq);
-    if (!fin || !(c.D > 0.0)) return C2P_FAIL | C2P_FAIL_D;
+    bool fin = finite64(c.D) && finite64(c.Qtsq) && finite64(c.nQ) && finite64(c.Bsq);
+    if (!fin || !(c.D > 0.0)) return fail(C2P_FAIL | C2P_FAIL_D);
 
     if (methods & 8) {
         bool low_beta;
         if (MIXED) {
-            float qf[NP];
-#pragma unroll
-            for (int m = 0; m < NP; m++) qf[m] = (float)guess[m];
             St<float> s;
-            get_state(qf, *gf, s);
-            float pg = ((float)gam - 1.0f) * qf[KUU];
-            low_beta = s.bsq > 0.0f && pg < (float)beta_ent * 0.5f * s.bsq;
+            get_state(guessf, *gf, s);
+            float pg = ((float)par.gam - 1.0f) * guessf[KUU];
+            low_beta = s.bsq > 0.0f && pg < (float)par.beta_ent * 0.5f * s.bsq;
         } else {
             St<double> s;
             get_state(guess, g, s);
-            double pg = (gam - 1.0) * guess[KUU];
-            low_beta = s.bsq > 0.0 && pg < beta_ent * 0.5 * s.bsq;
+            double pg = (par.gam - 1.0) * guess[KUU];
+            low_beta = s.bsq > 0.0 && pg < par.beta_ent * 0.5 * s.bsq;
         }
         if (low_beta) {
-            if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY_BETA;
-            return C2P_FAIL | C2P_FAIL_ENT;
+            if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY_BETA;
+            return fail(C2P_FAIL | C2P_FAIL_ENT);
         }
     }
     if (methods & 1) {
-        double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
-        double v2 = usq / (1.0 + usq);
-        double W = (1.0 + usq) * (guess[KRHO] + gam * guess[KUU]);
+        double v2, W;
+        if (MIXED) {
+            float usq = spatial_sq(*gf, guessf[KU1], guessf[KU2], guessf[KU3]);
+            v2 = (double)(usq / (1.0f + usq));
+            W = (double)((1.0f + usq) * (guessf[KRHO] + (float)par.gam * guessf[KUU]));
+        } else {
+            double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
+            v2 = usq / (1.0 + usq);
+            W = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
+        }
         if (wguess > 0.0) {
             W = wguess;
             v2 = ResidW{&c}.v2(W);
         }
-        if (!(W > 0.0) || !isfinite(W)) W = c.D;
+        if (!(W > 0.0) || !finite64(W)) W = c.D;
         v2 = fmin(v2, V2MAX);
-        if (c2p_newton<!MIXED>(c, W, v2, tol, nr_maxit, iters)) {
+        if (c2p_newton<!MIXED>(c, W, v2, MIXED ? par.tol_mixed : par.tol, par.nr_maxit, iters)) {
             c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
             if (c2p_physical(P, v2)) return C2P_NR;
-            if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY;
-            return C2P_FAIL | C2P_FAIL_ENT;
+            if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
+            return fail(C2P_FAIL | C2P_FAIL_ENT);
         }
     }
-    if ((methods & 2) && c2p_brent_w(c, brent_maxit, P)) return C2P_BRENT_W;
-    if ((methods & 4) && c2p_entropy(c, brent_maxit, P)) return C2P_ENTROPY;
-    return C2P_FAIL | C2P_FAIL_ENT;
+    if ((methods & 2) && c2p_brent_w(c, par.brent_maxit, P)) return C2P_BRENT_W;
+    if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
+    return fail(C2P_FAIL | C2P_FAIL_ENT);
 }
 
 } // namespace grmhd

@@ -138,7 +138,7 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
     double wg = mlp ? mlp_w_start(mlp, Uz, geo) : 0.0;
     int it;
-    flags[t] = con2prim(Uz, geo, q0, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, q, it, wg);
+    flags[t] = con2prim(Uz, geo, g.gsp + 6LL * midx(g, l / g.n2, l % g.n2), q0, nullptr, c2p_par(g), 15, q, it, wg);
     if (iters) iters[t] = it;
     for (int c = 0; c < NP; c++) P[c * n + t] = q[c];
 }

@@ -27,36 +27,40 @@ __device__ __forceinline__ bool gamma_cap(const Grid &g, const Geo<double> &geo,
     return false;
 }
 
-// b^2 of primitives q; in the mixed path from the FP32 record gf
-template <bool MIXED>
-__device__ __forceinline__ double bsq_of(const double q[NP], const Geo<double> &geo, const Geo<float> *gf)
-{
-    if (MIXED) {
-        float qf[NP];
-#pragma unroll
-        for (int m = 0; m < NP; m++) qf[m] = (float)q[m];
-        St<float> s;
-        get_state(qf, *gf, s);
-        return (double)s.bsq;
-    }
-    St<double> s;
-    get_state(q, geo, s);
-    return s.bsq;
-}
-
-// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied
+// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied.
+// gsp: the zone's spatial inverse metric (for the re-inversion of a ceiling).
+// MIXED: b^2 and ut^2 (neither involves rho or u) come from one FP32 state of
+// the record gf; the exact FP64 Lorentz test runs only where the FP32 ut^2 is
+// within 1e-4 of the cap; qf receives the FP32 primitives to store.
 template <bool MIXED = false>
-__device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, double q[NP],
-                                     const double Un[NU], const Geo<float> *gf = nullptr)
+__device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, const double *gsp, double q[NP],
+                                     const double Un[NU], const Geo<float> *gf = nullptr, float *qf = nullptr)
 {
     int res = 0;
     if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
     if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }
-    double bsq = bsq_of<MIXED>(q, geo, gf);
-    double drho = fmax(0.0, bsq / g.sigma_max - q[KRHO]);
-    double du = fmax(0.0, bsq / g.bu_max - q[KUU]);
+    double bsq;
+    float usqf = 0.0f;
+    if (MIXED) {
+        qf[KRHO] = 0.0f;
+        qf[KUU] = 0.0f;
+#pragma unroll
+        for (int m = KU1; m < NP; m++) qf[m] = (float)q[m];
+        St<float> s;
+        get_state(qf, *gf, s);
+        bsq = (double)s.bsq;
+        usqf = s.usq;
+    } else {
+        St<double> s;
+        get_state(q, geo, s);
+        bsq = s.bsq;
+    }
+    double drho = fmax(0.0, bsq * g.isig - q[KRHO]);
+    double du = fmax(0.0, bsq * g.ibu - q[KUU]);
+    bool moved = false;
     if (drho > 0.0 || du > 0.0) {
         res |= 3;
+        moved = true;
         double dq[NP] = {drho, du, 0, 0, 0, 0, 0, 0};
         St<double> ds;
         get_state(dq, geo, ds);
@@ -69,7 +73,7 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, doub
         gs[KRHO] += drho;
         gs[KUU] += du;
         int it;
-        int fl = con2prim<false>(U2, geo, gs, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 1, qn, it);
+        int fl = con2prim<false>(U2, geo, gsp, gs, nullptr, c2p_par(g), 1, qn, it);
         if (fl == C2P_NR) {
 #pragma unroll
             for (int c = 0; c < NP; c++) q[c] = qn[c];
@@ -78,7 +82,23 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, doub
             q[KUU] += du;
         }
     }
-    if (gamma_cap(g, geo, q)) res |= 5;
+    bool test_cap = true;
+    if (MIXED && !moved) {
+        float gm = (float)g.gamma_max;
+        test_cap = 1.0f + usqf > gm * gm * 0.9999f;
+    }
+    if (test_cap && gamma_cap(g, geo, q)) {
+        res |= 5;
+        moved = true;
+    }
+    if (MIXED) {
+        if (moved) {
+#pragma unroll
+            for (int m = KU1; m < NP; m++) qf[m] = (float)q[m];
+        }
+        qf[KRHO] = (float)q[KRHO];
+        qf[KUU] = (float)q[KUU];
+    }
     return res;
 }
 
@@ -102,14 +122,16 @@ __device__ inline void post_fixup(const Grid &g, const Geo<double> &geo, double 
 // U_E = (U_E + U_rho) - U_rho is assembled in FP64.  The inversion depends on
 // E - D, which is therefore carried with FP32 relative accuracy of the
 // thermal + kinetic + binding energy, not of the rest mass.
+//
+// qf (mixed path, may be null): the FP32 primitives of q, if the caller has them.
 template <bool MIXED = false>
 __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, double gam, double U[NU],
-                               const Geo<float> *gf = nullptr)
+                               const Geo<float> *gf = nullptr, const float *qfin = nullptr)
 {
     if (MIXED) {
         float qf[NP];
 #pragma unroll
-        for (int m = 0; m < NP; m++) qf[m] = (float)q[m];
+        for (int m = 0; m < NP; m++) qf[m] = qfin ? qfin[m] : (float)q[m];
         St<float> s;
         get_state(qf, *gf, s);
         float Uf[NU], Ff[NU];

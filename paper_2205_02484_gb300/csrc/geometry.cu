@@ -99,6 +99,15 @@ __global__ void k_geometry(Grid g, GeomBuild b)
     double X2c = g.x2in + (j + 0.5) * g.dx[1], X2f = g.x2in + j * g.dx[1];
     double gi[4][4];
     make_geo(b.cp, X1c, X2c, b.gc[t], b.gcF[t], gi);
+    {
+        // spatial part of the projector j^{mu nu} = g^{mu nu} + n^mu n^nu:
+        // gamma^{ij} = g^{ij} - g^{ti} g^{tj} / g^{tt}
+        const double *gu = b.gc[t].gcon;
+        int q = 0;
+        for (int a = 1; a < 4; a++)
+            for (int c = a; c < 4; c++)
+                b.gsp[(long long)t * 6 + q++] = gu[0] != 0.0 ? gu[sym(a, c)] - gu[sym(0, a)] * gu[sym(0, c)] / gu[0] : 0.0;
+    }
     // connection at the centre
     Dual dg[2][4][4];
     {

@@ -20,6 +20,7 @@ struct GeomBuild {
     double *conn;
     float *connF;
     double *rc;
+    double *gsp;
     unsigned char *polar2;
 };
 void launch_geometry(const Grid &g, const GeomBuild &b, cudaStream_t s);

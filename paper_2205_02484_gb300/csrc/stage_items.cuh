@@ -354,24 +354,35 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     int m = midx(g, i, j);
     const long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
     const double dts = dtfac * g.scal[0];
+    constexpr bool MX = sizeof(R) == 4;
+    // the stage primitives: FP64 (FP64 path), or as stored in FP32 (mixed
+    // path; widened only where the FP64 source needs them)
     double q[NP];
+    float qin[NP];
+    if constexpr (MX) {
 #pragma unroll
-    for (int c = 0; c < NP; c++) q[c] = (double)Pin[c * nz + z];
+        for (int c = 0; c < NP; c++) qin[c] = (float)Pin[c * nz + z];
+    } else {
+#pragma unroll
+        for (int c = 0; c < NP; c++) q[c] = (double)Pin[c * nz + z];
+    }
     const Geo<double> geo = g.gc[m];
     // source (Eq. 15)
     double src[4];
-    if (sizeof(R) == 8 || i < g.i_h + NHZ) {
+    if (!MX || i < g.i_h + NHZ) {
+        if constexpr (MX) {
+#pragma unroll
+            for (int c = 0; c < NP; c++) q[c] = (double)qin[c];
+        }
         St<double> s;
         get_state(q, geo, s);
         source_terms(q, geo, g.conn + (long long)m * 40, s, g.gam, src);
     } else {
         const Geo<float> gf = g.gcF[m];
-        float qf[NP], sf[4];
-#pragma unroll
-        for (int c = 0; c < NP; c++) qf[c] = (float)Pin[c * nz + z];
+        float sf[4];
         St<float> s;
-        get_state(qf, gf, s);
-        source_terms(qf, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
+        get_state(qin, gf, s);
+        source_terms(qin, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
 #pragma unroll
         for (int c = 0; c < 4; c++) src[c] = sf[c];
     }
@@ -420,13 +431,14 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         }
     }
     double qn[NP];
+    float qnf[NP];
     int it;
-    constexpr bool MX = sizeof(R) == 4;
     const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
+    const double *gsp = g.gsp + 6LL * m;
     double wg = 0.0;
     if constexpr (LEARN) wg = mlp_w_start(g.mlp, Un, geo);
-    int fl = con2prim<MX>(Un, geo, q, g.gam, g.beta_ent, g.nr_tol, g.nr_maxit, g.brent_maxit, 15, qn, it, wg,
-                          gfr);
+    int fl = con2prim<MX>(Un, geo, gsp, q, qin, c2p_par(g), 15, qn, it, wg, gfr);
+    bool ok = !(fl & C2P_FAIL);
     cn.it += it;
     int meth = fl & 7;
     if (fl & C2P_FAIL) {
@@ -440,16 +452,21 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         cn.br += meth == C2P_BRENT_W;
         cn.en += meth == C2P_ENTROPY;
         cn.eb += meth == C2P_ENTROPY_BETA;
-        int res = post_inversion<MX>(g, geo, qn, Un, gfr);
+        int res = post_inversion<MX>(g, geo, gsp, qn, Un, gfr, qnf);
         if (res & 1) {
             cn.fl += 1;
-            cons_of<MX>(qn, geo, g.gam, Un, gfr);
+            cons_of<MX>(qn, geo, g.gam, Un, gfr, MX ? qnf : nullptr);
         }
         cn.ce += (res & 2) != 0;
         cn.gc += (res & 4) != 0;
     }
+    if (MX && ok) {
 #pragma unroll
-    for (int c = 0; c < NP; c++) Pout[c * nz + z] = (R)qn[c];
+        for (int c = 0; c < NP; c++) Pout[c * nz + z] = (R)qnf[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < NP; c++) Pout[c * nz + z] = (R)qn[c];
+    }
     if (corr) {
 #pragma unroll
         for (int c = 0; c < NU; c++) g.U[c * nz + z] = Un[c];
