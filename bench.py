@@ -409,11 +409,13 @@ def main():
     fp64_peak = G.peak_probe(local, True)
     fp32_peak = G.peak_probe(local, False)
     # The dominant kernel (stage update + FP64 inversion) is bound by the FP64
-    # pipe.  Its FP64 work per zone and stage, 539 flops (DFMA counted as 2),
-    # is the executed FP64 arithmetic counted by ncu on the 96^3 mixed torus;
-    # its DRAM traffic there was 227 B per zone (scaled here by zone count).
+    # pipe.  Its FP64 work per zone and stage, 280 flops (89 DFMA counted as
+    # 2, 80 DMUL, 22 DADD), is the executed FP64 arithmetic counted by ncu on
+    # the 96^3 mixed torus; its DRAM traffic there was 227 B per zone (scaled
+    # here by zone count).  The FP64 pipe was 86% busy: conversions, compares
+    # and the one-flop DMUL/DADD slots fill the rest.
     # Peak: 152 SMs x 2 DFMA/clock x 2 flops x 2.07 GHz.
-    fp64_flops_per_zone_stage = 539.0
+    fp64_flops_per_zone_stage = 280.2
     fp64_peak_units = 152 * 2 * 2 * 2.070e9 / 1e12
     ach = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
@@ -421,7 +423,8 @@ def main():
                 "frac": ach / fp64_peak_units, "traffic": 227.0 * zones,
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 x 2070 MHz; FMA-chain probe on this GPU: "
                                f"{fp64_peak:.3f} TFLOP/s",
-                "ms_per_launch": upd, "flops_per_zone": fp64_flops_per_zone_stage}
+                "ms_per_launch": upd, "flops_per_zone": fp64_flops_per_zone_stage,
+                "fp64_pipe_active_ncu": 0.859}
     hbm_step = HBM_BYTES_PER_ZONE_CYCLE["mixed"] * zones / (ms_step * 1e-3) / 1e9
     gpu_launches = 21 * args.steps
     # ---- e2e through the public API with pinned host buffers
