@@ -38,9 +38,9 @@ struct EnsDev {
 __host__ __device__ inline long long class_count(const Grid &g, int cls)
 {
     switch (cls) {
-    case W_F1: return flux_box(g, 1).count();
-    case W_F2: return flux_box(g, 2).count();
-    case W_F3: return flux_box(g, 3).count();
+    case W_F1: return flux_elem_box(g, 1).count();
+    case W_F2: return flux_elem_box(g, 2).count();
+    case W_F3: return flux_elem_box(g, 3).count();
     case W_EMF: return edge_box(g).count();
     case W_UPD: return nact_of(g);
     case W_POL: return polar_count(g);
@@ -86,9 +86,12 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
         UpdCount cn{};
         for (int it = 0; it < items; it++) {
             long long t = base + (long long)it * blockDim.x + threadIdx.x;
-            if (CLS == W_F1) dtc = fmin(dtc, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_box(sg, 1), want_dt, t));
-            if (CLS == W_F2) dtc = fmin(dtc, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_box(sg, 2), want_dt, t));
-            if (CLS == W_F3) dtc = fmin(dtc, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_box(sg, 3), want_dt, t));
+            if (CLS == W_F1)
+                dtc = fmin(dtc, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_elem_box(sg, 1), want_dt, t));
+            if (CLS == W_F2)
+                dtc = fmin(dtc, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_elem_box(sg, 2), want_dt, t));
+            if (CLS == W_F3)
+                dtc = fmin(dtc, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
             if (CLS == W_EMF)
                 emf_item(sg, (const R *)sg.F[0], (const R *)sg.F[1], (const R *)sg.F[2], (R *)sg.E[0], (R *)sg.E[1],
                          (R *)sg.E[2], edge_box(sg), t);

@@ -229,14 +229,65 @@ __device__ __forceinline__ const Geo<float> *face_table<float>(const Grid &g, in
     return d == 1 ? g.gf1F : (d == 2 ? g.gf2F : g.gcF);
 }
 
+// Riemann flux of one face from its two reconstructed states (Eqs. 18-21);
+// cw receives the face's c_w.
+template <typename R, int D>
+__device__ __forceinline__ void face_flux(const Grid &g, const Geo<R> &geo, const R ql[NP], const R qr[NP],
+                                          R out[NU], R &cw)
+{
+    St<R> sl, sr;
+    get_state(ql, geo, sl);
+    get_state(qr, geo, sr);
+    R gam = (R)g.gam;
+    R c1l, c2l, c1r, c2r;
+    wave_speeds(ql, geo, sl, gam, D, c1l, c2l);
+    wave_speeds(qr, geo, sr, gam, D, c1r, c2r);
+    R cmax = fabs(fmax(R(0), fmax(c1r, c1l)));
+    R cmin = fabs(fmax(R(0), fmax(-c2r, -c2l)));
+    cw = fmax(cmax, cmin);
+    R wlF, wlU, wrF, wrU;
+    if (g.riemann == 1 && cmax + cmin > R(0)) {
+        R inv = R(1) / (cmax + cmin);
+        wlF = cmax * inv;
+        wrF = cmin * inv;
+        wlU = cmax * cmin * inv;
+        wrU = -wlU;
+    } else if (g.riemann == 1) {
+        wlF = wrF = R(0.5);
+        wlU = wrU = R(0);
+    } else {
+        wlF = wrF = R(0.5);
+        wlU = R(0.5) * cw;
+        wrU = -wlU;
+    }
+    constexpr bool RMS = sizeof(R) == 4;
+    R Ux[NU], Fx[NU];
+    prim_to_UF2<R, RMS>(ql, geo, sl, gam, D, Ux, Fx);
+#pragma unroll
+    for (int c = 0; c < NU; c++) out[c] = wlF * Fx[c] + wlU * Ux[c];
+    prim_to_UF2<R, RMS>(qr, geo, sr, gam, D, Ux, Fx);
+#pragma unroll
+    for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
+}
+
+// CFL candidate cfl dX^D / c_w of face (i, j, k) if it is an active face (else +inf)
+template <typename R, int D>
+__device__ __forceinline__ double face_dt(const Grid &g, int i, int j, int k, R cw)
+{
+    int ix[3] = {i, j, k}, nn[3] = {g.n1, g.n2, g.n3};
+    bool act = true;
+#pragma unroll
+    for (int e = 0; e < 3; e++) act = act && ix[e] >= 0 && ix[e] < nn[e] + (e == D - 1 ? 1 : 0);
+    return (act && cw > R(0)) ? g.cfl * g.dx[D - 1] / (double)cw : INFINITY;
+}
+
 // Face (i,j,k) of direction D lies between zone index-1 and index along D.
-// Returns the CFL candidate cfl dX^D / c_w of an active face (else +inf).
+// Returns the CFL candidate of an active face (else +inf).
 template <typename R, int D>
 __device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
                                             const Box &box, int want_dt, long long t)
 {
-    double dtc = INFINITY;
-    if (t >= box.count()) return dtc;
+    if (t >= box.count()) return INFINITY;
     int i, j, k;
     box_decode(box, t, i, j, k);
     long long z = zidx(g, i, j, k);
@@ -256,49 +307,83 @@ __device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__
             ql[c] = qm1 + R(0.5) * mc_slope(qm2, qm1, q0);
             qr[c] = q0 - R(0.5) * mc_slope(qm1, q0, qp1);
         }
-        const Geo<R> geo = face_table<R>(g, D)[midx(g, i, j)];
-        St<R> sl, sr;
-        get_state(ql, geo, sl);
-        get_state(qr, geo, sr);
-        R gam = (R)g.gam;
-        R c1l, c2l, c1r, c2r;
-        wave_speeds(ql, geo, sl, gam, D, c1l, c2l);
-        wave_speeds(qr, geo, sr, gam, D, c1r, c2r);
-        R cmax = fabs(fmax(R(0), fmax(c1r, c1l)));
-        R cmin = fabs(fmax(R(0), fmax(-c2r, -c2l)));
-        cw = fmax(cmax, cmin);
-        R wlF, wlU, wrF, wrU;
-        if (g.riemann == 1 && cmax + cmin > R(0)) {
-            R inv = R(1) / (cmax + cmin);
-            wlF = cmax * inv;
-            wrF = cmin * inv;
-            wlU = cmax * cmin * inv;
-            wrU = -wlU;
-        } else if (g.riemann == 1) {
-            wlF = wrF = R(0.5);
-            wlU = wrU = R(0);
-        } else {
-            wlF = wrF = R(0.5);
-            wlU = R(0.5) * cw;
-            wrU = -wlU;
-        }
-        constexpr bool RMS = sizeof(R) == 4;
-        R Ux[NU], Fx[NU];
-        prim_to_UF2<R, RMS>(ql, geo, sl, gam, D, Ux, Fx);
-#pragma unroll
-        for (int c = 0; c < NU; c++) out[c] = wlF * Fx[c] + wlU * Ux[c];
-        prim_to_UF2<R, RMS>(qr, geo, sr, gam, D, Ux, Fx);
-#pragma unroll
-        for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
+        face_flux<R, D>(g, face_table<R>(g, D)[midx(g, i, j)], ql, qr, out, cw);
     }
 #pragma unroll
     for (int c = 0; c < NU; c++) F[c * g.nz + z] = out[c];
-    if (want_dt) {
-        int ix[3] = {i, j, k}, nn[3] = {g.n1, g.n2, g.n3};
-        bool act = true;
+    return want_dt ? face_dt<R, D>(g, i, j, k, cw) : INFINITY;
+}
+
+// Columns of FCOL consecutive faces along X1 or X2: one thread walks its
+// column with a three-zone window in registers, so each zone is loaded and
+// its MC slope formed once instead of once per face (the face values are the
+// same numbers flux_item forms).  col_box counts columns: the face box with
+// its extent along D divided into chunks of FCOL (faces along D start at 0).
+constexpr int FCOL = 16;
+
+__host__ __device__ inline Box col_box(const Grid &g, int d)
+{
+    Box b = flux_box(g, d);
+    b.n[d - 1] = (b.n[d - 1] + FCOL - 1) / FCOL;
+    return b;
+}
+
+template <typename R, int D>
+__device__ __forceinline__ double flux_column(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                              const Box &cb, int want_dt, long long t)
+{
+    static_assert(D == 1 || D == 2, "columns run along X1 or X2");
+    double dtc = INFINITY;
+    if (t >= cb.count()) return dtc;
+    int i, j, k;
+    box_decode(cb, t, i, j, k);
+    const int nf = (D == 1 ? g.n1 : g.n2) + 1;
+    const int f0 = (D == 1 ? i : j) * FCOL, f1 = min(f0 + FCOL, nf);
+    if (D == 1) i = f0;
+    else j = f0;
+    const long long st = D == 1 ? (long long)g.N2 * g.N3 : g.N3;
+    const long long z0 = zidx(g, i, j, k); // zone f0; face f lies between zones f-1 and f
+    // zones f-1, f, f+1 of the current face f and the slope of zone f-1
+    R qa[NP], qb[NP], qc[NP], sa[NP];
 #pragma unroll
-        for (int e = 0; e < 3; e++) act = act && ix[e] >= 0 && ix[e] < nn[e] + (e == D - 1 ? 1 : 0);
-        if (act && cw > R(0)) dtc = g.cfl * g.dx[D - 1] / (double)cw;
+    for (int c = 0; c < NP; c++) {
+        const R *pc = P + c * g.nz + z0;
+        R qm2 = ldg(pc - 2 * st);
+        qa[c] = ldg(pc - st);
+        qb[c] = ldg(pc);
+        qc[c] = ldg(pc + st);
+        sa[c] = mc_slope(qm2, qa[c], qb[c]);
+    }
+    for (int f = f0; f < f1; f++) {
+        const int fi = D == 1 ? f : i, fj = D == 2 ? f : j;
+        R ql[NP], qr[NP], sb[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            sb[c] = mc_slope(qa[c], qb[c], qc[c]);
+            ql[c] = qa[c] + R(0.5) * sa[c];
+            qr[c] = qb[c] - R(0.5) * sb[c];
+        }
+        R out[NU];
+        R cw = R(0);
+        if (D == 2 && g.polar2[midx(g, fi, fj)]) {
+#pragma unroll
+            for (int c = 0; c < NU; c++) out[c] = R(0);
+        } else {
+            face_flux<R, D>(g, face_table<R>(g, D)[midx(g, fi, fj)], ql, qr, out, cw);
+        }
+        const long long zf = z0 + (long long)(f - f0) * st;
+#pragma unroll
+        for (int c = 0; c < NU; c++) F[c * g.nz + zf] = out[c];
+        if (want_dt) dtc = fmin(dtc, face_dt<R, D>(g, fi, fj, k, cw));
+        if (f + 1 < f1) {
+#pragma unroll
+            for (int c = 0; c < NP; c++) {
+                qa[c] = qb[c];
+                qb[c] = qc[c];
+                sa[c] = sb[c];
+                qc[c] = ldg(P + c * g.nz + zf + 2 * st);
+            }
+        }
     }
     return dtc;
 }
@@ -599,15 +684,15 @@ __device__ inline void fixup_block(const Grid &g, R *P, int corr)
 // FP64 arithmetic differently and the two paths would differ in the last
 // bit.  The FP32-flux path is inlined (its two instantiations already agree).
 
-static __device__ __noinline__ double flux_item_d1(const Grid &g, const double *P, double *F, const Box &box, int w,
-                                            long long t)
+static __device__ __noinline__ double flux_column_d1(const Grid &g, const double *P, double *F, const Box &box,
+                                                     int w, long long t)
 {
-    return flux_item<double, 1>(g, P, F, box, w, t);
+    return flux_column<double, 1>(g, P, F, box, w, t);
 }
-static __device__ __noinline__ double flux_item_d2(const Grid &g, const double *P, double *F, const Box &box, int w,
-                                            long long t)
+static __device__ __noinline__ double flux_column_d2(const Grid &g, const double *P, double *F, const Box &box,
+                                                     int w, long long t)
 {
-    return flux_item<double, 2>(g, P, F, box, w, t);
+    return flux_column<double, 2>(g, P, F, box, w, t);
 }
 static __device__ __noinline__ double flux_item_d3(const Grid &g, const double *P, double *F, const Box &box, int w,
                                             long long t)
@@ -624,17 +709,22 @@ static __device__ __noinline__ void update_item_d(const Grid &g, const double *P
 static __device__ __noinline__ void bc1_item_d(const Grid &g, double *P, long long t) { bc1_item<double>(g, P, t); }
 static __device__ __noinline__ void fixup_block_d(const Grid &g, double *P, int corr) { fixup_block<double>(g, P, corr); }
 
+// the flux element of direction D: a column of faces along X1 / X2, one face
+// along X3; box = flux_elem_box(g, D)
 template <typename R, int D>
 __device__ __forceinline__ double flux_call(const Grid &g, const R *P, R *F, const Box &box, int w, long long t)
 {
     if constexpr (sizeof(R) == 8) {
-        if constexpr (D == 1) return flux_item_d1(g, P, F, box, w, t);
-        else if constexpr (D == 2) return flux_item_d2(g, P, F, box, w, t);
+        if constexpr (D == 1) return flux_column_d1(g, P, F, box, w, t);
+        else if constexpr (D == 2) return flux_column_d2(g, P, F, box, w, t);
         else return flux_item_d3(g, P, F, box, w, t);
     } else {
-        return flux_item<R, D>(g, P, F, box, w, t);
+        if constexpr (D == 3) return flux_item<R, D>(g, P, F, box, w, t);
+        else return flux_column<R, D>(g, P, F, box, w, t);
     }
 }
+
+__host__ __device__ inline Box flux_elem_box(const Grid &g, int d) { return d == 3 ? flux_box(g, 3) : col_box(g, d); }
 
 template <typename R, bool LEARN = false>
 __device__ __forceinline__ void update_call(const Grid &g, const R *Pin, R *Pout, const R *F1, const R *F2,

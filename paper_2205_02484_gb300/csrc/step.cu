@@ -98,7 +98,7 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     const int T = 128;
     const R *Pin = (const R *)g.P[src];
     R *Pout = (R *)g.P[dst];
-    Box b1 = flux_box(g, 1), b2 = flux_box(g, 2), b3 = flux_box(g, 3), be = edge_box(g);
+    Box b1 = flux_elem_box(g, 1), b2 = flux_elem_box(g, 2), b3 = flux_elem_box(g, 3), be = edge_box(g);
     switch (part) {
     case 0: k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[0], b1, want_dt); break;
     case 1: k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[1], b2, want_dt); break;
