@@ -142,15 +142,19 @@ def aggregate_value(zones_per_rank, steps, world, ms_max):
 ENSEMBLE_SHAPES = [(64, 64, 1), (96, 64, 1), (128, 64, 32), (128, 96, 64), (192, 128, 64)]
 
 
-def ensemble_specs(n=24, master_seed=2024):
+SMALL_SHAPES = [(64, 64, 1), (96, 64, 1), (128, 64, 1), (64, 64, 4)]
+
+
+def ensemble_specs(n=24, master_seed=2024, shapes=None):
     """Batched-ensemble workload: n tori with shapes drawn from 64x64x1 up to
     192x128x64, spin U[0, 0.98], gamma in {4/3, 13/9, 5/3}, beta_0 U[30, 300],
     perturbation seeds 100.. (one master seed)."""
     import numpy as np
+    shapes = shapes or ENSEMBLE_SHAPES
     rng = np.random.Generator(np.random.PCG64(master_seed))
     out = []
     for m in range(n):
-        shape = ENSEMBLE_SHAPES[int(rng.integers(len(ENSEMBLE_SHAPES)))]
+        shape = shapes[int(rng.integers(len(shapes)))]
         a = float(rng.uniform(0.0, 0.98))
         gam = [4.0 / 3.0, 13.0 / 9.0, 5.0 / 3.0][int(rng.integers(3))]
         b0 = float(rng.uniform(30.0, 300.0))
@@ -158,10 +162,10 @@ def ensemble_specs(n=24, master_seed=2024):
     return out
 
 
-def run_ensemble(G, torch, stream, device, steps=10):
+def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload=None):
     from paper_2205_02484_gb300 import tuning
     members = []
-    for shape, a, gam, b0, seed in ensemble_specs():
+    for shape, a, gam, b0, seed in ensemble_specs(n=n, shapes=shapes):
         gp = G.default_grid(*shape, a=a, r_out=100.0, precision=G.MIXED, device=device)
         gp.stream = stream.cuda_stream
         c = G.init_grid(gp, G.default_phys(gam=gam))
@@ -197,9 +201,9 @@ def run_ensemble(G, torch, stream, device, steps=10):
     ens.close()
     for c in members:
         c.close()
-    return {"workload": "24 FM tori, shapes 64x64x1..192x128x64, a U[0,0.98], gamma {4/3,13/9,5/3}, "
-                        "beta_0 U[30,300], r_out 100 M, mixed precision, one persistent launch per kernel "
-                        "class and one CUDA graph per ensemble step",
+    return {"workload": workload or ("24 FM tori, shapes 64x64x1..192x128x64, a U[0,0.98], gamma {4/3,13/9,5/3}, "
+                                     "beta_0 U[30,300], r_out 100 M, mixed precision, one persistent launch per "
+                                     "kernel class and one CUDA graph per ensemble step"),
             "members": len(members), "zones": zones, "steps": steps,
             "value": zones * steps / (ms_ens * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms_ens / steps,
             "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
@@ -467,6 +471,10 @@ def main():
     ensemble = None
     if world == 1 and not args.no_ensemble:
         ensemble = run_ensemble(G, torch, stream, local)
+        ensemble["small_tori"] = run_ensemble(
+            G, torch, stream, local, steps=20, n=96, shapes=SMALL_SHAPES,
+            workload="96 small FM tori (64x64x1, 96x64x1, 128x64x1, 64x64x4), same parameter draws, where a loop "
+                     "of per-torus step graphs is bound by launches")
     # ---- learned Newton start: training, inversions, the 256x192x192 step
     mlp = None
     if world == 1 and not args.no_mlp:

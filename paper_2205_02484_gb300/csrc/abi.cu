@@ -138,6 +138,13 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.isig = 1.0 / g.sigma_max;
     g.ibu = 1.0 / g.bu_max;
     g.nr_tol_mixed = std::sqrt(g.nr_tol);
+    {
+        // column length of the X1 / X2 flux sweeps: at least ~2^17 threads per sweep
+        long long faces = (long long)(g.n1 + 1) * (g.n2 + 2) * (g.n3 + 2);
+        int fc = 1;
+        while (fc < 16 && faces / (2LL * fc) >= (1LL << 17)) fc *= 2;
+        g.fcol = fc;
+    }
     g.nr_maxit = phys->nr_maxit; g.brent_maxit = phys->brent_maxit; g.fix_maxsweep = phys->fix_maxsweep;
     long long nact = (long long)g.n1 * g.n2 * g.n3;
     g.nfix_cap = (int)std::min<long long>(nact, 1LL << 20);

@@ -77,7 +77,8 @@ struct Grid {
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max
     double nr_tol_mixed;        // sqrt(nr_tol): Newton acceptance of the mixed path
-    int nr_maxit, brent_maxit, fix_maxsweep, pad0;
+    int nr_maxit, brent_maxit, fix_maxsweep;
+    int fcol;                   // faces per thread of the X1 / X2 flux sweeps (columns)
     // metric tables
     const Geo<double> *gc, *gf1, *gf2;
     const Geo<float> *gcF, *gf1F, *gf2F;

@@ -314,17 +314,18 @@ __device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__
     return want_dt ? face_dt<R, D>(g, i, j, k, cw) : INFINITY;
 }
 
-// Columns of FCOL consecutive faces along X1 or X2: one thread walks its
+// Columns of g.fcol consecutive faces along X1 or X2: one thread walks its
 // column with a three-zone window in registers, so each zone is loaded and
 // its MC slope formed once instead of once per face (the face values are the
-// same numbers flux_item forms).  col_box counts columns: the face box with
-// its extent along D divided into chunks of FCOL (faces along D start at 0).
-constexpr int FCOL = 16;
-
+// same numbers flux_item forms, whatever the column length).  col_box counts
+// columns: the face box with its extent along D divided into chunks of
+// g.fcol (faces along D start at 0).  The host picks g.fcol per grid: long
+// columns for large grids, single faces where columns would leave the GPU
+// with too few threads.
 __host__ __device__ inline Box col_box(const Grid &g, int d)
 {
     Box b = flux_box(g, d);
-    b.n[d - 1] = (b.n[d - 1] + FCOL - 1) / FCOL;
+    b.n[d - 1] = (b.n[d - 1] + g.fcol - 1) / g.fcol;
     return b;
 }
 
@@ -338,7 +339,7 @@ __device__ __forceinline__ double flux_column(const Grid &g, const R *__restrict
     int i, j, k;
     box_decode(cb, t, i, j, k);
     const int nf = (D == 1 ? g.n1 : g.n2) + 1;
-    const int f0 = (D == 1 ? i : j) * FCOL, f1 = min(f0 + FCOL, nf);
+    const int f0 = (D == 1 ? i : j) * g.fcol, f1 = min(f0 + g.fcol, nf);
     if (D == 1) i = f0;
     else j = f0;
     const long long st = D == 1 ? (long long)g.N2 * g.N3 : g.N3;
