@@ -116,3 +116,33 @@ def test_perturbation_amplitude_and_determinism():
     ratio = P1[1][torus] / P0[1][torus]
     assert ratio.min() >= 0.96 and ratio.max() <= 1.04 and ratio.std() > 0.01
     assert np.array_equal(P0[0], P1[0])
+
+
+def _torus_drift(n, t_end=10.0):
+    """Mean relative change of rho in the torus body after t_end of the
+    unmagnetised, unperturbed Fishbone-Moncrief torus (an equilibrium)."""
+    p = oracle.default_params(n1=n, n2=n, n3=1, a=0.9375, r_out=40.0, gam=4.0 / 3.0)
+    og = oracle.Grid(p)
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=0.0, pert_amp=0.0, seed=1)
+    P0 = og.get_state()[0].copy()
+    while True:
+        _, _, t, dt = og.get_state()
+        if t >= t_end - 1e-12:
+            break
+        if t + dt > t_end:
+            og.set_dt(t_end - t)
+        assert og.step() == 0
+    P = og.get_state()[0]
+    r = np.array([og.r_of_x1(og.x1in + (i + 0.5) * og.dx[0]) for i in range(n)])
+    th = np.array([og.th_of_x2(og.x2in + (j + 0.5) * og.dx[1]) for j in range(n)])
+    R, TH = np.meshgrid(r, th, indexing="ij")
+    body = (R > 9.0) & (R < 16.0) & (np.abs(TH - np.pi / 2) < 0.25)
+    return np.abs(P[0, :, :, 0][body] / P0[0, :, :, 0][body] - 1.0).mean()
+
+
+def test_unmagnetised_torus_is_stationary_to_second_order():
+    # the whole step (fluxes, Kerr connection sources, RK2, inversion) keeps
+    # the equilibrium up to truncation error, which falls at second order
+    e32, e64 = _torus_drift(32), _torus_drift(64)
+    assert e32 / e64 > 3.0, (e32, e64)
+    assert e64 < 1e-3
