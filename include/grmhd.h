@@ -325,7 +325,7 @@ int grmhd_mlp_samples(grmhd_ctx *ctx, unsigned long long seed, long first, long 
 int grmhd_mlp_forward(grmhd_ctx *ctx, const float *feat, long n, float *y, int on_device);
 
 /* Loss and its gradient (GRMHD_MLP_NPARAM FP32 values) over one batch of n
- * samples (n <= 1048576), for the given parameters and norm. The context's
+ * samples (n <= 262144), for the given parameters and norm. The context's
  * loaded network is left unchanged.  feat, label, grad follow on_device;
  * theta and norm are host arrays; loss (may be NULL) is a host double. */
 int grmhd_mlp_loss_grad(grmhd_ctx *ctx, const float *theta, const float *norm, const float *feat,
@@ -335,7 +335,7 @@ int grmhd_mlp_loss_grad(grmhd_ctx *ctx, const float *theta, const float *norm, c
  * (host, FP32) with zero moments.  Step s uses samples (s*batch + b) mod n,
  * for b < batch.  theta_inout receives the result.  loss_last (may be NULL)
  * receives the mean loss of the last step, taken before its update.  The
- * loaded network is left unchanged.  batch <= 1048576. */
+ * loaded network is left unchanged.  batch <= 262144. */
 int grmhd_mlp_train_steps(grmhd_ctx *ctx, float *theta_inout, const float *norm, const float *feat,
                           const float *label, long n, long batch, long nsteps, double lr, double beta1,
                           double beta2, double eps, double weight_decay, double *loss_last, int on_device);
@@ -346,7 +346,7 @@ typedef struct {
     unsigned long long seed; /* sample seed */
     unsigned long long init_seed; /* weight initialisation seed */
     int epochs;
-    int batch;               /* <= 1048576 */
+    int batch;               /* <= 262144 */
     double lr, lr_min;       /* cosine schedule from lr to lr_min over all steps */
     double beta1, beta2, eps, weight_decay;
 } grmhd_mlp_train_params;

@@ -831,13 +831,13 @@ extern "C" int grmhd_mlp_forward(grmhd_ctx *ctx, const float *feat, long n, floa
     return 0;
 }
 
-static const long MLP_MAX_BATCH = 1L << 20;
+static const long MLP_MAX_BATCH = 1L << 18;
 
 extern "C" int grmhd_mlp_loss_grad(grmhd_ctx *ctx, const float *theta, const float *norm, const float *feat,
                                    const float *label, long n, float *grad, double *loss, int on_device)
 {
     if (!ctx || !theta || !norm || !feat || !label || !grad) return fail(ctx, GRMHD_EINVAL, "null argument");
-    if (n < 1 || n > MLP_MAX_BATCH) return fail(ctx, GRMHD_EINVAL, "n must be in [1, 1048576]");
+    if (n < 1 || n > MLP_MAX_BATCH) return fail(ctx, GRMHD_EINVAL, "n must be in [1, 262144]");
     if (int rc = check_norm(ctx, norm)) return rc;
     DevTmp tmp;
     MlpTrainer T{};
@@ -870,7 +870,7 @@ extern "C" int grmhd_mlp_train_steps(grmhd_ctx *ctx, float *theta, const float *
 {
     if (!ctx || !theta || !norm || !feat || !label) return fail(ctx, GRMHD_EINVAL, "null argument");
     if (n < 1 || batch < 1 || batch > MLP_MAX_BATCH || nsteps < 1)
-        return fail(ctx, GRMHD_EINVAL, "need n >= 1, 1 <= batch <= 1048576, nsteps >= 1");
+        return fail(ctx, GRMHD_EINVAL, "need n >= 1, 1 <= batch <= 262144, nsteps >= 1");
     if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
         return fail(ctx, GRMHD_EINVAL, "bad optimiser parameters");
     if (int rc = check_norm(ctx, norm)) return rc;
@@ -909,7 +909,7 @@ extern "C" int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp,
     if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
     const long long N = tp->n_samples, V = tp->n_val;
     if (N < 1 || N > (1LL << 31) - 1 || V < 0 || tp->epochs < 1 || tp->batch < 1 || tp->batch > MLP_MAX_BATCH)
-        return fail(ctx, GRMHD_EINVAL, "need 1 <= n_samples < 2^31, n_val >= 0, epochs >= 1, 1 <= batch <= 1048576");
+        return fail(ctx, GRMHD_EINVAL, "need 1 <= n_samples < 2^31, n_val >= 0, epochs >= 1, 1 <= batch <= 262144");
     if (!(tp->lr >= 0.0) || !(tp->lr_min >= 0.0) || !(tp->beta1 >= 0.0 && tp->beta1 < 1.0) ||
         !(tp->beta2 >= 0.0 && tp->beta2 < 1.0) || !(tp->eps > 0.0))
         return fail(ctx, GRMHD_EINVAL, "bad optimiser parameters");

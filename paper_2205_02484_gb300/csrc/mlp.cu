@@ -16,9 +16,6 @@
 
 namespace grmhd {
 
-constexpr int TB = 128; // samples (= threads) per block of the gradient kernel
-constexpr int LD = 65;  // padded row of the per-sample activations in shared memory
-
 // ----------------------------------------------------------------- samples
 
 __global__ void k_mlp_samples(Grid g, unsigned long long seed, long long first, long long n, double *P, int *loc,
@@ -179,17 +176,25 @@ void launch_mlp_pack(const float *theta, float *fwd, cudaStream_t s)
 
 // ------------------------------------------------------- training: gradient
 //
-// One block takes TB samples of the minibatch, one per thread.  Forward:
-// h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), s = W3 h2 + b3 with the BF16
-// weights expanded to FP32 in shared memory.  Backward of L = (1/B) sum
-// (s - t)^2: ds = 2 (s - t) / B, dh2 = ds W3 [a2 > 0], dh1 = W2^T dh2 [a1 > 0].
-// Weight gradients of the block are sums over its samples, written to its
-// own row of part[]; the AdamW kernel adds the rows in block order.
+// One block takes SB = 32 samples of the minibatch with 128 threads.  The
+// three 64-wide products of the pass are register-tiled block GEMMs in shared
+// memory (4 x 4 outputs per thread, W2 kept in both orientations so every
+// read is a conflict-free row or a float4 broadcast):
+//   forward   A2 = H1 W2^T (+ b2), h2 = relu(A2), s = h2 . W3 + b3;
+//   backward  ds = 2 (s - t) / B; dh2 = ds W3 [h2 > 0]; dh1 = dh2 W2 [h1 > 0];
+//   weights   dW2 = dh2^T H1, dW1 = dh1^T x, db1, db2, dW3 = ds^T h2, db3,
+// summed over the block's samples into its own row of part[]; the AdamW
+// kernel adds the rows in block order.  Inputs, activations and accumulation
+// are FP32, the weights the BF16 values of the forward buffer.
 //
 // Sample of batch position b at step s: k = s B + b, epoch e = k / n,
 // index ((k mod n) mul + e * 0x9E3779B1) mod n with mul coprime with n (one
 // permutation of the set per epoch); mul = 1 takes the set in order,
 // (k mod n), in every epoch.
+
+constexpr int SB = 32;      // samples per block
+constexpr int NT = 128;     // threads per block
+constexpr int LDH = 68;     // padded activation row (16-byte aligned)
 
 struct GradArgs {
     const float *fwd, *feat, *label;
@@ -201,156 +206,206 @@ struct GradArgs {
     double *lpart;
 };
 
-__global__ void __launch_bounds__(TB) k_mlp_grad(GradArgs A)
+__global__ void __launch_bounds__(NT) k_mlp_grad(GradArgs A)
 {
-    extern __shared__ float sm[];
-    float *W2s = sm;                  // [64][64]
-    float *W1s = W2s + MLP_NW2;       // [64][5]
-    float *b1s = W1s + MLP_NW1;       // [64]
-    float *b2s = b1s + MLP_H;         // [64]
-    float *W3s = b2s + MLP_H;         // [64]
-    float *H1 = W3s + MLP_H;          // [TB][LD]  h1
-    float *H2 = H1 + TB * LD;         // [TB][LD]  h2
-    float *G1 = H2 + TB * LD;         // [TB][LD]  dL/da1
-    float *X = G1 + TB * LD;          // [TB][5]   standardised inputs
-    float *DS = X + TB * MLP_IN;      // [TB]      dL/ds
-    __shared__ double lred[TB / 32];
+    extern __shared__ __align__(16) float sm[];
+    float *W2R = sm;                   // [o][i]
+    float *W2T = W2R + MLP_NW2;        // [i][o]
+    float *H1 = W2T + MLP_NW2;         // [SB][LDH]  h1
+    float *H2 = H1 + SB * LDH;         // [SB][LDH]  h2
+    float *G1 = H2 + SB * LDH;         // [SB][LDH]  dL/da1
+    float *W1s = G1 + SB * LDH;        // [64][5]
+    float *b1s = W1s + MLP_NW1;        // [64]
+    float *b2s = b1s + MLP_H;          // [64]
+    float *W3s = b2s + MLP_H;          // [64]
+    float *X = W3s + MLP_H;            // [SB][5]
+    float *DS = X + SB * MLP_IN;       // [SB]
+    __shared__ double lred[NT / 32];
 
     const float *buf = A.fwd;
     const __nv_bfloat16 *Wb = reinterpret_cast<const __nv_bfloat16 *>(buf + MLP_OFF_W);
     const int tid = threadIdx.x;
-    for (int k = tid; k < MLP_NW2; k += TB) W2s[k] = __bfloat162float(Wb[MLP_NW1 + k]);
-    for (int k = tid; k < MLP_NW1; k += TB) W1s[k] = __bfloat162float(Wb[k]);
+    for (int k = tid; k < MLP_NW2; k += NT) {
+        float w = __bfloat162float(Wb[MLP_NW1 + k]);
+        W2R[k] = w;
+        W2T[(k & 63) * MLP_H + (k >> 6)] = w;
+    }
+    for (int k = tid; k < MLP_NW1; k += NT) W1s[k] = __bfloat162float(Wb[k]);
     if (tid < MLP_H) {
         b1s[tid] = buf[MLP_OFF_B1 + tid];
         b2s[tid] = buf[MLP_OFF_B2 + tid];
         W3s[tid] = __bfloat162float(Wb[MLP_NW1 + MLP_NW2 + tid]);
     }
+    // standardised inputs of the block's samples (zero rows past the batch)
+    const long long step = *A.step;
+    if (tid < SB) {
+        const int b = blockIdx.x * SB + tid;
+        float x[MLP_IN] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (b < A.batch) {
+            long long k = step * (long long)A.batch + b;
+            long long e = k / A.n;
+            unsigned long long kk = (unsigned long long)(k % A.n);
+            unsigned long long off = A.mul == 1ull ? 0ull : (unsigned long long)e * 0x9E3779B1ull;
+            long long idx = (long long)((kk * A.mul + off) % (unsigned long long)A.n);
+#pragma unroll
+            for (int i = 0; i < MLP_IN; i++) x[i] = (A.feat[i * A.n + idx] - buf[i]) / buf[5 + i];
+            DS[tid] = (A.label[idx] - buf[10]) / buf[11]; // target, replaced by dL/ds below
+        } else {
+            DS[tid] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < MLP_IN; i++) X[tid * MLP_IN + i] = x[i];
+    }
     __syncthreads();
 
-    const int b = blockIdx.x * TB + tid;
-    const bool act = b < A.batch;
-    float ds = 0.0f, r2 = 0.0f;
-    float *h1r = H1 + tid * LD, *h2r = H2 + tid * LD, *g1r = G1 + tid * LD;
-    if (act) {
-        long long k = *A.step * (long long)A.batch + b;
-        long long e = k / A.n;
-        unsigned long long kk = (unsigned long long)(k % A.n);
-        unsigned long long off = A.mul == 1ull ? 0ull : (unsigned long long)e * 0x9E3779B1ull;
-        long long idx = (long long)((kk * A.mul + off) % (unsigned long long)A.n);
+    // h1 = relu(W1 x + b1): thread (sample tid/4, outputs 16 (tid%4) .. +16)
+    {
+        const int s = tid >> 2, o0 = (tid & 3) * 16;
         float x[MLP_IN];
 #pragma unroll
-        for (int i = 0; i < MLP_IN; i++) {
-            x[i] = (A.feat[i * A.n + idx] - buf[i]) / buf[5 + i];
-            X[tid * MLP_IN + i] = x[i];
-        }
-        float h1[MLP_H];
+        for (int i = 0; i < MLP_IN; i++) x[i] = X[s * MLP_IN + i];
 #pragma unroll
-        for (int o = 0; o < MLP_H; o++) {
+        for (int oo = 0; oo < 16; oo++) {
+            const int o = o0 + oo;
             float a = b1s[o];
 #pragma unroll
             for (int i = 0; i < MLP_IN; i++) a = fmaf(W1s[o * MLP_IN + i], x[i], a);
-            h1[o] = fmaxf(a, 0.0f);
-            h1r[o] = h1[o];
+            H1[s * LDH + o] = fmaxf(a, 0.0f);
         }
-        float s = buf[MLP_OFF_B3];
-        for (int o = 0; o < MLP_H; o += 4) {
-            float a0 = b2s[o], a1 = b2s[o + 1], a2 = b2s[o + 2], a3 = b2s[o + 3];
-            const float4 *w0 = reinterpret_cast<const float4 *>(W2s + o * MLP_H);
-#pragma unroll
-            for (int i = 0; i < MLP_H / 4; i++) {
-                float4 p0 = w0[i], p1 = w0[i + 16], p2 = w0[i + 32], p3 = w0[i + 48];
-                a0 = fmaf(p0.x, h1[4 * i], fmaf(p0.y, h1[4 * i + 1], fmaf(p0.z, h1[4 * i + 2], fmaf(p0.w, h1[4 * i + 3], a0))));
-                a1 = fmaf(p1.x, h1[4 * i], fmaf(p1.y, h1[4 * i + 1], fmaf(p1.z, h1[4 * i + 2], fmaf(p1.w, h1[4 * i + 3], a1))));
-                a2 = fmaf(p2.x, h1[4 * i], fmaf(p2.y, h1[4 * i + 1], fmaf(p2.z, h1[4 * i + 2], fmaf(p2.w, h1[4 * i + 3], a2))));
-                a3 = fmaf(p3.x, h1[4 * i], fmaf(p3.y, h1[4 * i + 1], fmaf(p3.z, h1[4 * i + 2], fmaf(p3.w, h1[4 * i + 3], a3))));
-            }
-            float v0 = fmaxf(a0, 0.0f), v1 = fmaxf(a1, 0.0f), v2 = fmaxf(a2, 0.0f), v3 = fmaxf(a3, 0.0f);
-            h2r[o] = v0;
-            h2r[o + 1] = v1;
-            h2r[o + 2] = v2;
-            h2r[o + 3] = v3;
-            s = fmaf(W3s[o], v0, s);
-            s = fmaf(W3s[o + 1], v1, s);
-            s = fmaf(W3s[o + 2], v2, s);
-            s = fmaf(W3s[o + 3], v3, s);
-        }
-        float t = (A.label[idx] - buf[10]) / buf[11];
-        float r = s - t;
-        r2 = r * r;
-        ds = 2.0f * r / (float)A.batch;
-    } else {
-        for (int o = 0; o < MLP_H; o++) h1r[o] = h2r[o] = 0.0f;
-        for (int i = 0; i < MLP_IN; i++) X[tid * MLP_IN + i] = 0.0f;
     }
-    DS[tid] = ds;
+    __syncthreads();
 
-    // dh1 = W2^T dh2, masked by a1 > 0
-    if (act) {
-        float acc[MLP_H];
+    // forward layer 2 and the output: thread (samples 4 (tid/16) .. +4, outputs 4 (tid%16) .. +4)
+    const int sb = tid >> 4, ob = tid & 15;
+    float r2 = 0.0f;
+    {
+        float acc[4][4];
 #pragma unroll
-        for (int i = 0; i < MLP_H; i++) acc[i] = 0.0f;
+        for (int c = 0; c < 4; c++) {
+            const float bb = b2s[4 * ob + c];
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[r][c] = bb;
+        }
+#pragma unroll 8
+        for (int k = 0; k < MLP_H; k++) {
+            const float4 w = *reinterpret_cast<const float4 *>(W2T + k * MLP_H + 4 * ob);
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const float h = H1[(4 * sb + r) * LDH + k];
+                acc[r][0] = fmaf(h, w.x, acc[r][0]);
+                acc[r][1] = fmaf(h, w.y, acc[r][1]);
+                acc[r][2] = fmaf(h, w.z, acc[r][2]);
+                acc[r][3] = fmaf(h, w.w, acc[r][3]);
+            }
+        }
+        float y[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            y[r] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float h2 = fmaxf(acc[r][c], 0.0f);
+                H2[(4 * sb + r) * LDH + 4 * ob + c] = h2;
+                y[r] = fmaf(W3s[4 * ob + c], h2, y[r]);
+            }
+        }
+        // sum over the 16 threads of the sample group (one half-warp)
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1)
+#pragma unroll
+            for (int r = 0; r < 4; r++) y[r] += __shfl_xor_sync(0xffffffffu, y[r], off);
+        if (ob == 0) {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int s = 4 * sb + r;
+                const bool act = blockIdx.x * SB + s < A.batch;
+                const float res = (y[r] + buf[MLP_OFF_B3]) - DS[s];
+                r2 += act ? res * res : 0.0f;
+                DS[s] = act ? 2.0f * res / (float)A.batch : 0.0f;
+            }
+        }
+    }
+    __syncthreads();
+
+    // dh1 = dh2 W2, masked by h1 > 0: thread (samples 4 sb .. +4, inputs 4 ob .. +4)
+    {
+        float acc[4][4] = {};
+        float d[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) d[r] = DS[4 * sb + r];
+#pragma unroll 4
         for (int o = 0; o < MLP_H; o++) {
-            float d2 = h2r[o] > 0.0f ? ds * W3s[o] : 0.0f;
-            const float4 *w = reinterpret_cast<const float4 *>(W2s + o * MLP_H);
+            const float4 w = *reinterpret_cast<const float4 *>(W2R + o * MLP_H + 4 * ob);
+            const float w3 = W3s[o];
 #pragma unroll
-            for (int i = 0; i < MLP_H / 4; i++) {
-                float4 p = w[i];
-                acc[4 * i] = fmaf(p.x, d2, acc[4 * i]);
-                acc[4 * i + 1] = fmaf(p.y, d2, acc[4 * i + 1]);
-                acc[4 * i + 2] = fmaf(p.z, d2, acc[4 * i + 2]);
-                acc[4 * i + 3] = fmaf(p.w, d2, acc[4 * i + 3]);
+            for (int r = 0; r < 4; r++) {
+                const float g = H2[(4 * sb + r) * LDH + o] > 0.0f ? d[r] * w3 : 0.0f;
+                acc[r][0] = fmaf(g, w.x, acc[r][0]);
+                acc[r][1] = fmaf(g, w.y, acc[r][1]);
+                acc[r][2] = fmaf(g, w.z, acc[r][2]);
+                acc[r][3] = fmaf(g, w.w, acc[r][3]);
             }
         }
 #pragma unroll
-        for (int i = 0; i < MLP_H; i++) g1r[i] = h1r[i] > 0.0f ? acc[i] : 0.0f;
-    } else {
-        for (int i = 0; i < MLP_H; i++) g1r[i] = 0.0f;
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int s = 4 * sb + r, i = 4 * ob + c;
+                G1[s * LDH + i] = H1[s * LDH + i] > 0.0f ? acc[r][c] : 0.0f;
+            }
     }
-
     // loss of the block
     float lv = r2;
-    for (int o = 16; o > 0; o >>= 1) lv += __shfl_down_sync(0xffffffffu, lv, o);
+    for (int off = 16; off > 0; off >>= 1) lv += __shfl_down_sync(0xffffffffu, lv, off);
     if ((tid & 31) == 0) lred[tid >> 5] = (double)lv;
     __syncthreads();
 
     float *gout = A.part + (size_t)blockIdx.x * MLP_NPARAM;
-    // dW2[o][i] = sum_t dh2[t][o] h1[t][i]: thread owns row o = tid/2, columns i = tid%2 + 2c
+    // dW2[o][i] = sum_s dh2[s][o] h1[s][i]: thread (outputs 4 (tid/8) .. +4, inputs 8 (tid%8) .. +8)
     {
-        const int o = tid >> 1, i0 = tid & 1;
-        const float w3 = W3s[o];
-        float acc[MLP_H / 2];
+        const int o0 = 4 * (tid >> 3), i0 = 8 * (tid & 7);
+        float acc[4][8] = {};
+        float w3[4];
 #pragma unroll
-        for (int c = 0; c < MLP_H / 2; c++) acc[c] = 0.0f;
-        for (int t = 0; t < TB; t++) {
-            float d2 = H2[t * LD + o] > 0.0f ? DS[t] * w3 : 0.0f;
-            const float *h = H1 + t * LD + i0;
+        for (int r = 0; r < 4; r++) w3[r] = W3s[o0 + r];
+#pragma unroll 4
+        for (int s = 0; s < SB; s++) {
+            const float ds = DS[s];
+            const float4 h0 = *reinterpret_cast<const float4 *>(H1 + s * LDH + i0);
+            const float4 h1 = *reinterpret_cast<const float4 *>(H1 + s * LDH + i0 + 4);
+            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-            for (int c = 0; c < MLP_H / 2; c++) acc[c] = fmaf(d2, h[2 * c], acc[c]);
+            for (int r = 0; r < 4; r++) {
+                const float g = H2[s * LDH + o0 + r] > 0.0f ? ds * w3[r] : 0.0f;
+#pragma unroll
+                for (int c = 0; c < 8; c++) acc[r][c] = fmaf(g, hv[c], acc[r][c]);
+            }
         }
 #pragma unroll
-        for (int c = 0; c < MLP_H / 2; c++) gout[TH_W2 + o * MLP_H + i0 + 2 * c] = acc[c];
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 8; c++) gout[TH_W2 + (o0 + r) * MLP_H + i0 + c] = acc[r][c];
     }
     if (tid < MLP_H) {
-        // dW1[o][i] = sum_t dh1[t][o] x[t][i]; db1[o] = sum_t dh1[t][o]
+        // dW1[o][i] = sum_s dh1[s][o] x[s][i]; db1[o] = sum_s dh1[s][o]
         const int o = tid;
         float acc[MLP_IN] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, bsum = 0.0f;
-        for (int t = 0; t < TB; t++) {
-            float d1 = G1[t * LD + o];
+        for (int s = 0; s < SB; s++) {
+            const float d1 = G1[s * LDH + o];
             bsum += d1;
 #pragma unroll
-            for (int i = 0; i < MLP_IN; i++) acc[i] = fmaf(d1, X[t * MLP_IN + i], acc[i]);
+            for (int i = 0; i < MLP_IN; i++) acc[i] = fmaf(d1, X[s * MLP_IN + i], acc[i]);
         }
 #pragma unroll
         for (int i = 0; i < MLP_IN; i++) gout[TH_W1 + o * MLP_IN + i] = acc[i];
         gout[TH_B1 + o] = bsum;
     } else {
-        // db2[o] = sum_t dh2[t][o]; dW3[o] = sum_t ds[t] h2[t][o]; db3 = sum_t ds[t]
+        // db2[o] = sum_s dh2[s][o]; dW3[o] = sum_s ds[s] h2[s][o]; db3 = sum_s ds[s]
         const int o = tid - MLP_H;
         const float w3 = W3s[o];
         float b2sum = 0.0f, w3sum = 0.0f, b3sum = 0.0f;
-        for (int t = 0; t < TB; t++) {
-            float h = H2[t * LD + o], d = DS[t];
+        for (int s = 0; s < SB; s++) {
+            const float h = H2[s * LDH + o], d = DS[s];
             b2sum += h > 0.0f ? d * w3 : 0.0f;
             w3sum = fmaf(d, h, w3sum);
             b3sum += d;
@@ -361,17 +416,17 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(GradArgs A)
     }
     if (tid == 0) {
         double l = 0.0;
-        for (int w = 0; w < TB / 32; w++) l += lred[w];
+        for (int w = 0; w < NT / 32; w++) l += lred[w];
         A.lpart[blockIdx.x] = l;
     }
 }
 
 size_t mlp_grad_smem()
 {
-    return sizeof(float) * (MLP_NW2 + MLP_NW1 + 3 * MLP_H + 3 * TB * LD + TB * MLP_IN + TB);
+    return sizeof(float) * (2 * MLP_NW2 + 3 * SB * LDH + MLP_NW1 + 3 * MLP_H + SB * MLP_IN + SB);
 }
 
-int mlp_grad_blocks(int batch) { return (batch + TB - 1) / TB; }
+int mlp_grad_blocks(int batch) { return (batch + SB - 1) / SB; }
 
 cudaError_t mlp_grad_setup()
 {
@@ -382,15 +437,16 @@ void launch_mlp_grad(const MlpTrainer &T, const float *feat, const float *label,
                      unsigned long long mul, cudaStream_t s)
 {
     GradArgs A{T.fwd, feat, label, n, batch, mul, T.step, T.part, T.lpart};
-    k_mlp_grad<<<mlp_grad_blocks(batch), TB, mlp_grad_smem(), s>>>(A);
+    k_mlp_grad<<<mlp_grad_blocks(batch), NT, mlp_grad_smem(), s>>>(A);
 }
 
 // ------------------------------------------------------------ training: AdamW
 //
-// g = sum of the block rows of part[] (FP64, block order); bias-corrected
-// AdamW (Kingma & Ba 2015; decoupled decay of Loshchilov & Hutter 2019) on
-// the FP32 master, weight decay on W1, W2, W3 only; learning rate constant,
-// or cosine from lr0 to lr_min over total_steps; then the BF16 forward view.
+// g = sum of the block rows of part[] (FP64, fixed order); bias-corrected
+// AdamW (Kingma & Ba 2015; decoupled decay of Loshchilov & Hutter 2019) in
+// FP32 on the FP32 master, weight decay on W1, W2, W3 only; learning rate
+// constant, or cosine from lr0 to lr_min over total_steps (rate and bias
+// corrections formed once per block); then the BF16 forward view.
 // The last block to finish advances the device step counter and records
 // the mean loss of the step.
 
@@ -406,39 +462,73 @@ struct AdamArgs {
     MlpHyper h;
 };
 
+// sum of the block rows of one parameter: eight independent partial sums
+// (so the loads overlap), combined in a fixed order.  T = double for the
+// gradient entry point; the optimiser sums in FP32 (the FP64 pipe would put
+// 128 dependent-rate adds per warp on every step's critical path).
+template <typename T>
+__device__ __forceinline__ T sum_rows(const float *part, int nblk, int k)
+{
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b = 0;
+    for (; b + 8 <= nblk; b += 8)
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] += (T)part[(size_t)(b + u) * MLP_NPARAM + k];
+    for (; b < nblk; b++) acc[0] += (T)part[(size_t)b * MLP_NPARAM + k];
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
 __global__ void k_mlp_adam(AdamArgs A)
 {
+    // the step's learning rate and bias corrections, once per block
+    __shared__ float sc[3];
     const long long s = *A.step;
+    if (threadIdx.x == 0) {
+        // FP32 transcendentals: a single thread's FP64 pow/cos chain costs tens of
+        // microseconds at the FP64 issue rate, and these scalars need no FP64
+        float lr = (float)A.h.lr0;
+        if (A.h.total_steps > 0) {
+            float fr = fminf((float)s, (float)A.h.total_steps) / (float)A.h.total_steps;
+            lr = (float)A.h.lr_min + 0.5f * (float)(A.h.lr0 - A.h.lr_min) * (1.0f + cosf(3.14159265358979f * fr));
+        }
+        const float t = (float)(s + 1);
+        sc[0] = lr;
+        sc[1] = 1.0f / (1.0f - powf((float)A.h.b1, t));
+        sc[2] = 1.0f / (1.0f - powf((float)A.h.b2, t));
+    }
+    __syncthreads();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < MLP_NPARAM) {
-        double g = 0.0;
-        for (int b = 0; b < A.nblk; b++) g += (double)A.part[(size_t)b * MLP_NPARAM + k];
-        double lr = A.h.lr0;
-        if (A.h.total_steps > 0) {
-            double fr = fmin((double)s, (double)A.h.total_steps) / (double)A.h.total_steps;
-            lr = A.h.lr_min + 0.5 * (A.h.lr0 - A.h.lr_min) * (1.0 + cos(M_PI * fr));
-        }
-        double t = (double)(s + 1);
-        double m = A.h.b1 * (double)A.m[k] + (1.0 - A.h.b1) * g;
-        double v = A.h.b2 * (double)A.v[k] + (1.0 - A.h.b2) * g * g;
-        double mh = m / (1.0 - pow(A.h.b1, t)), vh = v / (1.0 - pow(A.h.b2, t));
-        double th = (double)A.theta[k];
-        bool decay = k < TH_B1 || (k >= TH_W2 && k < TH_B2) || (k >= TH_W3 && k < TH_B3);
-        if (decay) th -= lr * A.h.wd * th;
-        th -= lr * mh / (sqrt(vh) + A.h.eps);
-        A.m[k] = (float)m;
-        A.v[k] = (float)v;
-        A.theta[k] = (float)th;
-        pack_one(A.fwd, k, (float)th);
+        const float g = sum_rows<float>(A.part, A.nblk, k);
+        const float b1 = (float)A.h.b1, b2 = (float)A.h.b2, lr = sc[0];
+        const float m = b1 * A.m[k] + (1.0f - b1) * g;
+        const float v = b2 * A.v[k] + (1.0f - b2) * g * g;
+        float th = A.theta[k];
+        const bool decay = k < TH_B1 || (k >= TH_W2 && k < TH_B2) || (k >= TH_W3 && k < TH_B3);
+        if (decay) th -= lr * (float)A.h.wd * th;
+        th -= lr * (m * sc[1]) / (sqrtf(v * sc[2]) + (float)A.h.eps);
+        A.m[k] = m;
+        A.v[k] = v;
+        A.theta[k] = th;
+        pack_one(A.fwd, k, th);
     }
+    // the last block to finish records the step's mean loss and advances the step
+    __shared__ unsigned int last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        unsigned int done = atomicAdd(A.ticket, 1u);
-        if (done == gridDim.x - 1) {
-            double l = 0.0;
-            for (int b = 0; b < A.nblk; b++) l += A.lpart[b];
-            if (A.loss_hist && A.hist_len > 0) A.loss_hist[s % A.hist_len] = l / (double)A.batch;
+        last = atomicAdd(A.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        double l = 0.0;
+        for (int b = threadIdx.x; b < A.nblk; b += blockDim.x) l += A.lpart[b];
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+        __shared__ double lw[2];
+        if ((threadIdx.x & 31) == 0) lw[threadIdx.x >> 5] = l;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (A.loss_hist && A.hist_len > 0) A.loss_hist[s % A.hist_len] = (lw[0] + lw[1]) / (double)A.batch;
             *A.ticket = 0u;
             *A.step = s + 1;
         }
@@ -449,7 +539,7 @@ void launch_mlp_adam(const MlpTrainer &T, int batch, const MlpHyper &h, cudaStre
 {
     AdamArgs A{T.theta, T.m, T.v, T.fwd, T.part, T.lpart, mlp_grad_blocks(batch), batch,
                T.step, T.ticket, T.loss_hist, T.hist_len, h};
-    k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(A);
+    k_mlp_adam<<<(MLP_NPARAM + 63) / 64, 64, 0, s>>>(A);
 }
 
 // gradient of the whole batch without an update (gradient checks)
@@ -457,9 +547,7 @@ __global__ void k_mlp_reduce_grad(const float *part, int nblk, float *grad)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= MLP_NPARAM) return;
-    double g = 0.0;
-    for (int b = 0; b < nblk; b++) g += (double)part[(size_t)b * MLP_NPARAM + k];
-    grad[k] = (float)g;
+    grad[k] = (float)sum_rows<double>(part, nblk, k);
 }
 
 void launch_mlp_reduce_grad(const MlpTrainer &T, int batch, float *grad, cudaStream_t s)
