@@ -161,8 +161,9 @@ int grmhd_step(grmhd_ctx *ctx, int nsteps);
  * included) at the centre metric of active zones loc[n] (loc = i*n2 + j),
  * starting from and overwriting P_inout (8 x n).  flags[n] receives the
  * GRMHD_C2P_* code, iters[n] (may be NULL) the Newton iterations.  With
- * use_learned_guess = 1 the Newton start comes from the loaded MLP.  Same
- * method order and tolerances as the step (Section 2.3). */
+ * use_learned_guess = 1 Newton first starts from the loaded MLP's W and, if
+ * it does not converge, again from P_inout; iters counts both.  Same method
+ * order and tolerances as the step (Section 2.3). */
 int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P_inout,
                    int *flags, int *iters, long n, int use_learned_guess, int on_device);
 
@@ -369,9 +370,10 @@ typedef struct {
 int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp, grmhd_mlp_train_report *rep);
 
 /* on = 1: every inversion of grmhd_step starts Newton from the loaded
- * network's W (and v^2 of Eq. 29) instead of the stage's primitives; on = 0
- * restores the plain start.  The method order, tolerances and fallbacks are
- * unchanged.  Needs a loaded network for on = 1; later loads or training
+ * network's W (and v^2 of Eq. 29); if that Newton does not converge, Newton
+ * runs again from the stage's primitives before the Brent and entropy
+ * fallbacks.  on = 0 restores the plain start.  Tolerances and the rest of
+ * the method order are unchanged.  Needs a loaded network for on = 1; later loads or training
  * runs replace the network in place.  Ensemble steps always use the plain
  * start. */
 int grmhd_set_learned_guess(grmhd_ctx *ctx, int on);

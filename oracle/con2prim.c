@@ -279,20 +279,28 @@ int orc_con2prim_w(const double U[ORC_NU], const orc_geom *g, const double *gues
         double usq = 0.0;
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) usq += g->gcov[i + 1][j + 1] * ut[i] * ut[j];
-        double v2 = usq / (1.0 + usq);
-        double W = (1.0 + usq) * (guess[KRHO] + prm->gam * guess[KUU]);
-        if (wguess > 0.0) {
-            W = wguess;
-            v2 = v2_of_W(&c, W);
-        }
-        if (!(W > 0.0) || !isfinite(W)) W = c.D;
-        if (v2 > V2MAX) v2 = V2MAX;
-        if (newton2d(&c, &W, &v2, prm, iters)) {
-            recover(&c, W, v2, pressure_of(&c, W, v2), P);
-            if (physical(P, v2)) return C2P_NR;
-            /* converged to unphysical values: entropy fix */
-            if ((methods & 4) && entropy_inv(&c, prm, P)) return C2P_ENTROPY;
-            return C2P_FAIL | C2P_FAIL_ENT;
+        /* a learned W is tried first; Newton from the guess primitives stays
+           the fallback when it does not converge */
+        int tries = wguess > 0.0 ? 2 : 1;
+        for (int a = 0; a < tries; a++) {
+            double v2 = usq / (1.0 + usq);
+            double W = (1.0 + usq) * (guess[KRHO] + prm->gam * guess[KUU]);
+            if (a == 0 && wguess > 0.0) {
+                W = wguess;
+                v2 = v2_of_W(&c, W);
+            }
+            if (!(W > 0.0) || !isfinite(W)) W = c.D;
+            if (v2 > V2MAX) v2 = V2MAX;
+            int it = 0;
+            int ok = newton2d(&c, &W, &v2, prm, &it);
+            *iters += it;
+            if (ok) {
+                recover(&c, W, v2, pressure_of(&c, W, v2), P);
+                if (physical(P, v2)) return C2P_NR;
+                /* converged to unphysical values: entropy fix */
+                if ((methods & 4) && entropy_inv(&c, prm, P)) return C2P_ENTROPY;
+                return C2P_FAIL | C2P_FAIL_ENT;
+            }
         }
     }
     if ((methods & 2) && brent_w(&c, prm, P)) return C2P_BRENT_W;

@@ -258,7 +258,8 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 // Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g), and on
 // failure P[0..4] keep the guess (the fixups repair the zone).
 // methods: 1 Newton, 2 Brent-W, 4 entropy, 8 beta switch (15 = paper order).
-// wguess > 0 replaces the Newton starting W (learned guess; v^2 from Eq. 29).
+// wguess > 0: Newton first starts from that W (learned guess; v^2 from
+// Eq. 29) and, if it does not converge, again from the guess primitives.
 // FP64 path: guess = the previous FP64 primitives, Newton takes one more step
 // after the tolerance.  MIXED: guessf = the previous FP32 primitives (guess
 // unused); the starting (W, v^2) and the beta switch are formed in FP32 with
@@ -326,27 +327,35 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         }
     }
     if (methods & 1) {
-        double v2, W;
+        double v2p, Wp;
         if (MIXED) {
             float usq = spatial_sq(*gf, guessf[KU1], guessf[KU2], guessf[KU3]);
-            v2 = (double)(usq / (1.0f + usq));
-            W = (double)((1.0f + usq) * (guessf[KRHO] + (float)par.gam * guessf[KUU]));
+            v2p = (double)(usq / (1.0f + usq));
+            Wp = (double)((1.0f + usq) * (guessf[KRHO] + (float)par.gam * guessf[KUU]));
         } else {
             double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
-            v2 = usq / (1.0 + usq);
-            W = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
+            v2p = usq / (1.0 + usq);
+            Wp = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
         }
-        if (wguess > 0.0) {
-            W = wguess;
-            v2 = ResidW{&c}.v2(W);
-        }
-        if (!(W > 0.0) || !finite64(W)) W = c.D;
-        v2 = fmin(v2, V2MAX);
-        if (c2p_newton<!MIXED>(c, W, v2, MIXED ? par.tol_mixed : par.tol, par.nr_maxit, iters)) {
-            c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
-            if (c2p_physical(P, v2)) return C2P_NR;
-            if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
-            return fail(C2P_FAIL | C2P_FAIL_ENT);
+        // a learned W is tried first; Newton from the guess primitives stays the
+        // fallback when it does not converge
+        const int tries = wguess > 0.0 ? 2 : 1;
+#pragma unroll 1
+        for (int a = 0; a < tries; a++) {
+            const bool learned = a == 0 && wguess > 0.0;
+            double W = learned ? wguess : Wp;
+            double v2 = learned ? ResidW{&c}.v2(wguess) : v2p;
+            if (!(W > 0.0) || !finite64(W)) W = c.D;
+            v2 = fmin(v2, V2MAX);
+            int it;
+            const bool conv = c2p_newton<!MIXED>(c, W, v2, MIXED ? par.tol_mixed : par.tol, par.nr_maxit, it);
+            iters += it;
+            if (conv) {
+                c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
+                if (c2p_physical(P, v2)) return C2P_NR;
+                if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
+                return fail(C2P_FAIL | C2P_FAIL_ENT);
+            }
         }
     }
     if ((methods & 2) && c2p_brent_w(c, par.brent_maxit, P)) return C2P_BRENT_W;
