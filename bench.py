@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--no-window", action="store_true")
     return ap.parse_args()
 
 
@@ -209,6 +210,64 @@ def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload
             "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
             "loop_ms_per_step": ms_loop / steps, "speedup_vs_loop": ms_loop / ms_ens,
             "tiling": tiling, "tiling_from_cache": cached}
+
+
+# ------------------------------------------- mixed vs FP64 short window
+
+def run_window(G, torch, stream, device, n=128, steps=200, every=10):
+    """The first `steps` steps of the n^3 torus (gamma 4/3, beta_0 100, 2%
+    perturbation, seed 2) from the same initial state in FP64 and in mixed
+    precision: horizon Mdot and phi_B every `every` steps, and the per-field
+    deviation of the final state (the FP64 GPU step is held to the FP64
+    oracle at 1e-10 per step by the parity tests)."""
+    import numpy as np
+    series, finals = {}, {}
+    for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
+        gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=prec, device=device)
+        gp.stream = stream.cuda_stream
+        c = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+        G.set_metric(c, 0.9375, G.KERR_MKS)
+        G.init_torus(c, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+        if name == "fp64":
+            P0, U0, t0, dt0 = G.get_state(c)
+        else:
+            G.set_state(c, P0, U0, t0, dt0)
+        rows = []
+        for k in range(steps // every):
+            G.step(c, every)
+            d = G.diagnostics(c)
+            rows.append((d["t"], d["mdot"], d["phib"]))
+        series[name] = np.array(rows)
+        finals[name] = G.get_state(c)
+        c.close()
+    a, b = series["fp64"], series["mixed"]
+    Pa, Ua = finals["fp64"][:2]
+    Pb, Ub = finals["mixed"][:2]
+    body = Pa[0] > 1e-3 * Pa[0].max()   # zones of the torus body (off the floored atmosphere)
+
+    def field_dev(x, y, positive):
+        out = []
+        for f in range(x.shape[0]):
+            if f in positive:
+                out.append(float(np.max(np.abs(y[f] - x[f]) / np.abs(x[f]))))
+            else:
+                out.append(float(np.max(np.abs(y[f] - x[f])) / max(np.max(np.abs(x[f])), 1e-300)))
+        return out
+    return {"workload": f"{n}^3 FM torus, gamma 4/3, beta_0 100, 2% perturbation, seed 2; first {steps} steps "
+                        "from the same initial state, FP64 vs mixed",
+            "t_end": float(a[-1, 0]),
+            # normwise over the series
+            "mdot_max_rel_dev": float(np.max(np.abs(b[:, 1] - a[:, 1])) / max(np.max(np.abs(a[:, 1])), 1e-300)),
+            "phib_max_rel_dev": (float(np.max(np.abs(b[:, 2] - a[:, 2])) / np.max(np.abs(a[:, 2])))
+                                 if np.max(np.abs(a[:, 2])) > 1e-30 else None),
+            "phib_note": ("the loop field lies inside the torus: phi_B at the horizon is zero in this window "
+                          "(the split-monopole test of the mixed path covers phi_B)"
+                          if np.max(np.abs(a[:, 2])) <= 1e-30 else None),
+            "mdot_fp64_last": float(a[-1, 1]), "phib_fp64_last": float(a[-1, 2]),
+            "prim_dev_final_torus_body": field_dev(Pa[:, body], Pb[:, body], (0, 1)),
+            "prim_dev_final": field_dev(Pa, Pb, (0, 1)),
+            "cons_dev_final": field_dev(Ua, Ub, (0, 1, 8)),
+            "metric_note": "pointwise relative for rho, u (U_rho, U_E, U_S), max-norm relative for the others"}
 
 
 # ------------------------------------------------------- learned Newton start
@@ -404,6 +463,18 @@ def main():
     value = aggregate_value(zones, args.steps, world, ms)
     ms_step = ms / args.steps
     diag = G.diagnostics(ctx)
+    # horizon diagnostics, timed on their own (no allocation, device only)
+    dout = torch.zeros(8, dtype=torch.float64, device=f"cuda:{local}")
+    G.diagnostics_noalloc(ctx, dout)
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(20):
+        G.diagnostics_noalloc(ctx, dout)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    diag_ms = d0.elapsed_time(d1) / 20
     # per-kernel breakdown (events between kernel groups, no graph)
     prof = G.step_profiled(ctx, 3)
     parts = {k: v / 3.0 for k, v in prof.items()}
@@ -475,6 +546,10 @@ def main():
             G, torch, stream, local, steps=20, n=96, shapes=SMALL_SHAPES,
             workload="96 small FM tori (64x64x1, 96x64x1, 128x64x1, 64x64x4), same parameter draws, where a loop "
                      "of per-torus step graphs is bound by launches")
+    # ---- mixed vs FP64 over the first 200 steps of the 128^3 torus
+    window = None
+    if world == 1 and not args.no_window:
+        window = run_window(G, torch, stream, local)
     # ---- learned Newton start: training, inversions, the 256x192x192 step
     mlp = None
     if world == 1 and not args.no_mlp:
@@ -500,6 +575,8 @@ def main():
             "fp64_step": fp64,
             "ensemble": ensemble,
             "learned_start": mlp,
+            "mixed_vs_fp64_window": window,
+            "diagnostics_ms": diag_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,

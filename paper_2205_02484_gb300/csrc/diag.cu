@@ -46,15 +46,22 @@ __global__ void k_horizon_partial(Grid g, const RS *P, double *part)
         for (int c = 0; c < 4; c++) part[4 * blockIdx.x + c] = sm[c][0];
 }
 
+// one warp: lanes take blocks lane, lane + 32, ...; the lane sums are then
+// combined by a fixed shuffle tree (deterministic)
 __global__ void k_horizon_sum(const double *part, int nb, double *out)
 {
-    if (threadIdx.x != 0) return;
     double a[4] = {0, 0, 0, 0};
-    for (int b = 0; b < nb; b++)
+    for (int b = threadIdx.x; b < nb; b += 32)
         for (int c = 0; c < 4; c++) a[c] += part[4 * b + c];
-    for (int c = 0; c < 4; c++) out[c] = a[c];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 4; c++) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; c++) out[c] = a[c];
 }
 
+// Corner divergence of Eq. 24 on U_B = sqrt(-g) B^i: for each direction the
+// four corner-adjacent values on the upper side minus the four on the lower
+// side, times 1/(4 dX^d) (the grid's tabulated 1/dX^d).
 __global__ void k_divb(Grid g, double *out)
 {
     bool per3 = g.metric == KERR_MKS || g.bc3 == BC_PERIODIC;
@@ -66,15 +73,21 @@ __global__ void k_divb(Grid g, double *out)
         int k = (int)(t % (g.n3 - k0)) + k0;
         long long r = t / (g.n3 - k0);
         int j = (int)(r % (g.n2 - 1)) + 1, i = (int)(r / (g.n2 - 1)) + 1;
+        const int kl = k - 1 < 0 ? k - 1 + g.n3 : k - 1; // periodic in X3 (k >= 1 otherwise)
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
         for (int l1 = 0; l1 < 2; l1++)
+#pragma unroll
             for (int l2 = 0; l2 < 2; l2++)
+#pragma unroll
                 for (int l3 = 0; l3 < 2; l3++) {
-                    int ii = i - 1 + l1, jj = j - 1 + l2, kk = ((k - 1 + l3) % g.n3 + g.n3) % g.n3;
-                    long long z = zidx(g, ii, jj, kk);
-                    dv += (2 * l1 - 1) * g.U[KB1 * g.nz + z] / (4.0 * g.dx[0]) +
-                          (2 * l2 - 1) * g.U[KB2 * g.nz + z] / (4.0 * g.dx[1]) +
-                          (2 * l3 - 1) * g.U[KB3 * g.nz + z] / (4.0 * g.dx[2]);
+                    long long z = zidx(g, i - 1 + l1, j - 1 + l2, l3 ? k : kl);
+                    double b1 = g.U[KB1 * g.nz + z], b2 = g.U[KB2 * g.nz + z], b3 = g.U[KB3 * g.nz + z];
+                    s1 += l1 ? b1 : -b1;
+                    s2 += l2 ? b2 : -b2;
+                    s3 += l3 ? b3 : -b3;
                 }
+        dv = 0.25 * (s1 * g.idx[0] + s2 * g.idx[1] + s3 * g.idx[2]);
     }
     dv = fabs(dv);
     for (int o = 16; o > 0; o >>= 1) dv = fmax(dv, __shfl_xor_sync(0xffffffffu, dv, o));
