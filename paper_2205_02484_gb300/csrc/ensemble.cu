@@ -82,16 +82,16 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
         const long long base = (w - pre[m]) * tile;
         const R *Pin = (const R *)sg.P[src];
         R *Pout = (R *)sg.P[dst];
-        double dtc = INFINITY;
+        R cwm = R(0);
         UpdCount cn{};
         for (int it = 0; it < items; it++) {
             long long t = base + (long long)it * blockDim.x + threadIdx.x;
             if (CLS == W_F1)
-                dtc = fmin(dtc, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_elem_box(sg, 1), want_dt, t));
+                cwm = max(cwm, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_elem_box(sg, 1), want_dt, t));
             if (CLS == W_F2)
-                dtc = fmin(dtc, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_elem_box(sg, 2), want_dt, t));
+                cwm = max(cwm, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_elem_box(sg, 2), want_dt, t));
             if (CLS == W_F3)
-                dtc = fmin(dtc, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
+                cwm = max(cwm, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
             if (CLS == W_EMF)
                 emf_item(sg, (const R *)sg.F[0], (const R *)sg.F[1], (const R *)sg.F[2], (R *)sg.E[0], (R *)sg.E[1],
                          (R *)sg.E[2], edge_box(sg), t);
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
             if (CLS == W_BC2) bc2_item(sg, Pout, t);
             if (CLS == W_BC3) bc3_item(sg, Pout, t);
         }
-        if ((CLS == W_F1 || CLS == W_F2 || CLS == W_F3) && want_dt) block_min_into(&sg.dtmin[CLS - W_F1], dtc);
+        if ((CLS == W_F1 || CLS == W_F2 || CLS == W_F3) && want_dt)
+            block_cfl_into(&sg.dtmin[CLS - W_F1], cwm, sg.cfl * sg.dx[CLS - W_F1]);
         if (CLS == W_UPD) flush_counts(sg, cn);
     }
 }

@@ -66,13 +66,6 @@ __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-__device__ __forceinline__ double warp_min(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -81,20 +74,25 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// block-wide minimum of v, combined into *dst (bits of a positive double);
-// every thread of the block must call it
-__device__ __forceinline__ void block_min_into(unsigned long long *dst, double v)
+// CFL step of a block's faces: min over faces of num / c_w = num / (max c_w)
+// exactly (IEEE division is monotonic in the divisor), so the block reduces
+// max c_w in the flux precision and divides once (num = cfl dX^D); every
+// thread of the block must call it; *dst holds the bits of a positive double
+template <typename R>
+__device__ __forceinline__ void block_cfl_into(unsigned long long *dst, R cw, double num)
 {
-    __shared__ double sm[32];
-    v = warp_min(v);
+    __shared__ R sm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cw = max(cw, __shfl_xor_sync(0xffffffffu, cw, o));
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) sm[w] = v;
+    if (lane == 0) sm[w] = cw;
     __syncthreads();
     if (w == 0) {
-        double x = lane < (int)(blockDim.x >> 5) ? sm[lane] : INFINITY;
-        x = warp_min(x);
-        if (lane == 0 && x < INFINITY) atomicMin(dst, dbits(x));
+        R x = lane < (int)(blockDim.x >> 5) ? sm[lane] : R(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0 && x > R(0)) atomicMin(dst, dbits(num / (double)x));
     }
 }
 
@@ -270,24 +268,25 @@ __device__ __forceinline__ void face_flux(const Grid &g, const Geo<R> &geo, cons
     for (int c = 0; c < NU; c++) out[c] += wrF * Fx[c] + wrU * Ux[c];
 }
 
-// CFL candidate cfl dX^D / c_w of face (i, j, k) if it is an active face (else +inf)
+// c_w of face (i, j, k) if it is an active face (it enters the CFL step of
+// Eq. 27), else 0
 template <typename R, int D>
-__device__ __forceinline__ double face_dt(const Grid &g, int i, int j, int k, R cw)
+__device__ __forceinline__ R face_cw(const Grid &g, int i, int j, int k, R cw)
 {
     int ix[3] = {i, j, k}, nn[3] = {g.n1, g.n2, g.n3};
     bool act = true;
 #pragma unroll
     for (int e = 0; e < 3; e++) act = act && ix[e] >= 0 && ix[e] < nn[e] + (e == D - 1 ? 1 : 0);
-    return (act && cw > R(0)) ? g.cfl * g.dx[D - 1] / (double)cw : INFINITY;
+    return act ? cw : R(0);
 }
 
 // Face (i,j,k) of direction D lies between zone index-1 and index along D.
-// Returns the CFL candidate of an active face (else +inf).
+// Returns the face's c_w if it is active (else 0).
 template <typename R, int D>
-__device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
-                                            const Box &box, int want_dt, long long t)
+__device__ __forceinline__ R flux_item(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                       const Box &box, int want_dt, long long t)
 {
-    if (t >= box.count()) return INFINITY;
+    if (t >= box.count()) return R(0);
     int i, j, k;
     box_decode(box, t, i, j, k);
     long long z = zidx(g, i, j, k);
@@ -311,7 +310,7 @@ __device__ __forceinline__ double flux_item(const Grid &g, const R *__restrict__
     }
 #pragma unroll
     for (int c = 0; c < NU; c++) F[c * g.nz + z] = out[c];
-    return want_dt ? face_dt<R, D>(g, i, j, k, cw) : INFINITY;
+    return want_dt ? face_cw<R, D>(g, i, j, k, cw) : R(0);
 }
 
 // Columns of g.fcol consecutive faces along X1 or X2: one thread walks its
@@ -330,12 +329,12 @@ __host__ __device__ inline Box col_box(const Grid &g, int d)
 }
 
 template <typename R, int D>
-__device__ __forceinline__ double flux_column(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
-                                              const Box &cb, int want_dt, long long t)
+__device__ __forceinline__ R flux_column(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                         const Box &cb, int want_dt, long long t)
 {
     static_assert(D == 1 || D == 2, "columns run along X1 or X2");
-    double dtc = INFINITY;
-    if (t >= cb.count()) return dtc;
+    R cwm = R(0); // largest c_w of the column's active faces
+    if (t >= cb.count()) return cwm;
     int i, j, k;
     box_decode(cb, t, i, j, k);
     const int nf = (D == 1 ? g.n1 : g.n2) + 1;
@@ -375,7 +374,7 @@ __device__ __forceinline__ double flux_column(const Grid &g, const R *__restrict
         const long long zf = z0 + (long long)(f - f0) * st;
 #pragma unroll
         for (int c = 0; c < NU; c++) F[c * g.nz + zf] = out[c];
-        if (want_dt) dtc = fmin(dtc, face_dt<R, D>(g, fi, fj, k, cw));
+        if (want_dt) cwm = max(cwm, face_cw<R, D>(g, fi, fj, k, cw));
         if (f + 1 < f1) {
 #pragma unroll
             for (int c = 0; c < NP; c++) {
@@ -386,7 +385,7 @@ __device__ __forceinline__ double flux_column(const Grid &g, const R *__restrict
             }
         }
     }
-    return dtc;
+    return cwm;
 }
 
 // -------------------------------------------------------------------- EMFs
@@ -713,7 +712,7 @@ static __device__ __noinline__ void fixup_block_d(const Grid &g, double *P, int 
 // the flux element of direction D: a column of faces along X1 / X2, one face
 // along X3; box = flux_elem_box(g, D)
 template <typename R, int D>
-__device__ __forceinline__ double flux_call(const Grid &g, const R *P, R *F, const Box &box, int w, long long t)
+__device__ __forceinline__ R flux_call(const Grid &g, const R *P, R *F, const Box &box, int w, long long t)
 {
     if constexpr (sizeof(R) == 8) {
         if constexpr (D == 1) return flux_column_d1(g, P, F, box, w, t);

@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && D < 3) ? 4 : 1) k_flux
                                               Box box, int want_dt)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double dtc = flux_call<R, D>(g, P, F, box, want_dt, t);
-    if (want_dt) block_min_into(&g.dtmin[D - 1], dtc);
+    R cw = flux_call<R, D>(g, P, F, box, want_dt, t);
+    if (want_dt) block_cfl_into(&g.dtmin[D - 1], cw, g.cfl * g.dx[D - 1]);
 }
 
 template <typename R>
