@@ -212,6 +212,57 @@ def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload
             "tiling": tiling, "tiling_from_cache": cached}
 
 
+# ---------------------------------------------- stand-alone inversion
+
+# FP64 flops per inversion of k_con2prim on these states (ncu count of DFMA x 2
+# + DMUL + DADD, 1e6 inversions from a guess within 1e-4): see the profile
+# summary of the kernel
+CON2PRIM_FP64_FLOPS = 1902.0
+
+
+def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
+    """Batched inversions (Section 2.3, FP64 path with its confirmation
+    step) of n seeded states from the learned-start sample distribution at
+    the 256x192 grid's metric, each started from its exact primitives
+    perturbed by up to `rel` (what the previous stage hands the step)."""
+    gp = G.default_grid(256, 192, 1, a=0.9375, r_out=1000.0, precision=G.FP64, device=device)
+    gp.stream = stream.cuda_stream
+    ctx = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+    G.set_metric(ctx, 0.9375, G.KERR_MKS)
+    P, loc, U, f, y = G.mlp_samples(ctx, 11, 0, n, device=True)
+    gen = torch.Generator(device=P.device).manual_seed(5)
+    g0 = P.clone()
+    g0[:5] *= 1.0 + rel * (2.0 * torch.rand((5, n), generator=gen, device=P.device, dtype=torch.float64) - 1.0)
+    flags = torch.zeros(n, dtype=torch.int32, device=P.device)
+    iters = torch.zeros(n, dtype=torch.int32, device=P.device)
+    G.con2prim(ctx, U, loc, g0.clone(), flags, iters)
+    best = None
+    for _ in range(3):
+        work = g0.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.con2prim(ctx, U, loc, work, flags, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    fl = flags.cpu().numpy()
+    it = iters.cpu().numpy()
+    ctx.close()
+    out = {"workload": f"{n} inversions (FP64 path), states of the seeded sample distribution at the 256x192 "
+                       f"grid's metric, guess = exact primitives x (1 + {rel} U[-1,1])",
+           "ms": best, "inversions_per_s": n / (best * 1e-3),
+           "newton_iters_mean": float(it[fl == 0].mean()), "frac_newton": float((fl == 0).mean()),
+           "frac_entropy_beta": float((fl == 3).mean()), "frac_fail": float(((fl & 8) != 0).mean())}
+    if CON2PRIM_FP64_FLOPS:
+        tf = CON2PRIM_FP64_FLOPS * n / (best * 1e-3) / 1e12
+        out.update({"fp64_flops_per_inversion": CON2PRIM_FP64_FLOPS, "tflops_fp64": tf,
+                    "frac_of_fp64_peak": tf / (152 * 2 * 2 * 2.070e9 / 1e12)})
+    return out
+
+
 # ------------------------------------------- mixed vs FP64 short window
 
 def run_window(G, torch, stream, device, n=128, steps=200, every=10):
@@ -546,6 +597,10 @@ def main():
             G, torch, stream, local, steps=20, n=96, shapes=SMALL_SHAPES,
             workload="96 small FM tori (64x64x1, 96x64x1, 128x64x1, 64x64x4), same parameter draws, where a loop "
                      "of per-torus step graphs is bound by launches")
+    # ---- stand-alone inversion throughput and its FP64 fraction
+    c2p = None
+    if world == 1 and not args.no_window:
+        c2p = run_con2prim(G, torch, stream, local)
     # ---- mixed vs FP64 over the first 200 steps of the 128^3 torus
     window = None
     if world == 1 and not args.no_window:
@@ -576,6 +631,7 @@ def main():
             "ensemble": ensemble,
             "learned_start": mlp,
             "mixed_vs_fp64_window": window,
+            "con2prim": c2p,
             "diagnostics_ms": diag_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
