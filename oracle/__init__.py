@@ -25,7 +25,7 @@ _lib = None
 
 NP, NU = 8, 9
 KERR_MKS, MINK_CART = 0, 1
-BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW = 0, 1, 2, 3
+BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW, BC_EXTERNAL = 0, 1, 2, 3, 4
 LLF, HLL = 0, 1
 C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
 C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT = 8, 16, 32
@@ -133,6 +133,12 @@ def lib():
                 "orc_fm_ucon_bl": (None, [C.c_double, C.c_double, C.c_double, C.c_double, _D]),
                 "orc_uniform": (C.c_double, [C.c_uint64, C.c_uint64]),
                 "orc_x1_of_r": (C.c_double, [V, C.c_double]),
+                "orc_stage0": (C.c_double, [V, _I]),
+                "orc_last_dtd": (None, [V, _D]),
+                "orc_combine_dt": (C.c_double, [_D]),
+                "orc_stage1": (None, [V, _I]),
+                "orc_get_xplane": (None, [V, C.c_int, C.c_int, _D]),
+                "orc_set_xplane": (None, [V, C.c_int, C.c_int, _D]),
                 "orc_mlp_nparam": (C.c_int, []),
                 "orc_bf16_round": (C.c_float, [C.c_float]),
                 "orc_mlp_features": (C.c_int, [_D, C.POINTER(Geom), _D]),
@@ -224,6 +230,35 @@ class Grid:
 
     def set_dt(self, dt):
         self.L.orc_set_dt(self.h, float(dt))
+
+    # ---- one slab of a phi-decomposed grid (bc3 = BC_EXTERNAL)
+    def stage0(self):
+        """Predictor stage; returns (dt candidate of this slab, status)."""
+        st = C.c_int(0)
+        dtn = self.L.orc_stage0(self.h, C.byref(st))
+        return dtn, st.value
+
+    def last_dtd(self):
+        """Per-direction CFL minima of the last flux sweep."""
+        out = np.zeros(3)
+        self.L.orc_last_dtd(self.h, _p(out))
+        return out
+
+    def stage1(self):
+        """Corrector stage (advances t); returns the status."""
+        st = C.c_int(0)
+        self.L.orc_stage1(self.h, C.byref(st))
+        return st.value
+
+    def xplane(self, which, k):
+        """(8, N1, N2) primitives of P (which 0) or P-hat (which 1) at local X3 index k."""
+        out = np.zeros((NP, self.N[0], self.N[1]))
+        self.L.orc_get_xplane(self.h, which, k, _p(out))
+        return out
+
+    def set_xplane(self, which, k, plane):
+        plane = np.ascontiguousarray(plane, dtype=np.float64)
+        self.L.orc_set_xplane(self.h, which, k, _p(plane))
 
     def invert_all(self):
         return self.L.orc_invert_all(self.h)
@@ -397,6 +432,12 @@ def mlp_train_steps(theta, norm, feat, label, batch, nsteps, lr, beta1=0.9, beta
 
 
 # ----------------------------------------------------------- pointwise helpers
+
+def combine_dt(dtd):
+    """Eq. 27: 1/dt = sum of 1/dt^l over the per-direction minima."""
+    d = np.ascontiguousarray(dtd, dtype=np.float64)
+    return lib().orc_combine_dt(_p(d))
+
 
 def geom_from(gcov: np.ndarray) -> Geom:
     """Geometry record (gcon, sqrt(-g), alpha) for a 4x4 covariant metric."""

@@ -81,7 +81,11 @@ orc_grid *orc_create(const orc_params *p)
             x1out = 0.5 * (lo + hi);
         }
         G->x2in = -1.0; x2out = 1.0;
-        G->x3in = 0.0; x3out = 2.0 * M_PI;
+        if (p->bc3 == ORC_BC_EXTERNAL) { /* a phi slab of the full circle, width x3max - x3min */
+            G->x3in = p->x3min; x3out = p->x3max;
+        } else {
+            G->x3in = 0.0; x3out = 2.0 * M_PI;
+        }
     } else {
         G->xb = 1e300;
         G->x1in = p->x1min; x1out = p->x1max;
@@ -189,7 +193,7 @@ void orc_bc_fill(orc_grid *G, double *P)
     int kerr = (p->metric == ORC_KERR_MKS);
     int bc1 = kerr ? ORC_BC_INFLOW : p->bc1;
     int bc2 = kerr ? ORC_BC_POLAR : p->bc2;
-    int bc3 = kerr ? ORC_BC_PERIODIC : p->bc3;
+    int bc3 = (kerr && p->bc3 != ORC_BC_EXTERNAL) ? ORC_BC_PERIODIC : p->bc3;
 
     /* polar ut^2 interpolation in the two zones next to each pole */
     if (bc2 == ORC_BC_POLAR && n2 >= 6) {
@@ -246,7 +250,8 @@ void orc_bc_fill(orc_grid *G, double *P)
                     scatter(G, P, orc_idx(G, i, jr, k), q);
                 }
             }
-    /* X3 ghosts over all i, j */
+    /* X3 ghosts over all i, j (a slab's come from its neighbours) */
+    if (bc3 == ORC_BC_EXTERNAL) return;
     for (int i = -ORC_NG; i < n1 + ORC_NG; i++)
         for (int j = -ORC_NG; j < n2 + ORC_NG; j++)
             for (int gh = 1; gh <= ORC_NG; gh++) {
@@ -351,10 +356,24 @@ double orc_compute_fluxes(orc_grid *G, const double *P)
                     if (act && cw > 0.0) dtd[d] = minf(dtd[d], p->cfl * G->dx[d] / cw);
                 }
     }
+    for (int d = 0; d < 3; d++) G->dtd[d] = dtd[d];
+    return orc_combine_dt(dtd);
+}
+
+/* Eq. 27: 1/dt = sum over directions of 1/dt^l, each dt^l the minimum over
+ * the faces of that direction */
+double orc_combine_dt(const double dtd[3])
+{
     double inv = 0.0;
     for (int d = 0; d < 3; d++)
         if (isfinite(dtd[d])) inv += 1.0 / dtd[d];
     return inv > 0.0 ? 1.0 / inv : INFINITY;
+}
+
+/* the per-direction minima of the grid's last flux sweep */
+void orc_last_dtd(const orc_grid *G, double out[3])
+{
+    for (int d = 0; d < 3; d++) out[d] = G->dtd[d];
 }
 
 /* Flux-CT of Eqs. 22-23: edge EMFs from the Riemann B-fluxes, then the
@@ -662,6 +681,44 @@ int orc_step(orc_grid *G)
     G->dt = dtn;
     G->cnt.n_steps++;
     return status;
+}
+
+/* The two stages of orc_step, for a grid that is one slab of a decomposed
+ * one: the caller exchanges the X3 ghost planes after each stage and sets the
+ * next step's dt from the per-direction minima over the slabs of the
+ * predictor's sweep (orc_last_dtd, combined by orc_combine_dt).  orc_stage0
+ * returns this slab's own combination; orc_stage1 advances t.  Both return
+ * the fixup status through *status (0, or -1 if some zone was not fixed). */
+double orc_stage0(orc_grid *G, int *status)
+{
+    return stage(G, G->P, G->Ph, 0.5 * G->dt, 0, status);
+}
+
+void orc_stage1(orc_grid *G, int *status)
+{
+    stage(G, G->Ph, G->P, G->dt, 1, status);
+    G->t += G->dt;
+    G->cnt.n_steps++;
+}
+
+/* the (N1 x N2) plane of all 8 primitives at local X3 index k (-NG .. n3-1+NG,
+ * ghosts of X1 and X2 included) of P (which = 0) or P-hat (which = 1) */
+void orc_get_xplane(const orc_grid *G, int which, int k, double *out)
+{
+    const double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < ORC_NP; c++)
+        for (int i = -ORC_NG; i < G->p.n1 + ORC_NG; i++)
+            for (int j = -ORC_NG; j < G->p.n2 + ORC_NG; j++) out[m++] = AT(P, c, orc_idx(G, i, j, k));
+}
+
+void orc_set_xplane(orc_grid *G, int which, int k, const double *in)
+{
+    double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < ORC_NP; c++)
+        for (int i = -ORC_NG; i < G->p.n1 + ORC_NG; i++)
+            for (int j = -ORC_NG; j < G->p.n2 + ORC_NG; j++) AT(P, c, orc_idx(G, i, j, k)) = in[m++];
 }
 
 

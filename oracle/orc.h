@@ -26,7 +26,8 @@
 
 enum { KRHO = 0, KUU, KU1, KU2, KU3, KB1, KB2, KB3, KENT };
 enum { ORC_KERR_MKS = 0, ORC_MINK_CART = 1 };
-enum { ORC_BC_INFLOW = 0, ORC_BC_POLAR = 1, ORC_BC_PERIODIC = 2, ORC_BC_OUTFLOW = 3 };
+enum { ORC_BC_INFLOW = 0, ORC_BC_POLAR = 1, ORC_BC_PERIODIC = 2, ORC_BC_OUTFLOW = 3,
+       ORC_BC_EXTERNAL = 4 /* X3 ghosts supplied by the caller (a phi slab of a decomposed grid) */ };
 enum { ORC_LLF = 0, ORC_HLL = 1 };
 
 /* con2prim result flags: low 3 bits = method that produced the primitives,
@@ -81,6 +82,7 @@ typedef struct orc_grid {
     double *F[3], *cw[3], *E[3];
     int *flag;
     double t, dt;
+    double dtd[3];    /* per-direction CFL minima of the last flux sweep (Eq. 27) */
     double disk_mass, disk_eb;
     orc_diag cnt;     /* running counters (cumulative) */
 } orc_grid;
@@ -128,6 +130,7 @@ long orc_idx(const orc_grid *G, int i, int j, int k);
 int orc_midx(const orc_grid *G, int i, int j);
 void orc_bc_fill(orc_grid *G, double *P);
 double orc_compute_fluxes(orc_grid *G, const double *P);
+double orc_combine_dt(const double dtd[3]);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
 

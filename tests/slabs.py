@@ -1,0 +1,87 @@
+"""A phi-slab decomposition of the step (one ghost exchange per stage, a
+global minimum for dt), run on the oracle: the host logic a multi-GPU run
+follows, checked against the undecomposed grid.
+
+Each slab r of R owns the active phi zones [r n3/R, (r+1) n3/R) and a copy of
+the (r, theta) metric; after every stage its NG = 2 X3 ghost planes on each
+side are the neighbours' outermost active planes (periodic in phi), taken
+after the neighbours' own X1/X2 boundary fill.  The predictor's per-direction
+CFL minima are reduced over slabs and then combined by Eq. 27.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle as O
+
+NG = 2
+
+
+def slab_params(base: O.Params, r: int, R: int) -> O.Params:
+    """Parameters of slab r: n3 / R phi zones, X3 ghosts external.  The
+    step never uses a slab's phi position (the metric does not depend on
+    phi), only dX3, so the slab's X3 range starts at 0 and spans
+    (n3 / R) 2 pi / n3: for power-of-two slab widths dX3 = 2 pi / n3 exactly,
+    as in the undecomposed grid."""
+    d = {name: getattr(base, name) for name, _ in O.Params._fields_}
+    n3 = base.n3 // R
+    d.update(n3=n3, bc3=O.BC_EXTERNAL, x3min=0.0, x3max=n3 * (2.0 * math.pi / base.n3))
+    return O.Params(**d)
+
+
+def split_state(P, U, R):
+    n3 = P.shape[3] // R
+    return [(np.ascontiguousarray(P[..., r * n3:(r + 1) * n3]), np.ascontiguousarray(U[..., r * n3:(r + 1) * n3]))
+            for r in range(R)]
+
+
+def ghost_planes_from(left, right, n3, which):
+    """The ghost planes of a slab: k = -2, -1 from its left neighbour's
+    k = n3-2, n3-1 and k = n3, n3+1 from its right neighbour's k = 0, 1."""
+    lo = [left.xplane(which, n3 - NG + g) for g in range(NG)]
+    hi = [right.xplane(which, g) for g in range(NG)]
+    return lo, hi
+
+
+def exchange(slabs, which):
+    n3 = slabs[0].shape[2]
+    R = len(slabs)
+    planes = [ghost_planes_from(slabs[(r - 1) % R], slabs[(r + 1) % R], n3, which) for r in range(R)]
+    for r, (lo, hi) in enumerate(planes):
+        for g in range(NG):
+            slabs[r].set_xplane(which, -NG + g, lo[g])
+            slabs[r].set_xplane(which, n3 + g, hi[g])
+
+
+def make_slabs(base: O.Params, P, U, t, dt, R):
+    slabs = [O.Grid(slab_params(base, r, R)) for r in range(R)]
+    for g, (Ps, Us) in zip(slabs, split_state(P, U, R)):
+        g.set_state(Ps, Us, t, dt)
+    exchange(slabs, 0)
+    return slabs
+
+
+def step_slabs(slabs):
+    cand, status = [], 0
+    for g in slabs:
+        _, st = g.stage0()
+        cand.append(g.last_dtd())
+        status = status or st
+    exchange(slabs, 1)
+    for g in slabs:
+        status = g.stage1() or status
+    exchange(slabs, 0)
+    # Eq. 27 over the whole grid: per-direction minima first, then combined
+    dt = O.combine_dt(np.min(np.array(cand), axis=0))
+    for g in slabs:
+        g.set_dt(dt)
+    return status
+
+
+def gather(slabs):
+    parts = [g.get_state() for g in slabs]
+    P = np.concatenate([p[0] for p in parts], axis=3)
+    U = np.concatenate([p[1] for p in parts], axis=3)
+    return P, U, parts[0][2], parts[0][3]
