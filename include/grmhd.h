@@ -56,6 +56,9 @@ extern "C" {
 #define GRMHD_BC_POLAR 1
 #define GRMHD_BC_PERIODIC 2
 #define GRMHD_BC_OUTFLOW 3
+#define GRMHD_BC_EXTERNAL 4 /* bc3 only: the X3 ghosts are written by the caller (grmhd_x3_unpack), for a
+                               phi slab of a decomposed grid; on a Kerr grid the slab spans
+                               [x3min, x3max) of phi, which sets dX3 */
 
 #define GRMHD_LLF 0 /* Eq. 18 */
 #define GRMHD_HLL 1 /* Eq. 21 */
@@ -377,6 +380,54 @@ int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp, grmhd_mlp_
  * runs replace the network in place.  Ensemble steps always use the plain
  * start. */
 int grmhd_set_learned_guess(grmhd_ctx *ctx, int on);
+
+/* ---------------------------------------------------------------------
+ * Phi-slab decomposition (the slab layout of the paper's multi-GPU runs,
+ * Section 3, split along phi).  Each slab is a context with bc3 =
+ * GRMHD_BC_EXTERNAL that owns n3 consecutive phi zones.  One step of a
+ * decomposed grid, on every slab:
+ *   grmhd_stage(ctx, 0);  exchange the X3 ghosts of buffer 1 (P-hat);
+ *   grmhd_stage(ctx, 1);  exchange the X3 ghosts of buffer 0 (P);
+ *   grmhd_step_dtd(ctx, d, acc);  d = the minimum over all slabs (acc = 1
+ *                                 folds a slab into d on one device; across
+ *                                 devices, a MIN all-reduce of d);
+ *   grmhd_finish_step(ctx, d);
+ * To exchange, a slab packs its own planes with grmhd_x3_pack and unpacks its
+ * neighbours' planes with grmhd_x3_unpack: side 0 takes the left
+ * neighbour's side-1 pack, side 1 the right neighbour's side-0 pack, with
+ * periodic wrap in phi.  The same sequence on a single context with bc3
+ * periodic reproduces grmhd_step.  Every call is asynchronous on the context
+ * stream and does not synchronise it.
+ * ------------------------------------------------------------------- */
+
+/* One RK2 stage (st = 0: predictor P^n -> P-hat; st = 1: corrector P-hat ->
+ * P^{n+1}, Eqs. 25-26), including fixups and the X1 / X2 (and, unless
+ * external, X3) boundary fill.  The predictor's faces record the
+ * per-direction CFL minima of Eq. 27. */
+int grmhd_stage(grmhd_ctx *ctx, int st);
+
+/* The per-direction CFL minima of the last predictor into dtd_dev (3 doubles,
+ * caller-owned device memory): stored (accumulate = 0) or folded in by a
+ * minimum (accumulate = 1).  Resets the context's minima. */
+int grmhd_step_dtd(grmhd_ctx *ctx, double *dtd_dev, int accumulate);
+
+/* Advance t by the current dt, then set the next dt from Eq. 27 applied to
+ * dtd_dev (3 doubles of device memory: the minima over all slabs). */
+int grmhd_finish_step(grmhd_ctx *ctx, const double *dtd_dev);
+
+/* Bytes of one side's X3 planes: NG = 2 planes of all 8 primitives over the
+ * ghosted (X1, X2) cross-section, layout [NG][8][n1 + 4][n2 + 4], element
+ * type double (GRMHD_FP64) or float (GRMHD_MIXED). */
+int grmhd_x3_plane_bytes(grmhd_ctx *ctx, unsigned long long *bytes);
+
+/* Pack the two outermost active planes of buffer `which` (0 = P, 1 = P-hat)
+ * on `side` (0 = low phi, k = 0, 1; 1 = high phi, k = n3-2, n3-1) into the
+ * caller's device buffer. */
+int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev);
+
+/* Write a neighbour's packed planes into the ghosts on `side` (0: k = -2, -1;
+ * 1: k = n3, n3+1) of buffer `which`. */
+int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev);
 
 /* Library version string. */
 const char *grmhd_version(void);

@@ -105,6 +105,11 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
         return fail(nullptr, GRMHD_EINVAL, "Kerr grid needs n1 >= 2");
     if (grid->precision != GRMHD_FP64 && grid->precision != GRMHD_MIXED)
         return fail(nullptr, GRMHD_EINVAL, "precision must be GRMHD_FP64 or GRMHD_MIXED");
+    if (grid->bc1 < 0 || grid->bc1 > GRMHD_BC_OUTFLOW || grid->bc2 < 0 || grid->bc2 > GRMHD_BC_OUTFLOW ||
+        grid->bc3 < 0 || grid->bc3 > GRMHD_BC_EXTERNAL)
+        return fail(nullptr, GRMHD_EINVAL, "bad boundary kind (external is for bc3 only)");
+    if (grid->bc3 == GRMHD_BC_EXTERNAL && grid->n3 < 2)
+        return fail(nullptr, GRMHD_EINVAL, "a phi slab needs n3 >= 2");
     if (grid->riemann != GRMHD_LLF && grid->riemann != GRMHD_HLL)
         return fail(nullptr, GRMHD_EINVAL, "riemann must be GRMHD_LLF or GRMHD_HLL");
     if (!(phys->gam > 1.0) || !(phys->cfl > 0.0) || phys->nr_maxit < 1 || phys->brent_maxit < 1 ||
@@ -236,10 +241,16 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         g.x1in = std::log(p.r_in - p.R0);
         double x1out = p.r_out <= p.r_br ? std::log(p.r_out - p.R0) : x1_of_r(cp, p.r_out);
         g.x2in = -1.0;
-        g.x3in = 0.0;
         g.dx[0] = (x1out - g.x1in) / g.n1;
         g.dx[1] = 2.0 / g.n2;
-        g.dx[2] = 2.0 * M_PI / g.n3;
+        if (g.bc3 == BC_EXTERNAL) { // a phi slab [x3min, x3max) of the full circle
+            g.x3in = p.x3min;
+            g.dx[2] = (p.x3max - p.x3min) / g.n3;
+            if (!(g.dx[2] > 0.0)) return fail(ctx, GRMHD_EINVAL, "phi slab needs x3max > x3min");
+        } else {
+            g.x3in = 0.0;
+            g.dx[2] = 2.0 * M_PI / g.n3;
+        }
         g.i_h = g.n1;
         for (int i = 0; i < g.n1; i++) {
             double r, dr;
@@ -1047,4 +1058,64 @@ extern "C" int grmhd_set_learned_guess(grmhd_ctx *ctx, int on)
     ctx->graph = nullptr;
     ctx->g.mlp = want;
     return 0;
+}
+
+// ------------------------------------------------------------- phi slabs
+
+extern "C" int grmhd_stage(grmhd_ctx *ctx, int st)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "stage needs a state (init_torus or set_state)");
+    if (st != 0 && st != 1) return fail(ctx, GRMHD_EINVAL, "st must be 0 or 1");
+    (void)cudaGetLastError();
+    launch_stage(ctx->g, st, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_step_dtd(grmhd_ctx *ctx, double *dtd_dev, int accumulate)
+{
+    if (!ctx || !dtd_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    (void)cudaGetLastError();
+    launch_step_dtd(ctx->g, dtd_dev, accumulate != 0, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_finish_step(grmhd_ctx *ctx, const double *dtd_dev)
+{
+    if (!ctx || !dtd_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    (void)cudaGetLastError();
+    launch_finish_step(ctx->g, dtd_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_x3_plane_bytes(grmhd_ctx *ctx, unsigned long long *bytes)
+{
+    if (!ctx || !bytes) return fail(ctx, GRMHD_EINVAL, "null argument");
+    *bytes = (unsigned long long)x3_plane_elems(ctx->g) * (ctx->g.mixed ? sizeof(float) : sizeof(double));
+    return 0;
+}
+
+static int x3_planes(grmhd_ctx *ctx, int which, int side, void *buf, int unpack)
+{
+    if (!ctx || !buf) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if ((which != 0 && which != 1) || (side != 0 && side != 1))
+        return fail(ctx, GRMHD_EINVAL, "which and side must be 0 or 1");
+    if (ctx->g.n3 < NG) return fail(ctx, GRMHD_EINVAL, "a slab needs n3 >= 2");
+    (void)cudaGetLastError();
+    launch_x3_planes(ctx->g, which, side, buf, unpack, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev)
+{
+    return x3_planes(ctx, which, side, buf_dev, 0);
+}
+
+extern "C" int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev)
+{
+    return x3_planes(ctx, which, side, const_cast<void *>(buf_dev), 1);
 }

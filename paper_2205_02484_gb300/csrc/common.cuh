@@ -21,7 +21,7 @@ constexpr int NP = 8;
 constexpr int NU = 9;
 enum { KRHO = 0, KUU, KU1, KU2, KU3, KB1, KB2, KB3, KENT };
 enum { KERR_MKS = 0, MINK_CART = 1 };
-enum { BC_INFLOW = 0, BC_POLAR = 1, BC_PERIODIC = 2, BC_OUTFLOW = 3 };
+enum { BC_INFLOW = 0, BC_POLAR = 1, BC_PERIODIC = 2, BC_OUTFLOW = 3, BC_EXTERNAL = 4 };
 
 // packed index of a symmetric 4x4 tensor: 00 01 02 03 11 12 13 22 23 33
 __host__ __device__ constexpr int sym(int m, int n)

@@ -9,6 +9,11 @@ void launch_step(const Grid &g, cudaStream_t s);
 void launch_step_profiled(const Grid &g, cudaStream_t s, cudaEvent_t *ev);
 double launch_fma_probe(int fp64, int sms, cudaStream_t s);
 void launch_bc(const Grid &g, int buf, cudaStream_t s);
+void launch_stage(const Grid &g, int st, cudaStream_t s);
+void launch_step_dtd(const Grid &g, double *dtd, int acc, cudaStream_t s);
+void launch_finish_step(const Grid &g, const double *dtd, cudaStream_t s);
+long long x3_plane_elems(const Grid &g);
+void launch_x3_planes(const Grid &g, int which, int side, void *buf, int unpack, cudaStream_t s);
 void launch_fluxes_dt(const Grid &g, int set_dt, cudaStream_t s);
 void launch_gather_fluxes(const Grid &g, double *out, cudaStream_t s);
 

@@ -204,7 +204,8 @@ __device__ __forceinline__ void bc3_item(const Grid &g, RS *P, long long t)
     int gh = 1 + (int)(r % NG);
     r /= NG;
     int j = (int)(r % (g.n2 + 2 * NG)) - NG, i = (int)(r / (g.n2 + 2 * NG)) - NG;
-    int bc = g.metric == KERR_MKS ? BC_PERIODIC : g.bc3;
+    int bc = (g.metric == KERR_MKS && g.bc3 != BC_EXTERNAL) ? BC_PERIODIC : g.bc3;
+    if (bc == BC_EXTERNAL) return; // a slab's X3 ghosts come from its neighbours
     int kd = side == 0 ? -gh : g.n3 - 1 + gh;
     int ks = bc == BC_PERIODIC ? wrapi(kd, g.n3) : (side == 0 ? 0 : g.n3 - 1);
     long long zs = zidx(g, i, j, ks), zd = zidx(g, i, j, kd);
@@ -752,19 +753,28 @@ __device__ __forceinline__ void fixup_call(const Grid &g, R *P, int corr)
 // --------------------------------------------------------------------- dt
 
 // 1/dt = sum_l 1/dt^l (Eq. 27); t += dt for a finished step; minima reset.
-__device__ inline void finalize_one(const Grid &g, int advance)
+// next dt from per-direction minima (Eq. 27: 1/dt = sum_l 1/dt^l)
+__device__ __forceinline__ double combine_dt(const double dtd[3])
 {
     double inv = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        if (dtd[d] < INFINITY) inv += 1.0 / dtd[d];
+    return inv > 0.0 ? 1.0 / inv : INFINITY;
+}
+
+__device__ inline void finalize_one(const Grid &g, int advance)
+{
+    double dtd[3];
     for (int d = 0; d < 3; d++) {
-        double v = __longlong_as_double((long long)g.dtmin[d]);
-        if (v < INFINITY) inv += 1.0 / v;
+        dtd[d] = __longlong_as_double((long long)g.dtmin[d]);
         g.dtmin[d] = dbits(INFINITY);
     }
     if (advance) {
         g.scal[1] += g.scal[0];
         g.cnt[C_STEPS] += 1;
     }
-    g.scal[0] = inv > 0.0 ? 1.0 / inv : INFINITY;
+    g.scal[0] = combine_dt(dtd);
 }
 
 } // namespace grmhd

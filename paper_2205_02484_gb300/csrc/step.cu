@@ -160,6 +160,63 @@ void launch_step(const Grid &g, cudaStream_t s)
     k_finalize<<<1, 32, 0, s>>>(g, 1);
 }
 
+// one stage of the step (st 0: predictor, st 1: corrector) for a slab
+void launch_stage(const Grid &g, int st, cudaStream_t s)
+{
+    int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
+    double fac = st == 0 ? 0.5 : 1.0;
+    if (g.mixed) stage<float>(g, src, dst, fac, st, st == 0, s);
+    else stage<double>(g, src, dst, fac, st, st == 0, s);
+}
+
+__global__ void k_step_dtd(Grid g, double *dtd, int acc)
+{
+    if (threadIdx.x < 3) {
+        double v = __longlong_as_double((long long)g.dtmin[threadIdx.x]);
+        dtd[threadIdx.x] = acc ? fmin(dtd[threadIdx.x], v) : v;
+        g.dtmin[threadIdx.x] = dbits(INFINITY);
+    }
+}
+
+__global__ void k_finish_step(Grid g, const double *dtd)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double d[3] = {dtd[0], dtd[1], dtd[2]};
+    g.scal[1] += g.scal[0];
+    g.cnt[C_STEPS] += 1;
+    g.scal[0] = combine_dt(d);
+}
+
+void launch_step_dtd(const Grid &g, double *dtd, int acc, cudaStream_t s) { k_step_dtd<<<1, 32, 0, s>>>(g, dtd, acc); }
+void launch_finish_step(const Grid &g, const double *dtd, cudaStream_t s) { k_finish_step<<<1, 32, 0, s>>>(g, dtd); }
+
+// X3 planes [NG][8][N1][N2]: pack k = base .. base+NG-1 into buf, or unpack buf there
+template <typename R>
+__global__ void k_x3_planes(Grid g, R *P, R *buf, int base, int unpack)
+{
+    long long plane = (long long)g.N1 * g.N2;
+    long long n = (long long)NG * NP * plane;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    long long e = t % plane;
+    int c = (int)((t / plane) % NP), gl = (int)(t / (plane * NP));
+    int i = (int)(e / g.N2) - NG, j = (int)(e % g.N2) - NG;
+    long long z = c * g.nz + zidx(g, i, j, base + gl);
+    if (unpack) P[z] = buf[t];
+    else buf[t] = P[z];
+}
+
+long long x3_plane_elems(const Grid &g) { return (long long)NG * NP * g.N1 * g.N2; }
+
+void launch_x3_planes(const Grid &g, int which, int side, void *buf, int unpack, cudaStream_t s)
+{
+    int base = unpack ? (side == 0 ? -NG : g.n3) : (side == 0 ? 0 : g.n3 - NG);
+    long long n = x3_plane_elems(g);
+    unsigned nb = (unsigned)((n + 255) / 256);
+    if (g.mixed) k_x3_planes<float><<<nb, 256, 0, s>>>(g, (float *)g.P[which], (float *)buf, base, unpack);
+    else k_x3_planes<double><<<nb, 256, 0, s>>>(g, (double *)g.P[which], (double *)buf, base, unpack);
+}
+
 void launch_bc(const Grid &g, int buf, cudaStream_t s)
 {
     if (g.mixed) fill_bc<float>(g, (float *)g.P[buf], s);

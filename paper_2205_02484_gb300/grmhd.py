@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 KERR_MKS, MINK_CART = 0, 1
-BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW = 0, 1, 2, 3
+BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW, BC_EXTERNAL = 0, 1, 2, 3, 4
 LLF, HLL = 0, 1
 FP64, MIXED = 0, 1
 C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
@@ -135,6 +135,12 @@ SIGNATURES = {
                                         C.POINTER(C.c_double), C.c_int]),
     "grmhd_mlp_train": (C.c_int, [_V, C.POINTER(MlpTrainParams), C.POINTER(MlpTrainReport)]),
     "grmhd_set_learned_guess": (C.c_int, [_V, C.c_int]),
+    "grmhd_stage": (C.c_int, [_V, C.c_int]),
+    "grmhd_step_dtd": (C.c_int, [_V, _V, C.c_int]),
+    "grmhd_finish_step": (C.c_int, [_V, _V]),
+    "grmhd_x3_plane_bytes": (C.c_int, [_V, C.POINTER(C.c_ulonglong)]),
+    "grmhd_x3_pack": (C.c_int, [_V, C.c_int, C.c_int, _V]),
+    "grmhd_x3_unpack": (C.c_int, [_V, C.c_int, C.c_int, _V]),
 }
 
 PROF_SLOTS = 16
@@ -278,6 +284,45 @@ def get_state(ctx: Context, P=None, U=None):
 
 def step(ctx: Context, nsteps: int = 1):
     ctx.check(ctx.L.grmhd_step(ctx.h, nsteps))
+
+
+# ------------------------------------------------- phi slabs (stage level)
+
+def _dev_ptr(t):
+    p, dev = _ptr(t)
+    if not dev:
+        raise ValueError("a device tensor is required")
+    return p
+
+
+def stage(ctx: Context, st: int):
+    """One RK2 stage: 0 predictor, 1 corrector (Eqs. 25-26)."""
+    ctx.check(ctx.L.grmhd_stage(ctx.h, st))
+
+
+def step_dtd(ctx: Context, dtd, accumulate: bool = False):
+    """The last predictor's per-direction CFL minima into dtd (3 doubles on
+    the device), stored or folded in by a minimum."""
+    ctx.check(ctx.L.grmhd_step_dtd(ctx.h, _dev_ptr(dtd), int(bool(accumulate))))
+
+
+def finish_step(ctx: Context, dtd):
+    """Advance t by dt and set the next dt from Eq. 27 over dtd (3 doubles on the device)."""
+    ctx.check(ctx.L.grmhd_finish_step(ctx.h, _dev_ptr(dtd)))
+
+
+def x3_plane_bytes(ctx: Context) -> int:
+    n = C.c_ulonglong(0)
+    ctx.check(ctx.L.grmhd_x3_plane_bytes(ctx.h, C.byref(n)))
+    return n.value
+
+
+def x3_pack(ctx: Context, which: int, side: int, buf):
+    ctx.check(ctx.L.grmhd_x3_pack(ctx.h, which, side, _dev_ptr(buf)))
+
+
+def x3_unpack(ctx: Context, which: int, side: int, buf):
+    ctx.check(ctx.L.grmhd_x3_unpack(ctx.h, which, side, _dev_ptr(buf)))
 
 
 def sync(ctx: Context):

@@ -85,3 +85,54 @@ def gather(slabs):
     P = np.concatenate([p[0] for p in parts], axis=3)
     U = np.concatenate([p[1] for p in parts], axis=3)
     return P, U, parts[0][2], parts[0][3]
+
+
+class OracleSlab:
+    """The SlabEngine interface of paper_2205_02484_gb300.decomp over one
+    oracle slab, so that the product's slab drivers (their exchange order,
+    tags and dt reduction) can run on the CPU with the oracle doing the
+    stages.  Buffers are CPU float64 tensors in the [NG][8][N1][N2] layout."""
+
+    def __init__(self, params: O.Params):
+        import torch
+        self.g = O.Grid(params)
+        self.n3 = params.n3
+        self.device = torch.device("cpu")
+        self.dtype = torch.float64
+        self.plane_numel = NG * O.NP * self.g.N[0] * self.g.N[1]
+
+    def set_state(self, P, U, t, dt):
+        self.g.set_state(np.asarray(P), np.asarray(U), t, dt)
+
+    def get_state(self):
+        return self.g.get_state()
+
+    def stage(self, st):
+        if st == 0:
+            assert self.g.stage0()[1] == 0
+        else:
+            assert self.g.stage1() == 0
+
+    def dtd(self, out, accumulate=False):
+        import torch
+        v = torch.from_numpy(self.g.last_dtd())
+        out.copy_(torch.minimum(out, v) if accumulate else v)
+
+    def finish(self, dtd):
+        # the oracle's corrector has already advanced t by the old dt
+        self.g.set_dt(O.combine_dt(dtd.numpy()))
+
+    def _ks(self, side, ghost):
+        if ghost:
+            return range(-NG, 0) if side == 0 else range(self.n3, self.n3 + NG)
+        return range(0, NG) if side == 0 else range(self.n3 - NG, self.n3)
+
+    def pack(self, which, side, buf):
+        import torch
+        planes = np.stack([self.g.xplane(which, k) for k in self._ks(side, False)])
+        buf.copy_(torch.from_numpy(planes.reshape(-1)))
+
+    def unpack(self, which, side, buf):
+        planes = buf.numpy().reshape(NG, O.NP, self.g.N[0], self.g.N[1])
+        for g_, k in enumerate(self._ks(side, True)):
+            self.g.set_xplane(which, k, planes[g_])

@@ -1,0 +1,116 @@
+"""The phi-slab decomposition through the C ABI (grmhd_stage, grmhd_step_dtd,
+grmhd_finish_step, grmhd_x3_pack / unpack) on one GPU: R slab contexts
+exchanging their X3 ghost planes through device buffers reproduce the
+undecomposed GPU step bit for bit, in FP64 and in the mixed path, and the
+slab state stays within the per-step parity bound of the undecomposed oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.gpu_common import field_err, gpu_mod
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SHAPE = (32, 24, 16)
+GAM = 13.0 / 9.0
+A = 0.9375
+
+
+def _start(G, precision):
+    """A perturbed torus (magnetised, so every term of the step is active) as
+    host arrays, and an undecomposed context started from it."""
+    grid = G.default_grid(*SHAPE, precision=precision, a=A)
+    phys = G.default_phys(gam=GAM)
+    src = G.init_grid(grid, phys)
+    G.set_metric(src, A)
+    G.init_torus(src, pert_amp=0.04, seed=11)
+    P0, U0, t0, dt0 = G.get_state(src)
+    src.close()
+    full = G.init_grid(grid, phys)
+    G.set_metric(full, A)
+    G.set_state(full, P0, U0, t0, dt0)
+    return grid, phys, full, (P0, U0, t0, dt0)
+
+
+def _ring_state(ring):
+    parts = [e.get_state() for e in ring.e]
+    P = np.concatenate([p[0] for p in parts], axis=3)
+    U = np.concatenate([p[1] for p in parts], axis=3)
+    return P, U, parts[0][2], parts[0][3]
+
+
+@pytest.mark.parametrize("precision,R", [(0, 1), (0, 2), (0, 4), (1, 2), (1, 8)])
+def test_slab_ring_equals_the_undecomposed_step(precision, R):
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import SlabRing
+    grid, phys, full, (P0, U0, t0, dt0) = _start(G, precision)
+    ring = SlabRing.create(grid, phys, R, A)
+    ring.set_state(P0, U0, t0, dt0)
+    nsteps = 5
+    G.step(full, nsteps)
+    ring.step(nsteps)
+    Pf, Uf, tf, dtf = G.get_state(full)
+    Pr, Ur, tr, dtr = _ring_state(ring)
+    assert tr == tf and dtr == dtf
+    assert np.array_equal(Pr, Pf)
+    assert np.array_equal(Ur, Uf)
+    ring.close()
+    full.close()
+
+
+def test_slab_ring_matches_the_oracle_per_step():
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import SlabRing
+    grid, phys, full, (P0, U0, t0, dt0) = _start(G, 0)
+    full.close()
+    ring = SlabRing.create(grid, phys, 4, A)
+    ring.set_state(P0, U0, t0, dt0)
+    og = O.Grid(O.default_params(n1=SHAPE[0], n2=SHAPE[1], n3=SHAPE[2], gam=GAM, a=A, r_out=40.0))
+    og.set_state(P0, U0, t0, dt0)
+    og.step()
+    ring.step(1)
+    Po, Uo, to, dto = og.get_state()
+    Pr, Ur, tr, dtr = _ring_state(ring)
+    assert tr == to
+    assert dtr == pytest.approx(dto, rel=1e-12)
+    assert field_err(Pr, Po).max() < 1e-10
+    assert field_err(Ur, Uo).max() < 1e-10
+    ring.close()
+
+
+def test_pack_unpack_planes():
+    """pack copies the two outermost active planes of a side; unpack writes
+    the ghost planes the step reads (checked through a one-slab ring, whose
+    ghosts are its own opposite planes, against the periodic fill)."""
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import SlabRing
+    grid, phys, full, (P0, U0, t0, dt0) = _start(G, 0)
+    full.close()
+    ring = SlabRing.create(grid, phys, 1, A)
+    ring.set_state(P0, U0, t0, dt0)
+    e = ring.e[0]
+    buf = torch.empty(e.plane_numel, dtype=torch.float64, device="cuda")
+    for side, ks in ((0, (0, 1)), (1, (SHAPE[2] - 2, SHAPE[2] - 1))):
+        e.pack(0, side, buf)
+        torch.cuda.synchronize()
+        planes = buf.cpu().numpy().reshape(2, 8, SHAPE[0] + 4, SHAPE[1] + 4)
+        for g, k in enumerate(ks):
+            # the active part of the packed plane is the state's plane k
+            assert np.array_equal(planes[g, :, 2:-2, 2:-2], P0[:, :, :, k])
+    assert G.x3_plane_bytes(e.ctx) == 2 * 8 * (SHAPE[0] + 4) * (SHAPE[1] + 4) * 8
+    with pytest.raises(G.GrmhdError):
+        G.x3_pack(e.ctx, 2, 0, buf)
+    with pytest.raises(G.GrmhdError):
+        G.x3_unpack(e.ctx, 0, -1, buf)
+    with pytest.raises(G.GrmhdError):
+        G.stage(e.ctx, 3)
+    ring.close()
+
+
+def test_external_is_for_bc3_only():
+    G = gpu_mod()
+    with pytest.raises(G.GrmhdError):
+        G.init_grid(G.default_grid(8, 8, 8, bc1=G.BC_EXTERNAL), G.default_phys())
+    with pytest.raises(G.GrmhdError):
+        G.init_grid(G.default_grid(8, 8, 1, bc3=G.BC_EXTERNAL), G.default_phys())

@@ -1,7 +1,8 @@
 """The phi-slab decomposition of the step (tests/slabs.py) reproduces the
-undecomposed oracle bit for bit: in-process with 2 and 4 slabs, and as two
-gloo ranks that exchange their ghost planes with send/recv and reduce the
-per-direction CFL minima with an all-reduce."""
+undecomposed oracle bit for bit: in-process with 2 and 4 slabs, and as 2 and
+4 gloo ranks driven by the library's rank driver (SlabRank), which exchanges
+ghost planes with send/recv and reduces the per-direction CFL minima with an
+all-reduce, the oracle doing each slab's stages."""
 import os
 import socket
 import sys
@@ -50,8 +51,8 @@ def _free_port():
 
 def _rank(rank, world, port, steps, out):
     sys.path.insert(0, ROOT)
-    import torch
     import torch.distributed as dist
+    from paper_2205_02484_gb300.decomp import SlabRank
     from tests import slabs as S2
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -59,35 +60,11 @@ def _rank(rank, world, port, steps, out):
     g = O.Grid(base)
     g.init_torus(pert_amp=0.04, seed=5)
     P0, U0, t0, dt0 = g.get_state()
-    Ps, Us = S2.split_state(P0, U0, world)[rank]
-    mine = O.Grid(S2.slab_params(base, rank, world))
-    mine.set_state(Ps, Us, t0, dt0)
-    n3 = mine.shape[2]
-    left, right = (rank - 1) % world, (rank + 1) % world
-
-    def exchange(which):
-        send_lo = torch.from_numpy(np.stack([mine.xplane(which, g_) for g_ in range(S2.NG)]))
-        send_hi = torch.from_numpy(np.stack([mine.xplane(which, n3 - S2.NG + g_) for g_ in range(S2.NG)]))
-        recv_lo, recv_hi = torch.empty_like(send_lo), torch.empty_like(send_hi)
-        ops = [dist.P2POp(dist.isend, send_hi, right), dist.P2POp(dist.isend, send_lo, left),
-               dist.P2POp(dist.irecv, recv_lo, left), dist.P2POp(dist.irecv, recv_hi, right)]
-        for req in dist.batch_isend_irecv(ops):
-            req.wait()
-        for g_ in range(S2.NG):
-            mine.set_xplane(which, -S2.NG + g_, recv_lo[g_].numpy())
-            mine.set_xplane(which, n3 + g_, recv_hi[g_].numpy())
-
-    exchange(0)
-    for _ in range(steps):
-        _, st = mine.stage0()
-        assert st == 0
-        d = torch.from_numpy(mine.last_dtd().copy())
-        exchange(1)
-        assert mine.stage1() == 0
-        exchange(0)
-        dist.all_reduce(d, op=dist.ReduceOp.MIN)
-        mine.set_dt(O.combine_dt(d.numpy()))
-    P, U, t, dt = mine.get_state()
+    # the product's rank driver, with the oracle doing the stages
+    slab = SlabRank(S2.OracleSlab(S2.slab_params(base, rank, world)))
+    slab.set_state(P0, U0, t0, dt0)
+    slab.step(steps)
+    P, U, t, dt = slab.e.get_state()
     gathered = [None] * world
     dist.all_gather_object(gathered, (P, U, t, dt))
     dist.destroy_process_group()
@@ -95,13 +72,16 @@ def _rank(rank, world, port, steps, out):
         out.put(gathered)
 
 
-def test_two_gloo_ranks_reproduce_the_undecomposed_step():
+@pytest.mark.parametrize("world", [2, 4])
+def test_gloo_ranks_reproduce_the_undecomposed_step(world):
+    """world 2: each rank is both neighbours of the other (the send/recv
+    matching case); world 4: distinct neighbours."""
     pytest.importorskip("torch")
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, 3, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, 3, q)) for r in range(world)]
     for p in procs:
         p.start()
     gathered = q.get(timeout=300)
