@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-window", action="store_true")
+    ap.add_argument("--no-slabs", action="store_true")
     return ap.parse_args()
 
 
@@ -210,6 +211,79 @@ def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload
             "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
             "loop_ms_per_step": ms_loop / steps, "speedup_vs_loop": ms_loop / ms_ens,
             "tiling": tiling, "tiling_from_cache": cached}
+
+
+# ------------------------------------------------- phi slabs on one GPU
+
+def run_slabs(G, torch, device, n, steps=10, warmup=2, counts=(2, 4, 8)):
+    """The n^3 mixed torus split into R phi slabs on one GPU (decomp.SlabRing:
+    stage-level launches, X3 ghost pack / unpack through device buffers, the
+    per-direction dt minima folded on the device), timed against the
+    undecomposed graph step from the same state, with a bitwise comparison
+    of the final states.  A slab's time per step approximates one rank's
+    compute in an R-GPU run; ghost_bytes_per_slab_step is what that rank would
+    send per step (2 stages x 2 sides x NG = 2 planes of 8 primitives)."""
+    from paper_2205_02484_gb300.decomp import SlabRing
+    phys = G.default_phys(gam=4.0 / 3.0)
+    gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
+    s = torch.cuda.Stream(device=device)
+    gp.stream = s.cuda_stream
+    full = G.init_grid(gp, phys)
+    G.set_metric(full, 0.9375, G.KERR_MKS)
+    G.init_torus(full, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
+    dev = f"cuda:{device}"
+    P0 = torch.empty((8, n, n, n), dtype=torch.float64, device=dev)
+    U0 = torch.empty((9, n, n, n), dtype=torch.float64, device=dev)
+    _, _, t0, dt0 = G.get_state(full, P0, U0)
+
+    def time_it(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    G.step(full, warmup)
+    ms_full = time_it(lambda: G.step(full, steps))
+    G.sync(full)
+    Pf = torch.empty_like(P0)
+    Uf = torch.empty_like(U0)
+    G.get_state(full, Pf, Uf)
+    full.close()
+    out = {"workload": f"{n}^3 FM torus (the headline state), mixed precision, R phi slabs on one GPU",
+           "steps": steps, "undecomposed_ms_per_step": ms_full / steps, "slabs": {}}
+    for R in counts:
+        ring = SlabRing.create(gp, phys, R, 0.9375, stream=s)
+        ring.set_state(P0, U0, t0, dt0)
+        ring.step(warmup)
+        ms = time_it(lambda: ring.step(steps))
+        for e in ring.e:
+            G.sync(e.ctx)
+        parts = [_slab_state(G, torch, e, dev) for e in ring.e]
+        Pr = torch.cat([p[0] for p in parts], dim=3)
+        Ur = torch.cat([p[1] for p in parts], dim=3)
+        del parts
+        out["slabs"][str(R)] = {
+            "ms_per_step": ms / steps, "vs_undecomposed": ms_full / ms,
+            "bitwise_equal_to_undecomposed": bool(torch.equal(Pr, Pf) and torch.equal(Ur, Uf)),
+            "ghost_bytes_per_slab_step": 4 * G.x3_plane_bytes(ring.e[0].ctx),
+            # per slab: 2 stages x 10 kernels, dt minima, finish; 2 exchanges x 4
+            "launches_per_step": R * (2 * 10 + 2 + 2 * 4),
+        }
+        del Pr, Ur
+        ring.close()
+    return out
+
+
+def _slab_state(G, torch, e, dev):
+    n1, n2, n3 = e.ctx.shape
+    P = torch.empty((8, n1, n2, n3), dtype=torch.float64, device=dev)
+    U = torch.empty((9, n1, n2, n3), dtype=torch.float64, device=dev)
+    G.get_state(e.ctx, P, U)
+    return P, U
 
 
 # ---------------------------------------------- stand-alone inversion
@@ -605,6 +679,10 @@ def main():
     window = None
     if world == 1 and not args.no_window:
         window = run_window(G, torch, stream, local)
+    # ---- the same torus as phi slabs on this GPU (the multi-GPU layout)
+    slabs = None
+    if world == 1 and not args.no_slabs:
+        slabs = run_slabs(G, torch, local, n)
     # ---- learned Newton start: training, inversions, the 256x192x192 step
     mlp = None
     if world == 1 and not args.no_mlp:
@@ -630,6 +708,7 @@ def main():
             "fp64_step": fp64,
             "ensemble": ensemble,
             "learned_start": mlp,
+            "phi_slabs": slabs,
             "mixed_vs_fp64_window": window,
             "con2prim": c2p,
             "diagnostics_ms": diag_ms,

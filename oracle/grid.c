@@ -848,7 +848,9 @@ void orc_diagnostics(orc_grid *G, orc_diag *out)
     out->PhiB = mdot != 0.0 ? phib / sqrt(fabs(mdot)) : 0.0;
     /* corner divergence of Eq. 24, acting on the conserved sqrt(-g) B^i */
     double dmax = 0.0;
-    int periodic3 = (p->metric == ORC_KERR_MKS) || p->bc3 == ORC_BC_PERIODIC;
+    /* a phi slab checks only the corners inside it: those on its low phi face
+       need the neighbouring slab's conserved B */
+    int periodic3 = p->bc3 != ORC_BC_EXTERNAL && ((p->metric == ORC_KERR_MKS) || p->bc3 == ORC_BC_PERIODIC);
     int k0 = (periodic3 || p->n3 == 1) ? 0 : 1;
     for (int i = 1; i < p->n1; i++)
         for (int j = 1; j < p->n2; j++)

@@ -64,7 +64,9 @@ __global__ void k_horizon_sum(const double *part, int nb, double *out)
 // side, times 1/(4 dX^d) (the grid's tabulated 1/dX^d).
 __global__ void k_divb(Grid g, double *out)
 {
-    bool per3 = g.metric == KERR_MKS || g.bc3 == BC_PERIODIC;
+    // a phi slab (external X3 ghosts) checks the corners inside it only: those
+    // on its low phi face need the neighbour's conserved B
+    bool per3 = g.bc3 != BC_EXTERNAL && (g.metric == KERR_MKS || g.bc3 == BC_PERIODIC);
     int k0 = (per3 || g.n3 == 1) ? 0 : 1;
     long long n = (long long)(g.n1 - 1) * (g.n2 - 1) * (g.n3 - k0);
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -86,6 +86,9 @@ class CtxSlab:
     def get_state(self):
         return G.get_state(self.ctx)
 
+    def diagnostics(self):
+        return G.diagnostics(self.ctx)
+
     def stage(self, st):
         G.stage(self.ctx, st)
 
@@ -103,6 +106,26 @@ class CtxSlab:
 
     def close(self):
         self.ctx.close()
+
+
+_SUMMED = ("mdot", "phib", "edot", "ldot", "nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta",
+           "n_fail", "n_floor", "n_ceil", "n_gcap", "n_fixed", "fix_sweeps")
+
+
+def combine_diagnostics(parts):
+    """Whole-grid horizon diagnostics (Eqs. 38-42) from the slabs' own: the
+    shell integrals and the counters add up, the normalised flux is formed
+    from the sums, div B is the largest over the slabs (each checks the
+    corners inside it).  t, dt and the step count are the slabs' common
+    values; the slab sums add in a different order from the undecomposed
+    grid's, so the integrals agree to rounding, not bit for bit."""
+    out = dict(parts[0])
+    for k in _SUMMED:
+        out[k] = type(parts[0][k])(sum(p[k] for p in parts))
+    out["divb_max"] = max(p["divb_max"] for p in parts)
+    out["PhiB"] = out["phib"] / math.sqrt(abs(out["mdot"])) if out["mdot"] != 0.0 else 0.0
+    out["disk_mass"] = out["disk_eb"] = 0.0  # set by the torus setup only
+    return out
 
 
 def _stream_of(engine):
@@ -127,9 +150,11 @@ class SlabRing:
         return cls([CtxSlab.create(sg, phys, a, stream) for _ in range(R)])
 
     def set_state(self, P, U, t, dt):
+        """P, U: the whole grid's state (host arrays or device tensors)."""
         R = len(self.e)
         for r, e in enumerate(self.e):
-            e.set_state(split_phi(P, R, r), split_phi(U, R, r), t, dt)
+            with _stream_of(e):  # a device slice is copied on the slab's stream
+                e.set_state(split_phi(P, R, r), split_phi(U, R, r), t, dt)
         self.exchange(0)
 
     def exchange(self, which):
@@ -152,6 +177,9 @@ class SlabRing:
             self.exchange(0)
             for e in self.e:
                 e.finish(self.dtd_buf)
+
+    def diagnostics(self):
+        return combine_diagnostics([e.diagnostics() for e in self.e])
 
     def close(self):
         for e in self.e:
@@ -185,7 +213,8 @@ class SlabRank:
     def set_state(self, P, U, t, dt):
         """P, U: the whole grid's state (every rank holds the same); this
         rank keeps its slab."""
-        self.e.set_state(split_phi(P, self.R, self.rank), split_phi(U, self.R, self.rank), t, dt)
+        with _stream_of(self.e):
+            self.e.set_state(split_phi(P, self.R, self.rank), split_phi(U, self.R, self.rank), t, dt)
         self.exchange(0)
 
     def exchange(self, which):
@@ -219,5 +248,12 @@ class SlabRank:
                     self.dist.all_reduce(self.dtd_buf, op=self.dist.ReduceOp.MIN, group=self.group)
             e.finish(self.dtd_buf)
 
+    def diagnostics(self):
+        """The whole grid's diagnostics on every rank (combine_diagnostics
+        over all ranks' slabs, gathered on the host)."""
+        parts = [None] * self.R
+        self.dist.all_gather_object(parts, self.e.diagnostics(), group=self.group)
+        return combine_diagnostics(parts)
 
-__all__ = ["NG", "slab_grid", "split_phi", "CtxSlab", "SlabRing", "SlabRank"]
+
+__all__ = ["NG", "slab_grid", "split_phi", "combine_diagnostics", "CtxSlab", "SlabRing", "SlabRank"]

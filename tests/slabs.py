@@ -107,6 +107,9 @@ class OracleSlab:
     def get_state(self):
         return self.g.get_state()
 
+    def diagnostics(self):
+        return self.g.diagnostics()
+
     def stage(self, st):
         if st == 0:
             assert self.g.stage0()[1] == 0

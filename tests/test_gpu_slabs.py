@@ -55,6 +55,14 @@ def test_slab_ring_equals_the_undecomposed_step(precision, R):
     assert tr == tf and dtr == dtf
     assert np.array_equal(Pr, Pf)
     assert np.array_equal(Ur, Uf)
+    # horizon integrals: the same sums in another order; div B over the
+    # corners inside the slabs, a subset of the whole grid's
+    df, dr = G.diagnostics(full), ring.diagnostics()
+    for k in ("mdot", "phib", "PhiB", "edot", "ldot"):
+        assert dr[k] == pytest.approx(df[k], rel=1e-12, abs=1e-300), k
+    for k in ("n_nr", "n_fail", "n_floor", "n_fixed"):
+        assert dr[k] == df[k], k
+    assert dr["divb_max"] <= df["divb_max"]
     ring.close()
     full.close()
 

@@ -20,6 +20,25 @@ def _base():
     return O.default_params(n1=20, n2=16, n3=8, gam=13.0 / 9.0, r_out=40.0)
 
 
+def _reference_grid(steps):
+    g = O.Grid(_base())
+    g.init_torus(pert_amp=0.04, seed=5)
+    for _ in range(steps):
+        assert g.step() == 0
+    return g
+
+
+def _check_combined(dr, df):
+    """Slab diagnostics combined vs the undecomposed grid's: the horizon
+    integrals (Eqs. 38-41) to rounding, the counters exactly, div B (Eq. 24)
+    over the corners inside the slabs, a subset of the grid's corners."""
+    for k in ("mdot", "phib", "PhiB", "edot", "ldot"):
+        assert dr[k] == pytest.approx(df[k], rel=1e-12), k
+    for k in ("n_nr", "n_brent", "n_fail", "n_floor", "n_ceil", "n_fixed"):
+        assert dr[k] == df[k], k
+    assert 0.0 < dr["divb_max"] <= df["divb_max"]
+
+
 def _reference(steps):
     g = O.Grid(_base())
     g.init_torus(pert_amp=0.04, seed=5)
@@ -39,6 +58,8 @@ def test_slabs_reproduce_the_undecomposed_step(R):
     assert t == tr and dt == dtr
     assert np.array_equal(P, Pr)
     assert np.array_equal(U, Ur)
+    from paper_2205_02484_gb300.decomp import combine_diagnostics
+    _check_combined(combine_diagnostics([g.diagnostics() for g in slabs]), _reference_grid(4).diagnostics())
 
 
 def _free_port():
@@ -65,8 +86,9 @@ def _rank(rank, world, port, steps, out):
     slab.set_state(P0, U0, t0, dt0)
     slab.step(steps)
     P, U, t, dt = slab.e.get_state()
+    diag = slab.diagnostics()
     gathered = [None] * world
-    dist.all_gather_object(gathered, (P, U, t, dt))
+    dist.all_gather_object(gathered, (P, U, t, dt, diag))
     dist.destroy_process_group()
     if rank == 0:
         out.put(gathered)
@@ -93,3 +115,6 @@ def test_gloo_ranks_reproduce_the_undecomposed_step(world):
     U = np.concatenate([g[1] for g in gathered], axis=3)
     assert gathered[0][2] == tr and gathered[0][3] == dtr
     assert np.array_equal(P, Pr) and np.array_equal(U, Ur)
+    # every rank holds the whole grid's diagnostics
+    assert all(g[4] == gathered[0][4] for g in gathered)
+    _check_combined(gathered[0][4], _reference_grid(3).diagnostics())
