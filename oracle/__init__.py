@@ -74,7 +74,7 @@ class Geom(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in
-                ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb")] + \
+                ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb", "eta")] + \
                [(n, C.c_longlong) for n in
                 ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_floor",
                  "n_ceil", "n_gcap", "n_fixed", "fix_sweeps", "n_steps")]
@@ -111,6 +111,7 @@ def lib():
                 "orc_set_dt": (None, [V, C.c_double]),
                 "orc_fluxes": (C.c_double, [V, _D]),
                 "orc_diagnostics": (None, [V, C.POINTER(Diag)]),
+                "orc_barycentric": (C.c_double, [V, C.c_double, _D]),
                 "orc_p2c_batch": (None, [V, _D, _I, _D, C.c_long]),
                 "orc_c2p_batch": (None, [V, _D, _I, _D, _D, _I, _I, C.c_long, C.c_int]),
                 "orc_geom_table": (None, [V, C.c_int, _D]),
@@ -276,6 +277,12 @@ class Grid:
         d = Diag()
         self.L.orc_diagnostics(self.h, C.byref(d))
         return d.as_dict()
+
+    def barycentric(self, r_bar_max=80.0):
+        """(<r>, mass sum, numerator) of Eq. 43 over r_H <= r <= r_bar_max."""
+        out = np.zeros(3)
+        self.L.orc_barycentric(self.h, float(r_bar_max), _p(out))
+        return tuple(out)
 
     def flags(self):
         out = np.zeros(self.shape, dtype=np.int32)

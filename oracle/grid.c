@@ -846,6 +846,8 @@ void orc_diagnostics(orc_grid *G, orc_diag *out)
     out->edot = edot;
     out->ldot = ldot;
     out->PhiB = mdot != 0.0 ? phib / sqrt(fabs(mdot)) : 0.0;
+    /* (Edot - Mdot) / |Mdot| of Eqs. 38 and 41 */
+    out->eta = mdot != 0.0 ? (edot - mdot) / fabs(mdot) : 0.0;
     /* corner divergence of Eq. 24, acting on the conserved sqrt(-g) B^i */
     double dmax = 0.0;
     /* a phi slab checks only the corners inside it: those on its low phi face
@@ -871,6 +873,38 @@ void orc_diagnostics(orc_grid *G, orc_diag *out)
     out->divb_max = dmax;
     out->disk_mass = G->disk_mass;
     out->disk_eb = G->disk_eb;
+}
+
+/* Barycentric radius of Eq. 43: <r> = int r rho sqrt(-g) dV / int rho sqrt(-g) dV
+   over r_H <= r <= r_bar_max, as midpoint sums over the active zones from the
+   horizon zone (i_h, as for Eq. 38) outwards whose centre radius is at most
+   r_bar_max.  sqrt(-g) dX1 dX2 dX3 of the code coordinates is the volume
+   element sqrt(-g) dr dtheta dphi of the paper's.  out = (<r>, denominator,
+   numerator); returns <r> (0 when the range holds no mass or the grid is not
+   Kerr). */
+double orc_barycentric(orc_grid *G, double r_bar_max, double out[3])
+{
+    const orc_params *p = &G->p;
+    double num = 0.0, den = 0.0;
+    double dV = G->dx[0] * G->dx[1] * G->dx[2];
+    if (p->metric == ORC_KERR_MKS) {
+        for (int i = G->i_h; i < p->n1; i++) {
+            if (G->rc[orc_midx(G, i, 0)] > r_bar_max) continue;
+            for (int j = 0; j < p->n2; j++) {
+                int m = orc_midx(G, i, j);
+                double r = G->rc[m], gdet = G->gc[m].gdet;
+                for (int k = 0; k < p->n3; k++) {
+                    double rho = AT(G->P, KRHO, orc_idx(G, i, j, k));
+                    num += r * rho * gdet * dV;
+                    den += rho * gdet * dV;
+                }
+            }
+        }
+    }
+    out[0] = den > 0.0 ? num / den : 0.0;
+    out[1] = den;
+    out[2] = num;
+    return out[0];
 }
 
 /* ---------------------------------------------- batched point operations */

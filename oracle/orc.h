@@ -63,7 +63,7 @@ typedef struct {
 } orc_state;
 
 typedef struct {
-    double t, dt, mdot, phib, PhiB, edot, ldot, divb_max, disk_mass, disk_eb;
+    double t, dt, mdot, phib, PhiB, edot, ldot, divb_max, disk_mass, disk_eb, eta;
     long long nr_iters, n_nr, n_brent, n_entropy, n_entropy_beta, n_fail, n_floor, n_ceil,
         n_gcap, n_fixed, fix_sweeps, n_steps;
 } orc_diag;
@@ -131,6 +131,7 @@ int orc_midx(const orc_grid *G, int i, int j);
 void orc_bc_fill(orc_grid *G, double *P);
 double orc_compute_fluxes(orc_grid *G, const double *P);
 double orc_combine_dt(const double dtd[3]);
+double orc_barycentric(orc_grid *G, double r_bar_max, double out[3]);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
 

@@ -104,3 +104,18 @@ def test_michel_horizon_mass_flux():
     e = [abs(_horizon_mdot_error(n2)) for n2 in (16, 32, 64)]
     assert e[0] / e[1] > 3.5 and e[1] / e[2] > 3.5, e
     assert e[2] < 2e-3
+
+
+def test_michel_horizon_efficiency():
+    """(Edot - Mdot)/|Mdot| of Eqs. 38 and 41: for the radial flow without
+    field every zone of the shell has T^r_t = rho h u^r u_t with the same
+    h u_t, so Edot = -h u_t Mdot and the ratio is 1 + h u_t = 1 - sqrt(B),
+    B = h^2 (1 - 2/r + u^2) the Bernoulli constant (u_t is the same in
+    Schwarzschild and Kerr-Schild time) -- at any resolution."""
+    mic = Michel(r_c=8.0, n=N_POLY)
+    og = _grid(16, 12)
+    _start(og, mic)
+    d = og.diagnostics()
+    assert d["mdot"] < 0.0 and d["edot"] < 0.0
+    assert d["eta"] == pytest.approx(1.0 - math.sqrt(mic.bern), abs=1e-12)
+    assert d["eta"] == pytest.approx((d["edot"] - d["mdot"]) / abs(d["mdot"]), rel=1e-15)
