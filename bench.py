@@ -588,6 +588,12 @@ def main():
     value = aggregate_value(zones, args.steps, world, ms)
     ms_step = ms / args.steps
     diag = G.diagnostics(ctx)
+    # barycentric radius of Eq. 43 (r_bar_max = 80 M), timed on its own
+    G.barycentric_radius(ctx, 80.0)
+    b0 = time.perf_counter()
+    for _ in range(5):
+        bary = G.barycentric_radius(ctx, 80.0)
+    bary_ms = (time.perf_counter() - b0) * 1e3 / 5
     # horizon diagnostics, timed on their own (no allocation, device only)
     dout = torch.zeros(8, dtype=torch.float64, device=f"cuda:{local}")
     G.diagnostics_noalloc(ctx, dout)
@@ -716,8 +722,10 @@ def main():
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
-            "diagnostics_after_bench": {k: diag[k] for k in ("t", "dt", "mdot", "divb_max", "n_fail", "n_fixed",
-                                                             "nr_iters", "n_nr", "n_entropy_beta", "n_floor")},
+            "diagnostics_after_bench": dict(
+                {k: diag[k] for k in ("t", "dt", "mdot", "eta", "divb_max", "n_fail", "n_fixed", "nr_iters", "n_nr",
+                                      "n_entropy_beta", "n_floor")},
+                barycentric_radius_r80=bary[0], barycentric_ms_host_sync=bary_ms),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

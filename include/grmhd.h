@@ -123,6 +123,7 @@ typedef struct {
  * integrals of Section 5.  Counters accumulate over all steps since init. */
 typedef struct {
     double t, dt, mdot, phib, PhiB, edot, ldot, divb_max, disk_mass, disk_eb;
+    double eta; /* (edot - mdot) / |mdot| (Eqs. 38, 41); 0 when mdot = 0 */
     long long nr_iters, n_nr, n_brent, n_entropy, n_entropy_beta, n_fail, n_floor, n_ceil,
         n_gcap, n_fixed, fix_sweeps, n_steps;
 } grmhd_diag;
@@ -428,6 +429,17 @@ int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev);
 /* Write a neighbour's packed planes into the ghosts on `side` (0: k = -2, -1;
  * 1: k = n3, n3+1) of buffer `which`. */
 int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev);
+
+/* Barycentric radius of the disk (Sec. 4.2, Eq. 43):
+ *   <r> = sum r rho sqrt(-g) dV / sum rho sqrt(-g) dV
+ * over the active zones from the horizon zone (the first with centre radius
+ * >= r_H, as for Eq. 38) outwards whose centre radius is <= r_bar_max;
+ * sqrt(-g) dX1 dX2 dX3 of the code coordinates is the volume element of the
+ * paper's integral.  out (host, 3 doubles) = (<r>, denominator, numerator);
+ * <r> = 0 when the range holds no mass.  Deterministic (fixed reduction
+ * order); synchronises the context stream.  Kerr grids only (GRMHD_EINVAL
+ * otherwise). */
+int grmhd_barycentric_radius(grmhd_ctx *ctx, double r_bar_max, double *out);
 
 /* Library version string. */
 const char *grmhd_version(void);

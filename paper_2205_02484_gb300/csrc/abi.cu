@@ -37,6 +37,7 @@ struct grmhd_ctx {
     unsigned char *intorus = nullptr;
     double *hpin = nullptr; // pinned host scratch (64 doubles)
     double disk_mass = 0.0, disk_eb = 0.0;
+    CoordParams cp{}; // coordinate map of the metric (Kerr grids)
     float *mlp = nullptr;       // packed forward buffer of the learned Newton start
     float *mlp_theta = nullptr; // its FP32 parameters
     bool mlp_loaded = false;
@@ -257,6 +258,7 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
             mks_radius<double>(cp, g.x1in + (i + 0.5) * g.dx[0], r, dr);
             if (r >= rh) { g.i_h = i; break; }
         }
+        ctx->cp = cp;
     } else {
         cp.xb = 1e300;
         g.x1in = p.x1min; g.x2in = p.x2min; g.x3in = p.x3min;
@@ -445,6 +447,7 @@ extern "C" int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out)
     out->ldot = ctx->hpin[3];
     out->divb_max = ctx->hpin[4];
     out->PhiB = out->mdot != 0.0 ? out->phib / std::sqrt(std::fabs(out->mdot)) : 0.0;
+    out->eta = out->mdot != 0.0 ? (out->edot - out->mdot) / std::fabs(out->mdot) : 0.0;
     out->dt = ctx->hpin[8];
     out->t = ctx->hpin[9];
     out->disk_mass = ctx->disk_mass;
@@ -1118,4 +1121,25 @@ extern "C" int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev)
 extern "C" int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev)
 {
     return x3_planes(ctx, which, side, const_cast<void *>(buf_dev), 1);
+}
+
+// ------------------------------------------------------ disk diagnostics
+
+extern "C" int grmhd_barycentric_radius(grmhd_ctx *ctx, double r_bar_max, double *out)
+{
+    if (!ctx || !out) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    if (ctx->g.metric != KERR_MKS) return fail(ctx, GRMHD_EINVAL, "the barycentric radius needs a Kerr grid");
+    const Grid &g = ctx->g;
+    double *part = ctx->scratch, *dout = ctx->scratch + 2LL * g.n1;
+    (void)cudaGetLastError();
+    launch_barycentric(g, ctx->cp, r_bar_max, part, dout, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->hpin, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double num = ctx->hpin[0], den = ctx->hpin[1];
+    out[0] = den > 0.0 ? num / den : 0.0;
+    out[1] = den;
+    out[2] = num;
+    return 0;
 }

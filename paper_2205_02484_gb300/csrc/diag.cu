@@ -116,6 +116,72 @@ void launch_diagnostics(const Grid &g, double *scratch, long scratch_len, double
     k_horizon_sum<<<1, 32, 0, s>>>(scratch, nb, out_dev);
 }
 
+// ----------------------------------------------- barycentric radius (Eq. 43)
+
+// One block per radial row: the row's centre radius decides whether it is in
+// [r_H, r_bar_max]; threads stride over its (j, k) zones (k fastest, so the
+// density loads coalesce) and a fixed tree adds the block's terms.
+template <typename RS>
+__global__ void __launch_bounds__(256) k_bary_partial(Grid g, CoordParams cp, const RS *P, double rbar, double *part)
+{
+    const int i = blockIdx.x;
+    double r, drdx;
+    mks_radius<double>(cp, g.x1in + (i + 0.5) * g.dx[0], r, drdx);
+    double num = 0.0, den = 0.0;
+    if (i >= g.i_h && r <= rbar) {
+        const int n = g.n2 * g.n3;
+        const double dV = g.dx[0] * g.dx[1] * g.dx[2];
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            int j = t / g.n3, k = t - j * g.n3;
+            double gdet = g.gc[midx(g, i, j)].gdet;
+            double rho = (double)P[KRHO * g.nz + zidx(g, i, j, k)];
+            num += r * rho * gdet * dV;
+            den += rho * gdet * dV;
+        }
+    }
+    __shared__ double sm[2][256];
+    sm[0][threadIdx.x] = num;
+    sm[1][threadIdx.x] = den;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + o];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * i] = sm[0][0];
+        part[2 * i + 1] = sm[1][0];
+    }
+}
+
+// one warp adds the rows in a fixed order
+__global__ void k_bary_sum(const double *part, int n1, double *out)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n1; i += 32) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+void launch_barycentric(const Grid &g, const CoordParams &cp, double r_bar_max, double *part, double *out,
+                        cudaStream_t s)
+{
+    if (g.mixed) k_bary_partial<float><<<g.n1, 256, 0, s>>>(g, cp, (const float *)g.P[0], r_bar_max, part);
+    else k_bary_partial<double><<<g.n1, 256, 0, s>>>(g, cp, (const double *)g.P[0], r_bar_max, part);
+    k_bary_sum<<<1, 32, 0, s>>>(part, g.n1, out);
+}
+
 // ------------------------------------------------------------ point batches
 
 __global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, long n)

@@ -89,6 +89,10 @@ class CtxSlab:
     def diagnostics(self):
         return G.diagnostics(self.ctx)
 
+    def barycentric_sums(self, r_bar_max):
+        _, den, num = G.barycentric_radius(self.ctx, r_bar_max)
+        return num, den
+
     def stage(self, st):
         G.stage(self.ctx, st)
 
@@ -124,8 +128,15 @@ def combine_diagnostics(parts):
         out[k] = type(parts[0][k])(sum(p[k] for p in parts))
     out["divb_max"] = max(p["divb_max"] for p in parts)
     out["PhiB"] = out["phib"] / math.sqrt(abs(out["mdot"])) if out["mdot"] != 0.0 else 0.0
+    out["eta"] = (out["edot"] - out["mdot"]) / abs(out["mdot"]) if out["mdot"] != 0.0 else 0.0
     out["disk_mass"] = out["disk_eb"] = 0.0  # set by the torus setup only
     return out
+
+
+def _bary(parts):
+    num = sum(p[0] for p in parts)
+    den = sum(p[1] for p in parts)
+    return (num / den if den > 0.0 else 0.0), den, num
 
 
 def _stream_of(engine):
@@ -180,6 +191,11 @@ class SlabRing:
 
     def diagnostics(self):
         return combine_diagnostics([e.diagnostics() for e in self.e])
+
+    def barycentric_radius(self, r_bar_max=80.0):
+        """(<r>, mass, numerator) of Eq. 43 over the whole grid: the slabs'
+        sums added in slab order."""
+        return _bary([e.barycentric_sums(r_bar_max) for e in self.e])
 
     def close(self):
         for e in self.e:
@@ -254,6 +270,11 @@ class SlabRank:
         parts = [None] * self.R
         self.dist.all_gather_object(parts, self.e.diagnostics(), group=self.group)
         return combine_diagnostics(parts)
+
+    def barycentric_radius(self, r_bar_max=80.0):
+        parts = [None] * self.R
+        self.dist.all_gather_object(parts, self.e.barycentric_sums(r_bar_max), group=self.group)
+        return _bary(parts)
 
 
 __all__ = ["NG", "slab_grid", "split_phi", "combine_diagnostics", "CtxSlab", "SlabRing", "SlabRank"]

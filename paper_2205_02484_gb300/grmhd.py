@@ -60,7 +60,7 @@ class TorusParams(C.Structure):
 
 class Diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in
-                ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb")] + \
+                ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb", "eta")] + \
                [(n, C.c_longlong) for n in
                 ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_floor",
                  "n_ceil", "n_gcap", "n_fixed", "fix_sweeps", "n_steps")]
@@ -135,6 +135,7 @@ SIGNATURES = {
                                         C.POINTER(C.c_double), C.c_int]),
     "grmhd_mlp_train": (C.c_int, [_V, C.POINTER(MlpTrainParams), C.POINTER(MlpTrainReport)]),
     "grmhd_set_learned_guess": (C.c_int, [_V, C.c_int]),
+    "grmhd_barycentric_radius": (C.c_int, [_V, C.c_double, C.POINTER(C.c_double)]),
     "grmhd_stage": (C.c_int, [_V, C.c_int]),
     "grmhd_step_dtd": (C.c_int, [_V, _V, C.c_int]),
     "grmhd_finish_step": (C.c_int, [_V, _V]),
@@ -333,6 +334,13 @@ def diagnostics(ctx: Context) -> dict:
     d = Diag()
     ctx.check(ctx.L.grmhd_diagnostics(ctx.h, C.byref(d)))
     return d.as_dict()
+
+
+def barycentric_radius(ctx: Context, r_bar_max: float = 80.0):
+    """(<r>, mass sum, numerator) of Eq. 43 over r_H <= r <= r_bar_max."""
+    out = (C.c_double * 3)()
+    ctx.check(ctx.L.grmhd_barycentric_radius(ctx.h, float(r_bar_max), out))
+    return tuple(out)
 
 
 def prim2cons(ctx: Context, P, loc, U=None):

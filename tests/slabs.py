@@ -110,6 +110,10 @@ class OracleSlab:
     def diagnostics(self):
         return self.g.diagnostics()
 
+    def barycentric_sums(self, r_bar_max):
+        _, den, num = self.g.barycentric(r_bar_max)
+        return num, den
+
     def stage(self, st):
         if st == 0:
             assert self.g.stage0()[1] == 0

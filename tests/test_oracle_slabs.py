@@ -32,7 +32,7 @@ def _check_combined(dr, df):
     """Slab diagnostics combined vs the undecomposed grid's: the horizon
     integrals (Eqs. 38-41) to rounding, the counters exactly, div B (Eq. 24)
     over the corners inside the slabs, a subset of the grid's corners."""
-    for k in ("mdot", "phib", "PhiB", "edot", "ldot"):
+    for k in ("mdot", "phib", "PhiB", "edot", "ldot", "eta"):
         assert dr[k] == pytest.approx(df[k], rel=1e-12), k
     for k in ("n_nr", "n_brent", "n_fail", "n_floor", "n_ceil", "n_fixed"):
         assert dr[k] == df[k], k
@@ -87,6 +87,7 @@ def _rank(rank, world, port, steps, out):
     slab.step(steps)
     P, U, t, dt = slab.e.get_state()
     diag = slab.diagnostics()
+    diag["bary"] = slab.barycentric_radius(30.0)
     gathered = [None] * world
     dist.all_gather_object(gathered, (P, U, t, dt, diag))
     dist.destroy_process_group()
@@ -117,4 +118,7 @@ def test_gloo_ranks_reproduce_the_undecomposed_step(world):
     assert np.array_equal(P, Pr) and np.array_equal(U, Ur)
     # every rank holds the whole grid's diagnostics
     assert all(g[4] == gathered[0][4] for g in gathered)
-    _check_combined(gathered[0][4], _reference_grid(3).diagnostics())
+    ref = _reference_grid(3)
+    _check_combined(gathered[0][4], ref.diagnostics())
+    for x, y in zip(gathered[0][4]["bary"], ref.barycentric(30.0)):
+        assert x == pytest.approx(y, rel=1e-13)
