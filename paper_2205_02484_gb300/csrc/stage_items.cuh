@@ -389,6 +389,68 @@ __device__ __forceinline__ R flux_column(const Grid &g, const R *__restrict__ P,
     return cwm;
 }
 
+// X3 faces of one (i, j) row by one warp (the PLM stencil shared through
+// warp-level primitives, Sec. 3).  The warp walks the row in segments of 29
+// faces: lane l holds zone k0 - 2 + l of the segment, forms that zone's MC
+// slope from its neighbours' values by shuffles, and lanes 2..30 evaluate
+// the faces k0 .. k0 + 28 between them, so each zone is loaded and its slope
+// formed once per segment instead of once per face; the next segment's
+// zones are loaded before the current faces are evaluated, so their latency
+// hides behind the face physics.  The face values are the numbers flux_item
+// forms.  x3_warp_box counts lanes: rows (i, j) x 32.
+constexpr int X3W_FACES = 29;
+
+__host__ __device__ inline Box x3_warp_box(const Grid &g) { return Box{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, 32}}; }
+
+template <typename R>
+__device__ __forceinline__ R flux_x3_warp(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                          const Box &wb, int want_dt, long long t)
+{
+    // the box count is a multiple of 32, so whole warps are in or out
+    R cwm = R(0);
+    if (t >= wb.count()) return cwm;
+    int i, j, lane;
+    box_decode(wb, t, i, j, lane);
+    const long long zrow = zidx(g, i, j, 0);
+    const Geo<R> &geo = face_table<R>(g, 3)[midx(g, i, j)];
+    const int nseg = (g.n3 + 1 + X3W_FACES - 1) / X3W_FACES;
+    // this lane's zone of a segment, clamped past the last ghost on lanes no face uses
+    auto zone_of = [&](int seg) { return min(seg * X3W_FACES - 2 + lane, g.n3 + 1); };
+    R qn[NP];
+    {
+        const long long z = zrow + zone_of(0);
+#pragma unroll
+        for (int c = 0; c < NP; c++) qn[c] = ldg(P + c * g.nz + z);
+    }
+    for (int seg = 0; seg < nseg; seg++) {
+        const int k = zone_of(seg); // face k lies between the zones of lanes l-1 and l
+        R ql[NP], qr[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const R q = qn[c];
+            const R qm = __shfl_up_sync(0xffffffffu, q, 1), qp = __shfl_down_sync(0xffffffffu, q, 1);
+            const R sl = mc_slope(qm, q, qp); // valid on lanes 1..30
+            const R up = q + R(0.5) * sl;     // the zone's value at its upper X3 face
+            ql[c] = __shfl_up_sync(0xffffffffu, up, 1);
+            qr[c] = q - R(0.5) * sl;
+        }
+        if (seg + 1 < nseg) {
+            const long long z = zrow + zone_of(seg + 1);
+#pragma unroll
+            for (int c = 0; c < NP; c++) qn[c] = ldg(P + c * g.nz + z);
+        }
+        if (lane >= 2 && lane <= 30 && k <= g.n3) {
+            R out[NU];
+            R cw = R(0);
+            face_flux<R, 3>(g, geo, ql, qr, out, cw);
+#pragma unroll
+            for (int c = 0; c < NU; c++) F[c * g.nz + zrow + k] = out[c];
+            if (want_dt) cwm = max(cwm, face_cw<R, 3>(g, i, j, k, cw));
+        }
+    }
+    return cwm;
+}
+
 // -------------------------------------------------------------------- EMFs
 
 // E3 at (i-1/2, j-1/2, k), E1 at (i, j-1/2, k-1/2), E2 at (i-1/2, j, k-1/2) (Eq. 22)
