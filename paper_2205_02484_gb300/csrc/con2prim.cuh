@@ -16,8 +16,9 @@
 // Newton step is written with three reciprocals (1/W, 1/sqrt(1-v^2), 1/det)
 // instead of a division per term.  In the FP64 path Newton takes one more
 // step after the tolerance is met (so that the oracle and this code stop on
-// the same rounding-level root); the mixed path stops at the tolerance,
-// where quadratic convergence already puts the iterate at ~tol^2.
+// the same rounding-level root); the mixed path (c2p_newton_mixed) keeps the
+// residuals in FP64 but forms the Newton step in FP32 and stops at
+// sqrt(tol).
 #pragma once
 #include "physics.cuh"
 
@@ -221,6 +222,77 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
     return false;
 }
 
+// Newton for the mixed path: the residuals of Eqs. 29-30 in FP64 (they fix
+// the root), the Jacobian, its inverse and the step in FP32 -- iterative
+// refinement: the fixed point is still the FP64 root, and an FP32 Jacobian
+// (relative error ~1e-7, ~1e-4 at the Lorentz cap) turns the quadratic
+// convergence into a linear one of that rate, from starts already within
+// ~1e-5.  Accepts once the step is below tol (sqrt(nr_tol)), tested in FP32.
+// An iteration whose FP32 determinant is not a normal number takes the FP64
+// step instead.
+__device__ inline bool c2p_newton_mixed(const C2PIn &c, double &W, double &v2, double tol, int maxit,
+                                        int &iters)
+{
+    const double g1 = c.g1;
+    const double QB2 = c.QB * c.QB;
+    const float g1f = (float)g1, Bsqf = (float)c.Bsq, Df = (float)c.D, tolf = (float)tol;
+    int n = 0;
+    for (int it = 1; it <= maxit; it++) {
+        n = it;
+        double omv = 1.0 - v2;
+        double is = rsqrt(omv); // 1 / sqrt(1 - v^2)
+        double s = omv * is;
+        double iW = 1.0 / W;
+        double qw2 = QB2 * iW * iW; // (Q.B)^2 / W^2
+        double p = g1 * (W * omv - c.D * s);
+        double BW = c.Bsq + W;
+        double f1 = v2 * BW * BW - qw2 * (c.Bsq + 2.0 * W) - c.Qtsq;
+        double f2 = -0.5 * c.Bsq * (1.0 + v2) + 0.5 * qw2 - W + p - c.nQ;
+        const float Wf = (float)W, v2f = (float)v2, omvf = (float)omv, qw2f = (float)qw2;
+        const float isf = rsqrtf(omvf), iWf = 1.0f / Wf, BWf = Bsqf + Wf;
+        const float a11 = 2.0f * v2f * BWf + 2.0f * qw2f * iWf * BWf;
+        const float a12 = BWf * BWf;
+        const float a21 = -qw2f * iWf - 1.0f + g1f * omvf;
+        const float a22 = -0.5f * Bsqf + g1f * (-Wf + 0.5f * Df * isf);
+        const float det = a11 * a22 - a12 * a21;
+        double dW, dv;
+        bool small;
+        if (fabsf(det) >= 1.17549435e-38f && fabsf(det) < INFINITY) {
+            const float idet = 1.0f / det, f1f = (float)f1, f2f = (float)f2;
+            const float dWf = -(a22 * f1f - a12 * f2f) * idet;
+            const float dvf = -(-a21 * f1f + a11 * f2f) * idet;
+            dW = (double)dWf;
+            dv = (double)dvf;
+            small = fabsf(dWf) < tolf * fabsf(Wf + dWf) && fabsf(dvf) < tolf;
+        } else {
+            double b11 = 2.0 * v2 * BW + 2.0 * qw2 * iW * BW;
+            double b12 = BW * BW;
+            double b21 = -qw2 * iW - 1.0 + g1 * omv;
+            double b22 = -0.5 * c.Bsq + g1 * (-W + 0.5 * c.D * is);
+            double d64 = b11 * b22 - b12 * b21;
+            if (!finite64(d64) || (__double_as_longlong(d64) << 1) == 0) break; // non-finite or +-0
+            double idet = 1.0 / d64;
+            dW = -(b22 * f1 - b12 * f2) * idet;
+            dv = -(-b21 * f1 + b11 * f2) * idet;
+            small = fabs(dW) < tol * fabs(W + dW) && fabs(dv) < tol;
+        }
+        double Wn = W + dW;
+        if (!(Wn > 0.0)) {
+            Wn = 0.5 * W;
+            small = false;
+        }
+        W = Wn;
+        v2 = fmin(fmax(v2 + dv, 0.0), V2MAX);
+        if (!finite64(W) || !finite64(v2)) break;
+        if (small) {
+            iters = n;
+            return true;
+        }
+    }
+    iters = n;
+    return false;
+}
+
 __device__ inline bool c2p_brent_w(const C2PIn &c, int maxit, double *P)
 {
     double E = -c.nQ;
@@ -348,7 +420,8 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             if (!(W > 0.0) || !finite64(W)) W = c.D;
             v2 = fmin(v2, V2MAX);
             int it;
-            const bool conv = c2p_newton<!MIXED>(c, W, v2, MIXED ? par.tol_mixed : par.tol, par.nr_maxit, it);
+            const bool conv = MIXED ? c2p_newton_mixed(c, W, v2, par.tol_mixed, par.nr_maxit, it)
+                                    : c2p_newton<true>(c, W, v2, par.tol, par.nr_maxit, it);
             iters += it;
             if (conv) {
                 c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
