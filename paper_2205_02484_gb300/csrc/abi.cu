@@ -143,6 +143,8 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.igm1 = 1.0 / (g.gam - 1.0);
     g.isig = 1.0 / g.sigma_max;
     g.ibu = 1.0 / g.bu_max;
+    g.isig_f = (float)g.isig;
+    g.ibu_f = (float)g.ibu;
     g.nr_tol_mixed = std::sqrt(g.nr_tol);
     {
         // column length of the X1 / X2 flux sweeps: at least ~2^17 threads per sweep

@@ -76,6 +76,7 @@ struct Grid {
     double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max
+    float isig_f, ibu_f;        // 1/sigma_max, 1/bu_max for the mixed path's FP32 ceiling test
     double nr_tol_mixed;        // sqrt(nr_tol): Newton acceptance of the mixed path
     int nr_maxit, brent_maxit, fix_maxsweep;
     int fcol;                   // faces per thread of the X1 / X2 flux sweeps (columns)

@@ -373,8 +373,9 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
     c.Qt[1] = gsp[1] * Q1 + gsp[3] * Q2 + gsp[4] * Q3;
     c.Qt[2] = gsp[2] * Q1 + gsp[4] * Q2 + gsp[5] * Q3;
     c.Qtsq = c.Qt[0] * Q1 + c.Qt[1] * Q2 + c.Qt[2] * Q3;
+    // Bf^i = alpha B^i = (alpha / sqrt(-g)) U_B^i (the mixed path uses the tabulated ratio)
 #pragma unroll
-    for (int i = 0; i < 3; i++) c.Bf[i] = g.alpha * P[KB1 + i];
+    for (int i = 0; i < 3; i++) c.Bf[i] = MIXED ? f * U[KB1 + i] : g.alpha * P[KB1 + i];
     c.QB = Q1 * c.Bf[0] + Q2 * c.Bf[1] + Q3 * c.Bf[2];
     c.Bsq = spatial_sq(g, c.Bf[0], c.Bf[1], c.Bf[2]);
     bool fin = finite64(c.D) && finite64(c.Qtsq) && finite64(c.nQ) && finite64(c.Bsq);

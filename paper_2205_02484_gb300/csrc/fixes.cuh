@@ -37,11 +37,15 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
                                      const double Un[NU], const Geo<float> *gf = nullptr, float *qf = nullptr)
 {
     int res = 0;
-    if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
-    if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }
     double bsq;
-    float usqf = 0.0f;
+    float usqf = 0.0f, rf = 0.0f, uf = 0.0f;
+    bool ceil;
     if (MIXED) {
+        // floors and ceilings decided in FP32, on the values that are stored
+        rf = (float)q[KRHO];
+        uf = (float)q[KUU];
+        if (rf < gf->rfl) { q[KRHO] = geo.rfl; rf = gf->rfl; res |= 1; }
+        if (uf < gf->ufl) { q[KUU] = geo.ufl; uf = gf->ufl; res |= 1; }
         qf[KRHO] = 0.0f;
         qf[KUU] = 0.0f;
 #pragma unroll
@@ -50,14 +54,21 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
         get_state(qf, *gf, s);
         bsq = (double)s.bsq;
         usqf = s.usq;
+        ceil = s.bsq * g.isig_f > rf || s.bsq * g.ibu_f > uf;
     } else {
+        if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
+        if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }
         St<double> s;
         get_state(q, geo, s);
         bsq = s.bsq;
+        ceil = true;
     }
-    double drho = fmax(0.0, bsq * g.isig - q[KRHO]);
-    double du = fmax(0.0, bsq * g.ibu - q[KUU]);
     bool moved = false;
+    double drho = 0.0, du = 0.0;
+    if (ceil) {
+        drho = fmax(0.0, bsq * g.isig - q[KRHO]);
+        du = fmax(0.0, bsq * g.ibu - q[KUU]);
+    }
     if (drho > 0.0 || du > 0.0) {
         res |= 3;
         moved = true;
@@ -95,9 +106,11 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
         if (moved) {
 #pragma unroll
             for (int m = KU1; m < NP; m++) qf[m] = (float)q[m];
+            rf = (float)q[KRHO];
+            uf = (float)q[KUU];
         }
-        qf[KRHO] = (float)q[KRHO];
-        qf[KUU] = (float)q[KUU];
+        qf[KRHO] = rf;
+        qf[KUU] = uf;
     }
     return res;
 }

@@ -515,9 +515,11 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         for (int c = 0; c < NP; c++) q[c] = (double)Pin[c * nz + z];
     }
     const Geo<double> geo = g.gc[m];
-    // source (Eq. 15)
+    // source (Eq. 15): FP64, or FP32 in the mixed path away from the horizon
     double src[4];
-    if (!MX || i < g.i_h + NHZ) {
+    float sf[4];
+    const bool src32 = MX && i >= g.i_h + NHZ;
+    if (!src32) {
         if constexpr (MX) {
 #pragma unroll
             for (int c = 0; c < NP; c++) q[c] = (double)qin[c];
@@ -527,12 +529,9 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         source_terms(q, geo, g.conn + (long long)m * 40, s, g.gam, src);
     } else {
         const Geo<float> gf = g.gcF[m];
-        float sf[4];
         St<float> s;
         get_state(qin, gf, s);
         source_terms(qin, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
-#pragma unroll
-        for (int c = 0; c < 4; c++) src[c] = sf[c];
     }
     // flux divergence; B components from the flux-CT edge averages (Eq. 23),
     // formed exactly as the replaced face values.  The mixed path takes the
@@ -572,9 +571,15 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         double dD = (double)dv[KRHO];
 #pragma unroll
         for (int c = 0; c < NU; c++) {
-            double rhs = -(double)dv[c];
-            if (c == 1 && sizeof(R) == 4) rhs += dD; // rest-mass-subtracted energy flux
-            if (c >= 1 && c <= 4) rhs += src[c - 1];
+            double rhs;
+            if (c >= 1 && c <= 4 && src32) {
+                // an FP32 source meets the FP32 divergence before the one conversion
+                rhs = (double)(sf[c - 1] - (float)dv[c]);
+            } else {
+                rhs = -(double)dv[c];
+                if (c >= 1 && c <= 4) rhs += src[c - 1];
+            }
+            if (c == 1 && MX) rhs += dD; // rest-mass-subtracted energy flux
             Un[c] = g.U[c * nz + z] + dts * rhs;
         }
     }
