@@ -72,6 +72,23 @@ __device__ __forceinline__ void c2p_recover(const C2PIn &c, double W, double v2,
     for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + qbw * c.Bf[i]);
 }
 
+// c2p_recover with the pressure of Eq. 31, sharing 1 - v^2 and its inverse
+// square root: sqrt(1 - v^2) = (1 - v^2) / sqrt(1 - v^2)
+__device__ __forceinline__ void c2p_recover_w(const C2PIn &c, double W, double v2, double *P)
+{
+    double omv = 1.0 - v2;
+    double lor = rsqrt(omv);
+    double s = omv * lor;
+    P[KRHO] = c.D * s;
+    P[KUU] = (c.g1 * (W * omv - c.D * s)) * c.igm1;
+    double WB = W + c.Bsq;
+    double r = 1.0 / (W * WB);
+    double f = lor * (W * r);
+    double qbw = c.QB * (WB * r);
+#pragma unroll
+    for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + qbw * c.Bf[i]);
+}
+
 __device__ __forceinline__ bool c2p_physical(const double *P, double v2)
 {
     bool fin = finite64(P[0]) && finite64(P[1]) && finite64(P[2]) && finite64(P[3]) && finite64(P[4]);
@@ -242,8 +259,11 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, double &W, double &v2, d
         double omv = 1.0 - v2;
         double is = rsqrt(omv); // 1 / sqrt(1 - v^2)
         double s = omv * is;
-        double iW = 1.0 / W;
-        double qw2 = QB2 * iW * iW; // (Q.B)^2 / W^2
+        double iW = 0.0, qw2 = 0.0; // (Q.B)^2 / W^2, no reciprocal where Q.B = 0 (no field)
+        if (QB2 != 0.0) {
+            iW = 1.0 / W;
+            qw2 = QB2 * iW * iW;
+        }
         double p = g1 * (W * omv - c.D * s);
         double BW = c.Bsq + W;
         double f1 = v2 * BW * BW - qw2 * (c.Bsq + 2.0 * W) - c.Qtsq;
@@ -303,7 +323,7 @@ __device__ inline bool c2p_brent_w(const C2PIn &c, int maxit, double *P)
     double W = brent_root(f, lo, hi, f(lo), f(hi), 0.0, maxit, ok);
     if (!ok) return false;
     double v2 = f.v2(W);
-    c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
+    c2p_recover_w(c, W, v2, P);
     return c2p_physical(P, v2);
 }
 
@@ -425,7 +445,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
                                     : c2p_newton<true>(c, W, v2, par.tol, par.nr_maxit, it);
             iters += it;
             if (conv) {
-                c2p_recover(c, W, v2, c2p_pressure(c, W, v2), P);
+                c2p_recover_w(c, W, v2, P);
                 if (c2p_physical(P, v2)) return C2P_NR;
                 if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
                 return fail(C2P_FAIL | C2P_FAIL_ENT);
