@@ -375,9 +375,8 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         return code;
     };
     const double f = g.aig;
-    P[KB1] = U[KB1] * g.igdet;
-    P[KB2] = U[KB2] * g.igdet;
-    P[KB3] = U[KB3] * g.igdet;
+#pragma unroll
+    for (int i = 0; i < 3; i++) P[KB1 + i] = U[KB1 + i] * g.igdet;
     C2PIn c;
     c.gam = par.gam;
     c.g1 = par.g1;
@@ -393,11 +392,20 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
     c.Qt[1] = gsp[1] * Q1 + gsp[3] * Q2 + gsp[4] * Q3;
     c.Qt[2] = gsp[2] * Q1 + gsp[4] * Q2 + gsp[5] * Q3;
     c.Qtsq = c.Qt[0] * Q1 + c.Qt[1] * Q2 + c.Qt[2] * Q3;
-    // Bf^i = alpha B^i = (alpha / sqrt(-g)) U_B^i (the mixed path uses the tabulated ratio)
+    // Bf^i = alpha B^i = (alpha / sqrt(-g)) U_B^i (the mixed path uses the tabulated ratio).
+    // A zone without field (all U_B bits zero but the sign) skips the field terms.
+    const bool field = ((__double_as_longlong(U[KB1]) | __double_as_longlong(U[KB2]) |
+                         __double_as_longlong(U[KB3])) << 1) != 0;
+    if (field) {
 #pragma unroll
-    for (int i = 0; i < 3; i++) c.Bf[i] = MIXED ? f * U[KB1 + i] : g.alpha * P[KB1 + i];
-    c.QB = Q1 * c.Bf[0] + Q2 * c.Bf[1] + Q3 * c.Bf[2];
-    c.Bsq = spatial_sq(g, c.Bf[0], c.Bf[1], c.Bf[2]);
+        for (int i = 0; i < 3; i++) c.Bf[i] = MIXED ? f * U[KB1 + i] : g.alpha * P[KB1 + i];
+        c.QB = Q1 * c.Bf[0] + Q2 * c.Bf[1] + Q3 * c.Bf[2];
+        c.Bsq = spatial_sq(g, c.Bf[0], c.Bf[1], c.Bf[2]);
+    } else {
+        c.Bf[0] = c.Bf[1] = c.Bf[2] = 0.0;
+        c.QB = 0.0;
+        c.Bsq = 0.0;
+    }
     bool fin = finite64(c.D) && finite64(c.Qtsq) && finite64(c.nQ) && finite64(c.Bsq);
     if (!fin || !(c.D > 0.0)) return fail(C2P_FAIL | C2P_FAIL_D);
 
