@@ -364,6 +364,17 @@ __device__ __forceinline__ R flux_column(const Grid &g, const R *__restrict__ P,
             ql[c] = qa[c] + R(0.5) * sa[c];
             qr[c] = qb[c] - R(0.5) * sb[c];
         }
+        // L1 prefetch of the next face's metric record and of the zone it adds
+        // to the window, so that their latency overlaps this face's physics
+        if (f + 1 < f1) {
+            const int ni = D == 1 ? f + 1 : i, nj = D == 2 ? f + 1 : j;
+            const char *gp = (const char *)&face_table<R>(g, D)[midx(g, ni, nj)];
+#pragma unroll
+            for (int o = 0; o < (int)sizeof(Geo<R>); o += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(gp + o));
+#pragma unroll
+            for (int c = 0; c < NP; c++)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P + c * g.nz + z0 + (long long)(f + 2 - f0) * st));
+        }
         R out[NU];
         R cw = R(0);
         if (D == 2 && g.polar2[midx(g, fi, fj)]) {
