@@ -145,7 +145,12 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.ibu = 1.0 / g.bu_max;
     g.isig_f = (float)g.isig;
     g.ibu_f = (float)g.ibu;
+    g.gam_f = (float)g.gam;
+    g.g1_f = (float)g.g1;
+    g.beta_ent_f = (float)g.beta_ent;
+    g.gamma_max_f = (float)g.gamma_max;
     g.nr_tol_mixed = std::sqrt(g.nr_tol);
+    g.tol_mixed_f = (float)g.nr_tol_mixed;
     {
         // column length of the X1 / X2 flux sweeps: at least ~2^17 threads per sweep
         long long faces = (long long)(g.n1 + 1) * (g.n2 + 2) * (g.n3 + 2);
@@ -270,7 +275,10 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         g.i_h = 0;
         if (!(g.dx[0] > 0) || !(g.dx[1] > 0) || !(g.dx[2] > 0)) return fail(ctx, GRMHD_EINVAL, "empty box");
     }
-    for (int d = 0; d < 3; d++) g.idx[d] = 1.0 / g.dx[d];
+    for (int d = 0; d < 3; d++) {
+        g.idx[d] = 1.0 / g.dx[d];
+        g.idx_f[d] = (float)g.idx[d];
+    }
     ctx->gb.cp = cp;
     ctx->a = a;
     (void)cudaGetLastError(); // a stale error of an unrelated earlier call is not ours

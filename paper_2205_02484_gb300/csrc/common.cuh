@@ -77,6 +77,9 @@ struct Grid {
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max
     float isig_f, ibu_f;        // 1/sigma_max, 1/bu_max for the mixed path's FP32 ceiling test
+    // FP32 copies of per-grid constants: the FP32 arithmetic of the mixed path
+    // reads them instead of converting the FP64 values in every zone
+    float gam_f, g1_f, beta_ent_f, gamma_max_f, tol_mixed_f, idx_f[3];
     double nr_tol_mixed;        // sqrt(nr_tol): Newton acceptance of the mixed path
     int nr_maxit, brent_maxit, fix_maxsweep;
     int fcol;                   // faces per thread of the X1 / X2 flux sweeps (columns)

@@ -38,11 +38,13 @@ struct C2PIn {
 struct C2PPar {
     double gam, g1, igm1, beta_ent, tol, tol_mixed;
     int nr_maxit, brent_maxit;
+    float gam_f, g1_f, beta_ent_f, tol_mixed_f; // FP32 copies for the mixed path
 };
 
 __device__ __forceinline__ C2PPar c2p_par(const Grid &g)
 {
-    return C2PPar{g.gam, g.g1, g.igm1, g.beta_ent, g.nr_tol, g.nr_tol_mixed, g.nr_maxit, g.brent_maxit};
+    return C2PPar{g.gam,        g.g1,          g.igm1, g.beta_ent, g.nr_tol, g.nr_tol_mixed, g.nr_maxit,
+                  g.brent_maxit, g.gam_f,       g.g1_f, g.beta_ent_f, g.tol_mixed_f};
 }
 
 // finite test on the high word: integer pipe instead of an FP64 compare
@@ -247,12 +249,12 @@ __device__ inline bool c2p_newton(const C2PIn &c, double &W, double &v2, double 
 // ~1e-5.  Accepts once the step is below tol (sqrt(nr_tol)), tested in FP32.
 // An iteration whose FP32 determinant is not a normal number takes the FP64
 // step instead.
-__device__ inline bool c2p_newton_mixed(const C2PIn &c, double &W, double &v2, double tol, int maxit,
-                                        int &iters)
+__device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, double &W, double &v2, int &iters)
 {
-    const double g1 = c.g1;
+    const double g1 = c.g1, tol = par.tol_mixed;
+    const int maxit = par.nr_maxit;
     const double QB2 = c.QB * c.QB;
-    const float g1f = (float)g1, Bsqf = (float)c.Bsq, Df = (float)c.D, tolf = (float)tol;
+    const float g1f = par.g1_f, Bsqf = (float)c.Bsq, Df = (float)c.D, tolf = par.tol_mixed_f;
     int n = 0;
     for (int it = 1; it <= maxit; it++) {
         n = it;
@@ -414,8 +416,8 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         if (MIXED) {
             St<float> s;
             get_state(guessf, *gf, s);
-            float pg = ((float)par.gam - 1.0f) * guessf[KUU];
-            low_beta = s.bsq > 0.0f && pg < (float)par.beta_ent * 0.5f * s.bsq;
+            float pg = (par.gam_f - 1.0f) * guessf[KUU];
+            low_beta = s.bsq > 0.0f && pg < par.beta_ent_f * 0.5f * s.bsq;
         } else {
             St<double> s;
             get_state(guess, g, s);
@@ -432,7 +434,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         if (MIXED) {
             float usq = spatial_sq(*gf, guessf[KU1], guessf[KU2], guessf[KU3]);
             v2p = (double)(usq / (1.0f + usq));
-            Wp = (double)((1.0f + usq) * (guessf[KRHO] + (float)par.gam * guessf[KUU]));
+            Wp = (double)((1.0f + usq) * (guessf[KRHO] + par.gam_f * guessf[KUU]));
         } else {
             double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
             v2p = usq / (1.0 + usq);
@@ -449,7 +451,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             if (!(W > 0.0) || !finite64(W)) W = c.D;
             v2 = fmin(v2, V2MAX);
             int it;
-            const bool conv = MIXED ? c2p_newton_mixed(c, W, v2, par.tol_mixed, par.nr_maxit, it)
+            const bool conv = MIXED ? c2p_newton_mixed(c, par, W, v2, it)
                                     : c2p_newton<true>(c, W, v2, par.tol, par.nr_maxit, it);
             iters += it;
             if (conv) {

@@ -95,7 +95,7 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
     }
     bool test_cap = true;
     if (MIXED && !moved) {
-        float gm = (float)g.gamma_max;
+        float gm = g.gamma_max_f;
         test_cap = 1.0f + usqf > gm * gm * 0.9999f;
     }
     if (test_cap && gamma_cap(g, geo, q)) {
@@ -139,7 +139,7 @@ __device__ inline void post_fixup(const Grid &g, const Geo<double> &geo, double 
 // qf (mixed path, may be null): the FP32 primitives of q, if the caller has them.
 template <bool MIXED = false>
 __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, double gam, double U[NU],
-                               const Geo<float> *gf = nullptr, const float *qfin = nullptr)
+                               const Geo<float> *gf = nullptr, const float *qfin = nullptr, float gam_f = 0.0f)
 {
     if (MIXED) {
         float qf[NP];
@@ -148,7 +148,7 @@ __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, doubl
         St<float> s;
         get_state(qf, *gf, s);
         float Uf[NU], Ff[NU];
-        prim_to_UF2<float, true>(qf, *gf, s, (float)gam, 1, Uf, Ff);
+        prim_to_UF2<float, true>(qf, *gf, s, gam_f, 1, Uf, Ff);
         double gm1 = (double)(s.usq / (s.gamma + 1.0f));
         U[KRHO] = geo.gdet * q[KRHO] * ((1.0 + gm1) * geo.ialpha);
         U[1] = (double)Uf[1] - U[KRHO];

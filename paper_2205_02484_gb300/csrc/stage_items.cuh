@@ -237,7 +237,7 @@ __device__ __forceinline__ void face_flux(const Grid &g, const Geo<R> &geo, cons
     St<R> sl, sr;
     get_state(ql, geo, sl);
     get_state(qr, geo, sr);
-    R gam = (R)g.gam;
+    R gam = sizeof(R) == 4 ? (R)g.gam_f : (R)g.gam;
     R c1l, c2l, c1r, c2r;
     wave_speeds(ql, geo, sl, gam, D, c1l, c2l);
     wave_speeds(qr, geo, sr, gam, D, c1r, c2r);
@@ -542,7 +542,7 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         const Geo<float> gf = g.gcF[m];
         St<float> s;
         get_state(qin, gf, s);
-        source_terms(qin, gf, g.connF + (long long)m * 40, s, (float)g.gam, sf);
+        source_terms(qin, gf, g.connF + (long long)m * 40, s, g.gam_f, sf);
     }
     // flux divergence; B components from the flux-CT edge averages (Eq. 23),
     // formed exactly as the replaced face values.  The mixed path takes the
@@ -553,7 +553,16 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     double Un[NU];
     {
         typedef R T;
-        const T ix1 = (T)g.idx[0], ix2 = (T)g.idx[1], ix3 = (T)g.idx[2];
+        T ix1, ix2, ix3;
+        if constexpr (MX) {
+            ix1 = g.idx_f[0];
+            ix2 = g.idx_f[1];
+            ix3 = g.idx_f[2];
+        } else {
+            ix1 = g.idx[0];
+            ix2 = g.idx[1];
+            ix3 = g.idx[2];
+        }
         T dv[NU];
 #pragma unroll
         for (int c = 0; c < NU; c++) {
@@ -619,7 +628,7 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         int res = post_inversion<MX>(g, geo, gsp, qn, Un, gfr, qnf);
         if (res & 1) {
             cn.fl += 1;
-            cons_of<MX>(qn, geo, g.gam, Un, gfr, MX ? qnf : nullptr);
+            cons_of<MX>(qn, geo, g.gam, Un, gfr, MX ? qnf : nullptr, g.gam_f);
         }
         cn.ce += (res & 2) != 0;
         cn.gc += (res & 4) != 0;

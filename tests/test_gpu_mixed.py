@@ -87,3 +87,20 @@ def test_mixed_short_window_horizon_fluxes():
     print("mdot rel err", np.abs(mg / mo - 1).max(), "phib", np.abs(pg - po).max() / np.abs(po).max())
     assert np.abs(mg / mo - 1).max() < 1e-2
     assert np.abs(pg - po).max() <= 1e-2 * np.abs(po).max() + 1e-30
+
+
+def test_mixed_newton_stays_cheap():
+    """The mixed inversion's cost guard: from the previous stage's primitives
+    Newton accepts within about one step per zone (its sqrt(tol) acceptance,
+    R30) and never needs the Brent or entropy fallbacks on a smooth torus;
+    an acceptance test that never passes would still give right answers
+    after 30 steps and Brent, but at several times the cost."""
+    G, og, ctx = _torus_pair(48, 48, 8, 1000.0)
+    d0 = G.diagnostics(ctx)
+    G.step(ctx, 5)
+    d1 = G.diagnostics(ctx)
+    n_nr = d1["n_nr"] - d0["n_nr"]
+    assert n_nr > 0
+    assert (d1["nr_iters"] - d0["nr_iters"]) / n_nr < 2.0
+    assert d1["n_brent"] == d0["n_brent"] and d1["n_entropy"] == d0["n_entropy"]
+    assert d1["n_fail"] == d0["n_fail"]
