@@ -95,8 +95,10 @@ __device__ __forceinline__ bool c2p_physical(const double *P, double v2)
 {
     bool fin = finite64(P[0]) && finite64(P[1]) && finite64(P[2]) && finite64(P[3]) && finite64(P[4]);
     // finite doubles: x > 0 exactly when the signed 64-bit pattern is > 0
-    return fin && __double_as_longlong(P[KRHO]) > 0 && __double_as_longlong(P[KUU]) > 0 && v2 >= 0.0 &&
-           v2 < 1.0;
+    // 0 <= v2 < 1 on the bit pattern: +-0, or a positive value below 1.0's bits
+    const long long vb = __double_as_longlong(v2);
+    const bool v2ok = (vb << 1) == 0 || (unsigned long long)vb < 0x3FF0000000000000ULL;
+    return fin && __double_as_longlong(P[KRHO]) > 0 && __double_as_longlong(P[KUU]) > 0 && v2ok;
 }
 
 // Brent's bracketing root finder (Brent 1973): bisection safeguarded
@@ -254,7 +256,9 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, doubl
     const double g1 = c.g1, tol = par.tol_mixed;
     const int maxit = par.nr_maxit;
     const double QB2 = c.QB * c.QB;
+    const bool has_qb = (__double_as_longlong(QB2) << 1) != 0; // Q.B != 0 (integer test)
     const float g1f = par.g1_f, Bsqf = (float)c.Bsq, Df = (float)c.D, tolf = par.tol_mixed_f;
+    const long long v2max_bits = __double_as_longlong(V2MAX);
     int n = 0;
     for (int it = 1; it <= maxit; it++) {
         n = it;
@@ -262,15 +266,17 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, doubl
         double is = rsqrt(omv); // 1 / sqrt(1 - v^2)
         double s = omv * is;
         double iW = 0.0, qw2 = 0.0; // (Q.B)^2 / W^2, no reciprocal where Q.B = 0 (no field)
-        if (QB2 != 0.0) {
+        float qw2f = 0.0f;
+        if (has_qb) {
             iW = 1.0 / W;
             qw2 = QB2 * iW * iW;
+            qw2f = (float)qw2;
         }
         double p = g1 * (W * omv - c.D * s);
         double BW = c.Bsq + W;
         double f1 = v2 * BW * BW - qw2 * (c.Bsq + 2.0 * W) - c.Qtsq;
         double f2 = -0.5 * c.Bsq * (1.0 + v2) + 0.5 * qw2 - W + p - c.nQ;
-        const float Wf = (float)W, v2f = (float)v2, omvf = (float)omv, qw2f = (float)qw2;
+        const float Wf = (float)W, v2f = (float)v2, omvf = (float)omv;
         const float isf = rsqrtf(omvf), iWf = 1.0f / Wf, BWf = Bsqf + Wf;
         const float a11 = 2.0f * v2f * BWf + 2.0f * qw2f * iWf * BWf;
         const float a12 = BWf * BWf;
@@ -298,14 +304,17 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, doubl
             dv = -(-b21 * f1 + b11 * f2) * idet;
             small = fabs(dW) < tol * fabs(W + dW) && fabs(dv) < tol;
         }
+        // the updates' sign and range tests on the bit patterns (integer pipe)
         double Wn = W + dW;
-        if (!(Wn > 0.0)) {
+        if (__double_as_longlong(Wn) <= 0) { // W + dW <= 0 (or a negative NaN): halve W instead
             Wn = 0.5 * W;
             small = false;
         }
         W = Wn;
-        v2 = fmin(fmax(v2 + dv, 0.0), V2MAX);
-        if (!finite64(W) || !finite64(v2)) break;
+        double vn = v2 + dv;
+        const long long vb = __double_as_longlong(vn);
+        v2 = vb < 0 ? 0.0 : (vb > v2max_bits ? V2MAX : vn); // clamp to [0, V2MAX]
+        if (!finite64(W)) break;
         if (small) {
             iters = n;
             return true;
