@@ -97,6 +97,17 @@ extern "C" void grmhd_destroy(grmhd_ctx *ctx)
     delete ctx;
 }
 
+// A new state is copied into the second primitive buffer too: the mixed
+// update reads that buffer's previous contents for its Newton start, which
+// after a new state must be the state itself (no history).
+static int copy_stage_buffer(grmhd_ctx *ctx)
+{
+    const Grid &g = ctx->g;
+    size_t bytes = (size_t)NP * g.nz * (g.mixed ? sizeof(float) : sizeof(double));
+    CK(cudaMemcpyAsync(g.P[1], g.P[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return 0;
+}
+
 extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_params *phys, grmhd_ctx **out)
 {
     grmhd_ctx *ctx = nullptr;
@@ -335,6 +346,7 @@ extern "C" int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *tp)
     ctx->disk_mass = ctx->hpin[4];
     ctx->disk_eb = ctx->hpin[5];
     launch_bc(g, 0, ctx->stream);
+    if (copy_stage_buffer(ctx)) return GRMHD_ECUDA;
     if (set_scalars(ctx, 0.0, 0.0)) return GRMHD_ECUDA;
     launch_fluxes_dt(g, 1, ctx->stream);
     CK(cudaGetLastError());
@@ -371,6 +383,7 @@ extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U,
     launch_copy_state_in(ctx->g, Pd, Ud, ctx->stream);
     launch_bc(ctx->g, 0, ctx->stream);
     CK(cudaGetLastError());
+    if (copy_stage_buffer(ctx)) return GRMHD_ECUDA;
     if (set_scalars(ctx, t, dt)) return GRMHD_ECUDA;
     ctx->state_set = true;
     return 0;

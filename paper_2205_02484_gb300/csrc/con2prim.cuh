@@ -368,10 +368,15 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 // unused); the starting (W, v^2) and the beta switch are formed in FP32 with
 // the FP32 metric record gf, and Newton stops once its step is below
 // sqrt(tol) -- quadratic convergence then leaves an error of order tol.
+// startf (MIXED, used where have_start): FP32 primitives to start Newton from
+// before the guess primitives (the update passes the stage input
+// extrapolated by the change over the previous half step); the beta switch
+// keeps guessf.
 template <bool MIXED = false>
 __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double gsp[6],
                                const double *guess, const float *guessf, const C2PPar &par, int methods,
-                               double P[NP], int &iters, double wguess = 0.0, const Geo<float> *gf = nullptr)
+                               double P[NP], int &iters, double wguess = 0.0, const Geo<float> *gf = nullptr,
+                               const float *startf = nullptr, bool have_start = false)
 {
     iters = 0;
     if (!MIXED) {
@@ -439,24 +444,30 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         }
     }
     if (methods & 1) {
-        double v2p, Wp;
-        if (MIXED) {
-            float usq = spatial_sq(*gf, guessf[KU1], guessf[KU2], guessf[KU3]);
-            v2p = (double)(usq / (1.0f + usq));
-            Wp = (double)((1.0f + usq) * (guessf[KRHO] + par.gam_f * guessf[KUU]));
-        } else {
-            double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
-            v2p = usq / (1.0 + usq);
-            Wp = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
-        }
-        // a learned W is tried first; Newton from the guess primitives stays the
-        // fallback when it does not converge
-        const int tries = wguess > 0.0 ? 2 : 1;
+        // a learned W, then the extrapolated start, are tried first; Newton from
+        // the guess primitives stays the fallback when they do not converge
 #pragma unroll 1
-        for (int a = 0; a < tries; a++) {
-            const bool learned = a == 0 && wguess > 0.0;
-            double W = learned ? wguess : Wp;
-            double v2 = learned ? ResidW{&c}.v2(wguess) : v2p;
+        for (int a = 0; a < 3; a++) {
+            const bool learned = a == 0, extrap = a == 1;
+            if (learned && !(wguess > 0.0)) continue;
+            if (extrap && !(MIXED && have_start)) continue;
+            double W, v2;
+            if (learned) {
+                W = wguess;
+                v2 = ResidW{&c}.v2(wguess);
+            } else if (MIXED) {
+                // (W, v^2) formed in FP32 from the chosen FP32 primitives
+                const float r0 = extrap ? startf[KRHO] : guessf[KRHO], e0 = extrap ? startf[KUU] : guessf[KUU];
+                const float u1 = extrap ? startf[KU1] : guessf[KU1], u2 = extrap ? startf[KU2] : guessf[KU2],
+                            u3 = extrap ? startf[KU3] : guessf[KU3];
+                const float usq = spatial_sq(*gf, u1, u2, u3);
+                v2 = (double)(usq / (1.0f + usq));
+                W = (double)((1.0f + usq) * (r0 + par.gam_f * e0));
+            } else {
+                const double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
+                v2 = usq / (1.0 + usq);
+                W = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
+            }
             if (!(W > 0.0) || !finite64(W)) W = c.D;
             v2 = fmin(v2, V2MAX);
             int it;

@@ -365,9 +365,11 @@ extern "C" int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_en
         Snap &sn = snaps[m];
         sn.pbytes = 8 * (size_t)g.nz * rs;
         sn.ubytes = 9 * (size_t)g.nz * sizeof(double);
-        ECK(cudaMalloc(&sn.P, sn.pbytes));
+        ECK(cudaMalloc(&sn.P, 2 * sn.pbytes));
         ECK(cudaMalloc(&sn.U, sn.ubytes));
         ECK(cudaMemcpyAsync(sn.P, g.P[0], sn.pbytes, cudaMemcpyDeviceToDevice, s));
+        // the second buffer too: the mixed update's Newton start reads it
+        ECK(cudaMemcpyAsync((char *)sn.P + sn.pbytes, g.P[1], sn.pbytes, cudaMemcpyDeviceToDevice, s));
         ECK(cudaMemcpyAsync(sn.U, g.U, sn.ubytes, cudaMemcpyDeviceToDevice, s));
         ECK(cudaMemcpyAsync(sn.scal, g.scal, sizeof(sn.scal), cudaMemcpyDeviceToHost, s));
         ECK(cudaMemcpyAsync(sn.cnt, g.cnt, sizeof(sn.cnt), cudaMemcpyDeviceToHost, s));
@@ -426,6 +428,7 @@ done:
         const Grid &g = ens->hgrids[m];
         Snap &sn = snaps[m];
         cudaMemcpyAsync(g.P[0], sn.P, sn.pbytes, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(g.P[1], (char *)sn.P + sn.pbytes, sn.pbytes, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(g.U, sn.U, sn.ubytes, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(g.scal, sn.scal, sizeof(sn.scal), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(g.cnt, sn.cnt, sizeof(sn.cnt), cudaMemcpyHostToDevice, s);

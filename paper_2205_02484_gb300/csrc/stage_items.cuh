@@ -610,7 +610,20 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     const double *gsp = g.gsp + 6LL * m;
     double wg = 0.0;
     if constexpr (LEARN) wg = mlp_w_start(g.mlp, Un, geo);
-    int fl = con2prim<MX>(Un, geo, gsp, q, qin, c2p_par(g), 15, qn, it, wg, gfr);
+    // mixed path: Newton starts from the stage input extrapolated by its change
+    // over the previous half step, 2 P_in - P_out(old) (P_out still holds the
+    // previous stage's result for this zone: P-hat before the corrector, the
+    // previous step's P-hat before the predictor), an O(dt^2) start in place of
+    // O(dt); used where rho and u move by less than 10%
+    float qx[5];
+    bool have_x = false;
+    if constexpr (MX) {
+#pragma unroll
+        for (int c = 0; c < 5; c++) qx[c] = 2.0f * qin[c] - (float)Pout[c * nz + z];
+        have_x = qx[KRHO] > 0.9f * qin[KRHO] && qx[KRHO] < 1.1f * qin[KRHO] && qx[KUU] > 0.9f * qin[KUU] &&
+                 qx[KUU] < 1.1f * qin[KUU];
+    }
+    int fl = con2prim<MX>(Un, geo, gsp, q, qin, c2p_par(g), 15, qn, it, wg, gfr, qx, have_x);
     bool ok = !(fl & C2P_FAIL);
     cn.it += it;
     int meth = fl & 7;

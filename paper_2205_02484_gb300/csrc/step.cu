@@ -54,7 +54,7 @@ __global__ void k_emf(Grid g, const R *__restrict__ F1, const R *__restrict__ F2
 }
 
 template <typename R, bool LEARN>
-__global__ void __launch_bounds__(128) k_update(Grid g, const R *__restrict__ Pin, R *__restrict__ Pout,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_update(Grid g, const R *__restrict__ Pin, R *__restrict__ Pout,
                                                 const R *__restrict__ F1, const R *__restrict__ F2,
                                                 const R *__restrict__ F3, const R *__restrict__ E1,
                                                 const R *__restrict__ E2, const R *__restrict__ E3,
