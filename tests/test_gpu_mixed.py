@@ -104,3 +104,22 @@ def test_mixed_newton_stays_cheap():
     assert (d1["nr_iters"] - d0["nr_iters"]) / n_nr < 2.0
     assert d1["n_brent"] == d0["n_brent"] and d1["n_entropy"] == d0["n_entropy"]
     assert d1["n_fail"] == d0["n_fail"]
+
+
+def test_mixed_step_after_set_state_has_no_history():
+    """The mixed update starts Newton from the stage input extrapolated with
+    the other primitive buffer's previous contents; a new state must erase
+    that history: a context that has run steps and is then given a state
+    advances it bit for bit like a fresh context given the same state."""
+    G, og, used = _torus_pair(32, 32, 4, 1000.0)
+    P0, U0, t0, dt0 = G.get_state(used)
+    G.step(used, 3)
+    G.set_state(used, P0, U0, t0, dt0)
+    G.step(used, 2)
+    _, _, fresh = _torus_pair(32, 32, 4, 1000.0)
+    G.set_state(fresh, P0, U0, t0, dt0)
+    G.step(fresh, 2)
+    Pa, Ua, ta, dta = G.get_state(used)
+    Pb, Ub, tb, dtb = G.get_state(fresh)
+    assert ta == tb and dta == dtb
+    assert np.array_equal(Pa, Pb) and np.array_equal(Ua, Ub)
