@@ -34,9 +34,10 @@ __global__ void k_bc3(Grid g, RS *P)
     bc3_item(g, P, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
-// X1 / X2 column sweeps of the mixed path: held to 4 resident blocks per SM
+// mixed path: X1 / X2 column sweeps held to 4 resident blocks per SM, the X3
+// row-warp sweep to 5
 template <typename R, int D>
-__global__ void __launch_bounds__(128, (sizeof(R) == 4 && D < 3) ? 4 : 1) k_flux(Grid g, const R *__restrict__ P, R *__restrict__ F,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (D < 3 ? 4 : 5) : 1) k_flux(Grid g, const R *__restrict__ P, R *__restrict__ F,
                                               Box box, int want_dt)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
