@@ -112,6 +112,7 @@ def lib():
                 "orc_fluxes": (C.c_double, [V, _D]),
                 "orc_diagnostics": (None, [V, C.POINTER(Diag)]),
                 "orc_barycentric": (C.c_double, [V, C.c_double, _D]),
+                "orc_face_flux_at": (C.c_double, [V, C.c_int, C.c_int, C.c_int, _D, _D]),
                 "orc_p2c_batch": (None, [V, _D, _I, _D, C.c_long]),
                 "orc_c2p_batch": (None, [V, _D, _I, _D, _D, _I, _I, C.c_long, C.c_int]),
                 "orc_geom_table": (None, [V, C.c_int, _D]),
@@ -283,6 +284,15 @@ class Grid:
         out = np.zeros(3)
         self.L.orc_barycentric(self.h, float(r_bar_max), _p(out))
         return tuple(out)
+
+    def face_flux_at(self, d, i, j, q4):
+        """(F[9], c_w) of the Riemann flux of a face of direction d (0..2) at
+        metric record (i, j) from the four zone states q4 (4, 8) along d
+        (zones idx-2 .. idx+1)."""
+        q = np.ascontiguousarray(q4, dtype=np.float64).reshape(4 * NP)
+        out = np.zeros(NU)
+        cw = self.L.orc_face_flux_at(self.h, int(d), int(i), int(j), _p(q), _p(out))
+        return out, cw
 
     def flags(self):
         out = np.zeros(self.shape, dtype=np.int32)

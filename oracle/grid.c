@@ -278,10 +278,11 @@ static const orc_geom *face_geom(const orc_grid *G, int d, int i, int j)
     return d == 0 ? &G->gf1[m] : (d == 1 ? &G->gf2[m] : &G->gc[m]);
 }
 
-/* One face: index (i,j,k) along direction d denotes the face between zones
- * (.., idx-1, ..) and (.., idx, ..).  Computes the Riemann flux into F and c_w. */
-static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, double *Fout,
-                      double *cwout)
+/* The Riemann flux (Eqs. 16-21) of one face of direction d at metric record
+ * (i, j) from the four zone states along d around it (zones idx-2 .. idx+1):
+ * PLM-MC face states, then LLF or HLL.  Polar X2 faces carry no flux. */
+static void face_flux_states(orc_grid *G, int d, int i, int j, const double *qm2, const double *qm1,
+                             const double *q0, const double *qp1, double *Fout, double *cwout)
 {
     const orc_params *p = &G->p;
     if (d == 1 && G->polar2[orc_midx(G, i, j)]) {
@@ -289,12 +290,6 @@ static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, 
         *cwout = 0.0;
         return;
     }
-    int di = d == 0, dj = d == 1, dk = d == 2;
-    double qm2[ORC_NP], qm1[ORC_NP], q0[ORC_NP], qp1[ORC_NP];
-    gather(G, P, orc_idx(G, i - 2 * di, j - 2 * dj, k - 2 * dk), qm2);
-    gather(G, P, orc_idx(G, i - di, j - dj, k - dk), qm1);
-    gather(G, P, orc_idx(G, i, j, k), q0);
-    gather(G, P, orc_idx(G, i + di, j + dj, k + dk), qp1);
     double ql[ORC_NP], qr[ORC_NP];
     for (int c = 0; c < ORC_NP; c++) {
         ql[c] = qm1[c] + 0.5 * orc_mc_slope(qm2[c], qm1[c], q0[c]);
@@ -324,6 +319,31 @@ static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, 
         for (int c = 0; c < ORC_NU; c++) Fout[c] = 0.5 * (Fl[c] + Fr[c] - cw * (Ur[c] - Ul[c]));
     }
     *cwout = cw;
+}
+
+/* One face of the grid: index (i,j,k) along direction d denotes the face
+ * between zones (.., idx-1, ..) and (.., idx, ..). */
+static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, double *Fout,
+                      double *cwout)
+{
+    int di = d == 0, dj = d == 1, dk = d == 2;
+    double qm2[ORC_NP], qm1[ORC_NP], q0[ORC_NP], qp1[ORC_NP];
+    gather(G, P, orc_idx(G, i - 2 * di, j - 2 * dj, k - 2 * dk), qm2);
+    gather(G, P, orc_idx(G, i - di, j - dj, k - dk), qm1);
+    gather(G, P, orc_idx(G, i, j, k), q0);
+    gather(G, P, orc_idx(G, i + di, j + dj, k + dk), qp1);
+    face_flux_states(G, d, i, j, qm2, qm1, q0, qp1, Fout, cwout);
+}
+
+/* The same Riemann flux for caller-given zone states q[4][8] (zones idx-2 ..
+ * idx+1 along d) at the face metric record (i, j), i in [0, n1], j in [0, n2]
+ * for its direction; returns c_w.  Lets a test check single faces of a grid
+ * too large for the oracle to sweep. */
+double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout)
+{
+    double cw = 0.0;
+    face_flux_states(G, d, i, j, q, q + ORC_NP, q + 2 * ORC_NP, q + 3 * ORC_NP, Fout, &cw);
+    return cw;
 }
 
 /* Fills F[d] over the boxes flux-CT needs and returns the CFL time step of

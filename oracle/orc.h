@@ -132,6 +132,7 @@ void orc_bc_fill(orc_grid *G, double *P);
 double orc_compute_fluxes(orc_grid *G, const double *P);
 double orc_combine_dt(const double dtd[3]);
 double orc_barycentric(orc_grid *G, double r_bar_max, double out[3]);
+double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
 
