@@ -177,8 +177,10 @@ int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, double *U, 
 
 /* Riemann fluxes after flux-CT for the current primitives, active faces only:
  * out[d][c][n1+1][n2+1][n3+1] (d = direction, c = 9 components, face index
- * along d; unused slots zero).  *dt_out (may be NULL) receives the CFL step of
- * Eq. 27.  For tests. */
+ * along d; unused slots zero).  In GRMHD_MIXED the energy component (c = 1)
+ * is carried rest-mass subtracted, the energy flux plus the mass flux, as the
+ * mixed update uses it.  *dt_out (may be NULL) receives the CFL step of
+ * Eq. 27.  Runs the step's own flux and EMF kernels.  For tests. */
 int grmhd_fluxes(grmhd_ctx *ctx, double *out, double *dt_out, int on_device);
 
 /* Synchronise the context stream and return the device-side status
