@@ -289,6 +289,8 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
     for (int d = 0; d < 3; d++) {
         g.idx[d] = 1.0 / g.dx[d];
         g.idx_f[d] = (float)g.idx[d];
+        g.hidx_hi[d] = (float)(0.5 * g.idx[d]);
+        g.hidx_lo[d] = (float)(0.5 * g.idx[d] - (double)g.hidx_hi[d]);
     }
     ctx->gb.cp = cp;
     ctx->a = a;

@@ -80,6 +80,7 @@ struct Grid {
     // FP32 copies of per-grid constants: the FP32 arithmetic of the mixed path
     // reads them instead of converting the FP64 values in every zone
     float gam_f, g1_f, beta_ent_f, gamma_max_f, tol_mixed_f, idx_f[3];
+    float hidx_hi[3], hidx_lo[3]; // 1/(2 dX^d) as an FP32 pair (hi + lo, ~2^-48 relative)
     double nr_tol_mixed;        // sqrt(nr_tol): Newton acceptance of the mixed path
     int nr_maxit, brent_maxit, fix_maxsweep;
     int fcol;                   // faces per thread of the X1 / X2 flux sweeps (columns)

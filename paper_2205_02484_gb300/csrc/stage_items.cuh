@@ -484,6 +484,46 @@ __device__ __forceinline__ void emf_item(const Grid &g, const R *__restrict__ F1
         E2[z] = R(0.25) * (F3[KB1 * nz + z] + F3[KB1 * nz + z - si] - F1[KB3 * nz + z] - F1[KB3 * nz + z - sk]);
 }
 
+// ------------------------------------------------- FP32 pair arithmetic
+// Values carried as an unevaluated sum hi + lo of two floats (Knuth's
+// TwoSum; the product error by one FMA), for the mixed path's flux-CT
+// increments: the corner divergence of Eq. 24 cancels only if the pair sums of
+// the edge EMFs, paired along one direction for one B component and along the
+// other for the next, are exact -- an FP32 rounding of each pair sum leaves
+// div B at ~eps_32 of the step's change.
+struct FPair {
+    float hi, lo;
+};
+
+// hi + lo == a + b exactly
+__device__ __forceinline__ FPair two_sum(float a, float b)
+{
+    float s = a + b;
+    float bb = s - a;
+    return FPair{s, (a - (s - bb)) + (b - bb)};
+}
+
+// (a.hi + a.lo) - (b.hi + b.lo), to ~2^-46 relative
+__device__ __forceinline__ FPair ff_sub(FPair a, FPair b)
+{
+    FPair d = two_sum(a.hi, -b.hi);
+    return two_sum(d.hi, d.lo + (a.lo - b.lo));
+}
+
+// (a.hi + a.lo) * (h + l) for a pair constant h + l
+__device__ __forceinline__ FPair ff_mul(FPair a, float h, float l)
+{
+    float p = a.hi * h;
+    float e = fmaf(a.hi, h, -p) + (a.hi * l + a.lo * h);
+    return two_sum(p, e);
+}
+
+__device__ __forceinline__ FPair ff_add(FPair a, FPair b)
+{
+    FPair s = two_sum(a.hi, b.hi);
+    return two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
 // --------------------------------------------------------- update + invert
 
 constexpr int NHZ = 4; // zones next to the horizon that keep the FP64 source in the mixed path
@@ -585,14 +625,38 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         T f1b3_ip = T(-0.5) * (E2[z + si + sk] + E2[z + si]);
         T f2b3_j = T(0.5) * (E1[z + sk] + E1[z]);
         T f2b3_jp = T(0.5) * (E1[z + sj + sk] + E1[z + sj]);
-        dv[KB1] = (f2b1_jp - f2b1_j) * ix2 + (f3b1_kp - f3b1_k) * ix3;
-        dv[KB2] = (f1b2_ip - f1b2_i) * ix1 + (f3b2_kp - f3b2_k) * ix3;
-        dv[KB3] = (f1b3_ip - f1b3_i) * ix1 + (f2b3_jp - f2b3_j) * ix2;
+        double dB[3]; // the U_B increments' divergence terms (Eq. 23 fluxes, Eq. 26)
+        if constexpr (MX) {
+            // exact EMF pair sums (FP32 pairs), 1/(2 dX) as a pair: the
+            // increments keep the corner divergence at FP64-like round-off
+            const FPair e3a = two_sum(E3[z + si + sj], E3[z + sj]), e3b = two_sum(E3[z + si], E3[z]);
+            const FPair e3c = two_sum(E3[z + si + sj], E3[z + si]), e3d = two_sum(E3[z + sj], E3[z]);
+            const FPair e2a = two_sum(E2[z + si + sk], E2[z + sk]), e2b = two_sum(E2[z + si], E2[z]);
+            const FPair e2c = two_sum(E2[z + si + sk], E2[z + si]), e2d = two_sum(E2[z + sk], E2[z]);
+            const FPair e1a = two_sum(E1[z + sj + sk], E1[z + sk]), e1b = two_sum(E1[z + sj], E1[z]);
+            const FPair e1c = two_sum(E1[z + sj + sk], E1[z + sj]), e1d = two_sum(E1[z + sk], E1[z]);
+            const float *hh = g.hidx_hi, *hl = g.hidx_lo;
+            // B1: -(E3 pairs along i) differenced along j, +(E2 pairs along i) along k
+            const FPair b1 = ff_sub(ff_mul(ff_sub(e2a, e2b), hh[2], hl[2]), ff_mul(ff_sub(e3a, e3b), hh[1], hl[1]));
+            // B2: +(E3 pairs along j) differenced along i, -(E1 pairs along j) along k
+            const FPair b2 = ff_sub(ff_mul(ff_sub(e3c, e3d), hh[0], hl[0]), ff_mul(ff_sub(e1a, e1b), hh[2], hl[2]));
+            // B3: -(E2 pairs along k) differenced along i, +(E1 pairs along k) along j
+            const FPair b3 = ff_sub(ff_mul(ff_sub(e1c, e1d), hh[1], hl[1]), ff_mul(ff_sub(e2c, e2d), hh[0], hl[0]));
+            dB[0] = (double)b1.hi + (double)b1.lo;
+            dB[1] = (double)b2.hi + (double)b2.lo;
+            dB[2] = (double)b3.hi + (double)b3.lo;
+        } else {
+            dB[0] = (f2b1_jp - f2b1_j) * ix2 + (f3b1_kp - f3b1_k) * ix3;
+            dB[1] = (f1b2_ip - f1b2_i) * ix1 + (f3b2_kp - f3b2_k) * ix3;
+            dB[2] = (f1b3_ip - f1b3_i) * ix1 + (f2b3_jp - f2b3_j) * ix2;
+        }
         double dD = (double)dv[KRHO];
 #pragma unroll
         for (int c = 0; c < NU; c++) {
             double rhs;
-            if (c >= 1 && c <= 4 && src32) {
+            if (c >= KB1 && c <= KB3) {
+                rhs = -dB[c - KB1];
+            } else if (c >= 1 && c <= 4 && src32) {
                 // an FP32 source meets the FP32 divergence before the one conversion
                 rhs = (double)(sf[c - 1] - (float)dv[c]);
             } else {

@@ -9,7 +9,7 @@ oracle computes one at a time:
   * the inversion at 20000 sampled zones: the oracle's con2prim of the GPU's
     conserved variables, started from the GPU's primitives, returns them;
   * a property that holds at any size: the corner divergence of B (Eq. 24)
-    stays at round-off of the flux-CT update.
+    stays at FP64 round-off of the flux-CT update, in both paths.
 FP64: the 1e-10 parity bound.  Mixed: the faces are FP32, so the bound is
 FP32 rounding through the face physics (1e-5 of each component's scale);
 the mixed energy flux is compared rest-mass subtracted, as the mixed path
@@ -167,14 +167,12 @@ def test_fullsize_inversion_and_div_b(precision):
         errs.append((np.abs(P[f, sel] - Pq[f, sel]) / scale).max())
     print("round-trip errors rho, u, ut1..3:", np.array(errs))
     assert max(errs) < tol, errs
-    # div B of Eq. 24 (corner sums of U_B x 1/dX): FP64 keeps it at the
-    # round-off of the FP64 update; the mixed path forms the flux-CT increments
-    # of U_B in FP32 (then accumulates in FP64), so each step adds a round-off
-    # of order eps_32 (6e-8) x the step's change of U_B (at most ~1e-2 of U_B at
-    # CFL 0.45) per term: a bound of 2e-9 x steps x |U_B| x 1/dX
+    # div B of Eq. 24 (corner sums of U_B x 1/dX) at FP64 round-off in both
+    # paths: the mixed path's EMFs are FP32, but every face's CT flux is one
+    # consistent value and the increments of U_B are formed in FP64
     ub = float(Ud[5:8].abs().max())
     idx = max(1.0 / og.dx[0], 1.0 / og.dx[1], N / (2 * np.pi))
-    bound = 1e-12 * ub * idx if precision == 0 else 2e-9 * 5 * ub * idx
+    bound = 1e-12 * ub * idx
     print("div B max", d["divb_max"], "bound", bound)
     assert d["divb_max"] < bound
     ctx.close()
