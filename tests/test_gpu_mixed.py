@@ -123,3 +123,18 @@ def test_mixed_step_after_set_state_has_no_history():
     Pb, Ub, tb, dtb = G.get_state(fresh)
     assert ta == tb and dta == dtb
     assert np.array_equal(Pa, Pb) and np.array_equal(Ua, Ub)
+
+
+def test_mixed_flux_ct_keeps_div_b_at_round_off():
+    """Flux-CT in the mixed path: the EMFs are FP32, but the corner divergence
+    of Eq. 24 (on U_B) stays at FP64 round-off over 20 steps of a magnetised
+    torus, as in the FP64 path (the pair sums of edge EMFs are formed exactly)."""
+    G, og, ctx = _torus_pair(32, 32, 16, 1000.0)
+    d0 = G.diagnostics(ctx)["divb_max"]
+    G.step(ctx, 20)
+    U = G.get_state(ctx)[1]
+    d1 = G.diagnostics(ctx)["divb_max"]
+    idx = max(1.0 / og.dx[0], 1.0 / og.dx[1], 1.0 / og.dx[2])
+    ub = np.abs(U[5:8]).max()
+    assert ub > 0.0
+    assert d1 < 1e-13 * ub * idx + d0, (d0, d1)
