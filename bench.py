@@ -617,28 +617,28 @@ def main():
     # The dominant kernel (stage update + FP64 inversion) is bound by the FP64
     # pipe, which executes the FP64 arithmetic and also every FP32 <-> FP64
     # conversion and FP64 compare at the same rate.  Per zone and stage ncu
-    # counts, on the 96^3 mixed torus, 193.2 FP64-pipe thread instructions
-    # (sm__inst_executed_pipe_fp64 x 32): DFMA 48.1, DMUL 48.5, DADD 17.7,
-    # other FP64 arithmetic 7.1, conversions 43.3 and 28.4 more FP64-pipe
-    # instructions outside ncu's operation classes -- 162.4 FP64 flops
-    # (DFMA = 2).  Its DRAM traffic there was 246.6 B per zone
+    # counts, on the 96^3 mixed torus, 199.2 FP64-pipe thread instructions
+    # (sm__inst_executed_pipe_fp64 x 32): DFMA 48.1, DMUL 48.5, DADD 20.7,
+    # other FP64 arithmetic 7.1, conversions 46.3 and 28.5 more FP64-pipe
+    # instructions outside ncu's operation classes -- 165.4 FP64 flops
+    # (DFMA = 2).  Its DRAM traffic there was 246.4 B per zone
     # (scaled here by zone count).  The roofline is the pipe's issue rate:
     # 152 SMs x 2 FP64 lanes per clock x 2.07 GHz = 629 G thread-instr/s
     # (x 2 flops for DFMA = 1.26 TFLOP/s).
-    fp64_slots_per_zone_stage = 193.2
-    fp64_flops_per_zone_stage = 162.4
+    fp64_slots_per_zone_stage = 199.2
+    fp64_flops_per_zone_stage = 165.4
     pipe_peak = 152 * 2 * 2.070e9 / 1e9
     fp64_peak_units = 2 * pipe_peak / 1e3
     ach = fp64_slots_per_zone_stage * zones / (upd * 1e-3) / 1e9
     ach_tf = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
                 "achieved": ach, "peak": pipe_peak, "unit": "G FP64-pipe thread-instr/s",
-                "frac": ach / pipe_peak, "traffic": 246.6 * zones,
+                "frac": ach / pipe_peak, "traffic": 246.4 * zones,
                 "peak_source": "152 SMs x 2 FP64 lanes/clk x 2070 MHz (nominal unit count and clock); FMA-chain "
                                f"probe on this GPU: {fp64_peak:.3f} TFLOP/s = {fp64_peak * 500:.0f} G DFMA/s",
                 "ms_per_launch": upd, "fp64_pipe_slots_per_zone": fp64_slots_per_zone_stage,
                 "fp64_flops_per_zone": fp64_flops_per_zone_stage, "fp64_tflops": ach_tf,
-                "fp64_tflops_frac": ach_tf / fp64_peak_units, "fp64_pipe_active_ncu": 0.845}
+                "fp64_tflops_frac": ach_tf / fp64_peak_units, "fp64_pipe_active_ncu": 0.844}
     hbm_step = HBM_BYTES_PER_ZONE_CYCLE["mixed"] * zones / (ms_step * 1e-3) / 1e9
     gpu_launches = 21 * args.steps
     # ---- e2e through the public API with pinned host buffers
