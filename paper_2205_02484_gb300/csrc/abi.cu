@@ -148,6 +148,8 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.bc1 = grid->bc1; g.bc2 = grid->bc2; g.bc3 = grid->bc3;
     g.riemann = grid->riemann;
     g.mixed = grid->precision == GRMHD_MIXED;
+    // a row warp evaluates 29 faces per 32 lanes: worth it only for rows of >= 32 faces
+    g.x3warp = g.mixed && g.n3 + 1 >= 32;
     g.gam = phys->gam; g.cfl = phys->cfl; g.nr_tol = phys->nr_tol; g.sigma_max = phys->sigma_max;
     g.bu_max = phys->bu_max; g.gamma_max = phys->gamma_max; g.beta_ent = phys->beta_entropy;
     g.g1 = (g.gam - 1.0) / g.gam;

@@ -73,6 +73,7 @@ struct Grid {
     int n1, n2, n3, N1, N2, N3;
     long long nz;
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
+    int x3warp;                 // X3 fluxes by row warps (mixed path, rows of >= 32 faces)
     double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max

@@ -40,7 +40,7 @@ __host__ __device__ inline long long class_count(const Grid &g, int cls)
     switch (cls) {
     case W_F1: return flux_elem_box(g, 1).count();
     case W_F2: return flux_elem_box(g, 2).count();
-    case W_F3: return flux_elem_box(g, 3).count();
+    case W_F3: return g.x3warp ? x3_warp_box(g).count() : flux_elem_box(g, 3).count(); // long mixed rows: warps
     case W_EMF: return edge_box(g).count();
     case W_UPD: return nact_of(g);
     case W_POL: return polar_count(g);
@@ -90,8 +90,16 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
                 cwm = max(cwm, flux_call<R, 1>(sg, Pin, (R *)sg.F[0], flux_elem_box(sg, 1), want_dt, t));
             if (CLS == W_F2)
                 cwm = max(cwm, flux_call<R, 2>(sg, Pin, (R *)sg.F[1], flux_elem_box(sg, 2), want_dt, t));
-            if (CLS == W_F3)
-                cwm = max(cwm, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
+            if (CLS == W_F3) {
+                // tiles are whole warps (blockDim and items multiples of 32), as the
+                // mixed path's row-warp X3 sweep needs
+                bool warp = false;
+                if constexpr (sizeof(R) == 4) warp = sg.x3warp;
+                if (warp)
+                    cwm = max(cwm, flux_x3_warp<R>(sg, Pin, (R *)sg.F[2], x3_warp_box(sg), want_dt, t));
+                else
+                    cwm = max(cwm, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
+            }
             if (CLS == W_EMF)
                 emf_item(sg, (const R *)sg.F[0], (const R *)sg.F[1], (const R *)sg.F[2], (R *)sg.E[0], (R *)sg.E[1],
                          (R *)sg.E[2], edge_box(sg), t);

@@ -42,8 +42,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (D < 3 ? 4 : 5) : 1) k_f
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     R cw;
-    if constexpr (D == 3 && sizeof(R) == 4) cw = flux_x3_warp<R>(g, P, F, box, want_dt, t);
-    else cw = flux_call<R, D>(g, P, F, box, want_dt, t);
+    if constexpr (D == 3 && sizeof(R) == 4) {
+        if (g.x3warp) cw = flux_x3_warp<R>(g, P, F, box, want_dt, t);
+        else cw = flux_call<R, D>(g, P, F, box, want_dt, t);
+    } else {
+        cw = flux_call<R, D>(g, P, F, box, want_dt, t);
+    }
     if (want_dt) block_cfl_into(&g.dtmin[D - 1], cw, g.cfl * g.dx[D - 1]);
 }
 
@@ -102,9 +106,9 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     const int T = 128;
     const R *Pin = (const R *)g.P[src];
     R *Pout = (R *)g.P[dst];
-    // the mixed path sweeps X3 by warps (x3_warp_box); the FP64 path by faces
+    // the mixed path sweeps X3 by warps (x3_warp_box) where rows are long; else by faces
     Box b1 = flux_elem_box(g, 1), b2 = flux_elem_box(g, 2), be = edge_box(g);
-    Box b3 = sizeof(R) == 4 ? x3_warp_box(g) : flux_elem_box(g, 3);
+    Box b3 = (sizeof(R) == 4 && g.x3warp) ? x3_warp_box(g) : flux_elem_box(g, 3);
     switch (part) {
     case 0: k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[0], b1, want_dt); break;
     case 1: k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[1], b2, want_dt); break;
