@@ -231,6 +231,11 @@ typedef struct grmhd_ens grmhd_ens;
  * persistent blocks per SM, for the face sweeps and for the update kernel. */
 typedef struct {
     int items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update;
+    /* members with at least 2^solo_log2 active zones step with their own
+     * single-grid kernels inside the ensemble graph (their flux and EMF
+     * arrays then stay in L2 between the kernels of their step); 0: every
+     * member is batched.  Range 0 or 10-40. */
+    int solo_log2;
 } grmhd_ens_tiling;
 
 /* Build an ensemble of n member contexts (each with metric and state).
@@ -241,13 +246,15 @@ int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens **out);
 /* Advance every member by nsteps RK2 steps (asynchronous; graph replay). */
 int grmhd_ensemble_step(grmhd_ens *ens, int nsteps);
 
-/* Set / read the tiling (1-16 elements per thread, 1-64 blocks per SM). */
+/* Set / read the tiling (1-16 elements per thread, 1-64 blocks per SM, the
+ * solo threshold). */
 int grmhd_ensemble_set_tiling(grmhd_ens *ens, const grmhd_ens_tiling *t);
 int grmhd_ensemble_get_tiling(const grmhd_ens *ens, grmhd_ens_tiling *t);
 
 /* Time trial steps over a grid of tilings (face sweeps and update timed
- * separately with CUDA events), keep the fastest, and restore every member's
- * state, counters and time step afterwards.  best / best_ms may be NULL. */
+ * separately with CUDA events), then over solo thresholds (whole steps),
+ * keep the fastest, and restore every member's state, counters and time step
+ * afterwards.  best / best_ms (one step of the chosen tiling) may be NULL. */
 int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_ens_tiling *best, double *best_ms);
 
 /* Synchronise and return the first member status error (GRMHD_EFIXUP ...). */

@@ -3,17 +3,25 @@
 // of the RK2 step is one persistent launch over a ragged work list that
 // spans all members, and the whole ensemble step is one captured CUDA graph.
 //
-// Work list: for kernel class c and member m the elements (faces, edges,
-// zones, ghost zones) are cut into tiles of blockDim * items elements;
+// Work list: for kernel class c and batched member m the elements (faces,
+// edges, zones, ghost zones) are cut into tiles of blockDim * items elements;
 // prefix[c][m] counts the tiles of members < m.  A persistent grid of
 // (SM count x blocks per SM) blocks walks the tiles; a block finds its
-// member by binary search on the prefix, stages that member's descriptor in
-// shared memory and runs the same item functions as the single-grid kernels,
-// so every member evolves bit-for-bit as it would alone.  Fixups run one
-// block per member, the CFL step and counters stay per member.
+// member by binary search on the prefix (staged in shared memory), copies
+// that member's descriptor into shared memory and runs the same item
+// functions as the single-grid kernels, so every member evolves bit-for-bit
+// as it would alone.  Fixups run one block per member, the CFL step and
+// counters stay per member.
 //
-// Tunables (tile length in elements per thread, persistent blocks per SM)
-// are picked by grmhd_ensemble_autotune from timed trial steps.
+// Members at or above a size threshold are not batched: they run their own
+// single-grid step kernels inside the same captured graph.  One launch per
+// kernel class over the batch keeps every member's face and EMF arrays of a
+// stage alive until the update of the whole batch, which for large members
+// overflows L2; a large member's own step keeps them in L2.
+//
+// Tunables (tile length in elements per thread, persistent blocks per SM,
+// the solo threshold) are picked by grmhd_ensemble_autotune from timed trial
+// steps.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -66,7 +74,11 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
                                                        int want_dt)
 {
     __shared__ Grid sg;
-    const long long *pre = E.prefix + (long long)CLS * (E.n + 1);
+    extern __shared__ long long s_pre[]; // this class's tile prefix, [n + 1]
+    const long long *gpre = E.prefix + (long long)CLS * (E.n + 1);
+    for (int q = threadIdx.x; q <= E.n; q += blockDim.x) s_pre[q] = gpre[q];
+    __syncthreads();
+    const long long *pre = s_pre;
     const long long total = pre[E.n];
     const int items = E.items[CLS];
     const long long tile = (long long)blockDim.x * items;
@@ -74,8 +86,11 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
     for (long long w = blockIdx.x; w < total; w += gridDim.x) {
         int m = find_member(pre, E.n, w);
         if (m != cur) {
+            // the member's descriptor, copied by the whole block word by word
             __syncthreads();
-            if (threadIdx.x == 0) sg = E.grids[m];
+            const unsigned *gw = (const unsigned *)&E.grids[m];
+            unsigned *sw = (unsigned *)&sg;
+            for (int q = threadIdx.x; q < (int)(sizeof(Grid) / 4); q += blockDim.x) sw[q] = gw[q];
             __syncthreads();
             cur = m;
         }
@@ -137,6 +152,8 @@ using namespace grmhd;
 struct grmhd_ens {
     std::vector<grmhd_ctx *> members;
     std::vector<Grid> hgrids;
+    std::vector<int> batched, solo; // member indices: batched kernels / own step kernels
+    std::vector<Grid> bgrids;       // descriptors of the batched members
     Grid *dgrids = nullptr;
     long long *dprefix = nullptr;
     cudaStream_t stream = nullptr;
@@ -168,10 +185,26 @@ static void drop_graph(grmhd_ens *ens)
     ens->graph = nullptr;
 }
 
-// tile prefix tables for the current tiling
+// the batched / solo split and the tile prefix tables for the current tiling
 static int build_tables(grmhd_ens *ens)
 {
-    int n = (int)ens->members.size();
+    ens->batched.clear();
+    ens->solo.clear();
+    ens->bgrids.clear();
+    const int sl = ens->tiling.solo_log2;
+    for (int m = 0; m < (int)ens->members.size(); m++) {
+        long long na = nact_of(ens->hgrids[m]);
+        if (sl > 0 && na >= (1LL << sl)) {
+            ens->solo.push_back(m);
+        } else {
+            ens->batched.push_back(m);
+            ens->bgrids.push_back(ens->hgrids[m]);
+        }
+    }
+    int n = (int)ens->batched.size();
+    if (n > 0)
+        ECK(cudaMemcpyAsync(ens->dgrids, ens->bgrids.data(), sizeof(Grid) * n, cudaMemcpyHostToDevice,
+                            ens->stream));
     int items[W_NCLASS];
     for (int c = 0; c < W_NCLASS; c++) items[c] = 4;
     items[W_F1] = items[W_F2] = items[W_F3] = ens->tiling.items_flux;
@@ -182,13 +215,14 @@ static int build_tables(grmhd_ens *ens)
         long long tile = (long long)ENS_THREADS * items[c];
         for (int m = 0; m < n; m++) {
             pre[(size_t)c * (n + 1) + m] = acc;
-            acc += (class_count(ens->hgrids[m], c) + tile - 1) / tile;
+            acc += (class_count(ens->bgrids[m], c) + tile - 1) / tile;
         }
         pre[(size_t)c * (n + 1) + n] = acc;
         ens->tiles[c] = acc;
     }
-    ECK(cudaMemcpyAsync(ens->dprefix, pre.data(), pre.size() * sizeof(long long), cudaMemcpyHostToDevice,
-                        ens->stream));
+    if (n > 0)
+        ECK(cudaMemcpyAsync(ens->dprefix, pre.data(), pre.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                            ens->stream));
     ECK(cudaStreamSynchronize(ens->stream));
     return 0;
 }
@@ -198,7 +232,7 @@ static EnsDev ens_dev(const grmhd_ens *ens)
     EnsDev E{};
     E.grids = ens->dgrids;
     E.prefix = ens->dprefix;
-    E.n = (int)ens->members.size();
+    E.n = (int)ens->batched.size();
     for (int c = 0; c < W_NCLASS; c++) E.items[c] = 4;
     E.items[W_F1] = E.items[W_F2] = E.items[W_F3] = ens->tiling.items_flux;
     E.items[W_UPD] = ens->tiling.items_update;
@@ -206,12 +240,14 @@ static EnsDev ens_dev(const grmhd_ens *ens)
 }
 
 // Launch one ensemble step; with ev != nullptr an event is recorded before
-// each launch (2 stages x 10 launches + finalize + end = 22 events).
+// each batched launch (2 stages x 10 launches + finalize + end = 22 events);
+// the solo members' own steps follow.
 template <typename R>
 static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *ev)
 {
     EnsDev E = ens_dev(ens);
     const int n = E.n;
+    const size_t smem = sizeof(long long) * (n + 1);
     auto grid_of = [&](int cls) {
         int bps = (cls == W_UPD) ? ens->tiling.blocks_per_sm_update
                                  : (cls <= W_F3 ? ens->tiling.blocks_per_sm_flux : 8);
@@ -219,26 +255,27 @@ static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *e
         return (unsigned)std::max<long long>(b, 1);
     };
     int e = 0;
-    for (int st = 0; st < 2; st++) {
+    for (int st = 0; st < 2 && n > 0; st++) {
         int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
         double fac = st == 0 ? 0.5 : 1.0;
         int corr = st, wdt = st == 0;
 #define REC() do { if (ev) cudaEventRecord(ev[e++], s); } while (0)
-        REC(); ek_sweep<R, W_F1><<<grid_of(W_F1), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_F2><<<grid_of(W_F2), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_F3><<<grid_of(W_F3), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_EMF><<<grid_of(W_EMF), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_UPD><<<grid_of(W_UPD), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_F1><<<grid_of(W_F1), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_F2><<<grid_of(W_F2), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_F3><<<grid_of(W_F3), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_EMF><<<grid_of(W_EMF), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_UPD><<<grid_of(W_UPD), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
         REC(); ek_fixup<R><<<n, 1024, 0, s>>>(E, dst, corr);
-        REC(); ek_sweep<R, W_POL><<<grid_of(W_POL), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_BC1><<<grid_of(W_BC1), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_BC2><<<grid_of(W_BC2), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_BC3><<<grid_of(W_BC3), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_POL><<<grid_of(W_POL), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC1><<<grid_of(W_BC1), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC2><<<grid_of(W_BC2), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_sweep<R, W_BC3><<<grid_of(W_BC3), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
     }
     REC();
-    ek_finalize<<<(n + 127) / 128, 128, 0, s>>>(E);
+    if (n > 0) ek_finalize<<<(n + 127) / 128, 128, 0, s>>>(E);
     REC();
 #undef REC
+    for (int m : ens->solo) launch_step(ens->hgrids[m], s);
 }
 
 static void ens_step_launch(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *ev)
@@ -269,7 +306,7 @@ extern "C" int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens
     ens->device = ctx_device(members[0]);
     ens->stream = ctx_stream(members[0]);
     cudaDeviceGetAttribute(&ens->sms, cudaDevAttrMultiProcessorCount, ens->device);
-    ens->tiling = grmhd_ens_tiling{2, 2, 8, 4};
+    ens->tiling = grmhd_ens_tiling{2, 2, 8, 4, 0};
     if (cudaMalloc(&ens->dgrids, sizeof(Grid) * n) != cudaSuccess ||
         cudaMalloc(&ens->dprefix, sizeof(long long) * W_NCLASS * (n + 1)) != cudaSuccess) {
         grmhd_ensemble_destroy(ens);
@@ -302,8 +339,8 @@ extern "C" int grmhd_ensemble_set_tiling(grmhd_ens *ens, const grmhd_ens_tiling 
     if (!ens || !t) return GRMHD_EINVAL;
     if (t->items_flux < 1 || t->items_flux > 16 || t->items_update < 1 || t->items_update > 16 ||
         t->blocks_per_sm_flux < 1 || t->blocks_per_sm_flux > 64 || t->blocks_per_sm_update < 1 ||
-        t->blocks_per_sm_update > 64)
-        return efail(ens, GRMHD_EINVAL, "tiling out of range (items 1-16, blocks per SM 1-64)");
+        t->blocks_per_sm_update > 64 || (t->solo_log2 != 0 && (t->solo_log2 < 10 || t->solo_log2 > 40)))
+        return efail(ens, GRMHD_EINVAL, "tiling out of range (items 1-16, blocks per SM 1-64, solo 0 or 10-40)");
     ECK(cudaStreamSynchronize(ens->stream));
     ens->tiling = *t;
     drop_graph(ens);
@@ -392,8 +429,9 @@ extern "C" int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_en
     const int items_c[3] = {1, 2, 4};
     const int bps_c[4] = {2, 4, 8, 16};
     grmhd_ens_tiling keep = ens->tiling, cur = keep;
-    double best_flux = 1e300, best_upd = 1e300;
-    grmhd_ens_tiling bt = keep;
+    double best_flux = 1e300, best_upd = 1e300, best_step = 1e300;
+    cur.solo_log2 = 0; // tiles are timed with every member batched
+    grmhd_ens_tiling bt = cur;
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 4; b++) {
             cur.items_flux = items_c[a];
@@ -428,6 +466,34 @@ extern "C" int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_en
                 bt.blocks_per_sm_update = cur.blocks_per_sm_update;
             }
         }
+    {
+        // the solo threshold, on whole steps with the chosen tiles: members of at
+        // least 2^k zones step on their own (k = 0: none); candidates that give
+        // the same split as the previous one are skipped
+        const int cands[6] = {0, 22, 21, 20, 19, 18};
+        long long last_nsolo = -1;
+        int best_sl = 0;
+        for (int q = 0; q < 6; q++) {
+            grmhd_ens_tiling t = bt;
+            t.solo_log2 = cands[q];
+            ens->tiling = t;
+            if (build_tables(ens)) break;
+            if ((long long)ens->solo.size() == last_nsolo) continue;
+            last_nsolo = (long long)ens->solo.size();
+            ens_step_launch(ens, s, nullptr); // warm-up
+            cudaEventRecord(ev[0], s);
+            for (int it = 0; it < trial_steps; it++) ens_step_launch(ens, s, nullptr);
+            cudaEventRecord(ev[1], s);
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (ms < best_step) {
+                best_step = ms;
+                best_sl = cands[q];
+            }
+        }
+        bt.solo_log2 = best_sl;
+    }
 done:
     for (int e = 0; e < NE; e++) cudaEventDestroy(ev[e]);
     cudaError_t err = cudaGetLastError();
@@ -458,6 +524,6 @@ done:
     int rc = build_tables(ens);
     if (rc) return rc;
     if (best) *best = bt;
-    if (best_ms) *best_ms = (best_flux + best_upd) / trial_steps;
+    if (best_ms) *best_ms = best_step < 1e300 ? best_step / trial_steps : (best_flux + best_upd) / trial_steps;
     return 0;
 }

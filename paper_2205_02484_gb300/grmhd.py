@@ -71,7 +71,7 @@ class Diag(C.Structure):
 
 class EnsTiling(C.Structure):
     _fields_ = [("items_flux", C.c_int), ("items_update", C.c_int), ("blocks_per_sm_flux", C.c_int),
-                ("blocks_per_sm_update", C.c_int)]
+                ("blocks_per_sm_update", C.c_int), ("solo_log2", C.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -449,8 +449,11 @@ def ensemble_sync(ens: Ensemble):
     ens.check(ens.L.grmhd_ensemble_sync(ens.h))
 
 
-def ensemble_set_tiling(ens: Ensemble, items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update):
-    t = EnsTiling(items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update)
+def ensemble_set_tiling(ens: Ensemble, items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update,
+                        solo_log2=0):
+    """solo_log2 > 0: members of at least 2**solo_log2 active zones step with
+    their own kernels inside the ensemble graph."""
+    t = EnsTiling(items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update, solo_log2)
     ens.check(ens.L.grmhd_ensemble_set_tiling(ens.h, C.byref(t)))
 
 

@@ -41,7 +41,7 @@ def tune_or_load(ens: G.Ensemble, gpu_name: str, trial_steps: int = 2) -> tuple[
     if key in db:
         t = db[key]
         G.ensemble_set_tiling(ens, t["items_flux"], t["items_update"], t["blocks_per_sm_flux"],
-                              t["blocks_per_sm_update"])
+                              t["blocks_per_sm_update"], t.get("solo_log2", 0))
         return t, True
     t, _ = G.ensemble_autotune(ens, trial_steps)
     db[key] = t

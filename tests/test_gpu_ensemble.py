@@ -1,6 +1,8 @@
 """Ensemble of independent tori stepped by persistent launches over a ragged
-tile list: every member must evolve bit-for-bit as the same torus alone, for
-any tiling, and the autotuner must leave the members' state untouched."""
+tile list (members above a size threshold on their own kernels inside the same
+graph): every member must evolve bit-for-bit as the same torus alone, for any
+tiling and threshold, and the autotuner must leave the members' state
+untouched."""
 import numpy as np
 import pytest
 
@@ -37,9 +39,12 @@ def test_members_evolve_as_alone(precision):
     G.ensemble_step(ens, 2)
     G.ensemble_set_tiling(ens, 1, 4, 16, 2)   # a different tiling mid-run
     G.ensemble_step(ens, 2)
+    # members of >= 2^12 zones on their own kernels inside the graph, the rest batched
+    G.ensemble_set_tiling(ens, 2, 2, 8, 3, solo_log2=12)
+    G.ensemble_step(ens, 2)
     G.ensemble_sync(ens)
     for c in solo:
-        G.step(c, 4)
+        G.step(c, 6)
     for a, b in zip(ens_members, solo):
         Pa, Ua, ta, dta = G.get_state(a)
         Pb, Ub, tb, dtb = G.get_state(b)
@@ -62,6 +67,7 @@ def test_autotune_restores_state_and_keeps_results():
     cnt_before = [G.diagnostics(c)["n_steps"] for c in mem]
     tiling, ms = G.ensemble_autotune(ens, 1)
     assert ms > 0 and 1 <= tiling["items_flux"] <= 16
+    assert tiling["solo_log2"] == 0 or 10 <= tiling["solo_log2"] <= 40
     for c, b, n in zip(mem, before, cnt_before):
         P, U, t, dt = G.get_state(c)
         assert np.array_equal(P, b[0]) and np.array_equal(U, b[1]) and t == b[2] and dt == b[3]
