@@ -505,6 +505,35 @@ def oracle_sample_run(n, n3s, steps, warmup):
     return zc, dt, desc
 
 
+def _oracle_core_worker(job):
+    """one host core's share for oracle_all_cores: its own n x n x n3s slab
+    torus, `steps` timed steps"""
+    n, n3s, steps, seed = job
+    import oracle
+    p = oracle.default_params(n1=n, n2=n, n3=n3s, gam=4.0 / 3.0, r_out=1000.0, a=0.9375)
+    og = oracle.Grid(p)
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=seed)
+    t0 = time.perf_counter()
+    og.step(steps)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(n, n3s, steps):
+    """The same oracle on every host core at once: one n x n x n3s slab per
+    core in its own process (spawned), as a phi-slab decomposition of an
+    n x n x (cores n3s) grid would run it without the ghost exchange.  Returns
+    (zone-cycles/s of all cores, cores, description)."""
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, 144))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        times = pool.map(_oracle_core_worker, [(n, n3s, steps, 3 + c) for c in range(cores)])
+    zc = cores * n * n * n3s * steps / max(times)
+    desc = (f"{cores} processes, each a {n}x{n}x{n3s} phi-slab of the {n}^3 torus, {steps} RK2 steps timed "
+            f"per process; the job time is the slowest process's (the ghost exchange of a decomposed run, "
+            f"{2 * 2 * 8 * (n + 4) ** 2 * 8 / 1e6:.1f} MB per slab and stage, left out)")
+    return zc, cores, desc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -706,6 +735,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         zc, dt, desc = oracle_sample_run(n, 2, 2, 0)
         cpu = {"value": zc, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle", "sample": desc}
+        # the same oracle on all host cores at once (the single-core figure is the baseline)
+        zca, cores, desca = oracle_all_cores(n, 2, 2)
+        cpu["all_cores"] = {"value": zca, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle",
+                            "sample": desca}
     if rank == 0:
         line = {
             "metric": "zone-cycles/s at 256^3 (FP64 vs mixed, same GB300); % of HBM roofline",
