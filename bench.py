@@ -339,9 +339,9 @@ def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
 
 # ------------------------------------------- mixed vs FP64 short window
 
-def run_window(G, torch, stream, device, n=128, steps=200, every=10):
-    """The first `steps` steps of the n^3 torus (gamma 4/3, beta_0 100, 2%
-    perturbation, seed 2) from the same initial state in FP64 and in mixed
+def run_window(G, torch, stream, device, n=128, steps=200, every=10, gam=4.0 / 3.0, beta0=100.0, pert=0.02, seed=2):
+    """The first `steps` steps of the n^3 torus (gamma, beta_0, perturbation,
+    seed as given) from the same initial state in FP64 and in mixed
     precision: horizon Mdot and phi_B every `every` steps, and the per-field
     deviation of the final state (the FP64 GPU step is held to the FP64
     oracle at 1e-10 per step by the parity tests)."""
@@ -350,9 +350,9 @@ def run_window(G, torch, stream, device, n=128, steps=200, every=10):
     for name, prec in (("fp64", G.FP64), ("mixed", G.MIXED)):
         gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=prec, device=device)
         gp.stream = stream.cuda_stream
-        c = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+        c = G.init_grid(gp, G.default_phys(gam=gam))
         G.set_metric(c, 0.9375, G.KERR_MKS)
-        G.init_torus(c, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+        G.init_torus(c, r_in=6.0, r_max=12.0, beta0=beta0, pert_amp=pert, seed=seed)
         if name == "fp64":
             P0, U0, t0, dt0 = G.get_state(c)
         else:
@@ -378,8 +378,8 @@ def run_window(G, torch, stream, device, n=128, steps=200, every=10):
             else:
                 out.append(float(np.max(np.abs(y[f] - x[f])) / max(np.max(np.abs(x[f])), 1e-300)))
         return out
-    return {"workload": f"{n}^3 FM torus, gamma 4/3, beta_0 100, 2% perturbation, seed 2; first {steps} steps "
-                        "from the same initial state, FP64 vs mixed",
+    return {"workload": f"{n}^3 FM torus, gamma {gam:.4g}, beta_0 {beta0:g}, {100 * pert:g}% perturbation, seed "
+                        f"{seed}; first {steps} steps from the same initial state, FP64 vs mixed",
             "t_end": float(a[-1, 0]),
             # normwise over the series
             "mdot_max_rel_dev": float(np.max(np.abs(b[:, 1] - a[:, 1])) / max(np.max(np.abs(a[:, 1])), 1e-300)),
@@ -393,6 +393,40 @@ def run_window(G, torch, stream, device, n=128, steps=200, every=10):
             "prim_dev_final": field_dev(Pa, Pb, (0, 1)),
             "cons_dev_final": field_dev(Ua, Ub, (0, 1, 8)),
             "metric_note": "pointwise relative for rho, u (U_rho, U_E, U_S), max-norm relative for the others"}
+
+
+def run_variants(G, torch, stream, device, n=256, steps=20, warmup=3):
+    """The 256^3 mixed step at each (gamma, beta_0) of {4/3, 5/3} x {100, 30}:
+    zone-cycles/s, Newton steps per zone and fallback counts."""
+    out = []
+    for gam in (4.0 / 3.0, 5.0 / 3.0):
+        for b0 in (100.0, 30.0):
+            gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
+            gp.stream = stream.cuda_stream
+            c = G.init_grid(gp, G.default_phys(gam=gam))
+            G.set_metric(c, 0.9375, G.KERR_MKS)
+            G.init_torus(c, r_in=6.0, r_max=12.0, beta0=b0, pert_amp=0.04, seed=3)
+            G.step(c, warmup)
+            G.sync(c)
+            d0 = G.diagnostics(c)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            G.step(c, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            d1 = G.diagnostics(c)
+            nr = max(d1["n_nr"] - d0["n_nr"], 1)
+            out.append({"gamma": gam, "beta0": b0, "value": n ** 3 * steps / (ms * 1e-3), "unit": "zone-cycles/s",
+                        "ms_per_step": ms / steps,
+                        "newton_steps_per_zone": (d1["nr_iters"] - d0["nr_iters"]) / nr,
+                        "fallbacks": {k: d1[k] - d0[k] for k in ("n_brent", "n_entropy", "n_entropy_beta", "n_fail",
+                                                                 "n_ceil", "n_gcap")}})
+            c.close()
+    return {"workload": f"{n}^3 FM torus, r_out 1000 M, a 0.9375, 4% perturbation, mixed precision; {steps} steps "
+                        f"after {warmup}", "runs": out}
 
 
 # ------------------------------------------------------- learned Newton start
@@ -726,6 +760,11 @@ def main():
     slabs = None
     if world == 1 and not args.no_slabs:
         slabs = run_slabs(G, torch, local, n)
+    # ---- the 256^3 workload's (gamma, beta_0) grid, and its FP64-vs-mixed window
+    variants = window256 = None
+    if world == 1 and not args.no_window:
+        variants = run_variants(G, torch, stream, local, n)
+        window256 = run_window(G, torch, stream, local, n=n, steps=100, every=10, pert=0.04, seed=3)
     # ---- learned Newton start: training, inversions, the 256x192x192 step
     mlp = None
     if world == 1 and not args.no_mlp:
@@ -757,6 +796,8 @@ def main():
             "learned_start": mlp,
             "phi_slabs": slabs,
             "mixed_vs_fp64_window": window,
+            "mixed_vs_fp64_window_256": window256,
+            "variants_256": variants,
             "con2prim": c2p,
             "diagnostics_ms": diag_ms,
             "cpu_baseline": cpu,
