@@ -158,7 +158,9 @@ int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,
  * (dt of step n+1 from the predictor sweep of step n).  Asynchronous on the
  * context stream; each step replays one captured CUDA graph.  Inversion
  * failures that the fixups cannot repair raise GRMHD_EFIXUP at the next
- * grmhd_sync or grmhd_diagnostics. */
+ * grmhd_sync or grmhd_diagnostics.  GRMHD_EINVAL for a phi slab
+ * (bc3 = GRMHD_BC_EXTERNAL), whose ghost planes must be exchanged between
+ * the stages (grmhd_stage). */
 int grmhd_step(grmhd_ctx *ctx, int nsteps);
 
 /* Batched stand-alone inversion of n conserved states U (9 x n, sqrt(-g)

@@ -422,6 +422,8 @@ extern "C" int grmhd_step(grmhd_ctx *ctx, int nsteps)
     if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
     if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "step needs a state (init_torus or set_state)");
     if (nsteps < 0) return fail(ctx, GRMHD_EINVAL, "nsteps < 0");
+    if (ctx->g.bc3 == BC_EXTERNAL)
+        return fail(ctx, GRMHD_EINVAL, "a phi slab steps by grmhd_stage with its ghost planes exchanged between stages");
     (void)cudaGetLastError();
     if (!ctx->gexec) {
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));

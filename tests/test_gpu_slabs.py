@@ -113,6 +113,8 @@ def test_pack_unpack_planes():
         G.x3_unpack(e.ctx, 0, -1, buf)
     with pytest.raises(G.GrmhdError):
         G.stage(e.ctx, 3)
+    with pytest.raises(G.GrmhdError):  # a slab steps stage by stage, with exchanges
+        G.step(e.ctx, 1)
     ring.close()
 
 
