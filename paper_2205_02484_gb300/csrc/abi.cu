@@ -150,6 +150,10 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.mixed = grid->precision == GRMHD_MIXED;
     // a row warp evaluates 29 faces per 32 lanes: worth it only for rows of >= 32 faces
     g.x3warp = g.mixed && g.n3 + 1 >= 32;
+    // an axisymmetric grid (n3 = 1, X3 ghosts copies of the one plane) computes
+    // the k = 0 faces only: the k = -1 and k = 1 planes hold the same states
+    g.flat3 = g.n3 == 1 && (grid->metric == GRMHD_KERR_MKS || grid->bc3 == GRMHD_BC_PERIODIC ||
+                            grid->bc3 == GRMHD_BC_OUTFLOW);
     g.gam = phys->gam; g.cfl = phys->cfl; g.nr_tol = phys->nr_tol; g.sigma_max = phys->sigma_max;
     g.bu_max = phys->bu_max; g.gamma_max = phys->gamma_max; g.beta_ent = phys->beta_entropy;
     g.g1 = (g.gam - 1.0) / g.gam;

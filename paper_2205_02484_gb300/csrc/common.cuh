@@ -74,6 +74,8 @@ struct Grid {
     long long nz;
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
     int x3warp;                 // X3 fluxes by row warps (mixed path, rows of >= 32 faces)
+    int flat3;                  // one phi zone with copied X3 ghosts: the face fluxes do not vary
+                                // along X3, so only k = 0 faces are computed and every k reads them
     double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max

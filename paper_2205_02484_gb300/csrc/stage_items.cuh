@@ -33,6 +33,11 @@ struct Box {
 // needs), edges, active zones
 __host__ __device__ inline Box flux_box(const Grid &g, int d)
 {
+    if (g.flat3) { // the k = 0 faces stand for every k
+        if (d == 1) return Box{{0, -1, 0}, {g.n1 + 1, g.n2 + 2, 1}};
+        if (d == 2) return Box{{-1, 0, 0}, {g.n1 + 2, g.n2 + 1, 1}};
+        return Box{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, 1}};
+    }
     if (d == 1) return Box{{0, -1, -1}, {g.n1 + 1, g.n2 + 2, g.n3 + 2}};
     if (d == 2) return Box{{-1, 0, -1}, {g.n1 + 2, g.n2 + 1, g.n3 + 2}};
     return Box{{-1, -1, 0}, {g.n1 + 2, g.n2 + 2, g.n3 + 1}};
@@ -475,13 +480,15 @@ __device__ __forceinline__ void emf_item(const Grid &g, const R *__restrict__ F1
     box_decode(box, t, i, j, k);
     const long long nz = g.nz;
     long long z = zidx(g, i, j, k);
-    long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
+    long long si = (long long)g.N2 * g.N3, sj = g.N3;
+    // face fluxes of plane k (and k - 1); an axisymmetric grid keeps them at k = 0
+    const long long zf = g.flat3 ? zidx(g, i, j, 0) : z, sk = g.flat3 ? 0 : 1;
     if (k < g.n3)
-        E3[z] = R(0.25) * (F1[KB2 * nz + z] + F1[KB2 * nz + z - sj] - F2[KB1 * nz + z] - F2[KB1 * nz + z - si]);
+        E3[z] = R(0.25) * (F1[KB2 * nz + zf] + F1[KB2 * nz + zf - sj] - F2[KB1 * nz + zf] - F2[KB1 * nz + zf - si]);
     if (i < g.n1)
-        E1[z] = R(0.25) * (F2[KB3 * nz + z] + F2[KB3 * nz + z - sk] - F3[KB2 * nz + z] - F3[KB2 * nz + z - sj]);
+        E1[z] = R(0.25) * (F2[KB3 * nz + zf] + F2[KB3 * nz + zf - sk] - F3[KB2 * nz + zf] - F3[KB2 * nz + zf - sj]);
     if (j < g.n2)
-        E2[z] = R(0.25) * (F3[KB1 * nz + z] + F3[KB1 * nz + z - si] - F1[KB3 * nz + z] - F1[KB3 * nz + z - sk]);
+        E2[z] = R(0.25) * (F3[KB1 * nz + zf] + F3[KB1 * nz + zf - si] - F1[KB3 * nz + zf] - F1[KB3 * nz + zf - sk]);
 }
 
 // ------------------------------------------------- FP32 pair arithmetic
@@ -610,7 +617,7 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
             const long long o = c * nz + z;
             T d1 = (F1[o + si] - F1[o]) * ix1;
             T d2 = (F2[o + sj] - F2[o]) * ix2;
-            T d3 = (F3[o + sk] - F3[o]) * ix3;
+            T d3 = (F3[o + (g.flat3 ? 0 : sk)] - F3[o]) * ix3; // axisymmetric: the k = 0 face twice
             dv[c] = d1 + d2 + d3;
         }
         T f2b1_j = T(-0.5) * (E3[z + si] + E3[z]);

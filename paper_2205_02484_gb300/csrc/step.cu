@@ -258,11 +258,12 @@ __global__ void k_gather_fluxes(Grid g, double *out)
     const R *F = (const R *)g.F[d];
     const R *E1 = (const R *)g.E[0], *E2 = (const R *)g.E[1], *E3 = (const R *)g.E[2];
     long long z = zidx(g, i, j, k);
+    const long long zf = g.flat3 ? zidx(g, i, j, 0) : z; // axisymmetric grids keep the k = 0 faces
     const long long si = (long long)g.N2 * g.N3, sj = g.N3, sk = 1;
     for (int c = 0; c < NU; c++) {
         double v = 0.0;
         if (ok) {
-            v = (double)F[c * g.nz + z];
+            v = (double)F[c * g.nz + zf];
             if (d == 0) {
                 if (c == KB1) v = 0.0;
                 if (c == KB2) v = 0.5 * ((double)E3[z + sj] + (double)E3[z]);
