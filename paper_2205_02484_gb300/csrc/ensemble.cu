@@ -132,6 +132,34 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
     }
 }
 
+// The update class as one block per tile (no persistent loop), so that its
+// registers match the single-grid update kernel's (3 resident blocks of 128
+// threads per SM in the mixed path)
+template <typename R>
+__global__ void __launch_bounds__(ENS_THREADS, sizeof(R) == 4 ? 3 : 1) ek_update(EnsDev E, int src, int dst,
+                                                                                 double dtfac, int corr)
+{
+    __shared__ Grid sg;
+    const long long *pre = E.prefix + (long long)W_UPD * (E.n + 1);
+    const long long w = blockIdx.x;
+    if (w >= pre[E.n]) return;
+    const int m = find_member(pre, E.n, w);
+    {
+        const unsigned *gw = (const unsigned *)&E.grids[m];
+        unsigned *sw = (unsigned *)&sg;
+        for (int q = threadIdx.x; q < (int)(sizeof(Grid) / 4); q += blockDim.x) sw[q] = gw[q];
+    }
+    __syncthreads();
+    const int items = E.items[W_UPD];
+    const long long base = (w - pre[m]) * (long long)blockDim.x * items;
+    UpdCount cn{};
+    for (int it = 0; it < items; it++)
+        update_call<R>(sg, (const R *)sg.P[src], (R *)sg.P[dst], (const R *)sg.F[0], (const R *)sg.F[1],
+                       (const R *)sg.F[2], (const R *)sg.E[0], (const R *)sg.E[1], (const R *)sg.E[2], dtfac, corr,
+                       base + (long long)it * blockDim.x + threadIdx.x, cn);
+    flush_counts(sg, cn);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(1024) ek_fixup(EnsDev E, int dst, int corr)
 {
@@ -264,7 +292,7 @@ static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *e
         REC(); ek_sweep<R, W_F2><<<grid_of(W_F2), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
         REC(); ek_sweep<R, W_F3><<<grid_of(W_F3), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
         REC(); ek_sweep<R, W_EMF><<<grid_of(W_EMF), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
-        REC(); ek_sweep<R, W_UPD><<<grid_of(W_UPD), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
+        REC(); ek_update<R><<<(unsigned)std::max<long long>(ens->tiles[W_UPD], 1), ENS_THREADS, 0, s>>>(E, src, dst, fac, corr);
         REC(); ek_fixup<R><<<n, 1024, 0, s>>>(E, dst, corr);
         REC(); ek_sweep<R, W_POL><<<grid_of(W_POL), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
         REC(); ek_sweep<R, W_BC1><<<grid_of(W_BC1), ENS_THREADS, smem, s>>>(E, src, dst, fac, corr, wdt);
