@@ -17,18 +17,20 @@ from tests.gpu_common import field_err, gpu_mod, make_pair
 pytestmark = pytest.mark.gpu
 
 
-def _torus_pair(n1, n2, n3, r_out, gam=4.0 / 3.0, seed=2):
+def _torus_pair(n1, n2, n3, r_out, gam=4.0 / 3.0, seed=2, riemann=0):
     G = gpu_mod()
-    og, ctx = make_pair(n1, n2, n3, gam=gam, r_out=r_out, precision=1)
+    og, ctx = make_pair(n1, n2, n3, gam=gam, r_out=r_out, precision=1, riemann=riemann)
     og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=seed)
     Po, Uo, to, dto = og.get_state()
     G.set_state(ctx, Po, Uo, to, dto)
     return G, og, ctx
 
 
-def test_mixed_one_step_error_by_region():
-    """48 x 48 x 8 torus (r_out = 1000 M): one step from the same state."""
-    G, og, ctx = _torus_pair(48, 48, 8, 1000.0)
+@pytest.mark.parametrize("riemann", [0, 1])
+def test_mixed_one_step_error_by_region(riemann):
+    """48 x 48 x 8 torus (r_out = 1000 M): one step from the same state, LLF
+    and HLL."""
+    G, og, ctx = _torus_pair(48, 48, 8, 1000.0, riemann=riemann)
     og.step()
     G.step(ctx)
     Po, Uo, _, _ = og.get_state()
