@@ -93,6 +93,15 @@ typedef struct {
     int precision; /* GRMHD_FP64 or GRMHD_MIXED */
     int device;    /* CUDA device ordinal */
     void *stream;  /* cudaStream_t to issue work on, or NULL */
+    /* A theta slab of a decomposed grid (Sec. 3): the active X2 rows
+     * [j0, j0 + n2) of a grid of n2_total rows (n2_total = 0: not a slab,
+     * j0 must be 0).  The metric is built at the rows' global X2 positions
+     * (dX2 from n2_total), the poles are the whole grid's, and the X2 ghost
+     * rows of a side inside the grid (or of a periodic side) are written by
+     * the caller (grmhd_x2_unpack).  A slab has n2 >= 4 rows, is not also a
+     * phi slab (bc3 external), steps by the stage parts below and takes its
+     * state from grmhd_set_state (grmhd_init_torus: GRMHD_EINVAL). */
+    int j0, n2_total;
 } grmhd_grid_params;
 
 /* Physics constants; the paper's values are cfl 0.45 (Eq. 27), nr_tol 1e-10
@@ -160,7 +169,8 @@ int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,
  * failures that the fixups cannot repair raise GRMHD_EFIXUP at the next
  * grmhd_sync or grmhd_diagnostics.  GRMHD_EINVAL for a phi slab
  * (bc3 = GRMHD_BC_EXTERNAL), whose ghost planes must be exchanged between
- * the stages (grmhd_stage). */
+ * the stages (grmhd_stage), and for a theta slab (n2_total > 0), which steps
+ * by the stage parts. */
 int grmhd_step(grmhd_ctx *ctx, int nsteps);
 
 /* Batched stand-alone inversion of n conserved states U (9 x n, sqrt(-g)
@@ -241,8 +251,8 @@ typedef struct {
 } grmhd_ens_tiling;
 
 /* Build an ensemble of n member contexts (each with metric and state).
- * Errors: EINVAL (mixed devices or precisions), ESTATE (member not ready),
- * ENOMEM. */
+ * Errors: EINVAL (mixed devices or precisions, or a member that is a phi or
+ * theta slab), ESTATE (member not ready), ENOMEM. */
 int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens **out);
 
 /* Advance every member by nsteps RK2 steps (asynchronous; graph replay). */
@@ -415,7 +425,7 @@ int grmhd_set_learned_guess(grmhd_ctx *ctx, int on);
 /* One RK2 stage (st = 0: predictor P^n -> P-hat; st = 1: corrector P-hat ->
  * P^{n+1}, Eqs. 25-26), including fixups and the X1 / X2 (and, unless
  * external, X3) boundary fill.  The predictor's faces record the
- * per-direction CFL minima of Eq. 27. */
+ * per-direction CFL minima of Eq. 27.  GRMHD_EINVAL for a theta slab. */
 int grmhd_stage(grmhd_ctx *ctx, int st);
 
 /* The per-direction CFL minima of the last predictor into dtd_dev (3 doubles,
@@ -440,6 +450,67 @@ int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev);
 /* Write a neighbour's packed planes into the ghosts on `side` (0: k = -2, -1;
  * 1: k = n3, n3+1) of buffer `which`. */
 int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev);
+
+/* ---------------------------------------------------------------------
+ * Theta slabs (grid parameters j0, n2_total).  The fixups of Eq. 33 average
+ * a failed zone's X1 / X2 neighbours, so on a theta slab they reach one row
+ * across a slab face and each sweep must see the neighbours' current edge
+ * rows.  One RK2 step of R slabs (st = 0, then 1; out = 1 for st 0, 0 for
+ * st 1, the buffer the stage writes):
+ *   grmhd_stage_update(ctx, st) on every slab;  (st 0:) grmhd_step_dtd;
+ *   n = 0;  left = sum over slabs of grmhd_fail_count;
+ *   while (left > 0 && n < fix_maxsweep):
+ *       exchange kind-1 rows of buffer `out`;
+ *       left = sum over slabs of grmhd_fix_sweep(ctx, st, .);  n++;
+ *   grmhd_fix_end(ctx, st, n) and grmhd_stage_bc(ctx, st) on every slab;
+ *   exchange kind-0 rows of buffer `out`;
+ * then grmhd_finish_step with the minima over all slabs.  To exchange, a
+ * slab packs its side 0 (low theta) and side 1 rows with grmhd_x2_pack and
+ * unpacks its low neighbour's side-1 pack into its side 0 and its high
+ * neighbour's side-0 pack into its side 1 (no neighbour across a pole).
+ * Every call is asynchronous on the context stream; reading `left` on the
+ * host is the caller's synchronisation.
+ * ------------------------------------------------------------------- */
+
+/* Fluxes, flux-CT, update and inversion of stage st (a stage up to its
+ * fixups); the predictor's faces record the CFL minima. */
+int grmhd_stage_update(grmhd_ctx *ctx, int st);
+
+/* Add the number of zones whose inversion failed in the last
+ * grmhd_stage_update to *acc_dev (one long long of device memory). */
+int grmhd_fail_count(grmhd_ctx *ctx, long long *acc_dev);
+
+/* One Jacobi sweep of the fixups (Eq. 33) over stage st's output, reading
+ * the kind-1 ghost rows as the neighbours' rows; adds the number of this
+ * slab's zones still failed after it to *acc_dev. */
+int grmhd_fix_sweep(grmhd_ctx *ctx, int st, long long *acc_dev);
+
+/* Close stage st's fixups: count nsweeps sweeps, mark GRMHD_EFIXUP (seen by
+ * grmhd_sync) if a zone stays failed, clear the failure list. */
+int grmhd_fix_end(grmhd_ctx *ctx, int st, int nsweeps);
+
+/* Boundary fill of stage st's output (poles, X1, X3; the external X2 sides
+ * are left to the exchange). */
+int grmhd_stage_bc(grmhd_ctx *ctx, int st);
+
+/* Bytes of one side's rows of an exchange, element type double
+ * (GRMHD_FP64) or float (GRMHD_MIXED):
+ *   kind 0: NG = 2 rows of all 8 primitives over the ghosted (X1, X3)
+ *           section, layout [NG][8][n1 + 4][n3 + 4];
+ *   kind 1: one row of the five primitives a fixup averages and the failure
+ *           flag (0 or 1), over the active (X1, X3) section, layout
+ *           [6][n1][n3]. */
+int grmhd_x2_row_bytes(grmhd_ctx *ctx, int kind, unsigned long long *bytes);
+
+/* Pack the outermost active rows of buffer `which` (0 = P, 1 = P-hat) on
+ * `side` (0: j = 0, 1 for kind 0, j = 0 for kind 1; 1: j = n2-2, n2-1, or
+ * j = n2-1) into the caller's device buffer. */
+int grmhd_x2_pack(grmhd_ctx *ctx, int kind, int which, int side, void *buf_dev);
+
+/* Write a neighbour's packed rows into the ghost rows on `side` (0: j = -2,
+ * -1, or j = -1; 1: j = n2, n2+1, or j = n2) of buffer `which` (kind 1
+ * writes the ghost rows' failure flags too). */
+int grmhd_x2_unpack(grmhd_ctx *ctx, int kind, int which, int side, const void *buf_dev);
 
 /* Barycentric radius of the disk (Sec. 4.2, Eq. 43):
  *   <r> = sum r rho sqrt(-g) dV / sum rho sqrt(-g) dV

@@ -59,6 +59,7 @@ class Params(C.Structure):
         ("gam", C.c_double), ("cfl", C.c_double), ("nr_tol", C.c_double), ("sigma_max", C.c_double),
         ("bu_max", C.c_double), ("gamma_max", C.c_double), ("beta_entropy", C.c_double),
         ("nr_maxit", C.c_int), ("brent_maxit", C.c_int), ("fix_maxsweep", C.c_int),
+        ("j0", C.c_int), ("n2_total", C.c_int),
     ]
 
 
@@ -140,6 +141,15 @@ def lib():
                 "orc_combine_dt": (C.c_double, [_D]),
                 "orc_stage1": (None, [V, _I]),
                 "orc_get_xplane": (None, [V, C.c_int, C.c_int, _D]),
+                "orc_stage_update": (C.c_double, [V, C.c_int]),
+                "orc_fail_count": (C.c_long, [V]),
+                "orc_fix_sweep": (C.c_long, [V, C.c_int]),
+                "orc_fix_end": (None, [V, C.c_int]),
+                "orc_stage_bc": (None, [V, C.c_int]),
+                "orc_get_yrow": (None, [V, C.c_int, C.c_int, _D]),
+                "orc_set_yrow": (None, [V, C.c_int, C.c_int, _D]),
+                "orc_get_fixrow": (None, [V, C.c_int, C.c_int, _D]),
+                "orc_set_fixrow": (None, [V, C.c_int, C.c_int, _D]),
                 "orc_set_xplane": (None, [V, C.c_int, C.c_int, _D]),
                 "orc_mlp_nparam": (C.c_int, []),
                 "orc_bf16_round": (C.c_float, [C.c_float]),
@@ -261,6 +271,46 @@ class Grid:
     def set_xplane(self, which, k, plane):
         plane = np.ascontiguousarray(plane, dtype=np.float64)
         self.L.orc_set_xplane(self.h, which, k, _p(plane))
+
+    # ---- one slab of a theta-decomposed grid (n2_total > 0)
+    def stage_update(self, st):
+        """Fluxes, flux-CT, update and inversion of stage st; returns this
+        slab's CFL step (meaningful for st 0)."""
+        return self.L.orc_stage_update(self.h, st)
+
+    def fail_count(self):
+        return int(self.L.orc_fail_count(self.h))
+
+    def fix_sweep(self, st):
+        """One fixup sweep over stage st's output; returns the zones still failed."""
+        return int(self.L.orc_fix_sweep(self.h, st))
+
+    def fix_end(self, nsweeps):
+        self.L.orc_fix_end(self.h, nsweeps)
+
+    def stage_bc(self, st):
+        """Boundary fill of stage st's output (st 1 advances t)."""
+        self.L.orc_stage_bc(self.h, st)
+
+    def yrow(self, which, j):
+        """(8, N1, N3) primitives of P (which 0) or P-hat (which 1) at local X2 index j."""
+        out = np.zeros((NP, self.N[0], self.N[2]))
+        self.L.orc_get_yrow(self.h, which, j, _p(out))
+        return out
+
+    def set_yrow(self, which, j, row):
+        row = np.ascontiguousarray(row, dtype=np.float64)
+        self.L.orc_set_yrow(self.h, which, j, _p(row))
+
+    def fixrow(self, which, j):
+        """(6, n1, n3): the five averaged primitives and the failure flag of row j."""
+        out = np.zeros((6, self.p.n1, self.p.n3))
+        self.L.orc_get_fixrow(self.h, which, j, _p(out))
+        return out
+
+    def set_fixrow(self, which, j, row):
+        row = np.ascontiguousarray(row, dtype=np.float64)
+        self.L.orc_set_fixrow(self.h, which, j, _p(row))
 
     def invert_all(self):
         return self.L.orc_invert_all(self.h)

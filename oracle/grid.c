@@ -56,9 +56,30 @@ static double maxf(double a, double b) { return a > b ? a : b; }
 
 /* ------------------------------------------------------------------ setup */
 
+/* X2 rows of the whole grid a theta slab belongs to (n2 for a whole grid) */
+int orc_n2_total(const orc_grid *G) { return G->p.n2_total > 0 ? G->p.n2_total : G->p.n2; }
+
+/* 1 if the X2 ghost rows of a side (0 low, 1 high) come from the caller: a
+ * theta slab's side inside the grid, or a periodic side of the whole grid
+ * (the ghost rows then hold the far slab's edge rows) */
+int orc_x2_external(const orc_grid *G, int side)
+{
+    const orc_params *p = &G->p;
+    int n2t = orc_n2_total(G);
+    if (n2t == p->n2) return 0;
+    int edge = side == 0 ? p->j0 == 0 : p->j0 + p->n2 == n2t;
+    if (!edge) return 1;
+    return p->metric != ORC_KERR_MKS && p->bc2 == ORC_BC_PERIODIC;
+}
+
 orc_grid *orc_create(const orc_params *p)
 {
     if (p->n1 < 1 || p->n2 < 1 || p->n3 < 1) return NULL;
+    if (p->n2_total != 0) { /* a theta slab: at least 4 rows, not also a phi slab */
+        if (p->j0 < 0 || p->n2 < 4 || p->j0 + p->n2 > p->n2_total || p->bc3 == ORC_BC_EXTERNAL) return NULL;
+    } else if (p->j0 != 0) {
+        return NULL;
+    }
     orc_grid *G = (orc_grid *)calloc(1, sizeof(orc_grid));
     G->p = *p;
     G->N1 = p->n1 + 2 * ORC_NG;
@@ -93,7 +114,8 @@ orc_grid *orc_create(const orc_params *p)
         G->x3in = p->x3min; x3out = p->x3max;
     }
     G->dx[0] = (x1out - G->x1in) / p->n1;
-    G->dx[1] = (x2out - G->x2in) / p->n2;
+    int n2t = p->n2_total > 0 ? p->n2_total : p->n2;
+    G->dx[1] = (x2out - G->x2in) / n2t;
     G->dx[2] = (x3out - G->x3in) / p->n3;
 
     long nm = (long)G->N1 * G->N2;
@@ -107,10 +129,11 @@ orc_grid *orc_create(const orc_params *p)
         for (int j = -ORC_NG; j < p->n2 + ORC_NG; j++) {
             int m = orc_midx(G, i, j);
             double X1c = G->x1in + (i + 0.5) * G->dx[0], X1f = G->x1in + i * G->dx[0];
-            double X2c = G->x2in + (j + 0.5) * G->dx[1], X2f = G->x2in + j * G->dx[1];
+            int jg = p->j0 + j; /* the row in the whole grid */
+            double X2c = G->x2in + (jg + 0.5) * G->dx[1], X2f = G->x2in + jg * G->dx[1];
             orc_geom_at(G, X1c, X2c, &G->gc[m]);
             orc_geom_at(G, X1f, X2c, &G->gf1[m]);
-            if (p->metric == ORC_KERR_MKS && (j == 0 || j == p->n2)) {
+            if (p->metric == ORC_KERR_MKS && (jg == 0 || jg == n2t)) {
                 G->polar2[m] = 1;
             } else {
                 orc_geom_at(G, X1c, X2f, &G->gf2[m]);
@@ -195,16 +218,24 @@ void orc_bc_fill(orc_grid *G, double *P)
     int bc2 = kerr ? ORC_BC_POLAR : p->bc2;
     int bc3 = (kerr && p->bc3 != ORC_BC_EXTERNAL) ? ORC_BC_PERIODIC : p->bc3;
 
-    /* polar ut^2 interpolation in the two zones next to each pole */
-    if (bc2 == ORC_BC_POLAR && n2 >= 6) {
+    int n2t = orc_n2_total(G);
+    int ext[2] = {orc_x2_external(G, 0), orc_x2_external(G, 1)};
+    /* polar ut^2 interpolation in the two zones next to each pole (of the
+     * whole grid: a theta slab holds a pole's three rows or none of them) */
+    if (bc2 == ORC_BC_POLAR && n2t >= 6) {
+        int lo = p->j0 == 0, hi = p->j0 + n2 == n2t;
         for (int i = 0; i < n1; i++)
             for (int k = 0; k < n3; k++) {
-                double u2a = AT(P, KU2, orc_idx(G, i, 2, k));
-                double u2b = AT(P, KU2, orc_idx(G, i, n2 - 3, k));
-                AT(P, KU2, orc_idx(G, i, 0, k)) = u2a * (0.5 / 2.5);
-                AT(P, KU2, orc_idx(G, i, 1, k)) = u2a * (1.5 / 2.5);
-                AT(P, KU2, orc_idx(G, i, n2 - 1, k)) = u2b * (0.5 / 2.5);
-                AT(P, KU2, orc_idx(G, i, n2 - 2, k)) = u2b * (1.5 / 2.5);
+                if (lo) {
+                    double u2a = AT(P, KU2, orc_idx(G, i, 2, k));
+                    AT(P, KU2, orc_idx(G, i, 0, k)) = u2a * (0.5 / 2.5);
+                    AT(P, KU2, orc_idx(G, i, 1, k)) = u2a * (1.5 / 2.5);
+                }
+                if (hi) {
+                    double u2b = AT(P, KU2, orc_idx(G, i, n2 - 3, k));
+                    AT(P, KU2, orc_idx(G, i, n2 - 1, k)) = u2b * (0.5 / 2.5);
+                    AT(P, KU2, orc_idx(G, i, n2 - 2, k)) = u2b * (1.5 / 2.5);
+                }
             }
     }
     /* X1 ghosts over active j, k */
@@ -226,28 +257,41 @@ void orc_bc_fill(orc_grid *G, double *P)
                     scatter(G, P, orc_idx(G, ir, j, k), q);
                 }
             }
-    /* X2 ghosts over all i, active k */
+    /* X2 ghosts over all i, active k (a theta slab's inner sides come from
+     * its neighbours) */
     for (int i = -ORC_NG; i < n1 + ORC_NG; i++)
         for (int k = 0; k < n3; k++)
             for (int gh = 1; gh <= ORC_NG; gh++) {
                 int jl = -gh, jr = n2 - 1 + gh;
                 if (bc2 == ORC_BC_POLAR) {
-                    gather(G, P, orc_idx(G, i, gh - 1, k), q);
-                    q[KU2] = -q[KU2]; q[KB2] = -q[KB2];
-                    scatter(G, P, orc_idx(G, i, jl, k), q);
-                    gather(G, P, orc_idx(G, i, n2 - gh, k), q);
-                    q[KU2] = -q[KU2]; q[KB2] = -q[KB2];
-                    scatter(G, P, orc_idx(G, i, jr, k), q);
+                    if (!ext[0]) {
+                        gather(G, P, orc_idx(G, i, gh - 1, k), q);
+                        q[KU2] = -q[KU2]; q[KB2] = -q[KB2];
+                        scatter(G, P, orc_idx(G, i, jl, k), q);
+                    }
+                    if (!ext[1]) {
+                        gather(G, P, orc_idx(G, i, n2 - gh, k), q);
+                        q[KU2] = -q[KU2]; q[KB2] = -q[KB2];
+                        scatter(G, P, orc_idx(G, i, jr, k), q);
+                    }
                 } else if (bc2 == ORC_BC_PERIODIC) {
-                    gather(G, P, orc_idx(G, i, wrap(jl, n2), k), q);
-                    scatter(G, P, orc_idx(G, i, jl, k), q);
-                    gather(G, P, orc_idx(G, i, wrap(jr, n2), k), q);
-                    scatter(G, P, orc_idx(G, i, jr, k), q);
+                    if (!ext[0]) {
+                        gather(G, P, orc_idx(G, i, wrap(jl, n2), k), q);
+                        scatter(G, P, orc_idx(G, i, jl, k), q);
+                    }
+                    if (!ext[1]) {
+                        gather(G, P, orc_idx(G, i, wrap(jr, n2), k), q);
+                        scatter(G, P, orc_idx(G, i, jr, k), q);
+                    }
                 } else {
-                    gather(G, P, orc_idx(G, i, 0, k), q);
-                    scatter(G, P, orc_idx(G, i, jl, k), q);
-                    gather(G, P, orc_idx(G, i, n2 - 1, k), q);
-                    scatter(G, P, orc_idx(G, i, jr, k), q);
+                    if (!ext[0]) {
+                        gather(G, P, orc_idx(G, i, 0, k), q);
+                        scatter(G, P, orc_idx(G, i, jl, k), q);
+                    }
+                    if (!ext[1]) {
+                        gather(G, P, orc_idx(G, i, n2 - 1, k), q);
+                        scatter(G, P, orc_idx(G, i, jr, k), q);
+                    }
                 }
             }
     /* X3 ghosts over all i, j (a slab's come from its neighbours) */
@@ -527,92 +571,120 @@ static void post_fixup(orc_grid *G, int i, int j, double *q)
 
 /* ------------------------------------------------------------- fixups */
 
-static int fixups(orc_grid *G, double *P, int corr)
+static long count_failed(const orc_grid *G)
+{
+    const orc_params *p = &G->p;
+    long nfail = 0;
+    for (int i = 0; i < p->n1; i++)
+        for (int j = 0; j < p->n2; j++)
+            for (int k = 0; k < p->n3; k++) nfail += (G->flag[orc_idx(G, i, j, k)] != 0);
+    return nfail;
+}
+
+/* a fixup neighbour (ii, jj) of Eq. 33 must be an active zone of the whole
+ * grid; a theta slab reads the rows jj = -1 and n2 next to its inner sides
+ * from its ghost rows, which the caller fills with the neighbour slab's
+ * current edge rows (primitives and flags) before each sweep */
+static int fix_inside(const orc_grid *G, int ii, int jj)
+{
+    int jg = G->p.j0 + jj;
+    return ii >= 0 && ii < G->p.n1 && jg >= 0 && jg < orc_n2_total(G);
+}
+
+/* One Jacobi sweep of the fixups (Eq. 33) over P: every failed zone whose
+ * four face neighbours are good takes their average, else whose four
+ * corner neighbours are good takes theirs, else the average of all its good
+ * neighbours; the averages are all formed from the state at the start of the
+ * sweep, then written.  Returns the number of zones still failed. */
+static long fix_sweep(orc_grid *G, double *P, int corr)
 {
     const orc_params *p = &G->p;
     int n1 = p->n1, n2 = p->n2, n3 = p->n3;
-    long nfail = 0;
-    for (int i = 0; i < n1; i++)
-        for (int j = 0; j < n2; j++)
-            for (int k = 0; k < n3; k++) nfail += (G->flag[orc_idx(G, i, j, k)] != 0);
-    if (!nfail) return 0;
     static const int fo[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
     static const int dg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
     int *newflag = (int *)malloc(sizeof(int) * G->nz);
     double *newq = (double *)malloc(sizeof(double) * 5 * G->nz);
-    int sweep;
-    for (sweep = 0; sweep < p->fix_maxsweep && nfail > 0; sweep++) {
-        memcpy(newflag, G->flag, sizeof(int) * G->nz);
-        for (int i = 0; i < n1; i++)
-            for (int j = 0; j < n2; j++)
-                for (int k = 0; k < n3; k++) {
-                    long z = orc_idx(G, i, j, k);
-                    if (!G->flag[z]) continue;
-                    const int(*sets[2])[2] = {fo, dg};
-                    int done = 0;
-                    for (int s = 0; s < 2 && !done; s++) {
-                        int allgood = 1;
+    memcpy(newflag, G->flag, sizeof(int) * G->nz);
+    for (int i = 0; i < n1; i++)
+        for (int j = 0; j < n2; j++)
+            for (int k = 0; k < n3; k++) {
+                long z = orc_idx(G, i, j, k);
+                if (!G->flag[z]) continue;
+                const int(*sets[2])[2] = {fo, dg};
+                int done = 0;
+                for (int s = 0; s < 2 && !done; s++) {
+                    int allgood = 1;
+                    for (int m = 0; m < 4; m++) {
+                        int ii = i + sets[s][m][0], jj = j + sets[s][m][1];
+                        if (!fix_inside(G, ii, jj) || G->flag[orc_idx(G, ii, jj, k)]) allgood = 0;
+                    }
+                    if (allgood) {
+                        for (int c = 0; c < 5; c++) {
+                            double acc = 0.0;
+                            for (int m = 0; m < 4; m++)
+                                acc += AT(P, c, orc_idx(G, i + sets[s][m][0], j + sets[s][m][1], k));
+                            newq[(long)c * G->nz + z] = 0.25 * acc;
+                        }
+                        done = 1;
+                    }
+                }
+                if (!done) {
+                    int cnt = 0;
+                    double acc[5] = {0, 0, 0, 0, 0};
+                    for (int s = 0; s < 2; s++)
                         for (int m = 0; m < 4; m++) {
-                            int ii = i + sets[s][m][0], jj = j + sets[s][m][1];
-                            if (ii < 0 || ii >= n1 || jj < 0 || jj >= n2 ||
-                                G->flag[orc_idx(G, ii, jj, k)]) allgood = 0;
+                            int ii = i + (s ? dg : fo)[m][0], jj = j + (s ? dg : fo)[m][1];
+                            if (!fix_inside(G, ii, jj)) continue;
+                            long zz = orc_idx(G, ii, jj, k);
+                            if (G->flag[zz]) continue;
+                            for (int c = 0; c < 5; c++) acc[c] += AT(P, c, zz);
+                            cnt++;
                         }
-                        if (allgood) {
-                            for (int c = 0; c < 5; c++) {
-                                double acc = 0.0;
-                                for (int m = 0; m < 4; m++)
-                                    acc += AT(P, c, orc_idx(G, i + sets[s][m][0], j + sets[s][m][1], k));
-                                newq[(long)c * G->nz + z] = 0.25 * acc;
-                            }
-                            done = 1;
-                        }
-                    }
-                    if (!done) {
-                        int cnt = 0;
-                        double acc[5] = {0, 0, 0, 0, 0};
-                        for (int s = 0; s < 2; s++)
-                            for (int m = 0; m < 4; m++) {
-                                int ii = i + (s ? dg : fo)[m][0], jj = j + (s ? dg : fo)[m][1];
-                                if (ii < 0 || ii >= n1 || jj < 0 || jj >= n2) continue;
-                                long zz = orc_idx(G, ii, jj, k);
-                                if (G->flag[zz]) continue;
-                                for (int c = 0; c < 5; c++) acc[c] += AT(P, c, zz);
-                                cnt++;
-                            }
-                        if (cnt > 0) {
-                            for (int c = 0; c < 5; c++) newq[(long)c * G->nz + z] = acc[c] / cnt;
-                            done = 1;
-                        }
-                    }
-                    if (done) newflag[z] = -1; /* fixed this sweep */
-                }
-        for (int i = 0; i < n1; i++)
-            for (int j = 0; j < n2; j++)
-                for (int k = 0; k < n3; k++) {
-                    long z = orc_idx(G, i, j, k);
-                    if (newflag[z] == -1) {
-                        double q[ORC_NP];
-                        gather(G, P, z, q);
-                        for (int c = 0; c < 5; c++) q[c] = newq[(long)c * G->nz + z];
-                        post_fixup(G, i, j, q);
-                        scatter(G, P, z, q);
-                        if (corr) {
-                            const orc_geom *g = &G->gc[orc_midx(G, i, j)];
-                            orc_state s;
-                            orc_state_of(q, g, &s);
-                            double Uz[ORC_NU];
-                            orc_prim_to_U(q, g, &s, p->gam, Uz);
-                            for (int c = 0; c < ORC_NU; c++) AT(G->U, c, z) = Uz[c];
-                        }
-                        G->flag[z] = 0;
-                        G->cnt.n_fixed++;
-                        nfail--;
+                    if (cnt > 0) {
+                        for (int c = 0; c < 5; c++) newq[(long)c * G->nz + z] = acc[c] / cnt;
+                        done = 1;
                     }
                 }
-    }
-    G->cnt.fix_sweeps += sweep;
+                if (done) newflag[z] = -1; /* fixed this sweep */
+            }
+    long left = 0;
+    for (int i = 0; i < n1; i++)
+        for (int j = 0; j < n2; j++)
+            for (int k = 0; k < n3; k++) {
+                long z = orc_idx(G, i, j, k);
+                if (newflag[z] == -1) {
+                    double q[ORC_NP];
+                    gather(G, P, z, q);
+                    for (int c = 0; c < 5; c++) q[c] = newq[(long)c * G->nz + z];
+                    post_fixup(G, i, j, q);
+                    scatter(G, P, z, q);
+                    if (corr) {
+                        const orc_geom *g = &G->gc[orc_midx(G, i, j)];
+                        orc_state s;
+                        orc_state_of(q, g, &s);
+                        double Uz[ORC_NU];
+                        orc_prim_to_U(q, g, &s, p->gam, Uz);
+                        for (int c = 0; c < ORC_NU; c++) AT(G->U, c, z) = Uz[c];
+                    }
+                    G->flag[z] = 0;
+                    G->cnt.n_fixed++;
+                } else if (G->flag[z]) {
+                    left++;
+                }
+            }
     free(newflag);
     free(newq);
+    return left;
+}
+
+/* the fixups of a stage: sweeps until no zone is left failed, at most
+ * fix_maxsweep of them; -1 if some zone stays failed */
+static int fixups(orc_grid *G, double *P, int corr)
+{
+    long nfail = count_failed(G);
+    int sweep = 0;
+    for (; sweep < G->p.fix_maxsweep && nfail > 0; sweep++) nfail = fix_sweep(G, P, corr);
+    G->cnt.fix_sweeps += sweep;
     return nfail > 0 ? -1 : 0;
 }
 
@@ -649,8 +721,9 @@ static void invert_zone(orc_grid *G, int i, int j, long z, double *Un, const dou
 
 /* -------------------------------------------------------------- stages */
 
-static double stage(orc_grid *G, const double *Pin, double *Pout, double dts, int corr,
-                    int *status)
+/* fluxes, flux-CT, and the update and inversion of every zone (a stage up
+ * to its fixups); returns the CFL step of the fluxes */
+static double stage_update(orc_grid *G, const double *Pin, double *Pout, double dts, int corr)
 {
     const orc_params *p = &G->p;
     int n1 = p->n1, n2 = p->n2, n3 = p->n3;
@@ -685,6 +758,13 @@ static double stage(orc_grid *G, const double *Pin, double *Pout, double dts, in
                     for (int c = 0; c < ORC_NU; c++) AT(G->U, c, z) = Un[c];
             }
         }
+    return dtn;
+}
+
+static double stage(orc_grid *G, const double *Pin, double *Pout, double dts, int corr,
+                    int *status)
+{
+    double dtn = stage_update(G, Pin, Pout, dts, corr);
     if (fixups(G, Pout, corr) != 0) *status = -1;
     orc_bc_fill(G, Pout);
     return dtn;
@@ -719,6 +799,84 @@ void orc_stage1(orc_grid *G, int *status)
     stage(G, G->Ph, G->P, G->dt, 1, status);
     G->t += G->dt;
     G->cnt.n_steps++;
+}
+
+/* The parts of a stage (st 0: predictor into P-hat, st 1: corrector into
+ * P) for a grid that is one theta slab of a decomposed one.  The fixup
+ * sweeps of Eq. 33 reach one row across a slab face, so the caller runs
+ *   orc_stage_update;  while some slab has failed zones (orc_fail_count)
+ *   and fewer than fix_maxsweep sweeps ran: exchange the edge rows
+ *   (orc_get_fixrow / orc_set_fixrow), orc_fix_sweep on every slab;
+ *   orc_fix_end with the number of sweeps;  orc_stage_bc;  exchange the NG
+ *   ghost rows (orc_get_yrow / orc_set_yrow).
+ * orc_stage_update returns this slab's CFL step (st 0), orc_stage_bc(1)
+ * advances t. */
+double orc_stage_update(orc_grid *G, int st)
+{
+    return st == 0 ? stage_update(G, G->P, G->Ph, 0.5 * G->dt, 0) : stage_update(G, G->Ph, G->P, G->dt, 1);
+}
+
+long orc_fail_count(const orc_grid *G) { return count_failed(G); }
+
+long orc_fix_sweep(orc_grid *G, int st) { return fix_sweep(G, st == 0 ? G->Ph : G->P, st); }
+
+void orc_fix_end(orc_grid *G, int nsweeps) { G->cnt.fix_sweeps += nsweeps; }
+
+void orc_stage_bc(orc_grid *G, int st)
+{
+    orc_bc_fill(G, st == 0 ? G->Ph : G->P);
+    if (st == 1) {
+        G->t += G->dt;
+        G->cnt.n_steps++;
+    }
+}
+
+/* the row of all 8 primitives at local X2 index j (-NG .. n2-1+NG), over
+ * i = -NG .. n1-1+NG and k = -NG .. n3-1+NG (layout [8][N1][N3]), of P
+ * (which = 0) or P-hat (which = 1) */
+void orc_get_yrow(const orc_grid *G, int which, int j, double *out)
+{
+    const double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < ORC_NP; c++)
+        for (int i = -ORC_NG; i < G->p.n1 + ORC_NG; i++)
+            for (int k = -ORC_NG; k < G->p.n3 + ORC_NG; k++) out[m++] = AT(P, c, orc_idx(G, i, j, k));
+}
+
+void orc_set_yrow(orc_grid *G, int which, int j, const double *in)
+{
+    double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < ORC_NP; c++)
+        for (int i = -ORC_NG; i < G->p.n1 + ORC_NG; i++)
+            for (int k = -ORC_NG; k < G->p.n3 + ORC_NG; k++) AT(P, c, orc_idx(G, i, j, k)) = in[m++];
+}
+
+/* what a fixup sweep reads of row j: the five averaged primitives and the
+ * failure flag (as 0 / 1) over the active i, k, layout [6][n1][n3] */
+void orc_get_fixrow(const orc_grid *G, int which, int j, double *out)
+{
+    const double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < 6; c++)
+        for (int i = 0; i < G->p.n1; i++)
+            for (int k = 0; k < G->p.n3; k++) {
+                long z = orc_idx(G, i, j, k);
+                out[m++] = c < 5 ? AT(P, c, z) : (G->flag[z] != 0);
+            }
+}
+
+void orc_set_fixrow(orc_grid *G, int which, int j, const double *in)
+{
+    double *P = which ? G->Ph : G->P;
+    long m = 0;
+    for (int c = 0; c < 6; c++)
+        for (int i = 0; i < G->p.n1; i++)
+            for (int k = 0; k < G->p.n3; k++) {
+                long z = orc_idx(G, i, j, k);
+                if (c < 5) AT(P, c, z) = in[m++];
+                else G->flag[z] = in[m++] != 0.0;
+            }
 }
 
 /* the (N1 x N2) plane of all 8 primitives at local X3 index k (-NG .. n3-1+NG,

@@ -47,6 +47,10 @@ typedef struct {
     int riemann;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_entropy;
     int nr_maxit, brent_maxit, fix_maxsweep;
+    /* a theta slab: the active X2 rows [j0, j0 + n2) of a grid of n2_total
+     * rows (n2_total = 0: the whole grid); its X2 ghost rows on a side
+     * inside the grid, or on a periodic side, are supplied by the caller */
+    int j0, n2_total;
 } orc_params;
 
 typedef struct {
@@ -135,5 +139,7 @@ double orc_barycentric(orc_grid *G, double r_bar_max, double out[3]);
 double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
+int orc_n2_total(const orc_grid *G);
+int orc_x2_external(const orc_grid *G, int side);
 
 #endif

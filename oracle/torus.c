@@ -113,6 +113,7 @@ int orc_init_torus(orc_grid *G, const orc_torus_params *tp)
 {
     const orc_params *p = &G->p;
     if (p->metric != ORC_KERR_MKS) return -1;
+    if (p->n2_total != 0) return -1; /* a theta slab takes its state from set_state */
     int n1 = p->n1, n2 = p->n2, n3 = p->n3;
     double a = p->a, gam = p->gam, kappa = tp->kappa > 0 ? tp->kappa : 1e-3;
     double l = orc_fm_ell(a, tp->r_max);

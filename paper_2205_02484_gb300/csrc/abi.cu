@@ -122,6 +122,14 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
         return fail(nullptr, GRMHD_EINVAL, "bad boundary kind (external is for bc3 only)");
     if (grid->bc3 == GRMHD_BC_EXTERNAL && grid->n3 < 2)
         return fail(nullptr, GRMHD_EINVAL, "a phi slab needs n3 >= 2");
+    if (grid->n2_total != 0) {
+        if (grid->n2 < 4 || grid->j0 < 0 || (long long)grid->j0 + grid->n2 > grid->n2_total)
+            return fail(nullptr, GRMHD_EINVAL, "a theta slab needs n2 >= 4 rows inside [0, n2_total)");
+        if (grid->bc3 == GRMHD_BC_EXTERNAL)
+            return fail(nullptr, GRMHD_EINVAL, "a grid is a theta slab or a phi slab, not both");
+    } else if (grid->j0 != 0) {
+        return fail(nullptr, GRMHD_EINVAL, "j0 needs n2_total (a theta slab)");
+    }
     if (grid->riemann != GRMHD_LLF && grid->riemann != GRMHD_HLL)
         return fail(nullptr, GRMHD_EINVAL, "riemann must be GRMHD_LLF or GRMHD_HLL");
     if (!(phys->gam > 1.0) || !(phys->cfl > 0.0) || phys->nr_maxit < 1 || phys->brent_maxit < 1 ||
@@ -142,6 +150,8 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     }
     Grid &g = ctx->g;
     g.n1 = grid->n1; g.n2 = grid->n2; g.n3 = grid->n3;
+    g.j0 = grid->j0;
+    g.n2t = grid->n2_total > 0 ? grid->n2_total : grid->n2;
     g.N1 = (int)N1; g.N2 = (int)N2; g.N3 = (int)N3;
     g.nz = nz;
     g.metric = grid->metric;
@@ -267,7 +277,7 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         double x1out = p.r_out <= p.r_br ? std::log(p.r_out - p.R0) : x1_of_r(cp, p.r_out);
         g.x2in = -1.0;
         g.dx[0] = (x1out - g.x1in) / g.n1;
-        g.dx[1] = 2.0 / g.n2;
+        g.dx[1] = 2.0 / g.n2t;
         if (g.bc3 == BC_EXTERNAL) { // a phi slab [x3min, x3max) of the full circle
             g.x3in = p.x3min;
             g.dx[2] = (p.x3max - p.x3min) / g.n3;
@@ -287,7 +297,7 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         cp.xb = 1e300;
         g.x1in = p.x1min; g.x2in = p.x2min; g.x3in = p.x3min;
         g.dx[0] = (p.x1max - p.x1min) / g.n1;
-        g.dx[1] = (p.x2max - p.x2min) / g.n2;
+        g.dx[1] = (p.x2max - p.x2min) / g.n2t;
         g.dx[2] = (p.x3max - p.x3min) / g.n3;
         g.i_h = 0;
         if (!(g.dx[0] > 0) || !(g.dx[1] > 0) || !(g.dx[2] > 0)) return fail(ctx, GRMHD_EINVAL, "empty box");
@@ -334,6 +344,8 @@ extern "C" int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *tp)
     if (!ctx->metric_set || ctx->g.metric != GRMHD_KERR_MKS)
         return fail(ctx, GRMHD_ESTATE, "init_torus needs grmhd_set_metric(GRMHD_KERR_MKS) first");
     if (!(tp->r_max > tp->r_in) || !(tp->r_in > 0.0)) return fail(ctx, GRMHD_EINVAL, "need 0 < r_in < r_max");
+    if (ctx->g.n2t != ctx->g.n2)
+        return fail(ctx, GRMHD_EINVAL, "a theta slab takes its state from set_state (the torus is normalised over the whole grid)");
     Grid &g = ctx->g;
     TorusArgs ta{};
     ta.a = ctx->a;
@@ -428,6 +440,8 @@ extern "C" int grmhd_step(grmhd_ctx *ctx, int nsteps)
     if (nsteps < 0) return fail(ctx, GRMHD_EINVAL, "nsteps < 0");
     if (ctx->g.bc3 == BC_EXTERNAL)
         return fail(ctx, GRMHD_EINVAL, "a phi slab steps by grmhd_stage with its ghost planes exchanged between stages");
+    if (ctx->g.n2t != ctx->g.n2)
+        return fail(ctx, GRMHD_EINVAL, "a theta slab steps by the stage parts with its rows exchanged");
     (void)cudaGetLastError();
     if (!ctx->gexec) {
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -1103,6 +1117,8 @@ extern "C" int grmhd_stage(grmhd_ctx *ctx, int st)
     if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
     if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "stage needs a state (init_torus or set_state)");
     if (st != 0 && st != 1) return fail(ctx, GRMHD_EINVAL, "st must be 0 or 1");
+    if (ctx->g.n2t != ctx->g.n2)
+        return fail(ctx, GRMHD_EINVAL, "a theta slab steps by the stage parts (its fixups exchange rows)");
     (void)cudaGetLastError();
     launch_stage(ctx->g, st, ctx->stream);
     CK(cudaGetLastError());
@@ -1154,6 +1170,91 @@ extern "C" int grmhd_x3_pack(grmhd_ctx *ctx, int which, int side, void *buf_dev)
 extern "C" int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev)
 {
     return x3_planes(ctx, which, side, const_cast<void *>(buf_dev), 1);
+}
+
+// ----------------------------------------------------------- theta slabs
+
+static int theta_check(grmhd_ctx *ctx, int st)
+{
+    if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "a stage needs a state (set_state)");
+    if (st != 0 && st != 1) return fail(ctx, GRMHD_EINVAL, "st must be 0 or 1");
+    if (ctx->g.n2t == ctx->g.n2) return fail(ctx, GRMHD_EINVAL, "not a theta slab (n2_total)");
+    (void)cudaGetLastError();
+    return 0;
+}
+
+extern "C" int grmhd_stage_update(grmhd_ctx *ctx, int st)
+{
+    if (int rc = theta_check(ctx, st)) return rc;
+    launch_stage_update(ctx->g, st, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_fail_count(grmhd_ctx *ctx, long long *acc_dev)
+{
+    if (int rc = theta_check(ctx, 0)) return rc;
+    if (!acc_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    launch_fail_count(ctx->g, acc_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_fix_sweep(grmhd_ctx *ctx, int st, long long *acc_dev)
+{
+    if (int rc = theta_check(ctx, st)) return rc;
+    if (!acc_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    launch_fix_sweep(ctx->g, st, acc_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_fix_end(grmhd_ctx *ctx, int st, int nsweeps)
+{
+    if (int rc = theta_check(ctx, st)) return rc;
+    if (nsweeps < 0) return fail(ctx, GRMHD_EINVAL, "nsweeps < 0");
+    launch_fix_end(ctx->g, nsweeps, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_stage_bc(grmhd_ctx *ctx, int st)
+{
+    if (int rc = theta_check(ctx, st)) return rc;
+    launch_bc(ctx->g, st == 0 ? 1 : 0, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_x2_row_bytes(grmhd_ctx *ctx, int kind, unsigned long long *bytes)
+{
+    if (!ctx || !bytes) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (kind != 0 && kind != 1) return fail(ctx, GRMHD_EINVAL, "kind must be 0 or 1");
+    *bytes = (unsigned long long)x2_row_elems(ctx->g, kind) * (ctx->g.mixed ? sizeof(float) : sizeof(double));
+    return 0;
+}
+
+static int x2_rows(grmhd_ctx *ctx, int kind, int which, int side, void *buf, int unpack)
+{
+    if (!ctx || !buf) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if ((kind != 0 && kind != 1) || (which != 0 && which != 1) || (side != 0 && side != 1))
+        return fail(ctx, GRMHD_EINVAL, "kind, which and side must be 0 or 1");
+    if (ctx->g.n2t == ctx->g.n2) return fail(ctx, GRMHD_EINVAL, "not a theta slab (n2_total)");
+    (void)cudaGetLastError();
+    launch_x2_rows(ctx->g, kind, which, side, buf, unpack, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_x2_pack(grmhd_ctx *ctx, int kind, int which, int side, void *buf_dev)
+{
+    return x2_rows(ctx, kind, which, side, buf_dev, 0);
+}
+
+extern "C" int grmhd_x2_unpack(grmhd_ctx *ctx, int kind, int which, int side, const void *buf_dev)
+{
+    return x2_rows(ctx, kind, which, side, const_cast<void *>(buf_dev), 1);
 }
 
 // ------------------------------------------------------ disk diagnostics

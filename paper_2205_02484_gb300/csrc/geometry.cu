@@ -96,7 +96,8 @@ __global__ void k_geometry(Grid g, GeomBuild b)
     if (t >= g.N1 * g.N2) return;
     int i = t / g.N2 - NG, j = t % g.N2 - NG;
     double X1c = g.x1in + (i + 0.5) * g.dx[0], X1f = g.x1in + i * g.dx[0];
-    double X2c = g.x2in + (j + 0.5) * g.dx[1], X2f = g.x2in + j * g.dx[1];
+    const int jg = g.j0 + j; // the row in the whole grid (a theta slab's rows sit at their global X2)
+    double X2c = g.x2in + (jg + 0.5) * g.dx[1], X2f = g.x2in + jg * g.dx[1];
     double gi[4][4];
     make_geo(b.cp, X1c, X2c, b.gc[t], b.gcF[t], gi);
     {
@@ -127,7 +128,7 @@ __global__ void k_geometry(Grid g, GeomBuild b)
                 b.connF[(long long)t * 40 + l * 10 + sym(m, n)] = (float)(0.5 * s);
             }
     make_geo(b.cp, X1f, X2c, b.gf1[t], b.gf1F[t], gi);
-    bool polar = b.cp.metric == KERR_MKS && (j == 0 || j == g.n2);
+    bool polar = b.cp.metric == KERR_MKS && (jg == 0 || jg == g.n2t);
     b.polar2[t] = polar;
     if (polar) {
         Geo<double> z{};

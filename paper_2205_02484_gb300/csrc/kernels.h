@@ -17,6 +17,12 @@ void launch_step_dtd(const Grid &g, double *dtd, int acc, cudaStream_t s);
 void launch_finish_step(const Grid &g, const double *dtd, cudaStream_t s);
 long long x3_plane_elems(const Grid &g);
 void launch_x3_planes(const Grid &g, int which, int side, void *buf, int unpack, cudaStream_t s);
+void launch_stage_update(const Grid &g, int st, cudaStream_t s);
+void launch_fail_count(const Grid &g, long long *acc, cudaStream_t s);
+void launch_fix_sweep(const Grid &g, int st, long long *acc, cudaStream_t s);
+void launch_fix_end(const Grid &g, int nsweeps, cudaStream_t s);
+long long x2_row_elems(const Grid &g, int kind);
+void launch_x2_rows(const Grid &g, int kind, int which, int side, void *buf, int unpack, cudaStream_t s);
 void launch_fluxes_dt(const Grid &g, int set_dt, cudaStream_t s);
 void launch_gather_fluxes(const Grid &g, double *out, cudaStream_t s);
 

@@ -13,7 +13,7 @@
 //                                   (Eqs. 25-26) with FP64 accumulation, FP64
 //                                   inversion (Section 2.3), floors/ceilings/cap
 //                                   (Section 2.4); failed zones are compacted
-//   fixups (Eq. 33)              -> fixup_block: Jacobi sweeps over the list (one block)
+//   fixups (Eq. 33)              -> fixup_block / fixup_sweep: Jacobi sweeps over the list (one block)
 //   dt                           -> finalize_one
 //
 // R is the flux arithmetic type (double, or float in the mixed path), which is
@@ -44,9 +44,21 @@ __host__ __device__ inline Box flux_box(const Grid &g, int d)
 }
 __host__ __device__ inline Box edge_box(const Grid &g) { return Box{{0, 0, 0}, {g.n1 + 1, g.n2 + 1, g.n3 + 1}}; }
 __host__ __device__ inline long long nact_of(const Grid &g) { return (long long)g.n1 * g.n2 * g.n3; }
+// a theta slab holds the whole grid's low / high pole rows
+__host__ __device__ inline bool has_pole_lo(const Grid &g) { return g.j0 == 0; }
+__host__ __device__ inline bool has_pole_hi(const Grid &g) { return g.j0 + g.n2 == g.n2t; }
+// the X2 ghost rows of a side come from the caller: a theta slab's side
+// inside the grid, or a periodic side of the whole grid
+__host__ __device__ inline bool x2_external(const Grid &g, int side)
+{
+    if (g.n2t == g.n2) return false;
+    if (!(side == 0 ? has_pole_lo(g) : has_pole_hi(g))) return true;
+    return g.metric != KERR_MKS && g.bc2 == BC_PERIODIC;
+}
 __host__ __device__ inline long long polar_count(const Grid &g)
 {
-    return (g.metric == KERR_MKS && g.n2 >= 6) ? (long long)g.n1 * g.n3 : 0;
+    return (g.metric == KERR_MKS && g.n2t >= 6 && (has_pole_lo(g) || has_pole_hi(g))) ? (long long)g.n1 * g.n3
+                                                                                       : 0;
 }
 __host__ __device__ inline long long bc1_count(const Grid &g) { return (long long)g.n2 * g.n3 * NG * 2; }
 __host__ __device__ inline long long bc2_count(const Grid &g) { return (long long)(g.n1 + 2 * NG) * g.n3 * NG * 2; }
@@ -117,11 +129,16 @@ __device__ __forceinline__ void polar_item(const Grid &g, RS *P, long long t)
     if (t >= polar_count(g)) return;
     int i = (int)(t / g.n3), k = (int)(t % g.n3);
     const long long f = (long long)KU2 * g.nz;
-    RS a = P[f + zidx(g, i, 2, k)], b = P[f + zidx(g, i, g.n2 - 3, k)];
-    P[f + zidx(g, i, 0, k)] = a * RS(0.5 / 2.5);
-    P[f + zidx(g, i, 1, k)] = a * RS(1.5 / 2.5);
-    P[f + zidx(g, i, g.n2 - 1, k)] = b * RS(0.5 / 2.5);
-    P[f + zidx(g, i, g.n2 - 2, k)] = b * RS(1.5 / 2.5);
+    if (has_pole_lo(g)) {
+        RS a = P[f + zidx(g, i, 2, k)];
+        P[f + zidx(g, i, 0, k)] = a * RS(0.5 / 2.5);
+        P[f + zidx(g, i, 1, k)] = a * RS(1.5 / 2.5);
+    }
+    if (has_pole_hi(g)) {
+        RS b = P[f + zidx(g, i, g.n2 - 3, k)];
+        P[f + zidx(g, i, g.n2 - 1, k)] = b * RS(0.5 / 2.5);
+        P[f + zidx(g, i, g.n2 - 2, k)] = b * RS(1.5 / 2.5);
+    }
 }
 
 // u^1 = 0 at fixed ut^2, ut^3: ut^1 = Gamma alpha g^{t1}, Gamma from its quadratic
@@ -179,6 +196,7 @@ __device__ __forceinline__ void bc2_item(const Grid &g, RS *P, long long t)
     int gh = 1 + (int)(r % NG);
     r /= NG;
     int k = (int)(r % g.n3), i = (int)(r / g.n3) - NG;
+    if (x2_external(g, side)) return; // a theta slab's inner side: the neighbour's rows
     int bc = g.metric == KERR_MKS ? BC_POLAR : g.bc2;
     int jd = side == 0 ? -gh : g.n2 - 1 + gh;
     int js;
@@ -745,106 +763,128 @@ __device__ __forceinline__ void flush_counts(const Grid &g, const UpdCount &cn)
 
 // ------------------------------------------------------------------ fixups
 
-// One block walks the compacted list of failed zones of one grid.  Each
-// sweep first computes every repairable zone's average from neighbours that
-// were good at the start of the sweep, then writes them (Jacobi), so the
-// result does not depend on the list order.  Every thread of the block calls it.
+// a fixup neighbour (ii, jj) must be an active zone of the whole grid; a
+// theta slab reads the rows jj = -1 and n2 from its ghost rows, which hold the
+// neighbour slab's current edge rows (primitives and flags) during its fixups
+__device__ __forceinline__ bool fix_inside(const Grid &g, int ii, int jj)
+{
+    const int jg = g.j0 + jj;
+    return ii >= 0 && ii < g.n1 && jg >= 0 && jg < g.n2t;
+}
+
+// One Jacobi sweep of the fixups by one block over the compacted list of
+// failed zones (nlist entries) of one grid: every repairable zone's average
+// is formed from neighbours that were good at the start of the sweep, then
+// all are written, so the result does not depend on the list order.  Every
+// thread of the block calls it and gets the number of zones still failed.
+// Out of line, so that the single-grid, ensemble and theta-slab kernels run
+// the same machine code (inlined, the compiler may contract or schedule the
+// FP64 arithmetic differently in each).
 template <typename R>
-__device__ inline void fixup_block(const Grid &g, R *P, int corr)
+__device__ __noinline__ int fixup_sweep(const Grid &g, R *P, int corr, int nlist)
 {
     __shared__ int s_left;
-    const int nlist = min(*g.nfail, g.nfix_cap);
-    if (nlist == 0) return;
     const long long nz = g.nz;
     const int cap = g.nfix_cap;
     double *nb = g.fixbuf;            // [5][cap]
     double *found = g.fixbuf + 5LL * cap;
-    int sweep = 0;
-    for (; sweep < g.fix_maxsweep; sweep++) {
-        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
-            int t = g.faillist[a];
-            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
-            found[a] = 0.0;
-            if (!g.flag[zidx(g, i, j, k)]) continue;
-            const int fo[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
-            const int dg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
-            bool done = false;
-            for (int s = 0; s < 2 && !done; s++) {
-                const int(*set)[2] = s == 0 ? fo : dg;
-                bool all = true;
+    for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+        int t = g.faillist[a];
+        int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
+        found[a] = 0.0;
+        if (!g.flag[zidx(g, i, j, k)]) continue;
+        const int fo[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+        const int dg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
+        bool done = false;
+        for (int s = 0; s < 2 && !done; s++) {
+            const int(*set)[2] = s == 0 ? fo : dg;
+            bool all = true;
+            for (int mm = 0; mm < 4; mm++) {
+                int ii = i + set[mm][0], jj = j + set[mm][1];
+                if (!fix_inside(g, ii, jj) || g.flag[zidx(g, ii, jj, k)]) all = false;
+            }
+            if (all) {
+                for (int c = 0; c < 5; c++) {
+                    double acc = 0.0;
+                    for (int mm = 0; mm < 4; mm++)
+                        acc += (double)P[c * nz + zidx(g, i + set[mm][0], j + set[mm][1], k)];
+                    nb[(long long)c * cap + a] = 0.25 * acc;
+                }
+                done = true;
+            }
+        }
+        if (!done) {
+            int cnt = 0;
+            double acc[5] = {0, 0, 0, 0, 0};
+            for (int s = 0; s < 2; s++)
                 for (int mm = 0; mm < 4; mm++) {
-                    int ii = i + set[mm][0], jj = j + set[mm][1];
-                    if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2 || g.flag[zidx(g, ii, jj, k)]) all = false;
+                    int ii = i + (s ? dg : fo)[mm][0], jj = j + (s ? dg : fo)[mm][1];
+                    if (!fix_inside(g, ii, jj)) continue;
+                    long long zz = zidx(g, ii, jj, k);
+                    if (g.flag[zz]) continue;
+                    for (int c = 0; c < 5; c++) acc[c] += (double)P[c * nz + zz];
+                    cnt++;
                 }
-                if (all) {
-                    for (int c = 0; c < 5; c++) {
-                        double acc = 0.0;
-                        for (int mm = 0; mm < 4; mm++)
-                            acc += (double)P[c * nz + zidx(g, i + set[mm][0], j + set[mm][1], k)];
-                        nb[(long long)c * cap + a] = 0.25 * acc;
-                    }
-                    done = true;
-                }
-            }
-            if (!done) {
-                int cnt = 0;
-                double acc[5] = {0, 0, 0, 0, 0};
-                for (int s = 0; s < 2; s++)
-                    for (int mm = 0; mm < 4; mm++) {
-                        int ii = i + (s ? dg : fo)[mm][0], jj = j + (s ? dg : fo)[mm][1];
-                        if (ii < 0 || ii >= g.n1 || jj < 0 || jj >= g.n2) continue;
-                        long long zz = zidx(g, ii, jj, k);
-                        if (g.flag[zz]) continue;
-                        for (int c = 0; c < 5; c++) acc[c] += (double)P[c * nz + zz];
-                        cnt++;
-                    }
-                if (cnt > 0) {
-                    for (int c = 0; c < 5; c++) nb[(long long)c * cap + a] = acc[c] / cnt;
-                    done = true;
-                }
-            }
-            if (done) found[a] = 1.0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_left = 0;
-        __syncthreads();
-        int left = 0;
-        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
-            int t = g.faillist[a];
-            int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
-            long long z = zidx(g, i, j, k);
-            if (found[a] != 0.0) {
-                int m = midx(g, i, j);
-                const Geo<double> geo = g.gc[m];
-                double q[NP];
-                for (int c = 0; c < NP; c++) q[c] = c < 5 ? nb[(long long)c * cap + a] : (double)P[c * nz + z];
-                post_fixup(g, geo, q);
-                for (int c = 0; c < NP; c++) P[c * nz + z] = (R)q[c];
-                if (corr) {
-                    St<double> s;
-                    get_state(q, geo, s);
-                    double Uz[NU];
-                    prim_to_UF<double, false>(q, geo, s, g.gam, 0, Uz);
-                    for (int c = 0; c < NU; c++) g.U[c * nz + z] = Uz[c];
-                }
-                g.flag[z] = 0;
-                atomicAdd(&g.cnt[C_FIXED], 1ULL);
-            } else if (g.flag[z]) {
-                left++;
+            if (cnt > 0) {
+                for (int c = 0; c < 5; c++) nb[(long long)c * cap + a] = acc[c] / cnt;
+                done = true;
             }
         }
-        __syncthreads(); // all flag writes of this sweep done before the next reads
-        if (left) atomicAdd(&s_left, left);
-        __syncthreads();
-        if (s_left == 0) {
-            sweep++;
-            break;
+        if (done) found[a] = 1.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_left = 0;
+    __syncthreads();
+    int left = 0;
+    for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+        int t = g.faillist[a];
+        int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
+        long long z = zidx(g, i, j, k);
+        if (found[a] != 0.0) {
+            int m = midx(g, i, j);
+            const Geo<double> geo = g.gc[m];
+            double q[NP];
+            for (int c = 0; c < NP; c++) q[c] = c < 5 ? nb[(long long)c * cap + a] : (double)P[c * nz + z];
+            post_fixup(g, geo, q);
+            for (int c = 0; c < NP; c++) P[c * nz + z] = (R)q[c];
+            if (corr) {
+                St<double> s;
+                get_state(q, geo, s);
+                double Uz[NU];
+                prim_to_UF<double, false>(q, geo, s, g.gam, 0, Uz);
+                for (int c = 0; c < NU; c++) g.U[c * nz + z] = Uz[c];
+            }
+            g.flag[z] = 0;
+            atomicAdd(&g.cnt[C_FIXED], 1ULL);
+        } else if (g.flag[z]) {
+            left++;
         }
-        __syncthreads();
+    }
+    __syncthreads(); // all flag writes of this sweep done before the next reads
+    if (left) atomicAdd(&s_left, left);
+    __syncthreads();
+    const int total = s_left;
+    __syncthreads(); // every thread has read s_left before a next sweep resets it
+    return total;
+}
+
+// The fixups of a stage on one grid: sweeps until no listed zone is left
+// failed, at most fix_maxsweep of them; then the sweep count, the status and
+// the list reset.  Every thread of the block calls it.
+template <typename R>
+__device__ inline void fixup_block(const Grid &g, R *P, int corr)
+{
+    const int nlist = min(*g.nfail, g.nfix_cap);
+    if (nlist == 0) return;
+    int sweep = 0, left = 1;
+    while (sweep < g.fix_maxsweep) {
+        left = fixup_sweep<R>(g, P, corr, nlist);
+        sweep++;
+        if (left == 0) break;
     }
     if (threadIdx.x == 0) {
         atomicAdd(&g.cnt[C_SWEEPS], (unsigned long long)sweep);
-        if (s_left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
+        if (left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
         *g.nfail = 0;
     }
 }
@@ -879,7 +919,6 @@ static __device__ __noinline__ void update_item_d(const Grid &g, const double *P
     update_item<double>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
 }
 static __device__ __noinline__ void bc1_item_d(const Grid &g, double *P, long long t) { bc1_item<double>(g, P, t); }
-static __device__ __noinline__ void fixup_block_d(const Grid &g, double *P, int corr) { fixup_block<double>(g, P, corr); }
 
 // the flux element of direction D: a column of faces along X1 / X2, one face
 // along X3; box = flux_elem_box(g, D)
@@ -917,8 +956,7 @@ __device__ __forceinline__ void bc1_call(const Grid &g, R *P, long long t)
 template <typename R>
 __device__ __forceinline__ void fixup_call(const Grid &g, R *P, int corr)
 {
-    if constexpr (sizeof(R) == 8) fixup_block_d(g, P, corr);
-    else fixup_block<R>(g, P, corr);
+    fixup_block<R>(g, P, corr);
 }
 
 // --------------------------------------------------------------------- dt

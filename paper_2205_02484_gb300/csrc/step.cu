@@ -217,6 +217,116 @@ __global__ void k_x3_planes(Grid g, R *P, R *buf, int base, int unpack)
 
 long long x3_plane_elems(const Grid &g) { return (long long)NG * NP * g.N1 * g.N2; }
 
+// ------------------------------------------------------------ theta slabs
+
+// stage st of a theta slab up to its fixups (parts 0-4 of stage_part)
+void launch_stage_update(const Grid &g, int st, cudaStream_t s)
+{
+    int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
+    double fac = st == 0 ? 0.5 : 1.0;
+    for (int part = 0; part < 5; part++) {
+        if (g.mixed) stage_part<float>(g, part, src, dst, fac, st, st == 0, s);
+        else stage_part<double>(g, part, src, dst, fac, st, st == 0, s);
+    }
+}
+
+__global__ void k_fail_count(Grid g, long long *acc)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *g.nfail > 0)
+        atomicAdd((unsigned long long *)acc, (unsigned long long)*g.nfail);
+}
+
+void launch_fail_count(const Grid &g, long long *acc, cudaStream_t s) { k_fail_count<<<1, 32, 0, s>>>(g, acc); }
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_fix_sweep(Grid g, R *P, int corr, long long *acc)
+{
+    const int nlist = min(*g.nfail, g.nfix_cap);
+    if (nlist == 0) return;
+    const int left = fixup_sweep<R>(g, P, corr, nlist);
+    if (threadIdx.x == 0 && left > 0) atomicAdd((unsigned long long *)acc, (unsigned long long)left);
+}
+
+void launch_fix_sweep(const Grid &g, int st, long long *acc, cudaStream_t s)
+{
+    int dst = st == 0 ? 1 : 0;
+    if (g.mixed) k_fix_sweep<float><<<1, 1024, 0, s>>>(g, (float *)g.P[dst], st, acc);
+    else k_fix_sweep<double><<<1, 1024, 0, s>>>(g, (double *)g.P[dst], st, acc);
+}
+
+// close a theta slab's fixups: the sweeps its decomposed loop ran, the status
+// if a listed zone is still failed (or the list overflowed), the list reset
+__global__ void __launch_bounds__(256) k_fix_end(Grid g, int nsweeps)
+{
+    __shared__ int s_left;
+    if (threadIdx.x == 0) s_left = 0;
+    __syncthreads();
+    const int nlist = min(*g.nfail, g.nfix_cap);
+    int left = 0;
+    for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+        int t = g.faillist[a];
+        int k = t % g.n3, r = t / g.n3, j = r % g.n2, i = r / g.n2;
+        left += g.flag[zidx(g, i, j, k)] != 0;
+    }
+    if (left) atomicAdd(&s_left, left);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&g.cnt[C_SWEEPS], (unsigned long long)nsweeps); // every slab counts the common rounds
+        if (s_left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
+        *g.nfail = 0;
+    }
+}
+
+void launch_fix_end(const Grid &g, int nsweeps, cudaStream_t s) { k_fix_end<<<1, 256, 0, s>>>(g, nsweeps); }
+
+__host__ __device__ inline long long x2_row_count(const Grid &g, int kind)
+{
+    return kind == 0 ? (long long)NG * NP * g.N1 * g.N3 : 6LL * g.n1 * g.n3;
+}
+
+long long x2_row_elems(const Grid &g, int kind) { return x2_row_count(g, kind); }
+
+// X2 rows: kind 0 packs / unpacks rows base .. base+NG-1 as [NG][8][N1][N3];
+// kind 1 row base as [6][n1][n3], the five averaged primitives and the flag
+template <typename R>
+__global__ void k_x2_rows(Grid g, R *P, R *buf, int kind, int base, int unpack)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= x2_row_count(g, kind)) return;
+    if (kind == 0) {
+        long long plane = (long long)g.N1 * g.N3;
+        long long e = t % plane;
+        int c = (int)((t / plane) % NP), gl = (int)(t / (plane * NP));
+        int i = (int)(e / g.N3) - NG, k = (int)(e % g.N3) - NG;
+        long long z = c * g.nz + zidx(g, i, base + gl, k);
+        if (unpack) P[z] = buf[t];
+        else buf[t] = P[z];
+        return;
+    }
+    long long plane = (long long)g.n1 * g.n3;
+    long long e = t % plane;
+    int c = (int)(t / plane);
+    int i = (int)(e / g.n3), k = (int)(e % g.n3);
+    long long z = zidx(g, i, base, k);
+    if (c < 5) {
+        if (unpack) P[c * g.nz + z] = buf[t];
+        else buf[t] = P[c * g.nz + z];
+    } else {
+        if (unpack) g.flag[z] = buf[t] != R(0) ? 1 : 0;
+        else buf[t] = g.flag[z] ? R(1) : R(0);
+    }
+}
+
+void launch_x2_rows(const Grid &g, int kind, int which, int side, void *buf, int unpack, cudaStream_t s)
+{
+    const int n = kind == 0 ? NG : 1;
+    int base = unpack ? (side == 0 ? -n : g.n2) : (side == 0 ? 0 : g.n2 - n);
+    long long ne = x2_row_elems(g, kind);
+    unsigned nb = (unsigned)((ne + 255) / 256);
+    if (g.mixed) k_x2_rows<float><<<nb, 256, 0, s>>>(g, (float *)g.P[which], (float *)buf, kind, base, unpack);
+    else k_x2_rows<double><<<nb, 256, 0, s>>>(g, (double *)g.P[which], (double *)buf, kind, base, unpack);
+}
+
 void launch_x3_planes(const Grid &g, int which, int side, void *buf, int unpack, cudaStream_t s)
 {
     int base = unpack ? (side == 0 ? -NG : g.n3) : (side == 0 ? 0 : g.n3 - NG);

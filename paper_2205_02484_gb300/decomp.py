@@ -113,7 +113,7 @@ class CtxSlab:
 
 
 _SUMMED = ("mdot", "phib", "edot", "ldot", "nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta",
-           "n_fail", "n_floor", "n_ceil", "n_gcap", "n_fixed", "fix_sweeps")
+           "n_fail", "n_floor", "n_ceil", "n_gcap", "n_fixed")
 
 
 def combine_diagnostics(parts):
@@ -127,6 +127,9 @@ def combine_diagnostics(parts):
     for k in _SUMMED:
         out[k] = type(parts[0][k])(sum(p[k] for p in parts))
     out["divb_max"] = max(p["divb_max"] for p in parts)
+    # theta slabs all count the sweeps their common loop ran (the whole
+    # grid's count); phi slabs sweep each on their own (the largest count)
+    out["fix_sweeps"] = max(p["fix_sweeps"] for p in parts)
     out["PhiB"] = out["phib"] / math.sqrt(abs(out["mdot"])) if out["mdot"] != 0.0 else 0.0
     out["eta"] = (out["edot"] - out["mdot"]) / abs(out["mdot"]) if out["mdot"] != 0.0 else 0.0
     out["disk_mass"] = out["disk_eb"] = 0.0  # set by the torus setup only
@@ -277,4 +280,311 @@ class SlabRank:
         return _bary(parts)
 
 
-__all__ = ["NG", "slab_grid", "split_phi", "combine_diagnostics", "CtxSlab", "SlabRing", "SlabRank"]
+# ------------------------------------------------------------ theta slabs
+#
+# The split of the paper's multi-GPU runs (Section 3) in theta, for
+# axisymmetric grids (n3 = 1), which cannot be split in phi.  Slab r of R owns
+# the active rows [r n2/R, (r+1) n2/R) of the whole grid (grid parameters j0,
+# n2_total) and builds the metric of its own rows from their global X2
+# positions, so its tables are bit for bit the whole grid's.  One step:
+#   for each stage st (Eq. 25, then Eq. 26):
+#     1. every slab runs the fluxes, flux-CT, update and inversion;
+#     2. fixups (Eq. 33): while some slab has a failed zone and fewer than
+#        fix_maxsweep sweeps ran, exchange the edge rows that a sweep reads
+#        across a slab face (five primitives and the failure flags), then
+#        run one sweep on every slab;
+#     3. every slab fills its own boundaries (poles, radial), then the NG = 2
+#        ghost rows of its inner sides are exchanged;
+#   the CFL minima of the predictor are reduced as for phi slabs.
+# Every value a slab reads across its faces is the one the whole grid reads
+# there, so the decomposed step is the undecomposed one bit for bit.
+
+
+def theta_grid(base: G.GridParams, R: int, r: int) -> G.GridParams:
+    """Grid parameters of theta slab r of R (n2 / R rows starting at row
+    r n2 / R of the whole grid; at least 4 rows)."""
+    if R < 1 or base.n2 % R:
+        raise ValueError(f"n2 = {base.n2} does not split into {R} slabs")
+    n2 = base.n2 // R
+    if n2 < 4:
+        raise ValueError(f"theta slabs of {n2} < 4 rows")
+    g = G.GridParams.from_buffer_copy(base)
+    g.n2, g.j0, g.n2_total = n2, r * n2, base.n2
+    return g
+
+
+def split_theta(x, R: int, r: int):
+    """Slab r's part of a (fields, n1, n2, n3) array (numpy or torch), contiguous."""
+    n2 = x.shape[2] // R
+    part = x[:, :, r * n2:(r + 1) * n2]
+    return part.contiguous() if isinstance(x, torch.Tensor) else part.copy(order="C")
+
+
+class CtxTheta:
+    """ThetaEngine over one grmhd context that is a theta slab.  Every call
+    is asynchronous on the context's stream (`stream`)."""
+
+    def __init__(self, ctx: G.Context, stream: torch.cuda.Stream):
+        if not (ctx.grid.n2_total > ctx.grid.n2):
+            raise ValueError("a theta slab context needs n2_total > n2")
+        self.ctx = ctx
+        self.stream = stream
+        self.device = torch.device("cuda", ctx.grid.device)
+        self.dtype = torch.float64 if ctx.grid.precision == G.FP64 else torch.float32
+        esz = 8 if self.dtype == torch.float64 else 4
+        self.row_numel = G.x2_row_bytes(ctx, 0) // esz
+        self.fix_numel = G.x2_row_bytes(ctx, 1) // esz
+        self.fix_maxsweep = ctx.phys.fix_maxsweep
+
+    @classmethod
+    def create(cls, grid: G.GridParams, phys: G.PhysParams, a: float, stream: torch.cuda.Stream):
+        g = G.GridParams.from_buffer_copy(grid)
+        g.stream = stream.cuda_stream
+        ctx = G.init_grid(g, phys)
+        G.set_metric(ctx, a, g.metric)
+        return cls(ctx, stream)
+
+    def set_state(self, P, U, t, dt):
+        G.set_state(self.ctx, P, U, t, dt)
+
+    def get_state(self):
+        return G.get_state(self.ctx)
+
+    def diagnostics(self):
+        return G.diagnostics(self.ctx)
+
+    def barycentric_sums(self, r_bar_max):
+        _, den, num = G.barycentric_radius(self.ctx, r_bar_max)
+        return num, den
+
+    def stage_update(self, st):
+        G.stage_update(self.ctx, st)
+
+    def dtd(self, out, accumulate=False):
+        G.step_dtd(self.ctx, out, accumulate)
+
+    def fail_count(self, acc):
+        G.fail_count(self.ctx, acc)
+
+    def fix_sweep(self, st, acc):
+        G.fix_sweep(self.ctx, st, acc)
+
+    def fix_end(self, st, nsweeps):
+        G.fix_end(self.ctx, st, nsweeps)
+
+    def stage_bc(self, st):
+        G.stage_bc(self.ctx, st)
+
+    def finish(self, dtd):
+        G.finish_step(self.ctx, dtd)
+
+    def pack(self, kind, which, side, buf):
+        G.x2_pack(self.ctx, kind, which, side, buf)
+
+    def unpack(self, kind, which, side, buf):
+        G.x2_unpack(self.ctx, kind, which, side, buf)
+
+    def close(self):
+        self.ctx.close()
+
+
+def _theta_sides(R: int, r: int, periodic: bool):
+    """(low, high) neighbour slab of slab r, None at a pole or closed side."""
+    lo = (r - 1) % R if (r > 0 or periodic) else None
+    hi = (r + 1) % R if (r < R - 1 or periodic) else None
+    return lo, hi
+
+
+class ThetaRing:
+    """All theta slabs of one grid on one device, in theta order, sharing one
+    stream.  `periodic`: the whole grid is periodic in X2 (a flat box), so
+    the first and last slabs are neighbours."""
+
+    ROWS, FIX = 0, 1  # the two exchanges: NG ghost rows, a fixup sweep's edge row
+
+    def __init__(self, engines, periodic: bool = False):
+        self.e = list(engines)
+        self.periodic = periodic
+        e0 = self.e[0]
+        R = len(self.e)
+        self.nb = [_theta_sides(R, r, periodic) for r in range(R)]
+        mk = lambda n: [torch.empty(n, dtype=e.dtype, device=e.device) for e in self.e]
+        self.buf = {self.ROWS: (mk(e0.row_numel), mk(e0.row_numel)),
+                    self.FIX: (mk(e0.fix_numel), mk(e0.fix_numel))}
+        self.dtd_buf = torch.empty(3, dtype=torch.float64, device=e0.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=e0.device)
+        self.fix_maxsweep = e0.fix_maxsweep
+        self.sweeps = []  # fixup sweeps of each stage of the last step
+
+    @classmethod
+    def create(cls, grid: G.GridParams, phys: G.PhysParams, R: int, a: float, stream=None, periodic=False):
+        stream = stream or torch.cuda.Stream(device=grid.device)
+        return cls([CtxTheta.create(theta_grid(grid, R, r), phys, a, stream) for r in range(R)], periodic)
+
+    def set_state(self, P, U, t, dt):
+        R = len(self.e)
+        for r, e in enumerate(self.e):
+            with _stream_of(e):
+                e.set_state(split_theta(P, R, r), split_theta(U, R, r), t, dt)
+        self.exchange(self.ROWS, 0)
+
+    def exchange(self, kind, which):
+        """Pack every slab's edge rows, then unpack each into its
+        neighbours' ghost rows (one stream, so ordered)."""
+        lo, hi = self.buf[kind]
+        for r, e in enumerate(self.e):
+            e.pack(kind, which, 0, lo[r])
+            e.pack(kind, which, 1, hi[r])
+        for r, e in enumerate(self.e):
+            left, right = self.nb[r]
+            if left is not None:
+                e.unpack(kind, which, 0, hi[left])
+            if right is not None:
+                e.unpack(kind, which, 1, lo[right])
+
+    def _count(self, fn):
+        self.count.zero_()
+        for e in self.e:
+            fn(e)
+        return int(self.count.item())
+
+    def step(self, nsteps=1):
+        with _stream_of(self.e[0]):
+            for _ in range(nsteps):
+                self.sweeps = []
+                for st in (0, 1):
+                    out = 1 if st == 0 else 0  # the stage's output buffer
+                    for r, e in enumerate(self.e):
+                        e.stage_update(st)
+                        if st == 0:
+                            e.dtd(self.dtd_buf, accumulate=r > 0)
+                    left = self._count(lambda e: e.fail_count(self.count))
+                    n = 0
+                    while left > 0 and n < self.fix_maxsweep:
+                        self.exchange(self.FIX, out)
+                        left = self._count(lambda e: e.fix_sweep(st, self.count))
+                        n += 1
+                    self.sweeps.append(n)
+                    for e in self.e:
+                        e.fix_end(st, n)
+                        e.stage_bc(st)
+                    self.exchange(self.ROWS, out)
+                for e in self.e:
+                    e.finish(self.dtd_buf)
+
+    def diagnostics(self):
+        return combine_diagnostics([e.diagnostics() for e in self.e])
+
+    def barycentric_radius(self, r_bar_max=80.0):
+        return _bary([e.barycentric_sums(r_bar_max) for e in self.e])
+
+    def close(self):
+        for e in self.e:
+            e.close()
+
+
+class ThetaRank:
+    """This process's theta slab of a grid split over the ranks of a
+    process group, rank r owning slab r.  Edge rows travel by send/recv
+    (tags by direction, as for phi slabs); the failure counts that decide
+    the fixup sweeps and the CFL minima are all-reduced (SUM, MIN)."""
+
+    TAG_UP, TAG_DOWN = 3, 4
+
+    def __init__(self, engine, group=None, periodic: bool = False):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.e = engine
+        self.rank = dist.get_rank(group)
+        self.R = dist.get_world_size(group)
+        lo, hi = _theta_sides(self.R, self.rank, periodic)
+        if group is not None:
+            lo = dist.get_global_rank(group, lo) if lo is not None else None
+            hi = dist.get_global_rank(group, hi) if hi is not None else None
+        self.left, self.right = lo, hi
+        mk = lambda n: torch.empty(n, dtype=engine.dtype, device=engine.device)
+        self.buf = {k: (mk(n), mk(n), mk(n), mk(n))
+                    for k, n in ((ThetaRing.ROWS, engine.row_numel), (ThetaRing.FIX, engine.fix_numel))}
+        self.dtd_buf = torch.empty(3, dtype=torch.float64, device=engine.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=engine.device)
+        self.fix_maxsweep = engine.fix_maxsweep
+        self.sweeps = []
+
+    def set_state(self, P, U, t, dt):
+        with _stream_of(self.e):
+            self.e.set_state(split_theta(P, self.R, self.rank), split_theta(U, self.R, self.rank), t, dt)
+        self.exchange(ThetaRing.ROWS, 0)
+
+    def exchange(self, kind, which):
+        e, dist = self.e, self.dist
+        send_lo, send_hi, recv_lo, recv_hi = self.buf[kind]
+        e.pack(kind, which, 0, send_lo)
+        e.pack(kind, which, 1, send_hi)
+        if self.R == 1:  # periodic single slab: its own far rows
+            if self.left is not None:
+                e.unpack(kind, which, 0, send_hi)
+                e.unpack(kind, which, 1, send_lo)
+            return
+        ops = []
+        if self.right is not None:
+            ops.append(dist.P2POp(dist.isend, send_hi, self.right, self.group, self.TAG_UP))
+        if self.left is not None:
+            ops.append(dist.P2POp(dist.isend, send_lo, self.left, self.group, self.TAG_DOWN))
+        if self.left is not None:
+            ops.append(dist.P2POp(dist.irecv, recv_lo, self.left, self.group, self.TAG_UP))
+        if self.right is not None:
+            ops.append(dist.P2POp(dist.irecv, recv_hi, self.right, self.group, self.TAG_DOWN))
+        with _stream_of(e):
+            for req in dist.batch_isend_irecv(ops):
+                req.wait()
+        if self.left is not None:
+            e.unpack(kind, which, 0, recv_lo)
+        if self.right is not None:
+            e.unpack(kind, which, 1, recv_hi)
+
+    def _count(self, fn):
+        with _stream_of(self.e):
+            self.count.zero_()
+            fn()
+            if self.R > 1:
+                self.dist.all_reduce(self.count, op=self.dist.ReduceOp.SUM, group=self.group)
+            return int(self.count.item())
+
+    def step(self, nsteps=1):
+        e = self.e
+        for _ in range(nsteps):
+            self.sweeps = []
+            for st in (0, 1):
+                out = 1 if st == 0 else 0
+                e.stage_update(st)
+                if st == 0:
+                    e.dtd(self.dtd_buf)
+                left = self._count(lambda: e.fail_count(self.count))
+                n = 0
+                while left > 0 and n < self.fix_maxsweep:
+                    self.exchange(ThetaRing.FIX, out)
+                    left = self._count(lambda: e.fix_sweep(st, self.count))
+                    n += 1
+                self.sweeps.append(n)
+                e.fix_end(st, n)
+                e.stage_bc(st)
+                self.exchange(ThetaRing.ROWS, out)
+            if self.R > 1:
+                with _stream_of(e):
+                    self.dist.all_reduce(self.dtd_buf, op=self.dist.ReduceOp.MIN, group=self.group)
+            e.finish(self.dtd_buf)
+
+    def diagnostics(self):
+        parts = [None] * self.R
+        self.dist.all_gather_object(parts, self.e.diagnostics(), group=self.group)
+        return combine_diagnostics(parts)
+
+    def barycentric_radius(self, r_bar_max=80.0):
+        parts = [None] * self.R
+        self.dist.all_gather_object(parts, self.e.barycentric_sums(r_bar_max), group=self.group)
+        return _bary(parts)
+
+
+__all__ = ["NG", "slab_grid", "split_phi", "combine_diagnostics", "CtxSlab", "SlabRing", "SlabRank",
+           "theta_grid", "split_theta", "CtxTheta", "ThetaRing", "ThetaRank"]

@@ -43,6 +43,7 @@ class GridParams(C.Structure):
         ("x3min", C.c_double), ("x3max", C.c_double),
         ("bc1", C.c_int), ("bc2", C.c_int), ("bc3", C.c_int), ("riemann", C.c_int),
         ("precision", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+        ("j0", C.c_int), ("n2_total", C.c_int),
     ]
 
 
@@ -142,6 +143,14 @@ SIGNATURES = {
     "grmhd_x3_plane_bytes": (C.c_int, [_V, C.POINTER(C.c_ulonglong)]),
     "grmhd_x3_pack": (C.c_int, [_V, C.c_int, C.c_int, _V]),
     "grmhd_x3_unpack": (C.c_int, [_V, C.c_int, C.c_int, _V]),
+    "grmhd_stage_update": (C.c_int, [_V, C.c_int]),
+    "grmhd_fail_count": (C.c_int, [_V, _V]),
+    "grmhd_fix_sweep": (C.c_int, [_V, C.c_int, _V]),
+    "grmhd_fix_end": (C.c_int, [_V, C.c_int, C.c_int]),
+    "grmhd_stage_bc": (C.c_int, [_V, C.c_int]),
+    "grmhd_x2_row_bytes": (C.c_int, [_V, C.c_int, C.POINTER(C.c_ulonglong)]),
+    "grmhd_x2_pack": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _V]),
+    "grmhd_x2_unpack": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _V]),
 }
 
 PROF_SLOTS = 16
@@ -318,12 +327,65 @@ def x3_plane_bytes(ctx: Context) -> int:
     return n.value
 
 
+def _buf_ptr(buf, nbytes):
+    if buf.numel() * buf.element_size() < nbytes:
+        raise ValueError(f"buffer of {buf.numel() * buf.element_size()} bytes < {nbytes}")
+    return _dev_ptr(buf)
+
+
 def x3_pack(ctx: Context, which: int, side: int, buf):
-    ctx.check(ctx.L.grmhd_x3_pack(ctx.h, which, side, _dev_ptr(buf)))
+    ctx.check(ctx.L.grmhd_x3_pack(ctx.h, which, side, _buf_ptr(buf, x3_plane_bytes(ctx))))
 
 
 def x3_unpack(ctx: Context, which: int, side: int, buf):
-    ctx.check(ctx.L.grmhd_x3_unpack(ctx.h, which, side, _dev_ptr(buf)))
+    ctx.check(ctx.L.grmhd_x3_unpack(ctx.h, which, side, _buf_ptr(buf, x3_plane_bytes(ctx))))
+
+
+# ----------------------------------------------- theta slabs (stage parts)
+
+def _acc_ptr(acc):
+    import torch
+    if acc.dtype != torch.int64 or acc.numel() < 1:
+        raise ValueError("the count accumulator is one int64 on the device")
+    return _dev_ptr(acc)
+
+
+def stage_update(ctx: Context, st: int):
+    """Fluxes, flux-CT, update and inversion of stage st (up to its fixups)."""
+    ctx.check(ctx.L.grmhd_stage_update(ctx.h, st))
+
+
+def fail_count(ctx: Context, acc):
+    """Add the number of failed inversions of the last stage_update to acc (int64 on the device)."""
+    ctx.check(ctx.L.grmhd_fail_count(ctx.h, _acc_ptr(acc)))
+
+
+def fix_sweep(ctx: Context, st: int, acc):
+    """One fixup sweep (Eq. 33) of stage st; adds the zones still failed to acc."""
+    ctx.check(ctx.L.grmhd_fix_sweep(ctx.h, st, _acc_ptr(acc)))
+
+
+def fix_end(ctx: Context, st: int, nsweeps: int):
+    ctx.check(ctx.L.grmhd_fix_end(ctx.h, st, nsweeps))
+
+
+def stage_bc(ctx: Context, st: int):
+    ctx.check(ctx.L.grmhd_stage_bc(ctx.h, st))
+
+
+def x2_row_bytes(ctx: Context, kind: int) -> int:
+    """Bytes of one side's rows: kind 0 the NG ghost rows, kind 1 a fixup sweep's edge row."""
+    n = C.c_ulonglong(0)
+    ctx.check(ctx.L.grmhd_x2_row_bytes(ctx.h, kind, C.byref(n)))
+    return n.value
+
+
+def x2_pack(ctx: Context, kind: int, which: int, side: int, buf):
+    ctx.check(ctx.L.grmhd_x2_pack(ctx.h, kind, which, side, _buf_ptr(buf, x2_row_bytes(ctx, kind))))
+
+
+def x2_unpack(ctx: Context, kind: int, which: int, side: int, buf):
+    ctx.check(ctx.L.grmhd_x2_unpack(ctx.h, kind, which, side, _buf_ptr(buf, x2_row_bytes(ctx, kind))))
 
 
 def sync(ctx: Context):
