@@ -213,6 +213,69 @@ def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload
             "tiling": tiling, "tiling_from_cache": cached}
 
 
+# ----------------------------------------------- theta slabs on one GPU
+
+def run_theta_slabs(G, torch, device, n1=1024, n2=1024, steps=20, warmup=2, counts=(2, 4, 8)):
+    """An n1 x n2 axisymmetric mixed torus split into R theta slabs on one GPU
+    (decomp.ThetaRing: stage parts, X2 ghost rows and fixup edge rows through
+    device buffers, the failed-zone count read on the host once per stage and
+    once per fixup sweep), timed against the undecomposed graph step from the
+    same state, with a bitwise comparison of the final states."""
+    from paper_2205_02484_gb300.decomp import ThetaRing
+    phys = G.default_phys(gam=13.0 / 9.0)
+    gp = G.default_grid(n1, n2, 1, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
+    s = torch.cuda.Stream(device=device)
+    gp.stream = s.cuda_stream
+    full = G.init_grid(gp, phys)
+    G.set_metric(full, 0.9375, G.KERR_MKS)
+    G.init_torus(full, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
+    dev = f"cuda:{device}"
+    P0 = torch.empty((8, n1, n2, 1), dtype=torch.float64, device=dev)
+    U0 = torch.empty((9, n1, n2, 1), dtype=torch.float64, device=dev)
+    _, _, t0, dt0 = G.get_state(full, P0, U0)
+
+    def time_it(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    G.step(full, warmup)
+    ms_full = time_it(lambda: G.step(full, steps))
+    G.sync(full)
+    Pf, Uf = torch.empty_like(P0), torch.empty_like(U0)
+    G.get_state(full, Pf, Uf)
+    nfix = G.diagnostics(full)["n_fixed"]
+    full.close()
+    out = {"workload": f"{n1}x{n2}x1 FM torus (axisymmetric), mixed precision, R theta slabs on one GPU",
+           "steps": steps, "undecomposed_ms_per_step": ms_full / steps, "zones_fixed_undecomposed": nfix,
+           "slabs": {}}
+    for R in counts:
+        ring = ThetaRing.create(gp, phys, R, 0.9375, stream=s)
+        ring.set_state(P0, U0, t0, dt0)
+        ring.step(warmup)
+        ms = time_it(lambda: ring.step(steps))
+        for e in ring.e:
+            G.sync(e.ctx)
+        parts = [_slab_state(G, torch, e, dev) for e in ring.e]
+        Pr = torch.cat([p[0] for p in parts], dim=2)
+        Ur = torch.cat([p[1] for p in parts], dim=2)
+        del parts
+        out["slabs"][str(R)] = {
+            "ms_per_step": ms / steps, "vs_undecomposed": ms_full / ms,
+            "bitwise_equal_to_undecomposed": bool(torch.equal(Pr, Pf) and torch.equal(Ur, Uf)),
+            "ghost_bytes_per_slab_step": 4 * G.x2_row_bytes(ring.e[0].ctx, 0),
+            "fixup_sweeps_last_step": list(ring.sweeps),
+        }
+        del Pr, Ur
+        ring.close()
+    return out
+
+
 # ------------------------------------------------- phi slabs on one GPU
 
 def run_slabs(G, torch, device, n, steps=10, warmup=2, counts=(2, 4, 8)):
@@ -757,9 +820,10 @@ def main():
     if world == 1 and not args.no_window:
         window = run_window(G, torch, stream, local)
     # ---- the same torus as phi slabs on this GPU (the multi-GPU layout)
-    slabs = None
+    slabs = theta_slabs = None
     if world == 1 and not args.no_slabs:
         slabs = run_slabs(G, torch, local, n)
+        theta_slabs = run_theta_slabs(G, torch, local)
     # ---- the 256^3 workload's (gamma, beta_0) grid, and its FP64-vs-mixed window
     variants = window256 = None
     if world == 1 and not args.no_window:
@@ -795,6 +859,7 @@ def main():
             "ensemble": ensemble,
             "learned_start": mlp,
             "phi_slabs": slabs,
+            "theta_slabs": theta_slabs,
             "mixed_vs_fp64_window": window,
             "mixed_vs_fp64_window_256": window256,
             "variants_256": variants,
