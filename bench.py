@@ -165,51 +165,80 @@ def ensemble_specs(n=24, master_seed=2024, shapes=None):
 
 
 def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload=None):
+    """The batched ensemble against its members stepped one by one: the same
+    contexts, all on one stream, each advancing by its own step graph in turn
+    (the sequential loop); and a second set of contexts from the same draws,
+    each on its own stream, whose step graphs the GPU overlaps (the
+    concurrent loop).  All three start from the same initial states and are
+    timed over the same number of steps after the same warm-up."""
     from paper_2205_02484_gb300 import tuning
-    members = []
-    for shape, a, gam, b0, seed in ensemble_specs(n=n, shapes=shapes):
-        gp = G.default_grid(*shape, a=a, r_out=100.0, precision=G.MIXED, device=device)
-        gp.stream = stream.cuda_stream
-        c = G.init_grid(gp, G.default_phys(gam=gam))
-        G.set_metric(c, a, G.KERR_MKS)
-        G.init_torus(c, r_in=6.0, r_max=12.0, beta0=b0, pert_amp=0.04, seed=seed)
-        members.append(c)
-    zones = sum(c.nact for c in members)
-    ens = G.ensemble_create(members)
-    tiling, cached = tuning.tune_or_load(ens, torch.cuda.get_device_name(device), trial_steps=2)
+    s = torch.cuda.Stream(device=device)
+
+    def make(shared_stream):
+        out = []
+        for shape, a, gam, b0, seed in ensemble_specs(n=n, shapes=shapes):
+            gp = G.default_grid(*shape, a=a, r_out=100.0, precision=G.MIXED, device=device)
+            gp.stream = shared_stream.cuda_stream if shared_stream is not None else None
+            c = G.init_grid(gp, G.default_phys(gam=gam))
+            G.set_metric(c, a, G.KERR_MKS)
+            G.init_torus(c, r_in=6.0, r_max=12.0, beta0=b0, pert_amp=0.04, seed=seed)
+            out.append(c)
+        return out
 
     def time_it(fn, k):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record(stream)
+        e0.record(s)
         fn(k)
-        e1.record(stream)
+        torch.cuda.synchronize()  # the concurrent loop's streams included
+        e1.record(s)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    def loop_of(ms):
+        def loop(k):
+            for _ in range(k):
+                for c in ms:
+                    G.step(c, 1)
+        return loop
+
+    members = make(s)
+    zones = sum(c.nact for c in members)
+    ens = G.ensemble_create(members)
+    tiling, cached = tuning.tune_or_load(ens, torch.cuda.get_device_name(device), trial_steps=2)
+    # the autotuner restored the initial states: every variant starts from them
     G.ensemble_step(ens, 2)
     ms_ens = time_it(lambda k: G.ensemble_step(ens, k), steps)
     G.ensemble_sync(ens)
-
-    def loop(k):
-        for _ in range(k):
-            for c in members:
-                G.step(c, 1)
-    loop(1)
+    ens.close()
+    for c in members:
+        c.close()
+    members = make(s)
+    loop = loop_of(members)
+    loop(2)
     ms_loop = time_it(loop, steps)
     for c in members:
         G.sync(c)
-    ens.close()
+        c.close()
+    members = make(None)
+    loop = loop_of(members)
+    loop(2)
+    ms_conc = time_it(loop, steps)
     for c in members:
+        G.sync(c)
         c.close()
     return {"workload": workload or ("24 FM tori, shapes 64x64x1..192x128x64, a U[0,0.98], gamma {4/3,13/9,5/3}, "
                                      "beta_0 U[30,300], r_out 100 M, mixed precision, one persistent launch per "
                                      "kernel class and one CUDA graph per ensemble step"),
-            "members": len(members), "zones": zones, "steps": steps,
+            "members": n, "zones": zones, "steps": steps,
             "value": zones * steps / (ms_ens * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms_ens / steps,
             "loop_of_singles_value": zones * steps / (ms_loop * 1e-3),
             "loop_ms_per_step": ms_loop / steps, "speedup_vs_loop": ms_loop / ms_ens,
+            "concurrent_streams_value": zones * steps / (ms_conc * 1e-3),
+            "concurrent_ms_per_step": ms_conc / steps, "speedup_vs_concurrent_streams": ms_conc / ms_ens,
+            "loop_note": "loop = the members' own step graphs one after another on one stream; "
+                         "concurrent = the same on one stream per member (the GPU overlaps them)",
             "tiling": tiling, "tiling_from_cache": cached}
 
 

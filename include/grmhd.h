@@ -244,9 +244,10 @@ typedef struct grmhd_ens grmhd_ens;
 typedef struct {
     int items_flux, items_update, blocks_per_sm_flux, blocks_per_sm_update;
     /* members with at least 2^solo_log2 active zones step with their own
-     * single-grid kernels inside the ensemble graph (their flux and EMF
-     * arrays then stay in L2 between the kernels of their step); 0: every
-     * member is batched.  Range 0 or 10-40. */
+     * single-grid kernels, on up to 16 parallel branches of the ensemble
+     * graph beside the batched kernels (their flux and EMF arrays then stay
+     * in L2 between the kernels of their step); 0: every member is batched.
+     * Range 0 or 10-40. */
     int solo_log2;
 } grmhd_ens_tiling;
 

@@ -177,10 +177,18 @@ __global__ void ek_finalize(EnsDev E)
 
 using namespace grmhd;
 
+// solo members step on up to this many branch streams, which a captured
+// ensemble graph turns into parallel branches beside the batched kernels
+static constexpr int ENS_BRANCHES = 16;
+
 struct grmhd_ens {
     std::vector<grmhd_ctx *> members;
     std::vector<Grid> hgrids;
     std::vector<int> batched, solo; // member indices: batched kernels / own step kernels
+    std::vector<int> branch_of;     // branch stream of each solo member (balanced by zones)
+    cudaStream_t bstream[ENS_BRANCHES] = {};
+    cudaEvent_t bjoin[ENS_BRANCHES] = {};
+    cudaEvent_t bfork = nullptr;
     std::vector<Grid> bgrids;       // descriptors of the batched members
     Grid *dgrids = nullptr;
     long long *dprefix = nullptr;
@@ -227,6 +235,22 @@ static int build_tables(grmhd_ens *ens)
         } else {
             ens->batched.push_back(m);
             ens->bgrids.push_back(ens->hgrids[m]);
+        }
+    }
+    // solo members to branches: largest first, each to the least loaded branch
+    {
+        const int ns = (int)ens->solo.size(), K = std::min(ns, ENS_BRANCHES);
+        std::vector<int> order(ns);
+        for (int i = 0; i < ns; i++) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return nact_of(ens->hgrids[ens->solo[x]]) > nact_of(ens->hgrids[ens->solo[y]]);
+        });
+        std::vector<long long> load(K > 0 ? K : 1, 0);
+        ens->branch_of.assign(ns, 0);
+        for (int i : order) {
+            int b = (int)(std::min_element(load.begin(), load.begin() + K) - load.begin());
+            ens->branch_of[i] = b;
+            load[b] += nact_of(ens->hgrids[ens->solo[i]]);
         }
     }
     int n = (int)ens->batched.size();
@@ -282,6 +306,18 @@ static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *e
         long long b = std::min<long long>((long long)ens->sms * bps, ens->tiles[cls]);
         return (unsigned)std::max<long long>(b, 1);
     };
+    // solo members: their own step graphs on the branch streams, forked from s
+    // before the batched kernels and joined after them (in a capture: parallel
+    // branches of the ensemble graph); under profiling events, after them on s
+    const int nsolo = (int)ens->solo.size();
+    const int K = std::min(nsolo, ENS_BRANCHES);
+    const bool fork = ev == nullptr && nsolo > 0;
+    if (fork) {
+        cudaEventRecord(ens->bfork, s);
+        for (int b = 0; b < K; b++) cudaStreamWaitEvent(ens->bstream[b], ens->bfork, 0);
+        for (int i = 0; i < nsolo; i++) launch_step(ens->hgrids[ens->solo[i]], ens->bstream[ens->branch_of[i]]);
+        for (int b = 0; b < K; b++) cudaEventRecord(ens->bjoin[b], ens->bstream[b]);
+    }
     int e = 0;
     for (int st = 0; st < 2 && n > 0; st++) {
         int src = st == 0 ? 0 : 1, dst = st == 0 ? 1 : 0;
@@ -303,7 +339,11 @@ static void launch_ens_step(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *e
     if (n > 0) ek_finalize<<<(n + 127) / 128, 128, 0, s>>>(E);
     REC();
 #undef REC
-    for (int m : ens->solo) launch_step(ens->hgrids[m], s);
+    if (fork) {
+        for (int b = 0; b < K; b++) cudaStreamWaitEvent(s, ens->bjoin[b], 0);
+    } else {
+        for (int m : ens->solo) launch_step(ens->hgrids[m], s);
+    }
 }
 
 static void ens_step_launch(const grmhd_ens *ens, cudaStream_t s, cudaEvent_t *ev)
@@ -342,6 +382,21 @@ extern "C" int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens
         grmhd_ensemble_destroy(ens);
         return GRMHD_ENOMEM;
     }
+    {
+        // branch streams and their events on the members' device
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(ens->device);
+        bool ok = cudaEventCreateWithFlags(&ens->bfork, cudaEventDisableTiming) == cudaSuccess;
+        for (int b = 0; b < ENS_BRANCHES && ok; b++)
+            ok = cudaStreamCreateWithFlags(&ens->bstream[b], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ens->bjoin[b], cudaEventDisableTiming) == cudaSuccess;
+        cudaSetDevice(prev);
+        if (!ok) {
+            grmhd_ensemble_destroy(ens);
+            return GRMHD_ECUDA;
+        }
+    }
     cudaMemcpyAsync(ens->dgrids, ens->hgrids.data(), sizeof(Grid) * n, cudaMemcpyHostToDevice, ens->stream);
     if (build_tables(ens) != 0) {
         grmhd_ensemble_destroy(ens);
@@ -357,6 +412,11 @@ extern "C" void grmhd_ensemble_destroy(grmhd_ens *ens)
     // The stream belongs to the first member, which may already be gone;
     // cudaFree below waits for all device work anyway.
     drop_graph(ens);
+    for (int b = 0; b < ENS_BRANCHES; b++) {
+        if (ens->bstream[b]) cudaStreamDestroy(ens->bstream[b]);
+        if (ens->bjoin[b]) cudaEventDestroy(ens->bjoin[b]);
+    }
+    if (ens->bfork) cudaEventDestroy(ens->bfork);
     if (ens->dgrids) cudaFree(ens->dgrids);
     if (ens->dprefix) cudaFree(ens->dprefix);
     delete ens;
@@ -500,19 +560,22 @@ extern "C" int grmhd_ensemble_autotune(grmhd_ens *ens, int trial_steps, grmhd_en
         // the solo threshold, on whole steps with the chosen tiles: members of at
         // least 2^k zones step on their own (k = 0: none); candidates that give
         // the same split as the previous one are skipped
-        const int cands[6] = {0, 22, 21, 20, 19, 18};
+        const int cands[10] = {0, 22, 21, 20, 19, 18, 16, 14, 12, 10};
         long long last_nsolo = -1;
         int best_sl = 0;
-        for (int q = 0; q < 6; q++) {
+        for (int q = 0; q < 10; q++) {
             grmhd_ens_tiling t = bt;
             t.solo_log2 = cands[q];
             ens->tiling = t;
             if (build_tables(ens)) break;
             if ((long long)ens->solo.size() == last_nsolo) continue;
             last_nsolo = (long long)ens->solo.size();
-            ens_step_launch(ens, s, nullptr); // warm-up
+            // timed as the step runs: a captured graph (the solo members'
+            // launches are many; launched one by one the host would bound them)
+            drop_graph(ens);
+            if (grmhd_ensemble_step(ens, 1) != 0) break; // capture and warm-up
             cudaEventRecord(ev[0], s);
-            for (int it = 0; it < trial_steps; it++) ens_step_launch(ens, s, nullptr);
+            if (grmhd_ensemble_step(ens, trial_steps) != 0) break;
             cudaEventRecord(ev[1], s);
             if (cudaEventSynchronize(ev[1]) != cudaSuccess) break;
             float ms = 0.0f;

@@ -1,6 +1,6 @@
 """Ensemble of independent tori stepped by persistent launches over a ragged
-tile list (members above a size threshold on their own kernels inside the same
-graph): every member must evolve bit-for-bit as the same torus alone, for any
+tile list (members above a size threshold on their own kernels, on parallel
+branches of the same graph): every member must evolve bit-for-bit as the same torus alone, for any
 tiling and threshold, and the autotuner must leave the members' state
 untouched."""
 import numpy as np
@@ -42,9 +42,12 @@ def test_members_evolve_as_alone(precision):
     # members of >= 2^12 zones on their own kernels inside the graph, the rest batched
     G.ensemble_set_tiling(ens, 2, 2, 8, 3, solo_log2=12)
     G.ensemble_step(ens, 2)
+    # four members on parallel branches of the graph, one batched beside them
+    G.ensemble_set_tiling(ens, 2, 2, 8, 3, solo_log2=10)
+    G.ensemble_step(ens, 2)
     G.ensemble_sync(ens)
     for c in solo:
-        G.step(c, 6)
+        G.step(c, 8)
     for a, b in zip(ens_members, solo):
         Pa, Ua, ta, dta = G.get_state(a)
         Pb, Ub, tb, dtb = G.get_state(b)
