@@ -631,6 +631,17 @@ def oracle_sample_run(n, n3s, steps, warmup):
     return zc, dt, desc
 
 
+def oracle_timed(n1, n2, n3, steps, gam, r_out, seed):
+    """Single-threaded oracle zone-cycles/s of an n1 x n2 x n3 torus (seeded
+    perturbation 0.04, beta_0 100) over `steps` RK2 steps."""
+    import oracle
+    og = oracle.Grid(oracle.default_params(n1=n1, n2=n2, n3=n3, gam=gam, r_out=r_out, a=0.9375))
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=seed)
+    t0 = time.perf_counter()
+    og.step(steps)
+    return n1 * n2 * n3 * steps / (time.perf_counter() - t0)
+
+
 def _oracle_core_worker(job):
     """one host core's share for oracle_all_cores: its own n x n x n3s slab
     torus, `steps` timed steps"""
@@ -742,6 +753,23 @@ def main():
     ms, clocks = timed(ctx, args.steps, args.warmup, True)
     value = aggregate_value(zones, args.steps, world, ms)
     ms_step = ms / args.steps
+    # the same step by windows: 5 windows of 20 steps, their median (the
+    # headline above is one window of exactly `steps` steps)
+    windows = None
+    if world == 1:
+        wms = []
+        for _ in range(5):
+            w0 = torch.cuda.Event(enable_timing=True)
+            w1 = torch.cuda.Event(enable_timing=True)
+            w0.record(stream)
+            G.step(ctx, 20)
+            w1.record(stream)
+            torch.cuda.synchronize()
+            wms.append(w0.elapsed_time(w1) / 20)
+        med = statistics.median(wms)
+        windows = {"windows": 5, "steps_per_window": 20, "ms_per_step": wms,
+                   "median_ms_per_step": med, "median_value": zones / (med * 1e-3)}
+        G.sync(ctx)
     diag = G.diagnostics(ctx)
     # barycentric radius of Eq. 43 (r_bar_max = 80 M), timed on its own
     G.barycentric_radius(ctx, 80.0)
@@ -871,6 +899,12 @@ def main():
         zca, cores, desca = oracle_all_cores(n, 2, 2)
         cpu["all_cores"] = {"value": zca, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle",
                             "sample": desca}
+        # the small configurations: 64x64x1 in full (20 steps), 128^3 as a 128x128x4 phi-slab sample
+        cpu["configs"] = {
+            "64x64x1 (gamma 13/9, r_out 40 M, 20 steps)": oracle_timed(64, 64, 1, 20, 13.0 / 9.0, 40.0, 1),
+            "128^3 sample: 128x128x4 (gamma 4/3, r_out 1000 M, 2 steps)": oracle_timed(128, 128, 4, 2, 4.0 / 3.0,
+                                                                                    1000.0, 2),
+        }
     if rank == 0:
         line = {
             "metric": "zone-cycles/s at 256^3 (FP64 vs mixed, same GB300); % of HBM roofline",
@@ -898,6 +932,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "windows": windows,
             "diagnostics_after_bench": dict(
                 {k: diag[k] for k in ("t", "dt", "mdot", "eta", "divb_max", "n_fail", "n_fixed", "nr_iters", "n_nr",
                                       "n_entropy_beta", "n_floor")},
