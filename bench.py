@@ -854,16 +854,19 @@ def main():
         torch.cuda.synchronize()
         el_seq = max_over_ranks(time.perf_counter() - t_start, dist, "cuda")
         seq_value = aggregate_value(zones, ne, world, el_seq * 1e3)
-        # the pipelined form: a second context and its own pinned buffers
-        ctx2 = make_ctx(G.MIXED)
-        Ph2 = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
-        Uh2 = torch.empty((9, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
-        Ph2[...] = Ph
-        Uh2[...] = Uh
-        e2e_steps(ctx2, Ph2, Uh2, 1)  # first use of its graph and staging
-        npipe = 6
-        workers = [threading.Thread(target=e2e_steps, args=(c, Pb, Ub, npipe))
-                   for c, Pb, Ub in ((ctx, Ph, Uh), (ctx2, Ph2, Uh2))]
+        # the pipelined form: more contexts, each with its own pinned buffers
+        nctx = 3
+        extra = [make_ctx(G.MIXED) for _ in range(nctx - 1)]
+        bufs = [(ctx, Ph, Uh)]
+        for c in extra:
+            Pb = torch.empty((8, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+            Ub = torch.empty((9, n, n, n), dtype=torch.float64, pin_memory=True).numpy()
+            Pb[...] = Ph
+            Ub[...] = Uh
+            e2e_steps(c, Pb, Ub, 1)  # first use of its graph and staging
+            bufs.append((c, Pb, Ub))
+        npipe = 4
+        workers = [threading.Thread(target=e2e_steps, args=(c, Pb, Ub, npipe)) for c, Pb, Ub in bufs]
         barrier()
         torch.cuda.synchronize()
         t_start = time.perf_counter()
@@ -873,15 +876,17 @@ def main():
             w.join()
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t_start, dist, "cuda")
-        e2e = {"value": aggregate_value(zones, 2 * npipe, world, el * 1e3), "unit": "zone-cycles/s",
+        e2e = {"value": aggregate_value(zones, nctx * npipe, world, el * 1e3), "unit": "zone-cycles/s",
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
-               "steps": 2 * npipe,
-               "path": "grmhd_set_state(host) + grmhd_step + grmhd_get_state(host) per step, pinned buffers; "
-                       "two contexts driven by two host threads, so one context's copies overlap the other's step",
+               "steps": nctx * npipe,
+               "path": f"grmhd_set_state(host) + grmhd_step + grmhd_get_state(host) per step, pinned buffers; "
+                       f"{nctx} contexts driven by {nctx} host threads, so one context's copies overlap the "
+                       f"others' steps",
                "sequential": {"value": seq_value, "steps": ne,
                               "path": "the same calls on one context, one step after another"}}
-        ctx2.close()
-        del Ph, Uh, Ph2, Uh2
+        for c in extra:
+            c.close()
+        del Ph, Uh, bufs
     ctx.close()
     torch.cuda.synchronize()
     # ---- the plain FP64 step beside it

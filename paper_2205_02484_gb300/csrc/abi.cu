@@ -4,6 +4,7 @@
 // and the CUDA graph of one full RK2 step.  The step graph is captured on the
 // first grmhd_step call and replayed afterwards; the time step lives on the
 // device, so replays need no host round trip.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,10 @@ struct grmhd_ctx {
     double *hpin = nullptr; // pinned host scratch (64 doubles)
     double disk_mass = 0.0, disk_eb = 0.0;
     CoordParams cp{}; // coordinate map of the metric (Kerr grids)
+    // host <-> device state copies split over several streams (copy engines)
+    static constexpr int NCOPY = 4;
+    cudaStream_t cstream[NCOPY] = {};
+    cudaEvent_t cfork = nullptr, cjoin[NCOPY] = {};
     float *mlp = nullptr;       // packed forward buffer of the learned Newton start
     float *mlp_theta = nullptr; // its FP32 parameters
     bool mlp_loaded = false;
@@ -93,6 +98,11 @@ extern "C" void grmhd_destroy(grmhd_ctx *ctx)
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    for (int k = 0; k < grmhd_ctx::NCOPY; k++) {
+        if (ctx->cstream[k]) cudaStreamDestroy(ctx->cstream[k]);
+        if (ctx->cjoin[k]) cudaEventDestroy(ctx->cjoin[k]);
+    }
+    if (ctx->cfork) cudaEventDestroy(ctx->cfork);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -386,6 +396,58 @@ static int ensure_staging(grmhd_ctx *ctx, long long n)
     return 0;
 }
 
+// A host <-> device copy of the state's parts (P, U) split into NCOPY nearly
+// equal byte ranges on as many streams, so that several copy engines share
+// it; forked from the context stream after the work already there and joined
+// back before the work that follows.
+struct CopyPart {
+    char *dst;
+    const char *src;
+    size_t bytes;
+};
+
+static int copy_split(grmhd_ctx *ctx, const CopyPart *parts, int np, cudaMemcpyKind kind)
+{
+    const int NC = grmhd_ctx::NCOPY;
+    if (!ctx->cfork) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaSetDevice(ctx->gp.device));
+        CK(cudaEventCreateWithFlags(&ctx->cfork, cudaEventDisableTiming));
+        for (int k = 0; k < NC; k++) {
+            CK(cudaStreamCreateWithFlags(&ctx->cstream[k], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ctx->cjoin[k], cudaEventDisableTiming));
+        }
+        CK(cudaSetDevice(dev));
+    }
+    size_t total = 0;
+    for (int q = 0; q < np; q++) total += parts[q].bytes;
+    const size_t align = 1 << 20;
+    size_t per = ((total + NC - 1) / NC + align - 1) / align * align;
+    CK(cudaEventRecord(ctx->cfork, ctx->stream));
+    for (int k = 0; k < NC; k++) CK(cudaStreamWaitEvent(ctx->cstream[k], ctx->cfork, 0));
+    int k = 0;
+    size_t filled = 0;
+    for (int q = 0; q < np; q++) {
+        size_t off = 0;
+        while (off < parts[q].bytes) {
+            size_t take = std::min(parts[q].bytes - off, per - filled);
+            CK(cudaMemcpyAsync(parts[q].dst + off, parts[q].src + off, take, kind, ctx->cstream[k]));
+            off += take;
+            filled += take;
+            if (filled == per && k < NC - 1) {
+                k++;
+                filled = 0;
+            }
+        }
+    }
+    for (int j = 0; j < NC; j++) {
+        CK(cudaEventRecord(ctx->cjoin[j], ctx->cstream[j]));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->cjoin[j], 0));
+    }
+    return 0;
+}
+
 extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt, int on_device)
 {
     if (!ctx || !P || !U) return fail(ctx, GRMHD_EINVAL, "null argument");
@@ -394,8 +456,9 @@ extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U,
     const double *Pd = P, *Ud = U;
     if (!on_device) {
         if (ensure_staging(ctx, 17 * na)) return GRMHD_ENOMEM;
-        CK(cudaMemcpyAsync(ctx->staging, P, 8 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->staging + 8 * na, U, 9 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        const CopyPart parts[2] = {{(char *)ctx->staging, (const char *)P, 8 * na * sizeof(double)},
+                                   {(char *)(ctx->staging + 8 * na), (const char *)U, 9 * na * sizeof(double)}};
+        if (int rc = copy_split(ctx, parts, 2, cudaMemcpyHostToDevice)) return rc;
         Pd = ctx->staging;
         Ud = ctx->staging + 8 * na;
     }
@@ -421,8 +484,11 @@ extern "C" int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, 
         } else {
             if (ensure_staging(ctx, 17 * na)) return GRMHD_ENOMEM;
             launch_copy_state_out(ctx->g, P ? ctx->staging : nullptr, U ? ctx->staging + 8 * na : nullptr, ctx->stream);
-            if (P) CK(cudaMemcpyAsync(P, ctx->staging, 8 * na * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-            if (U) CK(cudaMemcpyAsync(U, ctx->staging + 8 * na, 9 * na * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+            CopyPart parts[2];
+            int np = 0;
+            if (P) parts[np++] = CopyPart{(char *)P, (const char *)ctx->staging, 8 * na * sizeof(double)};
+            if (U) parts[np++] = CopyPart{(char *)U, (const char *)(ctx->staging + 8 * na), 9 * na * sizeof(double)};
+            if (int rc = copy_split(ctx, parts, np, cudaMemcpyDeviceToHost)) return rc;
         }
         CK(cudaGetLastError());
     }
