@@ -409,16 +409,27 @@ struct CopyPart {
 static int copy_split(grmhd_ctx *ctx, const CopyPart *parts, int np, cudaMemcpyKind kind)
 {
     const int NC = grmhd_ctx::NCOPY;
-    if (!ctx->cfork) {
+    if (!ctx->cfork) { // created once, all or nothing
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaSetDevice(ctx->gp.device));
-        CK(cudaEventCreateWithFlags(&ctx->cfork, cudaEventDisableTiming));
-        for (int k = 0; k < NC; k++) {
-            CK(cudaStreamCreateWithFlags(&ctx->cstream[k], cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&ctx->cjoin[k], cudaEventDisableTiming));
+        cudaEvent_t fork = nullptr;
+        bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < NC && ok; k++)
+            ok = cudaStreamCreateWithFlags(&ctx->cstream[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->cjoin[k], cudaEventDisableTiming) == cudaSuccess;
+        cudaSetDevice(dev);
+        if (!ok) {
+            if (fork) cudaEventDestroy(fork);
+            for (int k = 0; k < NC; k++) {
+                if (ctx->cstream[k]) cudaStreamDestroy(ctx->cstream[k]);
+                if (ctx->cjoin[k]) cudaEventDestroy(ctx->cjoin[k]);
+                ctx->cstream[k] = nullptr;
+                ctx->cjoin[k] = nullptr;
+            }
+            return fail(ctx, GRMHD_ECUDA, "copy streams could not be created");
         }
-        CK(cudaSetDevice(dev));
+        ctx->cfork = fork;
     }
     size_t total = 0;
     for (int q = 0; q < np; q++) total += parts[q].bytes;
