@@ -202,7 +202,7 @@ def _rank(rank, world, port, steps, periodic, out):
         out.put(gathered)
 
 
-@pytest.mark.parametrize("world,periodic", [(2, False), (4, False), (2, True)])
+@pytest.mark.parametrize("world,periodic", [(2, False), (3, False), (4, False), (2, True)])
 def test_gloo_theta_ranks_reproduce_the_undecomposed_step(world, periodic):
     pytest.importorskip("torch")
     import torch.multiprocessing as mp
@@ -228,3 +228,21 @@ def test_gloo_theta_ranks_reproduce_the_undecomposed_step(world, periodic):
     _check_combined(gathered[0][4], ref.diagnostics())
     for x, y in zip(gathered[0][4]["bary"], ref.barycentric(30.0)):
         assert x == pytest.approx(y, rel=1e-13, abs=1e-300)
+
+
+def test_library_theta_grid_parameters():
+    """decomp.theta_grid: slab r's rows and the whole grid's, the split's
+    checks, and split_theta's parts tiling the whole array."""
+    from paper_2205_02484_gb300 import grmhd as G
+    from paper_2205_02484_gb300.decomp import split_theta, theta_grid
+    base = G.default_grid(24, 48, 1)
+    g = theta_grid(base, 4, 3)
+    assert (g.n2, g.j0, g.n2_total, g.n1, g.n3) == (12, 36, 48, 24, 1)
+    with pytest.raises(ValueError):
+        theta_grid(base, 5, 0)   # 48 rows do not split into 5
+    with pytest.raises(ValueError):
+        theta_grid(base, 16, 0)  # 3-row slabs
+    x = np.arange(2 * 24 * 48 * 1, dtype=np.float64).reshape(2, 24, 48, 1)
+    parts = [split_theta(x, 4, r) for r in range(4)]
+    assert all(p.flags["C_CONTIGUOUS"] for p in parts)
+    assert np.array_equal(np.concatenate(parts, axis=2), x)
