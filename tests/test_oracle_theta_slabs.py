@@ -246,3 +246,42 @@ def test_library_theta_grid_parameters():
     parts = [split_theta(x, 4, r) for r in range(4)]
     assert all(p.flags["C_CONTIGUOUS"] for p in parts)
     assert np.array_equal(np.concatenate(parts, axis=2), x)
+
+
+def _rank_that_leaves(rank, world, port, out):
+    """Rank 1 exits after the first exchange (a crash between steps); rank 0's
+    next collective of the step must raise instead of waiting forever."""
+    import datetime
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_2205_02484_gb300.decomp import ThetaRank
+    from tests import slabs as S2
+    from tests import test_oracle_theta_slabs as T
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    base, state = T._base(), T._torus_start(1, world)
+    slab = ThetaRank(S2.OracleThetaSlab(S2.theta_params(base, rank, world)))
+    slab.set_state(*state)
+    dist.barrier()
+    if rank == 1:
+        os._exit(0)
+    try:
+        slab.step(1)
+        out.put("no error")
+    except Exception as e:  # the process group reports the lost peer
+        out.put(f"raised {type(e).__name__}")
+
+
+def test_a_rank_that_leaves_is_detected():
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_that_leaves, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    msg = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert msg.startswith("raised"), msg
