@@ -155,11 +155,15 @@ int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *torus);
 
 /* Copy a full active-zone state in (P: 8 fields, U: 9 fields) with the time
  * t and the next step dt; ghosts are refilled from the boundary conditions.
- * In GRMHD_MIXED mode P is rounded to FP32. */
+ * In GRMHD_MIXED mode P is rounded to FP32.  A host state (on_device = 0)
+ * is copied in four byte ranges on four internal streams (several copy
+ * engines), ordered after the work already on the context stream; the call
+ * returns when the state is on the device. */
 int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt,
                     int on_device);
 
-/* Copy the active-zone state out (any of P, U, t, dt may be NULL). */
+/* Copy the active-zone state out (any of P, U, t, dt may be NULL); a host
+ * copy is split as in grmhd_set_state.  Returns when the copy is done. */
 int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,
                     int on_device);
 
