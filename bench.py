@@ -866,7 +866,15 @@ def main():
             e2e_steps(c, Pb, Ub, 1)  # first use of its graph and staging
             bufs.append((c, Pb, Ub))
         npipe = 4
-        workers = [threading.Thread(target=e2e_steps, args=(c, Pb, Ub, npipe)) for c, Pb, Ub in bufs]
+        errors = []
+
+        def worker(c, Pb, Ub):
+            try:
+                e2e_steps(c, Pb, Ub, npipe)
+            except BaseException as exc:  # re-raised below: a failed worker voids the number
+                errors.append(exc)
+
+        workers = [threading.Thread(target=worker, args=b) for b in bufs]
         barrier()
         torch.cuda.synchronize()
         t_start = time.perf_counter()
@@ -874,6 +882,8 @@ def main():
             w.start()
         for w in workers:
             w.join()
+        if errors:
+            raise errors[0]
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t_start, dist, "cuda")
         e2e = {"value": aggregate_value(zones, nctx * npipe, world, el * 1e3), "unit": "zone-cycles/s",
