@@ -827,8 +827,8 @@ def main():
     # ---- e2e through the public API with pinned host buffers: every step
     # copies its inputs (P, U) in from pinned host memory, steps, and copies
     # its result back.  Sequential: one context, one step after another.
-    # Pipelined: two contexts, each driven by its own host thread, so that one
-    # context's copies overlap the other's step (the serving pattern: the
+    # Pipelined: three contexts, each driven by its own host thread, so that
+    # one context's copies overlap the others' steps (the serving pattern: the
     # copies of a step and the step itself still run in order).
     e2e = None
     if not args.no_e2e:
