@@ -28,8 +28,8 @@ def _spoil(U, rows, cols):
     return U
 
 
-def _start(G, precision, R, shape=(40, 48, 1)):
-    grid = G.default_grid(*shape, precision=precision, a=A)
+def _start(G, precision, R, shape=(40, 48, 1), riemann=0):
+    grid = G.default_grid(*shape, precision=precision, a=A, riemann=riemann)
     phys = G.default_phys(gam=GAM)
     src = G.init_grid(grid, phys)
     G.set_metric(src, A)
@@ -52,11 +52,11 @@ def _ring_state(ring):
     return P, U, parts[0][2], parts[0][3]
 
 
-@pytest.mark.parametrize("precision,R", [(0, 2), (0, 3), (0, 4), (1, 2), (1, 4)])
-def test_theta_ring_equals_the_undecomposed_step(precision, R):
+@pytest.mark.parametrize("precision,R,riemann", [(0, 2, 0), (0, 3, 0), (0, 4, 0), (1, 2, 0), (1, 4, 0), (1, 3, 1)])
+def test_theta_ring_equals_the_undecomposed_step(precision, R, riemann):
     G = gpu_mod()
     from paper_2205_02484_gb300.decomp import ThetaRing
-    grid, phys, full, (P0, U0, t0, dt0) = _start(G, precision, R)
+    grid, phys, full, (P0, U0, t0, dt0) = _start(G, precision, R, riemann=riemann)
     ring = ThetaRing.create(grid, phys, R, A)
     ring.set_state(P0, U0, t0, dt0)
     nsteps = 4
