@@ -164,6 +164,7 @@ def lib():
                                                      C.c_double, C.c_double, C.c_double, C.c_double,
                                                      C.c_double, _F, _F, _D]),
                 "orc_c2p_batch_w": (None, [V, _D, _I, _D, _D, _D, _I, _I, C.c_long, C.c_int]),
+                "orc_post_inversion_at": (None, [V, C.c_int, C.c_int, _D, _D, _I]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -411,6 +412,16 @@ class Grid:
         self.L.orc_c2p_batch_w(self.h, _p(U), _p(loc, _I), _p(guess), _p(wguess), _p(P), _p(flags, _I),
                                _p(iters, _I), n, methods)
         return P, flags, iters
+
+    def post_inversion(self, i, j, q, U):
+        """Floors, magnetisation ceilings and Lorentz cap (Section 2.4) of
+        active zone (i, j) after a successful inversion: (q', modified,
+        ceiling hits, cap hits) from primitives q (8) and conserved U (9)."""
+        q = np.array(q, dtype=np.float64).copy()
+        U = np.array(U, dtype=np.float64).copy()
+        out = np.zeros(3, dtype=np.int32)
+        self.L.orc_post_inversion_at(self.h, int(i), int(j), _p(q), _p(U), _p(out, _I))
+        return q, int(out[0]), int(out[1]), int(out[2])
 
     def mlp_samples(self, seed, first, n):
         """Samples first..first+n-1 of the seeded MLP training distribution:

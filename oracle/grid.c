@@ -552,7 +552,12 @@ static void post_inversion(orc_grid *G, int i, int j, double *q, double *U, int 
         }
         *mod = 1;
     }
-    gamma_cap(G, g, q, mod);
+    int capped = 0;
+    gamma_cap(G, g, q, &capped);
+    if (capped) {
+        G->cnt.n_gcap++;
+        *mod = 1;
+    }
 }
 
 /* direct version for fixed-up zones (no second inversion) */
@@ -1120,6 +1125,22 @@ void orc_c2p_batch(const orc_grid *G, const double *U, const int *loc, const dou
         if (iters) iters[a] = it;
         for (int c = 0; c < ORC_NP; c++) P[c * n + a] = q[c];
     }
+}
+
+/* The limits of Section 2.4 applied to one zone (i, j) whose inversion
+ * succeeded: floors (Eq. 34), the magnetisation ceilings by mass added at
+ * rest in the normal frame, and the Lorentz cap.  q (8) is updated in place
+ * from the zone's conserved vector U (9); out[0] = 1 if q was modified,
+ * out[1] / out[2] = the zone's ceiling / cap counts.  Test access to the
+ * same routine the step calls. */
+void orc_post_inversion_at(orc_grid *G, int i, int j, double *q, double *U, int *out)
+{
+    long long c0 = G->cnt.n_ceil, g0 = G->cnt.n_gcap;
+    int mod = 0;
+    post_inversion(G, i, j, q, U, &mod);
+    out[0] = mod;
+    out[1] = (int)(G->cnt.n_ceil - c0);
+    out[2] = (int)(G->cnt.n_gcap - g0);
 }
 
 /* --------------------------------------------------- table access (tests) */

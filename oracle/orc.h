@@ -139,6 +139,7 @@ double orc_barycentric(orc_grid *G, double r_bar_max, double out[3]);
 double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
+void orc_post_inversion_at(orc_grid *G, int i, int j, double *q, double *U, int *out);
 int orc_n2_total(const orc_grid *G);
 int orc_x2_external(const orc_grid *G, int side);
 

@@ -3,8 +3,8 @@
 Each pin is fixed by something other than the oracle's own formula:
 normalisation identities of u^mu and b^mu, the closed-form stress tensor of a
 fluid at rest in flat space, relativistic velocity addition for the wave
-speeds of Eq. 19, a brute-force minmod table for the MC limiter of Eq. 16,
-and the consistency / equivalence properties of the LLF and HLL fluxes.
+speeds of Eq. 19 and a brute-force minmod table for the MC limiter of Eq.
+16.  The Riemann fluxes (Eqs. 18, 21) are pinned in test_oracle_limits.py.
 """
 import numpy as np
 import pytest

@@ -16,9 +16,10 @@ RIGHT = State(1.0, 0.1, -0.1)
 T_END = 0.3
 
 
-def _tube(n, bc=oracle.BC_OUTFLOW):
+def _tube(n, bc=oracle.BC_OUTFLOW, riemann=oracle.LLF):
     p = oracle.default_params(metric=oracle.MINK_CART, n1=n, n2=1, n3=1, x1min=0.0, x1max=1.0,
-                              x2min=0.0, x2max=1.0, x3min=0.0, x3max=1.0, bc1=bc, bc2=bc, bc3=bc, gam=GAM)
+                              x2min=0.0, x2max=1.0, x3min=0.0, x3max=1.0, bc1=bc, bc2=bc, bc3=bc, gam=GAM,
+                              riemann=riemann)
     return oracle.Grid(p)
 
 
@@ -70,8 +71,8 @@ def test_exact_solution_satisfies_the_jump_conditions():
     assert ex.sample(0.99) == (RIGHT.rho, RIGHT.p, RIGHT.v)
 
 
-def _l1_error(n):
-    og = _tube(n)
+def _l1_error(n, riemann=oracle.LLF):
+    og = _tube(n, riemann=riemann)
     x = (np.arange(n) + 0.5) / n
     P = _run(og, _prims_1d(x, LEFT, RIGHT, GAM), T_END)
     ex = ExactRiemann(LEFT, RIGHT, GAM)
@@ -79,12 +80,20 @@ def _l1_error(n):
     return np.abs(P[0, :, 0, 0] - rho_ex).mean()
 
 
-def test_tube_converges_to_the_exact_solution():
-    e = [_l1_error(n) for n in (100, 200, 400)]
+@pytest.mark.parametrize("riemann", [oracle.LLF, oracle.HLL])
+def test_tube_converges_to_the_exact_solution(riemann):
+    e = [_l1_error(n, riemann) for n in (100, 200, 400)]
     # shocks and the contact limit L1 convergence to about first order; the
     # shocked shell between the contact and the shock is 0.04 wide at t = 0.3
     assert e[0] / e[1] > 1.5 and e[1] / e[2] > 1.5, e
     assert e[2] < 0.04
+
+
+def test_hll_resolves_the_tube_better_than_llf():
+    # HLL (Eq. 21) uses the one-sided signal speeds, LLF (Eq. 18) the largest
+    # speed on both sides, so HLL adds less dissipation on this tube
+    for n in (100, 200):
+        assert _l1_error(n, oracle.HLL) < 0.9 * _l1_error(n, oracle.LLF)
 
 
 def test_magnetised_tube_mirror_symmetry():
