@@ -158,7 +158,11 @@ int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *torus);
  * In GRMHD_MIXED mode P is rounded to FP32.  A host state (on_device = 0)
  * is copied in four byte ranges on four internal streams (several copy
  * engines), ordered after the work already on the context stream; the call
- * returns when the state is on the device. */
+ * returns when the state is on the device.  The status word read by
+ * grmhd_sync is cleared (counters keep accumulating).  If P or U holds a
+ * non-finite value the call returns GRMHD_ENONFINITE and the context has no
+ * state until a later grmhd_set_state or grmhd_init_torus succeeds
+ * (grmhd_step: GRMHD_ESTATE). */
 int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt,
                     int on_device);
 
@@ -170,8 +174,12 @@ int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,
 /* Advance nsteps full RK2 steps (Eqs. 25-26) with the CFL time step of Eq. 27
  * (dt of step n+1 from the predictor sweep of step n).  Asynchronous on the
  * context stream; each step replays one captured CUDA graph.  Inversion
- * failures that the fixups cannot repair raise GRMHD_EFIXUP at the next
- * grmhd_sync or grmhd_diagnostics.  GRMHD_EINVAL for a phi slab
+ * failures that the fixups cannot repair within fix_maxsweep Jacobi sweeps
+ * (Eq. 33) raise GRMHD_EFIXUP, and a failed zone whose conserved vector is
+ * not finite raises GRMHD_ENONFINITE, at the next grmhd_sync or
+ * grmhd_diagnostics; the state is still stepped (the unrepaired zones keep
+ * their previous primitives) and grmhd_set_state clears the status.
+ * GRMHD_EINVAL for a phi slab
  * (bc3 = GRMHD_BC_EXTERNAL), whose ghost planes must be exchanged between
  * the stages (grmhd_stage), and for a theta slab (n2_total > 0), which steps
  * by the stage parts. */

@@ -178,6 +178,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.bu_max = phys->bu_max; g.gamma_max = phys->gamma_max; g.beta_ent = phys->beta_entropy;
     g.g1 = (g.gam - 1.0) / g.gam;
     g.igm1 = 1.0 / (g.gam - 1.0);
+    g.ig = 1.0 / g.gam;
     g.isig = 1.0 / g.sigma_max;
     g.ibu = 1.0 / g.bu_max;
     g.isig_f = (float)g.isig;
@@ -474,11 +475,21 @@ extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U,
         Ud = ctx->staging + 8 * na;
     }
     (void)cudaGetLastError();
+    ctx->state_set = false;
+    // a new state starts with a clear status word (the counters keep running)
+    CK(cudaMemsetAsync(ctx->g.status, 0, sizeof(int), ctx->stream));
     launch_copy_state_in(ctx->g, Pd, Ud, ctx->stream);
     launch_bc(ctx->g, 0, ctx->stream);
     CK(cudaGetLastError());
     if (copy_stage_buffer(ctx)) return GRMHD_ECUDA;
-    if (set_scalars(ctx, t, dt)) return GRMHD_ECUDA;
+    CK(cudaMemcpyAsync(&ctx->hpin[8], ctx->g.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (set_scalars(ctx, t, dt)) return GRMHD_ECUDA; // synchronises the stream
+    int st = 0;
+    std::memcpy(&st, &ctx->hpin[8], sizeof(int));
+    if (st & ST_NONFINITE) {
+        CK(cudaMemsetAsync(ctx->g.status, 0, sizeof(int), ctx->stream));
+        return fail(ctx, GRMHD_ENONFINITE, "set_state: P or U holds a non-finite value; the context has no state");
+    }
     ctx->state_set = true;
     return 0;
 }
@@ -782,6 +793,7 @@ extern "C" int grmhd_diagnostics_noalloc(grmhd_ctx *ctx, double *out_dev)
     double *partials = nullptr;
     int rc = noalloc_partials(ctx, dev, &partials);
     if (rc) return rc;
+    (void)cudaGetLastError(); // an earlier asynchronous error is not this call's failure
     launch_diagnostics(g, partials, NOALLOC_DOUBLES, out_dev, ctx->stream);
     CK(cudaGetLastError());
     return 0;

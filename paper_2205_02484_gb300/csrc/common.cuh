@@ -80,6 +80,7 @@ struct Grid {
     double dx[3], idx[3], x1in, x2in, x3in;
     double gam, cfl, nr_tol, sigma_max, bu_max, gamma_max, beta_ent;
     double g1, igm1, isig, ibu; // (gam-1)/gam, 1/(gam-1), 1/sigma_max, 1/bu_max
+    double ig;                  // 1/gam
     float isig_f, ibu_f;        // 1/sigma_max, 1/bu_max for the mixed path's FP32 ceiling test
     // FP32 copies of per-grid constants: the FP32 arithmetic of the mixed path
     // reads them instead of converting the FP64 values in every zone

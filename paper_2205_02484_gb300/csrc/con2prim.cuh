@@ -36,15 +36,15 @@ struct C2PIn {
 // solver parameters of a grid; the EOS ratios and the mixed path's Newton
 // acceptance sqrt(tol) are formed once on the host
 struct C2PPar {
-    double gam, g1, igm1, beta_ent, tol, tol_mixed;
+    double gam, g1, igm1, beta_ent, tol, tol_mixed, ig; // ig = 1/gam
     int nr_maxit, brent_maxit;
     float gam_f, g1_f, beta_ent_f, tol_mixed_f; // FP32 copies for the mixed path
 };
 
 __device__ __forceinline__ C2PPar c2p_par(const Grid &g)
 {
-    return C2PPar{g.gam,        g.g1,          g.igm1, g.beta_ent, g.nr_tol, g.nr_tol_mixed, g.nr_maxit,
-                  g.brent_maxit, g.gam_f,       g.g1_f, g.beta_ent_f, g.tol_mixed_f};
+    return C2PPar{g.gam,      g.g1,          g.igm1,  g.beta_ent, g.nr_tol,   g.nr_tol_mixed, g.ig,
+                  g.nr_maxit, g.brent_maxit, g.gam_f, g.g1_f,     g.beta_ent_f, g.tol_mixed_f};
 }
 
 // finite test on the high word: integer pipe instead of an FP64 compare
@@ -85,6 +85,25 @@ __device__ __forceinline__ void c2p_recover_w(const C2PIn &c, double W, double v
     P[KUU] = (c.g1 * (W * omv - c.D * s)) * c.igm1;
     double WB = W + c.Bsq;
     double r = 1.0 / (W * WB);
+    double f = lor * (W * r);
+    double qbw = c.QB * (WB * r);
+#pragma unroll
+    for (int i = 0; i < 3; i++) P[KU1 + i] = f * (c.Qt[i] + qbw * c.Bf[i]);
+}
+
+// c2p_recover_w for the mixed path, whose primitives are stored in FP32: rho
+// and u (the difference of W (1 - v^2) and D sqrt(1 - v^2)) in FP64, the
+// velocity factors Gamma / (W + B^2) and (Q.B) / W from an FP32 reciprocal
+// of W (W + B^2), relative error ~1e-7 like the FP32 store itself
+__device__ __forceinline__ void c2p_recover_mixed(const C2PIn &c, double W, double v2, double ig, double *P)
+{
+    double omv = 1.0 - v2;
+    double lor = rsqrt(omv);
+    double s = omv * lor;
+    P[KRHO] = c.D * s;
+    P[KUU] = (W * omv - c.D * s) * ig; // p / (gam - 1) = (W (1 - v^2) - D sqrt(1 - v^2)) / gam
+    double WB = W + c.Bsq;
+    double r = (double)(1.0f / (float)(W * WB));
     double f = lor * (W * r);
     double qbw = c.QB * (WB * r);
 #pragma unroll
@@ -258,6 +277,7 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, doubl
     const double QB2 = c.QB * c.QB;
     const bool has_qb = (__double_as_longlong(QB2) << 1) != 0; // Q.B != 0 (integer test)
     const float g1f = par.g1_f, Bsqf = (float)c.Bsq, Df = (float)c.D, tolf = par.tol_mixed_f;
+    const float QB2f = has_qb ? (float)QB2 : 0.0f;
     const long long v2max_bits = __double_as_longlong(V2MAX);
     int n = 0;
     for (int it = 1; it <= maxit; it++) {
@@ -266,18 +286,19 @@ __device__ inline bool c2p_newton_mixed(const C2PIn &c, const C2PPar &par, doubl
         double is = rsqrt(omv); // 1 / sqrt(1 - v^2)
         double s = omv * is;
         double iW = 0.0, qw2 = 0.0; // (Q.B)^2 / W^2, no reciprocal where Q.B = 0 (no field)
-        float qw2f = 0.0f;
         if (has_qb) {
             iW = 1.0 / W;
             qw2 = QB2 * iW * iW;
-            qw2f = (float)qw2;
         }
         double p = g1 * (W * omv - c.D * s);
         double BW = c.Bsq + W;
         double f1 = v2 * BW * BW - qw2 * (c.Bsq + 2.0 * W) - c.Qtsq;
         double f2 = -0.5 * c.Bsq * (1.0 + v2) + 0.5 * qw2 - W + p - c.nQ;
-        const float Wf = (float)W, v2f = (float)v2, omvf = (float)omv;
+        // the Jacobian's inputs formed in FP32 from the FP32 (W, v^2): only the
+        // step's rate of convergence depends on them, not the root
+        const float Wf = (float)W, v2f = (float)v2, omvf = 1.0f - v2f;
         const float isf = rsqrtf(omvf), iWf = 1.0f / Wf, BWf = Bsqf + Wf;
+        const float qw2f = QB2f * iWf * iWf;
         const float a11 = 2.0f * v2f * BWf + 2.0f * qw2f * iWf * BWf;
         const float a12 = BWf * BWf;
         const float a21 = -qw2f * iWf - 1.0f + g1f * omvf;
@@ -399,7 +420,12 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
     c.igm1 = par.igm1;
     c.D = f * U[KRHO];
     const double Q0 = f * U[1], Q1 = f * U[2], Q2 = f * U[3], Q3 = f * U[4];
-    c.Sent = f * U[KENT];
+    // the entropy density, needed only by the entropy inversion, is formed there
+    c.Sent = 0.0;
+    auto entropy = [&]() {
+        c.Sent = f * U[KENT];
+        return c2p_entropy(c, par.brent_maxit, P);
+    };
     // n^mu = (1/alpha, -alpha g^{ti}); the projection j^{mu nu} = g^{mu nu} +
     // n^mu n^nu has j^{t mu} = 0 and j^{ij} = gamma^{ij}, so Qt^i = gamma^{ij} Q_j
     // and Qt^2 = Qt^i Q_i (no cancellation against the energy)
@@ -423,7 +449,8 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         c.Bsq = 0.0;
     }
     bool fin = finite64(c.D) && finite64(c.Qtsq) && finite64(c.nQ) && finite64(c.Bsq);
-    if (!fin || !(c.D > 0.0)) return fail(C2P_FAIL | C2P_FAIL_D);
+    // a finite D is > 0 exactly when its signed bit pattern is (integer test)
+    if (!fin || __double_as_longlong(c.D) <= 0) return fail(C2P_FAIL | C2P_FAIL_D);
 
     if (methods & 8) {
         bool low_beta;
@@ -439,7 +466,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             low_beta = s.bsq > 0.0 && pg < par.beta_ent * 0.5 * s.bsq;
         }
         if (low_beta) {
-            if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY_BETA;
+            if ((methods & 4) && entropy()) return C2P_ENTROPY_BETA;
             return fail(C2P_FAIL | C2P_FAIL_ENT);
         }
     }
@@ -455,35 +482,40 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             if (learned) {
                 W = wguess;
                 v2 = ResidW{&c}.v2(wguess);
+                if (!(W > 0.0) || !finite64(W)) W = c.D;
+                v2 = fmin(v2, V2MAX);
             } else if (MIXED) {
-                // (W, v^2) formed in FP32 from the chosen FP32 primitives
+                // (W, v^2) formed and checked in FP32 from the chosen FP32 primitives
                 const float r0 = extrap ? startf[KRHO] : guessf[KRHO], e0 = extrap ? startf[KUU] : guessf[KUU];
                 const float u1 = extrap ? startf[KU1] : guessf[KU1], u2 = extrap ? startf[KU2] : guessf[KU2],
                             u3 = extrap ? startf[KU3] : guessf[KU3];
                 const float usq = spatial_sq(*gf, u1, u2, u3);
-                v2 = (double)(usq / (1.0f + usq));
-                W = (double)((1.0f + usq) * (r0 + par.gam_f * e0));
+                const float Wf = (1.0f + usq) * (r0 + par.gam_f * e0);
+                // v^2 below 1 (the largest float under 1.0): usq / (1 + usq) rounds to 1 for usq > ~1.7e7
+                v2 = (double)fminf(usq / (1.0f + usq), 0.99999994f);
+                W = (Wf > 0.0f && Wf < INFINITY) ? (double)Wf : c.D;
             } else {
                 const double usq = spatial_sq(g, guess[KU1], guess[KU2], guess[KU3]);
                 v2 = usq / (1.0 + usq);
                 W = (1.0 + usq) * (guess[KRHO] + par.gam * guess[KUU]);
+                if (!(W > 0.0) || !finite64(W)) W = c.D;
+                v2 = fmin(v2, V2MAX);
             }
-            if (!(W > 0.0) || !finite64(W)) W = c.D;
-            v2 = fmin(v2, V2MAX);
             int it;
             const bool conv = MIXED ? c2p_newton_mixed(c, par, W, v2, it)
                                     : c2p_newton<true>(c, W, v2, par.tol, par.nr_maxit, it);
             iters += it;
             if (conv) {
-                c2p_recover_w(c, W, v2, P);
+                if (MIXED) c2p_recover_mixed(c, W, v2, par.ig, P);
+                else c2p_recover_w(c, W, v2, P);
                 if (c2p_physical(P, v2)) return C2P_NR;
-                if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
+                if ((methods & 4) && entropy()) return C2P_ENTROPY;
                 return fail(C2P_FAIL | C2P_FAIL_ENT);
             }
         }
     }
     if ((methods & 2) && c2p_brent_w(c, par.brent_maxit, P)) return C2P_BRENT_W;
-    if ((methods & 4) && c2p_entropy(c, par.brent_maxit, P)) return C2P_ENTROPY;
+    if ((methods & 4) && entropy()) return C2P_ENTROPY;
     return fail(C2P_FAIL | C2P_FAIL_ENT);
 }
 

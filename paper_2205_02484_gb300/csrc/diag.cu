@@ -248,8 +248,19 @@ __global__ void k_state_in(Grid g, const double *Pa, const double *Ua)
     int j = (int)(r % g.n2), i = (int)(r / g.n2);
     long long z = zidx(g, i, j, k);
     RS *P = (RS *)g.P[0];
-    for (int c = 0; c < NP; c++) P[c * g.nz + z] = (RS)Pa[c * nact + t];
-    for (int c = 0; c < NU; c++) g.U[c * g.nz + z] = Ua[c * nact + t];
+    // a value is finite unless its exponent bits are all set (integer test on the high word)
+    unsigned bad = 0;
+    for (int c = 0; c < NP; c++) {
+        const double v = Pa[c * nact + t];
+        bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+        P[c * g.nz + z] = (RS)v;
+    }
+    for (int c = 0; c < NU; c++) {
+        const double v = Ua[c * nact + t];
+        bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+        g.U[c * g.nz + z] = v;
+    }
+    if (bad) atomicOr(g.status, ST_NONFINITE);
 }
 
 template <typename RS>

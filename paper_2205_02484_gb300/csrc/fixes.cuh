@@ -52,9 +52,9 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
         for (int m = KU1; m < NP; m++) qf[m] = (float)q[m];
         St<float> s;
         get_state(qf, *gf, s);
-        bsq = (double)s.bsq;
         usqf = s.usq;
         ceil = s.bsq * g.isig_f > rf || s.bsq * g.ibu_f > uf;
+        bsq = ceil ? (double)s.bsq : 0.0; // widened only where a ceiling acts
     } else {
         if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
         if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }

@@ -718,6 +718,12 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     int meth = fl & 7;
     if (fl & C2P_FAIL) {
         cn.fail += 1;
+        // a non-finite conserved component cannot be repaired by the fixups
+        // (they average the primitives, never B): report it
+        bool fin = true;
+#pragma unroll
+        for (int c = 0; c < NU; c++) fin = fin && finite64(Un[c]);
+        if (!fin) atomicOr(g.status, ST_NONFINITE);
         g.flag[z] = 1;
         int slot = atomicAdd(g.nfail, 1);
         if (slot < g.nfix_cap) g.faillist[slot] = (int)t;

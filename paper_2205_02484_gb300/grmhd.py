@@ -24,6 +24,7 @@ C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
 C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT = 8, 16, 32
 NP, NU = 8, 9
 
+EINVAL, ECUDA, ENOMEM, ENONFINITE, EFIXUP, EITER, ESTATE = -1, -2, -3, -4, -5, -6, -7
 ERRORS = {-1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENONFINITE", -5: "EFIXUP", -6: "EITER",
           -7: "ESTATE"}
 

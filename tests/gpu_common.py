@@ -33,11 +33,14 @@ def gpu_mod():
 
 
 def make_pair(n1, n2, n3, gam=13.0 / 9.0, a=0.9375, r_out=40.0, precision=0, metric=0, riemann=0,
-              stream=True, **box):
-    """Oracle grid and GPU context with identical parameters."""
+              stream=True, phys=None, **box):
+    """Oracle grid and GPU context with identical parameters (phys: solver
+    and limit parameters set on both sides, e.g. nr_maxit)."""
     G = gpu_mod()
+    phys = dict(phys or {})
     kw = dict(n1=n1, n2=n2, n3=n3, gam=gam, a=a, r_out=r_out, metric=metric, riemann=riemann)
     kw.update(box)
+    kw.update(phys)
     op = oracle.default_params(**kw)
     og = oracle.Grid(op)
     gkw = dict(r_out=r_out, precision=precision, metric=metric, riemann=riemann, a=a)
@@ -45,7 +48,7 @@ def make_pair(n1, n2, n3, gam=13.0 / 9.0, a=0.9375, r_out=40.0, precision=0, met
     gp = G.default_grid(n1, n2, n3, **gkw)
     if stream:
         gp.stream = torch.cuda.current_stream().cuda_stream
-    ctx = G.init_grid(gp, G.default_phys(gam=gam))
+    ctx = G.init_grid(gp, G.default_phys(gam=gam, **phys))
     G.set_metric(ctx, a, metric)
     return og, ctx
 
@@ -69,4 +72,16 @@ def field_err(x_gpu, x_orc, positive=None):
             out.append((np.abs(a - b) / np.abs(b)).max())
         else:
             out.append(np.abs(a - b).max() / scale)
+    return np.array(out)
+
+
+def pointwise_err(x_gpu, x_orc):
+    """The per-field metric err_f = max_z |x_gpu - x_orc| / (|x_orc| +
+    1e-12 max_z |x_orc|), pointwise for every field (reported beside
+    field_err, whose signed fields use the max-norm)."""
+    out = []
+    for f in range(x_orc.shape[0]):
+        a, b = x_gpu[f], x_orc[f]
+        den = np.abs(b) + 1e-12 * np.abs(b).max() + 1e-300
+        out.append((np.abs(a - b) / den).max())
     return np.array(out)

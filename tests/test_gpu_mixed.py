@@ -2,11 +2,11 @@
 variables and inversion) against the FP64 oracle.
 
 Error metric as in gpu_common.field_err.  Targets: per-step primitive error
-<= 1e-4 away from the cold atmosphere, and short-window horizon accretion rate
-and magnetic flux within 1%.  The cold, nearly static atmosphere at large
-radius is where FP32 fluxes lose the most: there the internal energy is
-1e-7..1e-4 of the rest mass, so an FP32 rounding of the momentum or energy
-flux becomes a large relative change of u.  The test states the error there
+<= 1e-4 on every zone, and short-window horizon accretion rate and magnetic
+flux within 1%.  The cold, nearly static atmosphere at large radius is where
+FP32 fluxes lose the most: there the internal energy is 1e-7..1e-4 of the
+rest mass, so an FP32 rounding of the momentum or energy flux becomes a large
+relative change of u; the test prints the torus body and the whole grid
 separately.
 """
 import numpy as np
@@ -43,8 +43,8 @@ def test_mixed_one_step_error_by_region(riemann):
     print("mixed per-field error, torus zones:", e_disk)
     print("mixed per-field error, all zones:  ", e_all)
     assert e_disk.max() < 1e-4, e_disk
-    # atmosphere: bounded by FP32 rounding of the fluxes times rho/u
-    assert np.isfinite(e_all).all() and e_all.max() < 1e-1, e_all
+    # every zone, the cold atmosphere included, within the same per-step bound
+    assert e_all.max() < 1e-4, e_all
     # conserved variables stay FP64-accumulated: their per-step error follows the fluxes
     eU = field_err(Ug, Uo)
     print("mixed conserved error:", eU)
