@@ -32,6 +32,51 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_BYTES_PER_ZONE_CYCLE = {"mixed": 344.0, "fp64": 472.0}
+# algorithmic HBM bytes per zone of one stage update: the predictor reads P^n
+# (8 x 4 B in the mixed path) and U^n (9 x 8 B) and writes P-hat; the corrector
+# reads P-hat and U^n and writes U^{n+1} and P^{n+1} (their sum is the step's 344 B)
+UPDATE_BYTES_PER_ZONE = {"pred": 136.0, "corr": 208.0}
+
+# Algorithmic FP64 flops of the inversion of Section 2.3, from the oracle's
+# operation counter (oracle/opcount.cpp: the oracle's own inversion compiled
+# with a counting scalar; the figures are pinned by tests/test_oracle_opcount.py
+# against a hand count): a Newton-only inversion costs C2P_FIXED_FLOPS (set-up
+# 106, start 33, Newton constants 3, recovery 29) plus C2P_NEWTON_FLOPS per
+# Newton step; the beta switch of the FP64 path (four-velocity and b^2 of the
+# guess, gas pressure, beta test) adds C2P_BETA_FLOPS.  The stage update adds
+# RK_FLOPS for U^n + dt_stage * rhs over the 9 conserved components.
+C2P_FIXED_FLOPS = 171.0
+C2P_NEWTON_FLOPS = 61.0
+C2P_BETA_FLOPS = 120.0
+RK_FLOPS = 18.0
+# FP64 roofline from unit counts and clocks: 152 SMs x 2 FP64 FMA per clock
+# x 2 flops x 2.07 GHz (the maximum SM clock); the FMA-chain probe is reported beside it
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes per zone of one k_update launch (dram__bytes_read.sum +
+# dram__bytes_write.sum, ncu, one predictor launch of the 96^3 mixed torus;
+# profiles/k_update_mixed_96cubed.md), valid while the kernel's sources hash to
+# UPDATE_SOURCES_SHA (else the bench reports traffic null)
+UPDATE_DRAM_BYTES_PER_ZONE = 246.6
+UPDATE_SOURCES = ("stage_items.cuh", "con2prim.cuh", "fixes.cuh", "physics.cuh", "common.cuh", "step.cu")
+UPDATE_SOURCES_SHA = "4da4859d40cb2a04"
+
+
+def update_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in UPDATE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2205_02484_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def parse():
@@ -383,7 +428,6 @@ def _slab_state(G, torch, e, dev):
 # FP64 flops per inversion of k_con2prim on these states (ncu count of DFMA x 2
 # + DMUL + DADD, 1e6 inversions from a guess within 1e-4): see the profile
 # summary of the kernel
-CON2PRIM_FP64_FLOPS = 1902.0
 
 
 def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
@@ -422,10 +466,16 @@ def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
            "ms": best, "inversions_per_s": n / (best * 1e-3),
            "newton_iters_mean": float(it[fl == 0].mean()), "frac_newton": float((fl == 0).mean()),
            "frac_entropy_beta": float((fl == 3).mean()), "frac_fail": float(((fl & 8) != 0).mean())}
-    if CON2PRIM_FP64_FLOPS:
-        tf = CON2PRIM_FP64_FLOPS * n / (best * 1e-3) / 1e12
-        out.update({"fp64_flops_per_inversion": CON2PRIM_FP64_FLOPS, "tflops_fp64": tf,
-                    "frac_of_fp64_peak": tf / (152 * 2 * 2 * 2.070e9 / 1e12)})
+    # algorithmic flops of the Newton inversions (oracle op counter); the
+    # entropy-branch zones are left out of the numerator (a lower bound)
+    nr = fl == 0
+    flops = float(((C2P_FIXED_FLOPS + C2P_BETA_FLOPS) + C2P_NEWTON_FLOPS * it[nr]).sum())
+    tf = flops / (best * 1e-3) / 1e12
+    out.update({"fp64_flops_newton_inversions": flops,
+                "flops_per_newton_inversion": flops / max(int(nr.sum()), 1),
+                "tflops_fp64_algorithmic": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
+                "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                "flops_source": "oracle operation counter (oracle/opcount.cpp), Newton inversions only"})
     return out
 
 
@@ -756,6 +806,7 @@ def main():
     # the same step by windows: 5 windows of 20 steps, their median (the
     # headline above is one window of exactly `steps` steps)
     windows = None
+    d_w0 = G.diagnostics(ctx)
     if world == 1:
         wms = []
         for _ in range(5):
@@ -797,31 +848,34 @@ def main():
     kernels_ms = {k: round(v, 4) for k, v in parts.items()}
     fp64_peak = G.peak_probe(local, True)
     fp32_peak = G.peak_probe(local, False)
-    # The dominant kernel (stage update + FP64 inversion) is bound by the FP64
-    # pipe, which executes the FP64 arithmetic and also every FP32 <-> FP64
-    # conversion and FP64 compare at the same rate.  Per zone and stage ncu
-    # counts, on the 96^3 mixed torus, 199.2 FP64-pipe thread instructions
-    # (sm__inst_executed_pipe_fp64 x 32): DFMA 48.1, DMUL 48.5, DADD 20.7,
-    # other FP64 arithmetic 7.1, conversions 46.3 and 28.5 more FP64-pipe
-    # instructions outside ncu's operation classes -- 165.4 FP64 flops
-    # (DFMA = 2).  Its DRAM traffic there was 246.4 B per zone
-    # (scaled here by zone count).  The roofline is the pipe's issue rate:
-    # 152 SMs x 2 FP64 lanes per clock x 2.07 GHz = 629 G thread-instr/s
-    # (x 2 flops for DFMA = 1.26 TFLOP/s).
-    fp64_slots_per_zone_stage = 199.2
-    fp64_flops_per_zone_stage = 165.4
-    pipe_peak = 152 * 2 * 2.070e9 / 1e9
-    fp64_peak_units = 2 * pipe_peak / 1e3
-    ach = fp64_slots_per_zone_stage * zones / (upd * 1e-3) / 1e9
-    ach_tf = fp64_flops_per_zone_stage * zones / (upd * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_update (stage update + FP64 inversion)",
-                "achieved": ach, "peak": pipe_peak, "unit": "G FP64-pipe thread-instr/s",
-                "frac": ach / pipe_peak, "traffic": 246.4 * zones,
-                "peak_source": "152 SMs x 2 FP64 lanes/clk x 2070 MHz (nominal unit count and clock); FMA-chain "
-                               f"probe on this GPU: {fp64_peak:.3f} TFLOP/s = {fp64_peak * 500:.0f} G DFMA/s",
-                "ms_per_launch": upd, "fp64_pipe_slots_per_zone": fp64_slots_per_zone_stage,
-                "fp64_flops_per_zone": fp64_flops_per_zone_stage, "fp64_tflops": ach_tf,
-                "fp64_tflops_frac": ach_tf / fp64_peak_units, "fp64_pipe_active_ncu": 0.844}
+    hbm_peak, hbm_peak_src = measured_peaks()
+    # Roofline of the dominant kernel, the stage update + inversion (k_update):
+    # bound by the FP64 pipe (GB300: 1/64 of the FP32 rate).  achieved = the
+    # algorithmic FP64 flops of one launch (the oracle's operation count of the
+    # inversion at the Newton steps per zone measured in this run, plus the RK
+    # accumulation) / the launch's CUDA-event time measured above.
+    dd = {k: diag[k] - d_w0[k] for k in ("nr_iters", "n_nr", "n_floor", "n_steps")}
+    stages = 2.0 * zones * max(dd["n_steps"], 1)
+    newton_per_zone = dd["nr_iters"] / stages
+    flops_zone = C2P_FIXED_FLOPS + C2P_NEWTON_FLOPS * newton_per_zone + RK_FLOPS
+    ach_tf = flops_zone * zones / (upd * 1e-3) / 1e12
+    upd_bytes = 0.5 * (UPDATE_BYTES_PER_ZONE["pred"] + UPDATE_BYTES_PER_ZONE["corr"])
+    upd_gbs = upd_bytes * zones / (upd * 1e-3) / 1e9
+    sha = update_sources_sha()
+    traffic = UPDATE_DRAM_BYTES_PER_ZONE * zones if sha == UPDATE_SOURCES_SHA else None
+    roofline = {"bound": "alu", "kernel": "k_update<float> (stage update + FP64 inversion, mixed path)",
+                "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach_tf / FP64_PEAK_TFLOPS,
+                "traffic": traffic,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (unit counts and maximum clock); "
+                               f"FMA-chain probe on this GPU {fp64_peak:.3f} TFLOP/s",
+                "ms_per_launch": upd, "zones_per_launch": zones,
+                "flops_per_zone_stage": flops_zone, "newton_steps_per_zone_stage": newton_per_zone,
+                "floored_zones_per_stage": dd["n_floor"] / stages,
+                "flops_source": "oracle operation counter: inversion 171 + 61 per Newton step, RK 18",
+                "traffic_source": "ncu dram bytes of one 96^3 launch, 246.6 B/zone, scaled by zone count"
+                                  if traffic else f"kernel sources changed since the ncu capture (sha {sha})",
+                "hbm": {"bytes_per_zone_stage": upd_bytes, "achieved": upd_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": upd_gbs / hbm_peak, "peak_source": hbm_peak_src}}
     hbm_step = HBM_BYTES_PER_ZONE_CYCLE["mixed"] * zones / (ms_step * 1e-3) / 1e9
     gpu_launches = 21 * args.steps
     # ---- e2e through the public API with pinned host buffers: every step
@@ -908,7 +962,7 @@ def main():
         prof64 = G.step_profiled(c64, 1)
         fp64 = {"value": aggregate_value(zones, k64, world, ms64), "unit": "zone-cycles/s", "steps": k64,
                 "ms_per_step": ms64 / k64,
-                "hbm_frac_of_measured": HBM_BYTES_PER_ZONE_CYCLE["fp64"] * zones / (ms64 / k64 * 1e-3) / 1e9 / 6674.5,
+                "hbm_frac_of_measured": HBM_BYTES_PER_ZONE_CYCLE["fp64"] * zones / (ms64 / k64 * 1e-3) / 1e9 / hbm_peak,
                 "kernels_ms": {k: round(v, 3) for k, v in prof64.items()}}
         c64.close()
     # ---- batched ensemble (independent tori, one launch per kernel class)
@@ -964,7 +1018,7 @@ def main():
             "vs_baseline": None, "dtype": "f32 fluxes + f64 U/inversion", "data": "synthetic",
             "config": workload_config(n),
             "hbm_roofline": {"bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE["mixed"], "achieved_gbs": hbm_step,
-                             "peak_gbs": 6674.5, "frac_of_measured": hbm_step / 6674.5,
+                             "peak_gbs": hbm_peak, "frac_of_measured": hbm_step / hbm_peak,
                              "frac_of_nominal_7900": hbm_step / 7900.0},
             "roofline": roofline,
             "peaks_probe_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},

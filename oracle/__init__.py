@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = ["geometry.c", "physics.c", "con2prim.c", "grid.c", "torus.c", "mlp.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_CNT_PATH = os.path.join(_HERE, "libopcount.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -44,7 +45,53 @@ def build(force: bool = False) -> str:
            "-o", tmp] + srcs + ["-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
+    build_counter(force=True)
     return _LIB_PATH
+
+
+def build_counter(force: bool = False) -> str:
+    """Compile libopcount.so: the oracle's physics.c and con2prim.c compiled
+    again as C++ with an operation-counting scalar (opcount.cpp)."""
+    deps = [os.path.join(_HERE, s) for s in ("opcount.cpp", "physics.c", "con2prim.c", "orc.h")]
+    if not force and os.path.exists(_CNT_PATH):
+        if all(os.path.getmtime(s) <= os.path.getmtime(_CNT_PATH) for s in deps):
+            return _CNT_PATH
+    tmp = _CNT_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, "opcount.cpp"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _CNT_PATH)
+    return _CNT_PATH
+
+
+_cnt = None
+
+
+def count_con2prim(U, geom34, guess, gam, methods=15, nr_tol=1e-10, beta_entropy=1e-2, nr_maxit=30,
+                   brent_maxit=100):
+    """The oracle's inversion of one state (Section 2.3) with its floating
+    point operations counted: (flag, P, iters, counts) where counts has
+    add, mul, div, sqrt, special (pow/exp/log calls) and flops (add + mul +
+    div + sqrt).  geom34: gcov (16), gcon (16), sqrt(-g), alpha."""
+    global _cnt
+    with _lock:
+        if _cnt is None:
+            build_counter()
+            L = C.CDLL(_CNT_PATH)
+            f = L.orc_count_con2prim
+            f.restype = C.c_int
+            f.argtypes = [_D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _D,
+                          C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+            _cnt = L
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    g = np.ascontiguousarray(geom34, dtype=np.float64)
+    q = np.ascontiguousarray(guess, dtype=np.float64)
+    P = np.zeros(NP)
+    it = C.c_int(0)
+    out = (C.c_longlong * 6)()
+    fl = _cnt.orc_count_con2prim(_p(U), _p(g), _p(q), gam, nr_tol, beta_entropy, nr_maxit, brent_maxit,
+                                 methods, _p(P), C.byref(it), out)
+    keys = ("add", "mul", "div", "sqrt", "special", "flops")
+    return fl, P, it.value, dict(zip(keys, (int(v) for v in out)))
 
 
 class Params(C.Structure):

@@ -17,7 +17,9 @@
 #ifndef ORC_H
 #define ORC_H
 
+#ifndef __cplusplus
 #include <complex.h>
+#endif
 #include <stdint.h>
 
 #define ORC_NG 2
@@ -95,8 +97,10 @@ typedef struct orc_grid {
 double orc_r_of_x1(const orc_grid *G, double X1);
 double orc_th_of_x2(const orc_grid *G, double X2);
 void orc_ks_gcov(double r, double th, double a, double g[4][4]);
+#ifndef __cplusplus /* complex-step derivatives: C only (the op counter compiles physics as C++) */
 void orc_code_gcov_c(const orc_grid *G, double complex X1, double complex X2,
                      double complex g[4][4]);
+#endif
 int orc_invert4(const double m[4][4], double inv[4][4], double *det);
 int orc_geom_at(const orc_grid *G, double X1, double X2, orc_geom *out);
 void orc_conn_at(const orc_grid *G, double X1, double X2, double conn[4][4][4]);
