@@ -27,7 +27,8 @@ __device__ __forceinline__ bool gamma_cap(const Grid &g, const Geo<double> &geo,
     return false;
 }
 
-// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied.
+// returns bit 1 = modified, bit 2 = ceiling applied, bit 4 = Lorentz cap applied,
+// bit 8 = density floored.
 // gsp: the zone's spatial inverse metric (for the re-inversion of a ceiling).
 // MIXED: b^2 and ut^2 (neither involves rho or u) come from one FP32 state of
 // the record gf; the exact FP64 Lorentz test runs only where the FP32 ut^2 is
@@ -44,7 +45,7 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
         // floors and ceilings decided in FP32, on the values that are stored
         rf = (float)q[KRHO];
         uf = (float)q[KUU];
-        if (rf < gf->rfl) { q[KRHO] = geo.rfl; rf = gf->rfl; res |= 1; }
+        if (rf < gf->rfl) { q[KRHO] = geo.rfl; rf = gf->rfl; res |= 9; }
         if (uf < gf->ufl) { q[KUU] = geo.ufl; uf = gf->ufl; res |= 1; }
         qf[KRHO] = 0.0f;
         qf[KUU] = 0.0f;
@@ -56,7 +57,7 @@ __device__ inline int post_inversion(const Grid &g, const Geo<double> &geo, cons
         ceil = s.bsq * g.isig_f > rf || s.bsq * g.ibu_f > uf;
         bsq = ceil ? (double)s.bsq : 0.0; // widened only where a ceiling acts
     } else {
-        if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 1; }
+        if (q[KRHO] < geo.rfl) { q[KRHO] = geo.rfl; res |= 9; }
         if (q[KUU] < geo.ufl) { q[KUU] = geo.ufl; res |= 1; }
         St<double> s;
         get_state(q, geo, s);
@@ -137,9 +138,13 @@ __device__ inline void post_fixup(const Grid &g, const Geo<double> &geo, double 
 // thermal + kinetic + binding energy, not of the rest mass.
 //
 // qf (mixed path, may be null): the FP32 primitives of q, if the caller has them.
+// keep_rho (mixed path): rho and the velocity are unchanged (only u was
+// floored), so U_rho = sqrt(-g) rho u^t keeps its accumulated FP64 value.  The
+// mixed path also keeps U_B, which no floor, ceiling or cap changes.
 template <bool MIXED = false>
 __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, double gam, double U[NU],
-                               const Geo<float> *gf = nullptr, const float *qfin = nullptr, float gam_f = 0.0f)
+                               const Geo<float> *gf = nullptr, const float *qfin = nullptr, float gam_f = 0.0f,
+                               bool keep_rho = false)
 {
     if (MIXED) {
         float qf[NP];
@@ -147,17 +152,16 @@ __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, doubl
         for (int m = 0; m < NP; m++) qf[m] = qfin ? qfin[m] : (float)q[m];
         St<float> s;
         get_state(qf, *gf, s);
-        float Uf[NU], Ff[NU];
-        prim_to_UF2<float, true>(qf, *gf, s, gam_f, 1, Uf, Ff);
-        double gm1 = (double)(s.usq / (s.gamma + 1.0f));
-        U[KRHO] = geo.gdet * q[KRHO] * ((1.0 + gm1) * geo.ialpha);
+        float Uf[NU];
+        prim_to_UF<float, true>(qf, *gf, s, gam_f, 0, Uf);
+        if (!keep_rho) {
+            double gm1 = (double)(s.usq / (s.gamma + 1.0f));
+            U[KRHO] = geo.gdet * q[KRHO] * ((1.0 + gm1) * geo.ialpha);
+        }
         U[1] = (double)Uf[1] - U[KRHO];
         U[2] = (double)Uf[2];
         U[3] = (double)Uf[3];
         U[4] = (double)Uf[4];
-        U[KB1] = geo.gdet * q[KB1];
-        U[KB2] = geo.gdet * q[KB2];
-        U[KB3] = geo.gdet * q[KB3];
         U[KENT] = (double)Uf[KENT];
         return;
     }

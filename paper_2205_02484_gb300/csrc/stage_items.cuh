@@ -736,7 +736,7 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         int res = post_inversion<MX>(g, geo, gsp, qn, Un, gfr, qnf);
         if (res & 1) {
             cn.fl += 1;
-            cons_of<MX>(qn, geo, g.gam, Un, gfr, MX ? qnf : nullptr, g.gam_f);
+            cons_of<MX>(qn, geo, g.gam, Un, gfr, MX ? qnf : nullptr, g.gam_f, (res & 14) == 0);
         }
         cn.ce += (res & 2) != 0;
         cn.gc += (res & 4) != 0;
