@@ -56,9 +56,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # dram__bytes_write.sum, ncu, one predictor launch of the 96^3 mixed torus;
 # profiles/k_update_mixed_96cubed.md), valid while the kernel's sources hash to
 # UPDATE_SOURCES_SHA (else the bench reports traffic null)
-UPDATE_DRAM_BYTES_PER_ZONE = 246.7
+UPDATE_DRAM_BYTES_PER_ZONE = 252.5
 UPDATE_SOURCES = ("stage_items.cuh", "con2prim.cuh", "fixes.cuh", "physics.cuh", "common.cuh", "step.cu")
-UPDATE_SOURCES_SHA = "6327773dd0e2291e"
+UPDATE_SOURCES_SHA = "c0e117bcc3478655"
 
 
 def update_sources_sha():
@@ -581,7 +581,8 @@ MLP_TRAIN_FLOPS = 2 * (5 * 64 + 64 * 64 + 64) + 2 * 64 * 64 * 2 + 2 * 64 * 5 + 3
 
 def counters(G, ctx):
     d = G.diagnostics(ctx)
-    return {k: d[k] for k in ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_fixed")}
+    return {k: d[k] for k in ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_fixed",
+                              "n_learned")}
 
 
 def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4, steps=10):
@@ -613,7 +614,7 @@ def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4,
     n = 1_000_000
     P, loc, U, f, y = G.mlp_samples(ctx, 7, 50_000_000, n, device=True)
     inv = {}
-    for name, learned in (("plain_static_start", False), ("learned_start", True)):
+    for name, learned in (("plain_static_start", 0), ("learned_start", 1), ("learned_rescue", 2)):
         g0 = P.clone()
         g0[2:5] = 0.0
         flags = torch.zeros(n, dtype=torch.int32, device=P.device)
@@ -623,8 +624,11 @@ def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4,
         fl = flags.cpu().numpy()
         it = iters.cpu().numpy()
         nr = fl == 0
+        nr = (fl & 7) == 0
+        nr &= (fl & 8) == 0
         inv[name] = {"ms": ms, "inversions_per_s": n / (ms * 1e-3), "newton_iters_mean": float(it[nr].mean()),
                      "frac_newton": float(nr.mean()), "frac_brent": float((fl == 1).mean()),
+                     "frac_learned_rescue": float(((fl & 64) != 0).mean()),
                      "frac_entropy": float((fl == 2).mean()), "frac_entropy_beta": float((fl == 3).mean()),
                      "frac_fail": float(((fl & 8) != 0).mean())}
     g0 = P.clone()
@@ -634,11 +638,12 @@ def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4,
     fl, it = flags.cpu().numpy(), iters.cpu().numpy()
     inv["exact_prims_start"] = {"newton_iters_mean": float(it[fl == 0].mean()), "frac_newton": float((fl == 0).mean())}
 
-    # the 256x192x192 step: plain start (previous-stage primitives) vs learned
+    # the 256x192x192 step: plain order (previous-stage primitives, extrapolated)
+    # vs the learned rescue before Brent
     G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
     zones = ctx.nact
     step = {}
-    for name, learned in (("plain_start", False), ("learned_start", True)):
+    for name, learned in (("plain_start", False), ("learned_rescue", True)):
         G.set_learned_guess(ctx, learned)
         G.step(ctx, 2)
         c0 = counters(G, ctx)
@@ -650,14 +655,48 @@ def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4,
                       "newton_iters_per_newton_zone": d["nr_iters"] / max(d["n_nr"], 1),
                       "fallback_per_inversion": (d["n_brent"] + d["n_entropy"]) / inversions,
                       "entropy_beta_per_inversion": d["n_entropy_beta"] / inversions,
-                      "fail_per_inversion": d["n_fail"] / inversions}
+                      "fail_per_inversion": d["n_fail"] / inversions,
+                      "learned_rescue_per_inversion": d["n_learned"] / inversions}
     G.set_learned_guess(ctx, False)
+    # the zone class the rescue serves: the first step after a restart whose
+    # primitives know rho, u and B but not the flow (velocities zero), with
+    # Newton capped at 8 steps; without the network the zones that need more
+    # Newton steps from that start take the 1D Brent solve
+    th, nm = G.mlp_get(ctx)
+    gp8 = G.default_grid(256, 192, 192, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
+    gp8.stream = stream.cuda_stream
+    c8 = G.init_grid(gp8, G.default_phys(gam=4.0 / 3.0, nr_maxit=8))
+    G.set_metric(c8, 0.9375, G.KERR_MKS)
+    G.mlp_load(c8, th, nm)
+    G.init_torus(c8, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.02, seed=2)
+    G.step(c8, 5)
+    Pd = torch.empty((8,) + c8.shape, dtype=torch.float64, device=f"cuda:{device}")
+    Ud = torch.empty((9,) + c8.shape, dtype=torch.float64, device=f"cuda:{device}")
+    _, _, t8, dt8 = G.get_state(c8, Pd, Ud)
+    Pd[2:5] = 0.0
+    restart = {}
+    for name, learned in (("plain_start", False), ("learned_rescue", True)):
+        G.set_learned_guess(c8, learned)
+        G.set_state(c8, Pd, Ud, t8, dt8)
+        G.step(c8, 1)   # the graph is captured on the first call: time the second restart
+        G.set_state(c8, Pd, Ud, t8, dt8)
+        c0 = counters(G, c8)
+        ms = ev_time(lambda: G.step(c8, 1))
+        c1 = counters(G, c8)
+        d = {k: c1[k] - c0[k] for k in c0}
+        restart[name] = {"ms_first_step": ms, "brent": d["n_brent"], "learned_rescue": d["n_learned"],
+                         "entropy": d["n_entropy"], "fail": d["n_fail"],
+                         "newton_iters_per_zone_stage": d["nr_iters"] / (2.0 * zones)}
+    G.set_learned_guess(c8, False)
+    c8.close()
+    del Pd, Ud
     ctx.close()
     return {"workload": "learned Newton start: 5-64-64-1 MLP, BF16 weights, FP32 accumulate; trained on the GPU "
                         f"on {n_samples} seeded samples x {epochs} epochs (log-uniform rho in [1e-6,1], u/rho in "
                         "[1e-4,10], Gamma in [1,50], b^2/rho in [1e-3,100]) at the 256x192x192 MKS grid's metric; "
                         "step: 256x192x192 FM torus, mixed precision",
-            "train": train, "inversion_1e6_heldout": inv, "step_256x192x192": step}
+            "train": train, "inversion_1e6_heldout": inv, "step_256x192x192": step,
+            "restart_no_velocity_newton_cap_8": restart}
 
 
 # ------------------------------------------------------------ CPU oracle

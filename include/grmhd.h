@@ -74,6 +74,7 @@ extern "C" {
 #define GRMHD_C2P_FAIL 8         /* inversion failed: zone needs a fixup */
 #define GRMHD_C2P_FAIL_D 16      /* D <= 0 or non-finite input */
 #define GRMHD_C2P_FAIL_ENT 32    /* entropy inversion impossible */
+#define GRMHD_C2P_LEARNED 64     /* with GRMHD_C2P_NR: Newton converged from the learned rescue start */
 
 typedef struct grmhd_ctx grmhd_ctx;
 
@@ -135,6 +136,7 @@ typedef struct {
     double eta; /* (edot - mdot) / |mdot| (Eqs. 38, 41); 0 when mdot = 0 */
     long long nr_iters, n_nr, n_brent, n_entropy, n_entropy_beta, n_fail, n_floor, n_ceil,
         n_gcap, n_fixed, fix_sweeps, n_steps;
+    long long n_learned; /* inversions converged by Newton from the learned rescue start (grmhd_set_learned_guess) */
 } grmhd_diag;
 
 /* Create a context: validates the parameters, allocates the device state and
@@ -190,8 +192,12 @@ int grmhd_step(grmhd_ctx *ctx, int nsteps);
  * starting from and overwriting P_inout (8 x n).  flags[n] receives the
  * GRMHD_C2P_* code, iters[n] (may be NULL) the Newton iterations.  With
  * use_learned_guess = 1 Newton first starts from the loaded MLP's W and, if
- * it does not converge, again from P_inout; iters counts both.  Same method
- * order and tolerances as the step (Section 2.3). */
+ * it does not converge, again from P_inout (for callers whose P_inout is a
+ * poor start); with use_learned_guess = 2 Newton starts from P_inout and, if
+ * it does not converge, from the MLP's W before Brent (the step's order, see
+ * grmhd_set_learned_guess; such zones are flagged GRMHD_C2P_NR |
+ * GRMHD_C2P_LEARNED).  iters counts every Newton run.  Same method order
+ * and tolerances as the step otherwise (Section 2.3). */
 int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P_inout,
                    int *flags, int *iters, long n, int use_learned_guess, int on_device);
 
@@ -407,13 +413,18 @@ typedef struct {
  * The training epochs take the set in a fresh permutation each. */
 int grmhd_mlp_train(grmhd_ctx *ctx, const grmhd_mlp_train_params *tp, grmhd_mlp_train_report *rep);
 
-/* on = 1: every inversion of grmhd_step starts Newton from the loaded
- * network's W (and v^2 of Eq. 29); if that Newton does not converge, Newton
- * runs again from the stage's primitives before the Brent and entropy
- * fallbacks.  on = 0 restores the plain start.  Tolerances and the rest of
- * the method order are unchanged.  Needs a loaded network for on = 1; later loads or training
- * runs replace the network in place.  Ensemble steps always use the plain
- * start. */
+/* on = 1: an inversion of grmhd_step whose Newton solves from the stage's
+ * own starts (the previous primitives, and in GRMHD_MIXED first their
+ * extrapolation over the previous half step) do not converge runs Newton once
+ * more from the loaded network's W (v^2 of Eq. 29) before the Brent and
+ * entropy fallbacks; grmhd_diag.n_learned counts the zones it converges.  The
+ * previous-step start stays first because it is far closer to the root in a
+ * smooth flow (1.08 Newton steps per zone at 256^3 against ~3 from the
+ * network's W); the network replaces Brent where that start fails.  The
+ * features are formed in FP32 from the inversion's FP64 invariants.  on = 0
+ * restores the plain order.  Tolerances are unchanged.  Needs a loaded
+ * network for on = 1; later loads or training runs replace the network in
+ * place.  Ensemble steps always use the plain order. */
 int grmhd_set_learned_guess(grmhd_ctx *ctx, int on);
 
 /* ---------------------------------------------------------------------

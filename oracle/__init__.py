@@ -67,11 +67,12 @@ _cnt = None
 
 
 def count_con2prim(U, geom34, guess, gam, methods=15, nr_tol=1e-10, beta_entropy=1e-2, nr_maxit=30,
-                   brent_maxit=100):
+                   brent_maxit=100, wguess=0.0):
     """The oracle's inversion of one state (Section 2.3) with its floating
     point operations counted: (flag, P, iters, counts) where counts has
     add, mul, div, sqrt, special (pow/exp/log calls) and flops (add + mul +
-    div + sqrt).  geom34: gcov (16), gcon (16), sqrt(-g), alpha."""
+    div + sqrt).  geom34: gcov (16), gcon (16), sqrt(-g), alpha; wguess > 0:
+    Newton first starts from that W."""
     global _cnt
     with _lock:
         if _cnt is None:
@@ -79,8 +80,8 @@ def count_con2prim(U, geom34, guess, gam, methods=15, nr_tol=1e-10, beta_entropy
             L = C.CDLL(_CNT_PATH)
             f = L.orc_count_con2prim
             f.restype = C.c_int
-            f.argtypes = [_D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _D,
-                          C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+            f.argtypes = [_D, _D, _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                          C.c_double, _D, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
             _cnt = L
     U = np.ascontiguousarray(U, dtype=np.float64)
     g = np.ascontiguousarray(geom34, dtype=np.float64)
@@ -89,7 +90,7 @@ def count_con2prim(U, geom34, guess, gam, methods=15, nr_tol=1e-10, beta_entropy
     it = C.c_int(0)
     out = (C.c_longlong * 6)()
     fl = _cnt.orc_count_con2prim(_p(U), _p(g), _p(q), gam, nr_tol, beta_entropy, nr_maxit, brent_maxit,
-                                 methods, _p(P), C.byref(it), out)
+                                 methods, float(wguess), _p(P), C.byref(it), out)
     keys = ("add", "mul", "div", "sqrt", "special", "flops")
     return fl, P, it.value, dict(zip(keys, (int(v) for v in out)))
 

@@ -69,12 +69,13 @@ inline bool isfinite(Num a) { return std::isfinite(a.v); }
 
 /* Inversion of one state by the oracle's con2prim, counted.  geom34: gcov
  * (16), gcon (16), sqrt(-g), alpha of the point; gam, nr_tol, beta_entropy,
- * nr_maxit, brent_maxit: the solver parameters (Sections 2.3-2.4); out[0..5]
- * = add, mul, div, sqrt, pow/exp/log calls, flops (the first four summed); P,
- * the returned flag and iters as orc_con2prim gives them. */
+ * nr_maxit, brent_maxit: the solver parameters (Sections 2.3-2.4); wguess > 0:
+ * Newton first starts from that W (orc_con2prim_w); out[0..5] = add, mul,
+ * div, sqrt, pow/exp/log calls, flops (the first four summed); P, the
+ * returned flag and iters as the oracle's inversion gives them. */
 extern "C" int orc_count_con2prim(const double *U, const double *geom34, const double *guess, double gam,
                                   double nr_tol, double beta_entropy, int nr_maxit, int brent_maxit,
-                                  int methods, double *P, int *iters, long long *out)
+                                  int methods, double wguess, double *P, int *iters, long long *out)
 {
     using namespace orc_count;
     orc_params pn;
@@ -96,7 +97,7 @@ extern "C" int orc_count_con2prim(const double *U, const double *geom34, const d
     for (int c = 0; c < ORC_NU; c++) Un[c] = U[c];
     for (int c = 0; c < ORC_NP; c++) gn[c] = guess[c];
     T = Tally{0, 0, 0, 0, 0};
-    int fl = orc_con2prim(Un, &g, gn, &pn, Pn, iters, methods);
+    int fl = orc_con2prim_w(Un, &g, gn, &pn, Pn, iters, methods, Num(wguess));
     Tally t = T;
     for (int c = 0; c < ORC_NP; c++) P[c] = Pn[c].v;
     out[0] = t.add; out[1] = t.mul; out[2] = t.div; out[3] = t.sqrt; out[4] = t.special;

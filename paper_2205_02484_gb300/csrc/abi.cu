@@ -599,6 +599,7 @@ extern "C" int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out)
     out->n_fixed = (long long)cnt[C_FIXED];
     out->fix_sweeps = (long long)cnt[C_SWEEPS];
     out->n_steps = (long long)cnt[C_STEPS];
+    out->n_learned = (long long)cnt[C_LEARN];
     return grmhd_sync(ctx);
 }
 
@@ -634,6 +635,7 @@ extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, d
     if (!ctx || (n > 0 && (!P || !loc || !U || !flags))) return fail(ctx, GRMHD_EINVAL, "null argument");
     if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
     if (n < 0) return fail(ctx, GRMHD_EINVAL, "n < 0");
+    if (use_learned_guess < 0 || use_learned_guess > 2) return fail(ctx, GRMHD_EINVAL, "use_learned_guess must be 0, 1 or 2");
     if (use_learned_guess && !ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
     if (n == 0) return 0;
     const double *Ud = U;
@@ -652,7 +654,8 @@ extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, d
         Ud = su; Pd = sp; ld = sl; fd = sf; id = iters ? si : nullptr;
     }
     (void)cudaGetLastError();
-    launch_con2prim(ctx->g, Ud, ld, Pd, fd, id, n, use_learned_guess ? ctx->mlp : nullptr, ctx->stream);
+    launch_con2prim(ctx->g, Ud, ld, Pd, fd, id, n, use_learned_guess ? ctx->mlp : nullptr, use_learned_guess,
+                    ctx->stream);
     CK(cudaGetLastError());
     if (!on_device) {
         CK(cudaMemcpyAsync(P, Pd, 8LL * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

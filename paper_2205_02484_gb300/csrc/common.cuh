@@ -63,7 +63,7 @@ struct Geo {
 // counters accumulated on the device (indices into Grid::cnt)
 enum {
     C_NR_ITERS = 0, C_NR, C_BRENT, C_ENT, C_ENT_BETA, C_FAIL, C_FLOOR, C_CEIL, C_GCAP,
-    C_FIXED, C_SWEEPS, C_STEPS, C_NCOUNT
+    C_FIXED, C_SWEEPS, C_STEPS, C_LEARN, C_NCOUNT
 };
 
 // device status word bits

@@ -20,12 +20,14 @@
 // residuals in FP64 but forms the Newton step in FP32 and stops at
 // sqrt(tol).
 #pragma once
+#include "mlp.cuh"
 #include "physics.cuh"
 
 namespace grmhd {
 
 constexpr int C2P_NR = 0, C2P_BRENT_W = 1, C2P_ENTROPY = 2, C2P_ENTROPY_BETA = 3;
 constexpr int C2P_FAIL = 8, C2P_FAIL_D = 16, C2P_FAIL_ENT = 32;
+constexpr int C2P_LEARNED = 64; // with C2P_NR: Newton converged from the learned start
 constexpr double V2MAX = 1.0 - 1.0e-16;
 
 struct C2PIn {
@@ -51,6 +53,38 @@ __device__ __forceinline__ C2PPar c2p_par(const Grid &g)
 __device__ __forceinline__ bool finite64(double x)
 {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
+// Newton starting W from the network for the inversion with invariants c:
+// the features of mlp.cuh formed in FP32 from the FP64 D, Q.n, Qt^2, Bf^2
+// and Q.Bf the inversion has already computed (tau = -Q.n - D subtracted in
+// FP64: it is the small difference of two large numbers for cold gas); the
+// log of a ratio is the difference of logs, clamped at log(1e-30) as the
+// ratio itself would be.  0 when the features are undefined.  Out of line:
+// the network's loops stay out of the register allocation of the update
+// kernel, which reaches this only for the rare zones Newton did not settle.
+// (Measured: with c passed by reference the mixed update runs 168.8 FP64-pipe
+// warp slots per zone-stage against 185.3 with the invariants passed by
+// value -- the same thread-level work, better reconvergence of the divergent
+// Newton steps -- so the reference is kept.)
+static __device__ __noinline__ double c2p_learned_w(const float *buf, const C2PIn &c)
+{
+    const float lo = -69.07755279f; // log(1e-30)
+    const float Df = (float)c.D;
+    const float lD = __logf(Df);
+    float f[MLP_IN];
+    f[0] = fmaxf(__logf((float)(-c.nQ - c.D)) - lD, lo);
+    f[1] = fmaxf(__logf((float)c.Qtsq) - 2.0f * lD, lo);
+    f[2] = fmaxf(__logf((float)c.Bsq) - lD, lo);
+    const float qb = (float)c.QB;
+    f[3] = fmaxf(__logf(qb * qb) - 3.0f * lD, lo);
+    f[4] = lD;
+#pragma unroll
+    for (int k = 0; k < MLP_IN; k++)
+        if (!(f[k] == f[k])) f[k] = lo; // a NaN feature (negative argument) takes the clamp
+    const float y = mlp_log_w_guess(buf, f);
+    const float w = Df * __expf(y);
+    return (w > 0.0f && w < INFINITY) ? (double)w : 0.0;
 }
 
 __device__ __forceinline__ double c2p_pressure(const C2PIn &c, double W, double v2)
@@ -382,8 +416,11 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 // Returns the C2P_* flag; P[5..7] always receive B = U_B / sqrt(-g), and on
 // failure P[0..4] keep the guess (the fixups repair the zone).
 // methods: 1 Newton, 2 Brent-W, 4 entropy, 8 beta switch (15 = paper order).
-// wguess > 0: Newton first starts from that W (learned guess; v^2 from
-// Eq. 29) and, if it does not converge, again from the guess primitives.
+// mlp_first (network buffer or null): Newton first starts from the network's W
+// (v^2 from Eq. 29) and, if it does not converge, from the guess primitives
+// (for callers without a good guess).  mlp_rescue: Newton from the network's
+// W is tried after Newton from the guess (and the extrapolated start) fails
+// and before Brent; a zone it converges returns C2P_NR | C2P_LEARNED.
 // FP64 path: guess = the previous FP64 primitives, Newton takes one more step
 // after the tolerance.  MIXED: guessf = the previous FP32 primitives (guess
 // unused); the starting (W, v^2) and the beta switch are formed in FP32 with
@@ -396,8 +433,9 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 template <bool MIXED = false>
 __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const double gsp[6],
                                const double *guess, const float *guessf, const C2PPar &par, int methods,
-                               double P[NP], int &iters, double wguess = 0.0, const Geo<float> *gf = nullptr,
-                               const float *startf = nullptr, bool have_start = false)
+                               double P[NP], int &iters, const float *mlp_first = nullptr,
+                               const Geo<float> *gf = nullptr, const float *startf = nullptr,
+                               bool have_start = false, const float *mlp_rescue = nullptr)
 {
     iters = 0;
     if (!MIXED) {
@@ -471,19 +509,20 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
         }
     }
     if (methods & 1) {
-        // a learned W, then the extrapolated start, are tried first; Newton from
-        // the guess primitives stays the fallback when they do not converge
+        // a learned W (mlp_first), then the extrapolated start, are tried first;
+        // Newton from the guess primitives follows, then the learned rescue
 #pragma unroll 1
-        for (int a = 0; a < 3; a++) {
-            const bool learned = a == 0, extrap = a == 1;
-            if (learned && !(wguess > 0.0)) continue;
+        for (int a = 0; a < 4; a++) {
+            const bool learned = a == 0 || a == 3, extrap = a == 1;
+            if (a == 0 && !mlp_first) continue;
+            if (a == 3 && !mlp_rescue) continue;
             if (extrap && !(MIXED && have_start)) continue;
             double W, v2;
             if (learned) {
-                W = wguess;
-                v2 = ResidW{&c}.v2(wguess);
-                if (!(W > 0.0) || !finite64(W)) W = c.D;
-                v2 = fmin(v2, V2MAX);
+                const double wl = c2p_learned_w(a == 0 ? mlp_first : mlp_rescue, c);
+                if (!(wl > 0.0)) continue;
+                W = wl;
+                v2 = fmin(ResidW{&c}.v2(wl), V2MAX);
             } else if (MIXED) {
                 // (W, v^2) formed and checked in FP32 from the chosen FP32 primitives
                 const float r0 = extrap ? startf[KRHO] : guessf[KRHO], e0 = extrap ? startf[KUU] : guessf[KUU];
@@ -508,7 +547,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             if (conv) {
                 if (MIXED) c2p_recover_mixed(c, W, v2, par.ig, P);
                 else c2p_recover_w(c, W, v2, P);
-                if (c2p_physical(P, v2)) return C2P_NR;
+                if (c2p_physical(P, v2)) return a == 3 ? (C2P_NR | C2P_LEARNED) : C2P_NR;
                 if ((methods & 4) && entropy()) return C2P_ENTROPY;
                 return fail(C2P_FAIL | C2P_FAIL_ENT);
             }

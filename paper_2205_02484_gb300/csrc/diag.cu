@@ -202,8 +202,10 @@ __global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, 
     for (int c = 0; c < NU; c++) U[c * n + t] = Uz[c];
 }
 
+// mode 0: plain start from P; 1: the network's W first, then P; 2: P, then the
+// network's W as a rescue before Brent (the step's use)
 __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                           long n, const float *mlp)
+                           long n, const float *mlp, int mode)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -217,9 +219,9 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     double Uz[NU], q0[NP], q[NP];
     for (int c = 0; c < NU; c++) Uz[c] = U[c * n + t];
     for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
-    double wg = mlp ? mlp_w_start(mlp, Uz, geo) : 0.0;
     int it;
-    flags[t] = con2prim(Uz, geo, g.gsp + 6LL * midx(g, l / g.n2, l % g.n2), q0, nullptr, c2p_par(g), 15, q, it, wg);
+    flags[t] = con2prim(Uz, geo, g.gsp + 6LL * midx(g, l / g.n2, l % g.n2), q0, nullptr, c2p_par(g), 15, q, it,
+                        mode == 1 ? mlp : nullptr, nullptr, nullptr, false, mode == 2 ? mlp : nullptr);
     if (iters) iters[t] = it;
     for (int c = 0; c < NP; c++) P[c * n + t] = q[c];
 }
@@ -230,9 +232,9 @@ void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U,
 }
 
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                     long n, const float *mlp, cudaStream_t s)
+                     long n, const float *mlp, int mode, cudaStream_t s)
 {
-    if (n > 0) k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp);
+    if (n > 0) k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, mode);
 }
 
 // ------------------------------------------------------------ state copies

@@ -371,6 +371,7 @@ extern "C" int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens
         }
         ens->members.push_back(members[m]);
         ens->hgrids.push_back(*g);
+        ens->hgrids.back().mlp = nullptr; // ensemble steps keep the plain method order
     }
     ens->mixed = ens->hgrids[0].mixed;
     ens->device = ctx_device(members[0]);

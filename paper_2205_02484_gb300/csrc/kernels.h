@@ -54,7 +54,7 @@ void launch_torus(const Grid &g, const TorusArgs &ta, double *scratch, unsigned 
 // points.cu
 void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U, long n, cudaStream_t s);
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                     long n, const float *mlp, cudaStream_t s);
+                     long n, const float *mlp, int mode, cudaStream_t s);
 
 // mlp.cu (learned Newton start)
 struct MlpHyper {

@@ -105,16 +105,4 @@ __device__ inline float mlp_log_w_guess(const float *buf, const float f[MLP_IN])
     return y * buf[11] + buf[10];
 }
 
-// Newton starting W for the inversion of U, or 0 (plain start) when the
-// features are undefined
-__device__ inline double mlp_w_start(const float *buf, const double U[NU], const Geo<double> &g)
-{
-    double feat[MLP_IN], D;
-    if (!mlp_features(U, g, feat, D)) return 0.0;
-    float f[MLP_IN];
-#pragma unroll
-    for (int k = 0; k < MLP_IN; k++) f[k] = (float)feat[k];
-    return D * exp((double)mlp_log_w_guess(buf, f));
-}
-
 } // namespace grmhd

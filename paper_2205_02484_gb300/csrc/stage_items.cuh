@@ -556,12 +556,14 @@ constexpr int NHZ = 4; // zones next to the horizon that keep the FP64 source in
 // per-thread counters of update_item: Newton iterations, methods, failures,
 // floor/ceiling/cap hits
 struct UpdCount {
-    unsigned it, nr, br, en, eb, fail, fl, ce, gc;
+    unsigned it, nr, br, en, eb, fail, fl, ce, gc, lr;
 };
 
-// LEARN: Newton starts from the learned W of the grid's network (g.mlp)
-// instead of the stage's guess primitives
-template <typename R, bool LEARN = false>
+// Where Newton from the stage's starts does not converge and the grid has a
+// network (g.mlp, set by grmhd_set_learned_guess), Newton from the learned W
+// is tried before Brent; the choice is made at run time, so the plain and the
+// learned order run the same machine code
+template <typename R>
 __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *__restrict__ Pout,
                                    const R *__restrict__ F1, const R *__restrict__ F2,
                                    const R *__restrict__ F3, const R *__restrict__ E1,
@@ -697,8 +699,6 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
     int it;
     const Geo<float> *gfr = MX ? &g.gcF[m] : nullptr;
     const double *gsp = g.gsp + 6LL * m;
-    double wg = 0.0;
-    if constexpr (LEARN) wg = mlp_w_start(g.mlp, Un, geo);
     // mixed path: Newton starts from the stage input extrapolated by its change
     // over the previous half step, 2 P_in - P_out(old) (P_out still holds the
     // previous stage's result for this zone: P-hat before the corrector, the
@@ -712,7 +712,8 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         have_x = qx[KRHO] > 0.9f * qin[KRHO] && qx[KRHO] < 1.1f * qin[KRHO] && qx[KUU] > 0.9f * qin[KUU] &&
                  qx[KUU] < 1.1f * qin[KUU];
     }
-    int fl = con2prim<MX>(Un, geo, gsp, q, qin, c2p_par(g), 15, qn, it, wg, gfr, qx, have_x);
+    int fl = con2prim<MX>(Un, geo, gsp, q, qin, c2p_par(g), 15, qn, it, nullptr, gfr, qx, have_x,
+                          g.mlp);
     bool ok = !(fl & C2P_FAIL);
     cn.it += it;
     int meth = fl & 7;
@@ -733,6 +734,7 @@ __device__ inline void update_item(const Grid &g, const R *__restrict__ Pin, R *
         cn.br += meth == C2P_BRENT_W;
         cn.en += meth == C2P_ENTROPY;
         cn.eb += meth == C2P_ENTROPY_BETA;
+        cn.lr += (fl & C2P_LEARNED) != 0;
         int res = post_inversion<MX>(g, geo, gsp, qn, Un, gfr, qnf);
         if (res & 1) {
             cn.fl += 1;
@@ -765,6 +767,7 @@ __device__ __forceinline__ void flush_counts(const Grid &g, const UpdCount &cn)
     block_count(&g.cnt[C_FLOOR], cn.fl);
     block_count(&g.cnt[C_CEIL], cn.ce);
     block_count(&g.cnt[C_GCAP], cn.gc);
+    block_count(&g.cnt[C_LEARN], cn.lr);
 }
 
 // ------------------------------------------------------------------ fixups
@@ -943,13 +946,13 @@ __device__ __forceinline__ R flux_call(const Grid &g, const R *P, R *F, const Bo
 
 __host__ __device__ inline Box flux_elem_box(const Grid &g, int d) { return d == 3 ? flux_box(g, 3) : col_box(g, d); }
 
-template <typename R, bool LEARN = false>
+template <typename R>
 __device__ __forceinline__ void update_call(const Grid &g, const R *Pin, R *Pout, const R *F1, const R *F2,
                                             const R *F3, const R *E1, const R *E2, const R *E3, double dtfac,
                                             int corr, long long t, UpdCount &cn)
 {
-    if constexpr (sizeof(R) == 8 && !LEARN) update_item_d(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
-    else update_item<R, LEARN>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+    if constexpr (sizeof(R) == 8) update_item_d(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
+    else update_item<R>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr, t, cn);
 }
 
 template <typename R>

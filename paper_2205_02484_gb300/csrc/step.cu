@@ -58,7 +58,7 @@ __global__ void k_emf(Grid g, const R *__restrict__ F1, const R *__restrict__ F2
     emf_item(g, F1, F2, F3, E1, E2, E3, box, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
-template <typename R, bool LEARN>
+template <typename R>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_update(Grid g, const R *__restrict__ Pin, R *__restrict__ Pout,
                                                 const R *__restrict__ F1, const R *__restrict__ F2,
                                                 const R *__restrict__ F3, const R *__restrict__ E1,
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_update(Grid g, 
                                                 double dtfac, int corr)
 {
     UpdCount cn{};
-    update_call<R, LEARN>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr,
+    update_call<R>(g, Pin, Pout, F1, F2, F3, E1, E2, E3, dtfac, corr,
                           blockIdx.x * (long long)blockDim.x + threadIdx.x, cn);
     flush_counts(g, cn);
 }
@@ -118,14 +118,9 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
                                                     (R *)g.E[0], (R *)g.E[1], (R *)g.E[2], be);
         break;
     case 4:
-        if (g.mlp)
-            k_update<R, true><<<nblk(nact_of(g), T), T, 0, s>>>(
-                g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1], (const R *)g.F[2], (const R *)g.E[0],
-                (const R *)g.E[1], (const R *)g.E[2], dtfac, corr);
-        else
-            k_update<R, false><<<nblk(nact_of(g), T), T, 0, s>>>(
-                g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1], (const R *)g.F[2], (const R *)g.E[0],
-                (const R *)g.E[1], (const R *)g.E[2], dtfac, corr);
+        k_update<R><<<nblk(nact_of(g), T), T, 0, s>>>(g, Pin, Pout, (const R *)g.F[0], (const R *)g.F[1],
+                                                      (const R *)g.F[2], (const R *)g.E[0], (const R *)g.E[1],
+                                                      (const R *)g.E[2], dtfac, corr);
         break;
     case 5: k_fixup<R><<<1, 1024, 0, s>>>(g, Pout, corr); break;
     default: fill_bc<R>(g, Pout, s); break;

@@ -21,7 +21,7 @@ BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW, BC_EXTERNAL = 0, 1, 2, 3, 4
 LLF, HLL = 0, 1
 FP64, MIXED = 0, 1
 C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
-C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT = 8, 16, 32
+C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT, C2P_LEARNED = 8, 16, 32, 64
 NP, NU = 8, 9
 
 EINVAL, ECUDA, ENOMEM, ENONFINITE, EFIXUP, EITER, ESTATE = -1, -2, -3, -4, -5, -6, -7
@@ -65,7 +65,7 @@ class Diag(C.Structure):
                 ("t", "dt", "mdot", "phib", "PhiB", "edot", "ldot", "divb_max", "disk_mass", "disk_eb", "eta")] + \
                [(n, C.c_longlong) for n in
                 ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_floor",
-                 "n_ceil", "n_gcap", "n_fixed", "fix_sweeps", "n_steps")]
+                 "n_ceil", "n_gcap", "n_fixed", "fix_sweeps", "n_steps", "n_learned")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
