@@ -10,9 +10,13 @@ whole grid, replayed from a captured CUDA graph; inputs are resident in HBM.
 The state (4.5 GB mixed, 7.7 GB FP64) is far larger than the 129 MB L2, so
 no L2 flush is needed between steps.
 
-Multi-GPU (torchrun, one rank per GPU): every rank advances its own torus
-(independent replicas, different perturbation seeds, weak scaling); the
-time is the max over ranks and the value the zone-cycles of all ranks.
+Multi-GPU (torchrun, one rank per GPU): the one 256^3 torus split into N phi
+slabs, rank r owning slab r (the slab layout of the paper's multi-GPU runs,
+Section 3): the X3 ghost planes travel between neighbour ranks by NCCL
+send/recv after each stage, the CFL minima by a MIN all-reduce (strong
+scaling; the value is the whole grid's zone-cycles over the slowest rank's
+time).  Independent replicas (one torus per rank, weak scaling) are a
+secondary key.
 
 --impl reference times the FP64 CPU oracle on the host cores instead.
 """
@@ -94,6 +98,8 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-window", action="store_true")
     ap.add_argument("--no-slabs", action="store_true")
+    ap.add_argument("--slab-arm", action="store_true",
+                    help="time the phi-slab decomposition (the multi-GPU arm) also at N = 1")
     return ap.parse_args()
 
 
@@ -781,6 +787,74 @@ def run_reference(args):
 
 # -------------------------------------------------------------- GPU arm
 
+def run_decomposed(G, torch, dist, world, rank, local, n, steps, warmup, barrier):
+    """The phi-slab decomposition of one n^3 torus over the ranks: the
+    headline of a multi-GPU run.  Every rank builds the whole initial torus
+    (seed 3), keeps its slab, frees the rest, and steps its slab; the
+    exchanges run on the slab's stream."""
+    from paper_2205_02484_gb300 import decomp as D
+    base = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=G.MIXED, device=local)
+    phys = G.default_phys(gam=4.0 / 3.0)
+    sstream = torch.cuda.Stream(device=local)
+    eng = D.CtxSlab.create(D.slab_grid(base, world), phys, 0.9375, sstream)
+    slab = D.SlabRank(eng)
+    full_g = G.GridParams.from_buffer_copy(base)
+    full_g.stream = sstream.cuda_stream
+    full = G.init_grid(full_g, phys)
+    G.set_metric(full, 0.9375, G.KERR_MKS)
+    G.init_torus(full, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
+    dev = f"cuda:{local}"
+    P = torch.empty((8, n, n, n), dtype=torch.float64, device=dev)
+    U = torch.empty((9, n, n, n), dtype=torch.float64, device=dev)
+    _, _, t0, dt0 = G.get_state(full, P, U)
+    full.close()
+    slab.set_state(P, U, t0, dt0)
+    del P, U
+    torch.cuda.empty_cache()
+    slab.step(warmup)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local if world > 1 else None)
+    barrier()
+    clk.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(sstream)
+    slab.step(steps)
+    e1.record(sstream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    clocks = clk.stop()
+    diag = slab.diagnostics()
+    zones = n * n * n
+    # end to end: each rank copies its slab's state in from pinned host
+    # buffers, steps, and copies it back, every step
+    n3 = n // world
+    Ph = torch.empty((8, n, n, n3), dtype=torch.float64, pin_memory=True).numpy()
+    Uh = torch.empty((9, n, n, n3), dtype=torch.float64, pin_memory=True).numpy()
+    _, _, t, dt = G.get_state(eng.ctx, Ph, Uh)
+    ne = 3
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(ne):
+        G.set_state(eng.ctx, Ph, Uh, t, dt)
+        slab.exchange(0)
+        slab.step(1)
+        _, _, t, dt = G.get_state(eng.ctx, Ph, Uh)
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - w0, dist, "cuda")
+    e2e = {"value": zones * ne / el, "unit": "zone-cycles/s",
+           "h2d_bytes_per_step": int(17 * 8 * zones), "d2h_bytes_per_step": int(17 * 8 * zones), "steps": ne,
+           "path": "per rank: grmhd_set_state(host slab) + ghost exchange + the slab step + grmhd_get_state(host "
+                   "slab), pinned buffers"}
+    eng.close()
+    return {"value": zones * steps / (ms * 1e-3), "ms_per_step": ms / steps, "clocks": clocks, "e2e": e2e,
+            "diag": {k: diag[k] for k in ("t", "dt", "mdot", "divb_max", "n_fail", "nr_iters", "n_steps")},
+            "launches_per_step": 2 * 10 + 2 + 2 * 4}  # stages of 10 kernels, dt minima and finish, 2 exchanges
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -837,6 +911,42 @@ def main():
         return ms, clocks
 
     zones = n * n * n
+    if world > 1 or args.slab_arm:
+        if dist is None:  # --slab-arm on one GPU: a one-rank group
+            import socket
+            import torch.distributed as dist
+            sk = socket.socket()
+            sk.bind(("127.0.0.1", 0))
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", str(sk.getsockname()[1]))
+            sk.close()
+            dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", local))
+        dec = run_decomposed(G, torch, dist, world, rank, local, n, args.steps, args.warmup, lambda: dist.barrier())
+        # secondary: independent replicas, one torus per rank (weak scaling)
+        rctx = make_ctx(G.MIXED)
+        rms, _ = timed(rctx, 10, min(args.warmup, 3), False)
+        rctx.close()
+        replicas = {"value": aggregate_value(zones, 10, world, rms), "unit": "zone-cycles/s", "steps": 10,
+                    "ms_per_step": rms / 10, "scaling": "weak",
+                    "path": "one 256^3 torus per rank (seed 3 + rank), no communication"}
+        if rank == 0:
+            line = {
+                "metric": "zone-cycles/s at 256^3 (FP64 vs mixed, same GB300); % of HBM roofline",
+                "value": dec["value"], "unit": "zone-cycles/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dec["ms_per_step"], "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32 fluxes + f64 U/inversion",
+                "data": "synthetic",
+                "config": dict(workload_config(n), parallelism=f"phi slabs x{world} (one 256^3 torus)",
+                               graph="none: host-driven stages, X3 ghost planes by NCCL send/recv, dt by a MIN "
+                                     "all-reduce"),
+                "hbm_roofline": {"bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE["mixed"],
+                                 "achieved_gbs": HBM_BYTES_PER_ZONE_CYCLE["mixed"] * dec["value"] / 1e9},
+                "clocks": dec["clocks"], "e2e": dec["e2e"], "gpu_launches": dec["launches_per_step"] * args.steps,
+                "replicas": replicas, "diagnostics_after_bench": dec["diag"],
+            }
+            print(json.dumps(line), flush=True)
+        dist.destroy_process_group()
+        return
     # ---- headline: mixed precision
     ctx = make_ctx(G.MIXED)
     ms, clocks = timed(ctx, args.steps, args.warmup, True)

@@ -201,6 +201,26 @@ int grmhd_step(grmhd_ctx *ctx, int nsteps);
 int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P_inout,
                    int *flags, int *iters, long n, int use_learned_guess, int on_device);
 
+/* Diagnostics of a grid split over several contexts (the slabs of the
+ * decomposition, Section 3), combined on the device.  grmhd_diag_partials
+ * writes this context's GRMHD_DIAG_NPART partial values to device memory
+ * out_dev (asynchronous on the context stream): its horizon-shell sums of
+ * Eqs. 38-41, its largest corner divergence (Eq. 24), its Eq. 43 numerator and
+ * mass sum over r_H <= r <= r_bar_max (r_bar_max <= 0 or a flat grid: 0), t,
+ * dt and its counters.  grmhd_diag_combine adds nparts such vectors stored
+ * one after another at parts_dev (device memory, e.g. gathered from all ranks)
+ * in their order, in one device thread, so that every rank forms the same
+ * bits: integrals and counters add, div B and the fixup sweep count take the
+ * largest, t, dt and the step count are the first vector's; then
+ * Phi_BH = phi_B / sqrt|Mdot| (Eq. 42), (Edot - Mdot)/|Mdot| and the Eq. 43
+ * quotient are formed.  out receives the whole grid's diagnostics (disk_mass
+ * and disk_eb from this context); bary3 (may be NULL) the barycentric radius,
+ * its mass sum and numerator.  Returns the context's status like
+ * grmhd_sync. */
+#define GRMHD_DIAG_NPART 26
+int grmhd_diag_partials(grmhd_ctx *ctx, double r_bar_max, double *out_dev);
+int grmhd_diag_combine(grmhd_ctx *ctx, const double *parts_dev, int nparts, grmhd_diag *out, double *bary3);
+
 /* Batched conserved variables of n primitive states at zones loc[n]. */
 int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, double *U, long n,
                     int on_device);

@@ -603,6 +603,65 @@ extern "C" int grmhd_diagnostics(grmhd_ctx *ctx, grmhd_diag *out)
     return grmhd_sync(ctx);
 }
 
+static_assert(GRMHD_DIAG_NPART == DIAG_NPART, "partial-vector length of the header and the kernels differ");
+
+static void diag_from_vector(const grmhd_ctx *ctx, const double *v, grmhd_diag *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    out->mdot = v[0];
+    out->phib = v[1];
+    out->edot = v[2];
+    out->ldot = v[3];
+    out->divb_max = v[4];
+    out->t = v[7];
+    out->dt = v[8];
+    out->PhiB = v[22];
+    out->eta = v[23];
+    out->disk_mass = ctx->disk_mass;
+    out->disk_eb = ctx->disk_eb;
+    long long *cnt[C_NCOUNT] = {&out->nr_iters, &out->n_nr,    &out->n_brent, &out->n_entropy, &out->n_entropy_beta,
+                                &out->n_fail,   &out->n_floor, &out->n_ceil,  &out->n_gcap,    &out->n_fixed,
+                                &out->fix_sweeps, &out->n_steps, &out->n_learned};
+    for (int c = 0; c < C_NCOUNT; c++) *cnt[c] = (long long)v[9 + c];
+}
+
+extern "C" int grmhd_diag_partials(grmhd_ctx *ctx, double r_bar_max, double *out_dev)
+{
+    if (!ctx || !out_dev) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->state_set) return fail(ctx, GRMHD_ESTATE, "no state yet");
+    const Grid &g = ctx->g;
+    const bool bary = r_bar_max > 0.0 && g.metric == KERR_MKS;
+    double *dout = ctx->scratch + ctx->scratch_len - 16;
+    double *bpart = ctx->scratch + ctx->scratch_len - 16 - 2LL * g.n1 - 8;
+    (void)cudaGetLastError();
+    launch_diagnostics(g, ctx->scratch, ctx->scratch_len - 16 - 2LL * g.n1 - 8, dout, ctx->stream);
+    if (bary) launch_barycentric(g, ctx->cp, r_bar_max, bpart, dout + 8, ctx->stream);
+    launch_diag_pack(g, dout, bary ? dout + 8 : nullptr, out_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+extern "C" int grmhd_diag_combine(grmhd_ctx *ctx, const double *parts_dev, int nparts, grmhd_diag *out, double *bary3)
+{
+    if (!ctx || !parts_dev || !out) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (nparts < 1) return fail(ctx, GRMHD_EINVAL, "nparts < 1");
+    double *dv = ctx->scratch + ctx->scratch_len - 16 - 2LL * ctx->g.n1 - 8 - DIAG_NPART;
+    (void)cudaGetLastError();
+    launch_diag_combine(parts_dev, nparts, dv, ctx->stream);
+    CK(cudaGetLastError());
+    double v[DIAG_NPART];
+    CK(cudaMemcpyAsync(ctx->hpin, dv, DIAG_NPART * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(v, ctx->hpin, sizeof(v));
+    diag_from_vector(ctx, v, out);
+    if (bary3) {
+        bary3[0] = v[24];
+        bary3[1] = v[6];
+        bary3[2] = v[5];
+    }
+    return grmhd_sync(ctx);
+}
+
 extern "C" int grmhd_prim2cons(grmhd_ctx *ctx, const double *P, const int *loc, double *U, long n, int on_device)
 {
     if (!ctx || (n > 0 && (!P || !loc || !U))) return fail(ctx, GRMHD_EINVAL, "null argument");

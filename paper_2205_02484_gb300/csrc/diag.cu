@@ -182,6 +182,67 @@ void launch_barycentric(const Grid &g, const CoordParams &cp, double r_bar_max, 
     k_bary_sum<<<1, 32, 0, s>>>(part, g.n1, out);
 }
 
+// ------------------------------------------- partial sums of a slab, combined
+//
+// The diagnostics of one context as a vector of DIAG_NPART doubles (its shell
+// integrals, its corner div B maximum, its Eq. 43 sums, t, dt and counters),
+// so that the slabs of a decomposed grid can gather the vectors on the device
+// and the library can combine them.  Layout: [0..3] Mdot, phi_B, Edot, Ldot
+// (Eqs. 38-41), [4] corner div B maximum (Eq. 24), [5] Eq. 43 numerator,
+// [6] its mass sum, [7] t, [8] dt, [9 .. 9+C_NCOUNT) the counters; the
+// combined vector adds [22] Phi_BH (Eq. 42), [23] (Edot - Mdot)/|Mdot|,
+// [24] the barycentric radius.
+__global__ void k_diag_pack(Grid g, const double *horizon, const double *bary, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int c = 0; c < 5; c++) out[c] = horizon[c];
+    out[5] = bary ? bary[0] : 0.0;
+    out[6] = bary ? bary[1] : 0.0;
+    out[7] = g.scal[1];
+    out[8] = g.scal[0];
+    for (int c = 0; c < C_NCOUNT; c++) out[9 + c] = (double)g.cnt[c];
+    for (int c = 9 + C_NCOUNT; c < DIAG_NPART; c++) out[c] = 0.0;
+}
+
+// Sum of nparts partial vectors in their order (one thread: the order of the
+// additions is fixed, so every rank forms the same bits): integrals and
+// counters add up, div B and the fixup sweep count take the largest, t, dt
+// and the step count are the slabs' common values; then Eq. 42, the
+// efficiency and the Eq. 43 quotient of the sums.
+__global__ void k_diag_combine(const double *parts, int nparts, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v[DIAG_NPART];
+    for (int c = 0; c < DIAG_NPART; c++) v[c] = parts[c];
+    for (int r = 1; r < nparts; r++) {
+        const double *p = parts + (long long)r * DIAG_NPART;
+        for (int c = 0; c < 4; c++) v[c] += p[c];
+        v[4] = fmax(v[4], p[4]);
+        v[5] += p[5];
+        v[6] += p[6];
+        for (int c = 0; c < C_NCOUNT; c++) {
+            if (c == C_SWEEPS) v[9 + c] = fmax(v[9 + c], p[9 + c]);
+            else if (c != C_STEPS) v[9 + c] += p[9 + c];
+        }
+    }
+    const double mdot = v[0];
+    v[22] = mdot != 0.0 ? v[1] / sqrt(fabs(mdot)) : 0.0;
+    v[23] = mdot != 0.0 ? (v[2] - mdot) / fabs(mdot) : 0.0;
+    v[24] = v[6] > 0.0 ? v[5] / v[6] : 0.0;
+    v[25] = 0.0;
+    for (int c = 0; c < DIAG_NPART; c++) out[c] = v[c];
+}
+
+void launch_diag_pack(const Grid &g, const double *horizon, const double *bary, double *out, cudaStream_t s)
+{
+    k_diag_pack<<<1, 32, 0, s>>>(g, horizon, bary, out);
+}
+
+void launch_diag_combine(const double *parts, int nparts, double *out, cudaStream_t s)
+{
+    k_diag_combine<<<1, 32, 0, s>>>(parts, nparts, out);
+}
+
 // ------------------------------------------------------------ point batches
 
 __global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, long n)

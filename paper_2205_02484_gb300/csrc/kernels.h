@@ -91,6 +91,9 @@ void launch_mlp_eval(const float *fwd, const float *feat, const float *label, lo
 
 // diag.cu
 void launch_diagnostics(const Grid &g, double *scratch, long scratch_len, double *out_dev, cudaStream_t s);
+constexpr int DIAG_NPART = 26; // partial-sum vector of one context (see diag.cu)
+void launch_diag_pack(const Grid &g, const double *horizon, const double *bary, double *out, cudaStream_t s);
+void launch_diag_combine(const double *parts, int nparts, double *out, cudaStream_t s);
 void launch_copy_state_in(const Grid &g, const double *P, const double *U, cudaStream_t s);
 void launch_copy_state_out(const Grid &g, double *P, double *U, cudaStream_t s);
 

@@ -89,9 +89,13 @@ class CtxSlab:
     def diagnostics(self):
         return G.diagnostics(self.ctx)
 
-    def barycentric_sums(self, r_bar_max):
-        _, den, num = G.barycentric_radius(self.ctx, r_bar_max)
-        return num, den
+    def diag_partials(self, r_bar_max):
+        out = torch.empty(G.DIAG_NPART, dtype=torch.float64, device=self.device)
+        G.diag_partials(self.ctx, r_bar_max, out)  # on the context stream
+        return out
+
+    def diag_combine(self, parts):
+        return G.diag_combine(self.ctx, parts)
 
     def stage(self, st):
         G.stage(self.ctx, st)
@@ -112,34 +116,14 @@ class CtxSlab:
         self.ctx.close()
 
 
-_SUMMED = ("mdot", "phib", "edot", "ldot", "nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta",
-           "n_fail", "n_floor", "n_ceil", "n_gcap", "n_fixed")
-
-
-def combine_diagnostics(parts):
-    """Whole-grid horizon diagnostics (Eqs. 38-42) from the slabs' own: the
-    shell integrals and the counters add up, the normalised flux is formed
-    from the sums, div B is the largest over the slabs (each checks the
-    corners inside it).  t, dt and the step count are the slabs' common
-    values; the slab sums add in a different order from the undecomposed
-    grid's, so the integrals agree to rounding, not bit for bit."""
-    out = dict(parts[0])
-    for k in _SUMMED:
-        out[k] = type(parts[0][k])(sum(p[k] for p in parts))
-    out["divb_max"] = max(p["divb_max"] for p in parts)
-    # theta slabs all count the sweeps their common loop ran (the whole
-    # grid's count); phi slabs sweep each on their own (the largest count)
-    out["fix_sweeps"] = max(p["fix_sweeps"] for p in parts)
-    out["PhiB"] = out["phib"] / math.sqrt(abs(out["mdot"])) if out["mdot"] != 0.0 else 0.0
-    out["eta"] = (out["edot"] - out["mdot"]) / abs(out["mdot"]) if out["mdot"] != 0.0 else 0.0
-    out["disk_mass"] = out["disk_eb"] = 0.0  # set by the torus setup only
-    return out
-
-
-def _bary(parts):
-    num = sum(p[0] for p in parts)
-    den = sum(p[1] for p in parts)
-    return (num / den if den > 0.0 else 0.0), den, num
+def _combine(engine, parts):
+    """Whole-grid diagnostics from the slabs' partial vectors (one row per
+    slab, in slab order), combined by the library on the device (integrals
+    and counters summed in that order, div B the largest, Eq. 42, the
+    efficiency and the Eq. 43 quotient formed there): (dict, barycentric)."""
+    with _stream_of(engine):
+        stacked = torch.stack(parts).contiguous()
+    return engine.diag_combine(stacked)
 
 
 def _stream_of(engine):
@@ -192,13 +176,13 @@ class SlabRing:
             for e in self.e:
                 e.finish(self.dtd_buf)
 
-    def diagnostics(self):
-        return combine_diagnostics([e.diagnostics() for e in self.e])
+    def diagnostics(self, r_bar_max=80.0):
+        return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[0]
 
     def barycentric_radius(self, r_bar_max=80.0):
         """(<r>, mass, numerator) of Eq. 43 over the whole grid: the slabs'
         sums added in slab order."""
-        return _bary([e.barycentric_sums(r_bar_max) for e in self.e])
+        return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[1]
 
     def close(self):
         for e in self.e:
@@ -267,17 +251,21 @@ class SlabRank:
                     self.dist.all_reduce(self.dtd_buf, op=self.dist.ReduceOp.MIN, group=self.group)
             e.finish(self.dtd_buf)
 
-    def diagnostics(self):
-        """The whole grid's diagnostics on every rank (combine_diagnostics
-        over all ranks' slabs, gathered on the host)."""
-        parts = [None] * self.R
-        self.dist.all_gather_object(parts, self.e.diagnostics(), group=self.group)
-        return combine_diagnostics(parts)
+    def _gathered(self, r_bar_max):
+        """Every rank's partial vector, gathered on the device in rank order
+        and combined by the library (the same bits on every rank)."""
+        buf = self.e.diag_partials(r_bar_max)
+        with _stream_of(self.e):
+            parts = [torch.empty_like(buf) for _ in range(self.R)]
+            self.dist.all_gather(parts, buf, group=self.group)
+        return _combine(self.e, parts)
+
+    def diagnostics(self, r_bar_max=80.0):
+        """The whole grid's diagnostics on every rank."""
+        return self._gathered(r_bar_max)[0]
 
     def barycentric_radius(self, r_bar_max=80.0):
-        parts = [None] * self.R
-        self.dist.all_gather_object(parts, self.e.barycentric_sums(r_bar_max), group=self.group)
-        return _bary(parts)
+        return self._gathered(r_bar_max)[1]
 
 
 # ------------------------------------------------------------ theta slabs
@@ -353,9 +341,13 @@ class CtxTheta:
     def diagnostics(self):
         return G.diagnostics(self.ctx)
 
-    def barycentric_sums(self, r_bar_max):
-        _, den, num = G.barycentric_radius(self.ctx, r_bar_max)
-        return num, den
+    def diag_partials(self, r_bar_max):
+        out = torch.empty(G.DIAG_NPART, dtype=torch.float64, device=self.device)
+        G.diag_partials(self.ctx, r_bar_max, out)  # on the context stream
+        return out
+
+    def diag_combine(self, parts):
+        return G.diag_combine(self.ctx, parts)
 
     def stage_update(self, st):
         G.stage_update(self.ctx, st)
@@ -472,11 +464,11 @@ class ThetaRing:
                 for e in self.e:
                     e.finish(self.dtd_buf)
 
-    def diagnostics(self):
-        return combine_diagnostics([e.diagnostics() for e in self.e])
+    def diagnostics(self, r_bar_max=80.0):
+        return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[0]
 
     def barycentric_radius(self, r_bar_max=80.0):
-        return _bary([e.barycentric_sums(r_bar_max) for e in self.e])
+        return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[1]
 
     def close(self):
         for e in self.e:
@@ -575,16 +567,14 @@ class ThetaRank:
                     self.dist.all_reduce(self.dtd_buf, op=self.dist.ReduceOp.MIN, group=self.group)
             e.finish(self.dtd_buf)
 
-    def diagnostics(self):
-        parts = [None] * self.R
-        self.dist.all_gather_object(parts, self.e.diagnostics(), group=self.group)
-        return combine_diagnostics(parts)
+    _gathered = SlabRank._gathered
+
+    def diagnostics(self, r_bar_max=80.0):
+        return self._gathered(r_bar_max)[0]
 
     def barycentric_radius(self, r_bar_max=80.0):
-        parts = [None] * self.R
-        self.dist.all_gather_object(parts, self.e.barycentric_sums(r_bar_max), group=self.group)
-        return _bary(parts)
+        return self._gathered(r_bar_max)[1]
 
 
-__all__ = ["NG", "slab_grid", "split_phi", "combine_diagnostics", "CtxSlab", "SlabRing", "SlabRank",
+__all__ = ["NG", "slab_grid", "split_phi", "CtxSlab", "SlabRing", "SlabRank",
            "theta_grid", "split_theta", "CtxTheta", "ThetaRing", "ThetaRank"]

@@ -112,6 +112,8 @@ SIGNATURES = {
     "grmhd_prim2cons": (C.c_int, [_V, _V, _V, _V, C.c_long, C.c_int]),
     "grmhd_fluxes": (C.c_int, [_V, _V, C.POINTER(C.c_double), C.c_int]),
     "grmhd_sync": (C.c_int, [_V]),
+    "grmhd_diag_partials": (C.c_int, [_V, C.c_double, _V]),
+    "grmhd_diag_combine": (C.c_int, [_V, _V, C.c_int, C.POINTER(Diag), C.POINTER(C.c_double)]),
     "grmhd_diagnostics": (C.c_int, [_V, C.POINTER(Diag)]),
     "grmhd_destroy": (None, [_V]),
     "grmhd_last_error": (C.c_char_p, [_V]),
@@ -387,6 +389,27 @@ def x2_pack(ctx: Context, kind: int, which: int, side: int, buf):
 
 def x2_unpack(ctx: Context, kind: int, which: int, side: int, buf):
     ctx.check(ctx.L.grmhd_x2_unpack(ctx.h, kind, which, side, _buf_ptr(buf, x2_row_bytes(ctx, kind))))
+
+
+DIAG_NPART = 26
+
+
+def diag_partials(ctx: Context, r_bar_max: float, out):
+    """This context's partial diagnostics (DIAG_NPART doubles) into the device
+    tensor out, asynchronously on the context stream."""
+    ctx.check(ctx.L.grmhd_diag_partials(ctx.h, float(r_bar_max), _dev_ptr(out)))
+
+
+def diag_combine(ctx: Context, parts):
+    """Whole-grid diagnostics from partial vectors parts (nparts x DIAG_NPART,
+    a contiguous device tensor), added in their order on the device: (dict,
+    (barycentric radius, mass sum, numerator))."""
+    if parts.dim() != 2 or parts.shape[1] != DIAG_NPART:
+        raise ValueError("parts must be (nparts, DIAG_NPART)")
+    d = Diag()
+    b = (C.c_double * 3)()
+    ctx.check(ctx.L.grmhd_diag_combine(ctx.h, _dev_ptr(parts), int(parts.shape[0]), C.byref(d), b))
+    return d.as_dict(), (b[0], b[1], b[2])
 
 
 def sync(ctx: Context):

@@ -87,6 +87,53 @@ def gather(slabs):
     return P, U, parts[0][2], parts[0][3]
 
 
+# ---------------------------------------------------- combined diagnostics
+# The layout of the library's partial vector (grmhd_diag_partials) filled from
+# an oracle slab, and its combination written out on the oracle side, so that
+# the product's slab drivers run over oracle slabs on the CPU.
+DIAG_NPART = 26
+_COUNTERS = ("nr_iters", "n_nr", "n_brent", "n_entropy", "n_entropy_beta", "n_fail", "n_floor", "n_ceil",
+             "n_gcap", "n_fixed", "fix_sweeps", "n_steps", "n_learned")
+
+
+def oracle_partials(g, r_bar_max):
+    import torch
+    d = g.diagnostics()
+    v = np.zeros(DIAG_NPART)
+    v[0:5] = [d["mdot"], d["phib"], d["edot"], d["ldot"], d["divb_max"]]
+    if r_bar_max > 0.0 and g.p.metric == O.KERR_MKS:
+        _, den, num = g.barycentric(r_bar_max)
+        v[5:7] = [num, den]
+    v[7:9] = [d["t"], d["dt"]]
+    for c, k in enumerate(_COUNTERS):
+        v[9 + c] = d.get(k, 0)
+    return torch.tensor(v, dtype=torch.float64)
+
+
+def oracle_combine(parts):
+    """Sum in row order, div B and sweeps by the largest, steps/t/dt of the
+    first row; Eq. 42, the efficiency and the Eq. 43 quotient of the sums."""
+    P = np.asarray(parts.cpu().numpy(), dtype=np.float64)
+    v = P[0].copy()
+    for p in P[1:]:
+        v[0:4] += p[0:4]
+        v[4] = max(v[4], p[4])
+        v[5:7] += p[5:7]
+        for c, k in enumerate(_COUNTERS):
+            if k == "fix_sweeps":
+                v[9 + c] = max(v[9 + c], p[9 + c])
+            elif k != "n_steps":
+                v[9 + c] += p[9 + c]
+    mdot = v[0]
+    d = {"t": v[7], "dt": v[8], "mdot": mdot, "phib": v[1], "edot": v[2], "ldot": v[3], "divb_max": v[4],
+         "PhiB": v[1] / np.sqrt(abs(mdot)) if mdot != 0.0 else 0.0,
+         "eta": (v[2] - mdot) / abs(mdot) if mdot != 0.0 else 0.0, "disk_mass": 0.0, "disk_eb": 0.0}
+    for c, k in enumerate(_COUNTERS):
+        d[k] = int(v[9 + c])
+    bary = (v[5] / v[6] if v[6] > 0.0 else 0.0, v[6], v[5])
+    return d, bary
+
+
 class OracleSlab:
     """The SlabEngine interface of paper_2205_02484_gb300.decomp over one
     oracle slab, so that the product's slab drivers (their exchange order,
@@ -113,6 +160,12 @@ class OracleSlab:
     def barycentric_sums(self, r_bar_max):
         _, den, num = self.g.barycentric(r_bar_max)
         return num, den
+
+    def diag_partials(self, r_bar_max):
+        return oracle_partials(self.g, r_bar_max)
+
+    def diag_combine(self, parts):
+        return oracle_combine(parts)
 
     def stage(self, st):
         if st == 0:
@@ -277,6 +330,12 @@ class OracleThetaSlab:
     def barycentric_sums(self, r_bar_max):
         _, den, num = self.g.barycentric(r_bar_max)
         return num, den
+
+    def diag_partials(self, r_bar_max):
+        return oracle_partials(self.g, r_bar_max)
+
+    def diag_combine(self, parts):
+        return oracle_combine(parts)
 
     def stage_update(self, st):
         self.g.stage_update(st)

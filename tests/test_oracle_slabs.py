@@ -58,8 +58,9 @@ def test_slabs_reproduce_the_undecomposed_step(R):
     assert t == tr and dt == dtr
     assert np.array_equal(P, Pr)
     assert np.array_equal(U, Ur)
-    from paper_2205_02484_gb300.decomp import combine_diagnostics
-    _check_combined(combine_diagnostics([g.diagnostics() for g in slabs]), _reference_grid(4).diagnostics())
+    import torch
+    parts = torch.stack([S.oracle_partials(g, 0.0) for g in slabs])
+    _check_combined(S.oracle_combine(parts)[0], _reference_grid(4).diagnostics())
 
 
 def _free_port():
