@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--no-window", action="store_true")
     ap.add_argument("--no-slabs", action="store_true")
+    ap.add_argument("--no-ppm", action="store_true")
     ap.add_argument("--slab-arm", action="store_true",
                     help="time the phi-slab decomposition (the multi-GPU arm) also at N = 1")
     return ap.parse_args()
@@ -365,7 +366,7 @@ def run_slabs(G, torch, device, n, steps=10, warmup=2, counts=(2, 4, 8)):
     undecomposed graph step from the same state, with a bitwise comparison
     of the final states.  A slab's time per step approximates one rank's
     compute in an R-GPU run; ghost_bytes_per_slab_step is what that rank would
-    send per step (2 stages x 2 sides x NG = 2 planes of 8 primitives)."""
+    send per step (2 stages x 2 sides x NG = 3 planes of 8 primitives)."""
     from paper_2205_02484_gb300.decomp import SlabRing
     phys = G.default_phys(gam=4.0 / 3.0)
     gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
@@ -787,6 +788,33 @@ def run_reference(args):
 
 # -------------------------------------------------------------- GPU arm
 
+def run_ppm(G, torch, stream, device, n=256, steps=10, warmup=3):
+    """The headline workload with PPM faces (GRMHD_PPM) instead of PLM: the
+    step time and the share of its face sweeps (CUDA events between kernel
+    groups)."""
+    gp = G.default_grid(n, n, n, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device, recon=G.PPM)
+    gp.stream = stream.cuda_stream
+    ctx = G.init_grid(gp, G.default_phys(gam=4.0 / 3.0))
+    G.set_metric(ctx, 0.9375, G.KERR_MKS)
+    G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
+    G.step(ctx, warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    G.step(ctx, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = G.step_profiled(ctx, 2)
+    flux = sum(prof[f"flux_x{d}_{s}"] for d in (1, 2, 3) for s in ("pred", "corr")) / 2.0
+    d = G.diagnostics(ctx)
+    ctx.close()
+    return {"workload": f"the {n}^3 torus of the headline with PPM faces (one face per thread, six-zone stencil)",
+            "value": n ** 3 / (ms * 1e-3), "unit": "zone-cycles/s", "ms_per_step": ms,
+            "face_sweeps_ms_per_step": flux, "n_fail": d["n_fail"], "divb_max": d["divb_max"]}
+
+
 def run_decomposed(G, torch, dist, world, rank, local, n, steps, warmup, barrier):
     """The phi-slab decomposition of one n^3 torus over the ranks: the
     headline of a multi-GPU run.  Every rank builds the whole initial torus
@@ -1140,6 +1168,10 @@ def main():
     if world == 1 and not args.no_window:
         variants = run_variants(G, torch, stream, local, n)
         window256 = run_window(G, torch, stream, local, n=n, steps=100, every=10, pert=0.04, seed=3)
+    # ---- the same workload with PPM faces
+    ppm = None
+    if world == 1 and not args.no_ppm:
+        ppm = run_ppm(G, torch, stream, local, n)
     # ---- learned Newton start: training, inversions, the 256x192x192 step
     mlp = None
     if world == 1 and not args.no_mlp:
@@ -1181,6 +1213,7 @@ def main():
             "mixed_vs_fp64_window_256": window256,
             "variants_256": variants,
             "con2prim": c2p,
+            "ppm_step": ppm,
             "diagnostics_ms": diag_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -60,6 +60,9 @@ extern "C" {
                                phi slab of a decomposed grid; on a Kerr grid the slab spans
                                [x3min, x3max) of phi, which sets dX3 */
 
+#define GRMHD_PLM 0 /* Eqs. 16-17 */
+#define GRMHD_PPM 1 /* the parabolic reconstruction of Section 2.2 */
+
 #define GRMHD_LLF 0 /* Eq. 18 */
 #define GRMHD_HLL 1 /* Eq. 21 */
 
@@ -103,6 +106,13 @@ typedef struct {
      * phi slab (bc3 external), steps by the stage parts below and takes its
      * state from grmhd_set_state (grmhd_init_torus: GRMHD_EINVAL). */
     int j0, n2_total;
+    /* Face reconstruction: GRMHD_PLM, the MC-limited linear slopes of Eqs.
+     * 16-17, or GRMHD_PPM, the piecewise parabolic method Section 2.2 names as
+     * its successor (Colella & Woodward 1984 for uniform zones in code
+     * coordinates: interface values from MC-limited slopes, then the
+     * monotonicity constraints; no contact steepening or shock flattening),
+     * whose face stencil reads three zones on each side. */
+    int recon;
 } grmhd_grid_params;
 
 /* Physics constants; the paper's values are cfl 0.45 (Eq. 27), nr_tol 1e-10
@@ -290,8 +300,9 @@ typedef struct {
 } grmhd_ens_tiling;
 
 /* Build an ensemble of n member contexts (each with metric and state).
- * Errors: EINVAL (mixed devices or precisions, or a member that is a phi or
- * theta slab), ESTATE (member not ready), ENOMEM. */
+ * Errors: EINVAL (mixed devices or precisions, a member that is a phi or
+ * theta slab, or a member with GRMHD_PPM faces: the batched sweeps walk PLM
+ * columns), ESTATE (member not ready), ENOMEM. */
 int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens **out);
 
 /* Advance every member by nsteps RK2 steps (asynchronous; graph replay). */
@@ -481,8 +492,8 @@ int grmhd_step_dtd(grmhd_ctx *ctx, double *dtd_dev, int accumulate);
  * dtd_dev (3 doubles of device memory: the minima over all slabs). */
 int grmhd_finish_step(grmhd_ctx *ctx, const double *dtd_dev);
 
-/* Bytes of one side's X3 planes: NG = 2 planes of all 8 primitives over the
- * ghosted (X1, X2) cross-section, layout [NG][8][n1 + 4][n2 + 4], element
+/* Bytes of one side's X3 planes: NG = 3 planes of all 8 primitives over the
+ * ghosted (X1, X2) cross-section, layout [NG][8][n1 + 2 NG][n2 + 2 NG], element
  * type double (GRMHD_FP64) or float (GRMHD_MIXED). */
 int grmhd_x3_plane_bytes(grmhd_ctx *ctx, unsigned long long *bytes);
 
@@ -539,8 +550,8 @@ int grmhd_stage_bc(grmhd_ctx *ctx, int st);
 
 /* Bytes of one side's rows of an exchange, element type double
  * (GRMHD_FP64) or float (GRMHD_MIXED):
- *   kind 0: NG = 2 rows of all 8 primitives over the ghosted (X1, X3)
- *           section, layout [NG][8][n1 + 4][n3 + 4];
+ *   kind 0: NG = 3 rows of all 8 primitives over the ghosted (X1, X3)
+ *           section, layout [NG][8][n1 + 2 NG][n3 + 2 NG];
  *   kind 1: one row of the five primitives a fixup averages and the failure
  *           flag (0 or 1), over the active (X1, X3) section, layout
  *           [6][n1][n3]. */

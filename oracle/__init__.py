@@ -25,6 +25,8 @@ _lock = threading.Lock()
 _lib = None
 
 NP, NU = 8, 9
+NG = 3  # ghost layers per side (ORC_NG)
+PLM, PPM = 0, 1  # reconstruction: Eqs. 16-17, or the parabolic method of Section 2.2
 KERR_MKS, MINK_CART = 0, 1
 BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW, BC_EXTERNAL = 0, 1, 2, 3, 4
 LLF, HLL = 0, 1
@@ -107,7 +109,7 @@ class Params(C.Structure):
         ("gam", C.c_double), ("cfl", C.c_double), ("nr_tol", C.c_double), ("sigma_max", C.c_double),
         ("bu_max", C.c_double), ("gamma_max", C.c_double), ("beta_entropy", C.c_double),
         ("nr_maxit", C.c_int), ("brent_maxit", C.c_int), ("fix_maxsweep", C.c_int),
-        ("j0", C.c_int), ("n2_total", C.c_int),
+        ("j0", C.c_int), ("n2_total", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -213,6 +215,7 @@ def lib():
                                                      C.c_double, _F, _F, _D]),
                 "orc_c2p_batch_w": (None, [V, _D, _I, _D, _D, _D, _I, _I, C.c_long, C.c_int]),
                 "orc_post_inversion_at": (None, [V, C.c_int, C.c_int, _D, _D, _I]),
+                "orc_ppm_face": (None, [_D, _D]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -231,7 +234,7 @@ def default_params(**kw) -> Params:
              r_br=400.0, n_x=4.0, R0=0.0, x1min=0.0, x1max=1.0, x2min=0.0, x2max=1.0,
              x3min=0.0, x3max=1.0, bc1=BC_OUTFLOW, bc2=BC_OUTFLOW, bc3=BC_PERIODIC,
              riemann=LLF, gam=13.0 / 9.0, cfl=0.45, nr_tol=1e-10, sigma_max=50.0, bu_max=2500.0,
-             gamma_max=50.0, beta_entropy=1e-2, nr_maxit=30, brent_maxit=100, fix_maxsweep=16)
+             gamma_max=50.0, beta_entropy=1e-2, nr_maxit=30, brent_maxit=100, fix_maxsweep=16, recon=PLM)
     d.update(kw)
     if d["r_in"] <= 0.0 and d["metric"] == KERR_MKS:
         d["r_in"] = 0.98 * (1.0 + (1.0 - d["a"] ** 2) ** 0.5)
@@ -253,6 +256,8 @@ class Grid:
         self.dx = info[3:6].copy()
         self.i_h = int(info[6])
         self.N = tuple(int(v) for v in info[7:10])
+        self.ng = (self.N[0] - params.n1) // 2  # ghost layers per side
+        assert self.ng == NG
         self.shape = (params.n1, params.n2, params.n3)
 
     def __del__(self):
@@ -386,9 +391,10 @@ class Grid:
 
     def face_flux_at(self, d, i, j, q4):
         """(F[9], c_w) of the Riemann flux of a face of direction d (0..2) at
-        metric record (i, j) from the four zone states q4 (4, 8) along d
-        (zones idx-2 .. idx+1)."""
-        q = np.ascontiguousarray(q4, dtype=np.float64).reshape(4 * NP)
+        metric record (i, j) from the zone states along d: (4, 8), zones
+        idx-2 .. idx+1, with PLM; (6, 8), zones idx-3 .. idx+2, with PPM."""
+        nz = 6 if self.p.recon == PPM else 4
+        q = np.ascontiguousarray(q4, dtype=np.float64).reshape(nz * NP)
         out = np.zeros(NU)
         cw = self.L.orc_face_flux_at(self.h, int(d), int(i), int(j), _p(q), _p(out))
         return out, cw
@@ -615,6 +621,14 @@ def wave_speeds(q, g: Geom, gam, d):
     c1, c2 = C.c_double(), C.c_double()
     L.orc_wave_speeds(_p(q), C.byref(g), _p(s), gam, d, C.byref(c1), C.byref(c2))
     return c1.value, c2.value
+
+
+def ppm_face(q6):
+    """(left, right) PPM states at the face between q6[2] and q6[3]."""
+    q = np.ascontiguousarray(q6, dtype=np.float64).reshape(6)
+    out = np.zeros(2)
+    lib().orc_ppm_face(_p(q), _p(out))
+    return out[0], out[1]
 
 
 def mc_slope(qm, q0, qp):

@@ -75,6 +75,7 @@ int orc_x2_external(const orc_grid *G, int side)
 orc_grid *orc_create(const orc_params *p)
 {
     if (p->n1 < 1 || p->n2 < 1 || p->n3 < 1) return NULL;
+    if (p->recon != ORC_PLM && p->recon != ORC_PPM) return NULL;
     if (p->n2_total != 0) { /* a theta slab: at least 4 rows, not also a phi slab */
         if (p->j0 < 0 || p->n2 < 4 || p->j0 + p->n2 > p->n2_total || p->bc3 == ORC_BC_EXTERNAL) return NULL;
     } else if (p->j0 != 0) {
@@ -322,22 +323,17 @@ static const orc_geom *face_geom(const orc_grid *G, int d, int i, int j)
     return d == 0 ? &G->gf1[m] : (d == 1 ? &G->gf2[m] : &G->gc[m]);
 }
 
-/* The Riemann flux (Eqs. 16-21) of one face of direction d at metric record
- * (i, j) from the four zone states along d around it (zones idx-2 .. idx+1):
- * PLM-MC face states, then LLF or HLL.  Polar X2 faces carry no flux. */
-static void face_flux_states(orc_grid *G, int d, int i, int j, const double *qm2, const double *qm1,
-                             const double *q0, const double *qp1, double *Fout, double *cwout)
+/* The Riemann flux (Eqs. 18-21) of one face of direction d at metric record
+ * (i, j) from its left and right states ql, qr: LLF or HLL.  Polar X2 faces
+ * carry no flux. */
+static void face_flux_lr(orc_grid *G, int d, int i, int j, const double *ql, const double *qr, double *Fout,
+                         double *cwout)
 {
     const orc_params *p = &G->p;
     if (d == 1 && G->polar2[orc_midx(G, i, j)]) {
         for (int c = 0; c < ORC_NU; c++) Fout[c] = 0.0;
         *cwout = 0.0;
         return;
-    }
-    double ql[ORC_NP], qr[ORC_NP];
-    for (int c = 0; c < ORC_NP; c++) {
-        ql[c] = qm1[c] + 0.5 * orc_mc_slope(qm2[c], qm1[c], q0[c]);
-        qr[c] = q0[c] - 0.5 * orc_mc_slope(qm1[c], q0[c], qp1[c]);
     }
     const orc_geom *g = face_geom(G, d, i, j);
     orc_state sl, sr;
@@ -365,12 +361,48 @@ static void face_flux_states(orc_grid *G, int d, int i, int j, const double *qm2
     *cwout = cw;
 }
 
+/* PLM-MC face states (Eqs. 16-17) from the four zone states along d around
+ * the face (zones idx-2 .. idx+1), then the Riemann flux. */
+static void face_flux_states(orc_grid *G, int d, int i, int j, const double *qm2, const double *qm1,
+                             const double *q0, const double *qp1, double *Fout, double *cwout)
+{
+    double ql[ORC_NP], qr[ORC_NP];
+    for (int c = 0; c < ORC_NP; c++) {
+        ql[c] = qm1[c] + 0.5 * orc_mc_slope(qm2[c], qm1[c], q0[c]);
+        qr[c] = q0[c] - 0.5 * orc_mc_slope(qm1[c], q0[c], qp1[c]);
+    }
+    face_flux_lr(G, d, i, j, ql, qr, Fout, cwout);
+}
+
+/* PPM face states from the six zone states along d around the face (zones
+ * idx-3 .. idx+2, q6[m * ORC_NP + c]), then the Riemann flux. */
+static void face_flux_states_ppm(orc_grid *G, int d, int i, int j, const double *q6, double *Fout,
+                                 double *cwout)
+{
+    double ql[ORC_NP], qr[ORC_NP];
+    for (int c = 0; c < ORC_NP; c++) {
+        double z[6], lr[2];
+        for (int m = 0; m < 6; m++) z[m] = q6[m * ORC_NP + c];
+        orc_ppm_face(z, lr);
+        ql[c] = lr[0];
+        qr[c] = lr[1];
+    }
+    face_flux_lr(G, d, i, j, ql, qr, Fout, cwout);
+}
+
 /* One face of the grid: index (i,j,k) along direction d denotes the face
  * between zones (.., idx-1, ..) and (.., idx, ..). */
 static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, double *Fout,
                       double *cwout)
 {
     int di = d == 0, dj = d == 1, dk = d == 2;
+    if (G->p.recon == ORC_PPM) {
+        double q6[6 * ORC_NP];
+        for (int m = 0; m < 6; m++)
+            gather(G, P, orc_idx(G, i + (m - 3) * di, j + (m - 3) * dj, k + (m - 3) * dk), q6 + m * ORC_NP);
+        face_flux_states_ppm(G, d, i, j, q6, Fout, cwout);
+        return;
+    }
     double qm2[ORC_NP], qm1[ORC_NP], q0[ORC_NP], qp1[ORC_NP];
     gather(G, P, orc_idx(G, i - 2 * di, j - 2 * dj, k - 2 * dk), qm2);
     gather(G, P, orc_idx(G, i - di, j - dj, k - dk), qm1);
@@ -379,14 +411,16 @@ static void face_flux(orc_grid *G, const double *P, int d, int i, int j, int k, 
     face_flux_states(G, d, i, j, qm2, qm1, q0, qp1, Fout, cwout);
 }
 
-/* The same Riemann flux for caller-given zone states q[4][8] (zones idx-2 ..
- * idx+1 along d) at the face metric record (i, j), i in [0, n1], j in [0, n2]
- * for its direction; returns c_w.  Lets a test check single faces of a grid
- * too large for the oracle to sweep. */
+/* The same Riemann flux for caller-given zone states along d: q[4][8] (zones
+ * idx-2 .. idx+1) with PLM, q[6][8] (zones idx-3 .. idx+2) with PPM, at the
+ * face metric record (i, j), i in [0, n1], j in [0, n2] for its direction;
+ * returns c_w.  Lets a test check single faces of a grid too large for the
+ * oracle to sweep. */
 double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout)
 {
     double cw = 0.0;
-    face_flux_states(G, d, i, j, q, q + ORC_NP, q + 2 * ORC_NP, q + 3 * ORC_NP, Fout, &cw);
+    if (G->p.recon == ORC_PPM) face_flux_states_ppm(G, d, i, j, q, Fout, &cw); /* q: six zones */
+    else face_flux_states(G, d, i, j, q, q + ORC_NP, q + 2 * ORC_NP, q + 3 * ORC_NP, Fout, &cw);
     return cw;
 }
 

@@ -22,7 +22,7 @@
 #endif
 #include <stdint.h>
 
-#define ORC_NG 2
+#define ORC_NG 3 /* ghost layers per side: PPM faces read zones i-3 .. i+2 */
 #define ORC_NP 8 /* primitives: rho, u, ut1, ut2, ut3, B1, B2, B3 (Eq. 11) */
 #define ORC_NU 9 /* conserved: the 8 of Section 2.1 plus entropy (Eq. 12) */
 
@@ -31,6 +31,7 @@ enum { ORC_KERR_MKS = 0, ORC_MINK_CART = 1 };
 enum { ORC_BC_INFLOW = 0, ORC_BC_POLAR = 1, ORC_BC_PERIODIC = 2, ORC_BC_OUTFLOW = 3,
        ORC_BC_EXTERNAL = 4 /* X3 ghosts supplied by the caller (a phi slab of a decomposed grid) */ };
 enum { ORC_LLF = 0, ORC_HLL = 1 };
+enum { ORC_PLM = 0, ORC_PPM = 1 };
 
 /* con2prim result flags: low 3 bits = method that produced the primitives,
  * bit 3 = failure (zone must be fixed by neighbour averaging, Eq. 33). */
@@ -53,6 +54,7 @@ typedef struct {
      * rows (n2_total = 0: the whole grid); its X2 ghost rows on a side
      * inside the grid, or on a periodic side, are supplied by the caller */
     int j0, n2_total;
+    int recon; /* ORC_PLM (Eqs. 16-17) or ORC_PPM (the parabolic reconstruction Section 2.2 names) */
 } orc_params;
 
 typedef struct {
@@ -141,6 +143,7 @@ double orc_compute_fluxes(orc_grid *G, const double *P);
 double orc_combine_dt(const double dtd[3]);
 double orc_barycentric(orc_grid *G, double r_bar_max, double out[3]);
 double orc_face_flux_at(orc_grid *G, int d, int i, int j, const double *q, double *Fout);
+void orc_ppm_face(const double q[6], double out[2]);
 void orc_flux_ct(orc_grid *G);
 void orc_floors(const orc_grid *G, int i, int j, double *q, int *mod);
 void orc_post_inversion_at(orc_grid *G, int i, int j, double *q, double *U, int *out);

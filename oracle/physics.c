@@ -42,6 +42,53 @@ void orc_state_of(const double *q, const orc_geom *g, orc_state *s)
     s->bsq = dot4(s->bcon, s->bcov);
 }
 
+/* ---- the piecewise parabolic method (Colella & Woodward 1984, uniform
+ * zones in code coordinates), which Section 2.2 names as the more accurate
+ * reconstruction after PLM.  Zone values a_j, MC-limited slopes d_j of Eq. 16
+ * (the monotonised slopes of CW84), and:
+ *   interface value  a_{j+1/2} = (a_j + a_{j+1})/2 - (d_{j+1} - d_j)/6;
+ *   the zone's parabola takes a_L = a_{j-1/2}, a_R = a_{j+1/2} and is made
+ *   monotone: flat (a_L = a_R = a_j) at a local extremum; else, where the
+ *   parabola would overshoot inside the zone, the far edge value is moved so
+ *   that the parabola's extremum sits on the near edge (a_L = 3 a_j - 2 a_R,
+ *   or a_R = 3 a_j - 2 a_L).
+ * Contact steepening and shock flattening are not used. */
+static double ppm_interface(double am, double a0, double a1, double a2)
+{
+    double d0 = orc_mc_slope(am, a0, a1), d1 = orc_mc_slope(a0, a1, a2);
+    return 0.5 * (a0 + a1) - (d1 - d0) / 6.0;
+}
+
+static void ppm_monotone(double a, double *aL, double *aR)
+{
+    double L = *aL, R = *aR;
+    if ((R - a) * (a - L) <= 0.0) {
+        L = a;
+        R = a;
+    } else {
+        double d = R - L, m = a - 0.5 * (L + R);
+        if (d * m > d * d / 6.0) L = 3.0 * a - 2.0 * R;
+        else if (-d * d / 6.0 > d * m) R = 3.0 * a - 2.0 * L;
+    }
+    *aL = L;
+    *aR = R;
+}
+
+/* The two states at the face between zones q[2] and q[3] from the six zone
+ * values q[0..5] along the direction: out[0] = a_R of zone 2 (the left
+ * state), out[1] = a_L of zone 3 (the right state). */
+void orc_ppm_face(const double q[6], double out[2])
+{
+    double i01 = ppm_interface(q[0], q[1], q[2], q[3]); /* a_{3/2}, zone 2's left edge */
+    double i12 = ppm_interface(q[1], q[2], q[3], q[4]); /* the face, a_{5/2} */
+    double i23 = ppm_interface(q[2], q[3], q[4], q[5]); /* zone 3's right edge */
+    double L2 = i01, R2 = i12, L3 = i12, R3 = i23;
+    ppm_monotone(q[2], &L2, &R2);
+    ppm_monotone(q[3], &L3, &R3);
+    out[0] = R2;
+    out[1] = L3;
+}
+
 /* Row mu of the mixed stress-energy tensor T^mu_nu, Eq. 5 with p = (gam-1) u. */
 void orc_tmunu(const double *q, const orc_state *s, double gam, int mu, double T[4])
 {

@@ -142,6 +142,8 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     }
     if (grid->riemann != GRMHD_LLF && grid->riemann != GRMHD_HLL)
         return fail(nullptr, GRMHD_EINVAL, "riemann must be GRMHD_LLF or GRMHD_HLL");
+    if (grid->recon != GRMHD_PLM && grid->recon != GRMHD_PPM)
+        return fail(nullptr, GRMHD_EINVAL, "recon must be GRMHD_PLM or GRMHD_PPM");
     if (!(phys->gam > 1.0) || !(phys->cfl > 0.0) || phys->nr_maxit < 1 || phys->brent_maxit < 1 ||
         phys->fix_maxsweep < 1 || !(phys->sigma_max > 0.0) || !(phys->bu_max > 0.0) || !(phys->gamma_max >= 1.0))
         return fail(nullptr, GRMHD_EINVAL, "bad physics parameters");
@@ -167,6 +169,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.metric = grid->metric;
     g.bc1 = grid->bc1; g.bc2 = grid->bc2; g.bc3 = grid->bc3;
     g.riemann = grid->riemann;
+    g.recon = grid->recon;
     g.mixed = grid->precision == GRMHD_MIXED;
     // a row warp evaluates 29 faces per 32 lanes: worth it only for rows of >= 32 faces
     g.x3warp = g.mixed && g.n3 + 1 >= 32;

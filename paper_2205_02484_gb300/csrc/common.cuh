@@ -16,7 +16,7 @@
 
 namespace grmhd {
 
-constexpr int NG = 2;
+constexpr int NG = 3; // ghost layers per side: the PPM face stencil reaches three zones (Sec. 2.2)
 constexpr int NP = 8;
 constexpr int NU = 9;
 enum { KRHO = 0, KUU, KU1, KU2, KU3, KB1, KB2, KB3, KENT };
@@ -75,6 +75,7 @@ struct Grid {
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
     int x3warp;                 // X3 fluxes by row warps (mixed path, rows of >= 32 faces)
     int flat3;                  // one phi zone with copied X3 ghosts: the face fluxes do not vary
+    int recon;                  // 0 PLM (Eqs. 16-17), 1 PPM (faces read three zones on each side)
     int j0, n2t;                // a theta slab's first row and the whole grid's rows (0, n2: whole grid)
                                 // along X3, so only k = 0 faces are computed and every k reads them
     double dx[3], idx[3], x1in, x2in, x3in;

@@ -364,8 +364,9 @@ extern "C" int grmhd_ensemble_create(grmhd_ctx *const *members, int n, grmhd_ens
             return GRMHD_ESTATE;
         }
         // a slab of a decomposed grid steps with its neighbours, not as a member
+        // the batched face sweeps walk PLM columns: a PPM member steps on its own
         if ((m > 0 && (g->mixed != ens->hgrids[0].mixed || ctx_device(members[m]) != ctx_device(members[0]))) ||
-            g->bc3 == BC_EXTERNAL || g->n2t != g->n2) {
+            g->bc3 == BC_EXTERNAL || g->n2t != g->n2 || g->recon != 0) {
             delete ens;
             return GRMHD_EINVAL;
         }

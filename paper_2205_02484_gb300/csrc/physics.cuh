@@ -191,6 +191,46 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp)
     return R(0.5) * dc;
 }
 
+// Piecewise parabolic faces (Colella & Woodward 1984 on uniform code-coordinate
+// zones, the reconstruction Section 2.2 names after PLM): interface value
+// (a_0 + a_1)/2 - (d_1 - d_0)/6 from the MC-limited slopes, then each zone's
+// parabola (a_L, a, a_R) made monotone -- flat at a local extremum, else the
+// far edge moved to 3 a - 2 (near edge) where the parabola would overshoot.
+template <typename R>
+__device__ __forceinline__ R ppm_interface(R am, R a0, R a1, R a2)
+{
+    const R d0 = mc_slope(am, a0, a1), d1 = mc_slope(a0, a1, a2);
+    return R(0.5) * (a0 + a1) - (d1 - d0) / R(6);
+}
+
+template <typename R>
+__device__ __forceinline__ void ppm_monotone(R a, R &L, R &Rt)
+{
+    if ((Rt - a) * (a - L) <= R(0)) {
+        L = a;
+        Rt = a;
+    } else {
+        const R d = Rt - L, m = a - R(0.5) * (L + Rt);
+        if (d * m > d * d / R(6)) L = R(3) * a - R(2) * Rt;
+        else if (-d * d / R(6) > d * m) Rt = R(3) * a - R(2) * L;
+    }
+}
+
+// left and right states at the face between zones q[2] and q[3] of six zone
+// values q[0..5] along the face's direction
+template <typename R>
+__device__ __forceinline__ void ppm_face(const R q[6], R &ql, R &qr)
+{
+    const R i01 = ppm_interface(q[0], q[1], q[2], q[3]);
+    const R i12 = ppm_interface(q[1], q[2], q[3], q[4]);
+    const R i23 = ppm_interface(q[2], q[3], q[4], q[5]);
+    R L2 = i01, R2 = i12, L3 = i12, R3 = i23;
+    ppm_monotone(q[2], L2, R2);
+    ppm_monotone(q[3], L3, R3);
+    ql = R2;
+    qr = L3;
+}
+
 // Source of Eq. 7 at the cell centre: S_nu = sqrt(-g) T^k_l Gamma^l_{nu k};
 // conn holds Gamma^l_{mn} as conn[l*10 + sym(m,n)].
 template <typename R>

@@ -337,6 +337,39 @@ __device__ __forceinline__ R flux_item(const Grid &g, const R *__restrict__ P, R
     return want_dt ? face_cw<R, D>(g, i, j, k, cw) : R(0);
 }
 
+// One face of direction D with the PPM face states (six zones along D, idx-3
+// .. idx+2); the same Riemann flux and c_w as flux_item.  Box: flux_box.
+template <typename R, int D>
+__device__ __forceinline__ R flux_item_ppm(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                           const Box &box, int want_dt, long long t)
+{
+    if (t >= box.count()) return R(0);
+    int i, j, k;
+    box_decode(box, t, i, j, k);
+    long long z = zidx(g, i, j, k);
+    R out[NU];
+    R cw = R(0);
+    if ((D == 2) && g.polar2[midx(g, i, j)]) {
+#pragma unroll
+        for (int c = 0; c < NU; c++) out[c] = R(0);
+    } else {
+        const long long st = D == 1 ? (long long)g.N2 * g.N3 : (D == 2 ? g.N3 : 1);
+        R ql[NP], qr[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const R *pc = P + c * g.nz + z;
+            R q6[6];
+#pragma unroll
+            for (int m = 0; m < 6; m++) q6[m] = ldg(pc + (m - 3) * st);
+            ppm_face(q6, ql[c], qr[c]);
+        }
+        face_flux<R, D>(g, face_table<R>(g, D)[midx(g, i, j)], ql, qr, out, cw);
+    }
+#pragma unroll
+    for (int c = 0; c < NU; c++) F[c * g.nz + z] = out[c];
+    return want_dt ? face_cw<R, D>(g, i, j, k, cw) : R(0);
+}
+
 // Columns of g.fcol consecutive faces along X1 or X2: one thread walks its
 // column with a three-zone window in registers, so each zone is loaded and
 // its MC slope formed once instead of once per face (the face values are the

@@ -51,6 +51,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (D < 3 ? 4 : 5) : 1) k_f
     if (want_dt) block_cfl_into(&g.dtmin[D - 1], cw, g.cfl * g.dx[D - 1]);
 }
 
+// PPM faces: one face per thread along every direction (six-zone stencil)
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_flux_ppm(Grid g, const R *__restrict__ P, R *__restrict__ F, Box box,
+                                                   int want_dt)
+{
+    const R cw = flux_item_ppm<R, D>(g, P, F, box, want_dt, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (want_dt) block_cfl_into(&g.dtmin[D - 1], cw, g.cfl * g.dx[D - 1]);
+}
+
 template <typename R>
 __global__ void k_emf(Grid g, const R *__restrict__ F1, const R *__restrict__ F2,
                       const R *__restrict__ F3, R *E1, R *E2, R *E3, Box box)
@@ -109,6 +118,14 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     // the mixed path sweeps X3 by warps (x3_warp_box) where rows are long; else by faces
     Box b1 = flux_elem_box(g, 1), b2 = flux_elem_box(g, 2), be = edge_box(g);
     Box b3 = (sizeof(R) == 4 && g.x3warp) ? x3_warp_box(g) : flux_elem_box(g, 3);
+    if (g.recon && part < 3) { // PPM faces: one per thread
+        const Box bp = flux_box(g, part + 1);
+        const unsigned nb = nblk(bp.count(), T);
+        if (part == 0) k_flux_ppm<R, 1><<<nb, T, 0, s>>>(g, Pin, (R *)g.F[0], bp, want_dt);
+        else if (part == 1) k_flux_ppm<R, 2><<<nb, T, 0, s>>>(g, Pin, (R *)g.F[1], bp, want_dt);
+        else k_flux_ppm<R, 3><<<nb, T, 0, s>>>(g, Pin, (R *)g.F[2], bp, want_dt);
+        return;
+    }
     switch (part) {
     case 0: k_flux<R, 1><<<nblk(b1.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[0], b1, want_dt); break;
     case 1: k_flux<R, 2><<<nblk(b2.count(), T), T, 0, s>>>(g, Pin, (R *)g.F[1], b2, want_dt); break;

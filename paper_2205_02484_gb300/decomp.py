@@ -5,7 +5,7 @@ are external (BC_EXTERNAL).
 One step of the decomposed grid:
   1. every slab runs the predictor (Eq. 25) and reports its per-direction
      CFL minima (the terms of Eq. 27);
-  2. the NG = 2 X3 ghost planes of P-hat are exchanged with the phi
+  2. the NG = 3 X3 ghost planes of P-hat are exchanged with the phi
      neighbours (periodic in phi);
   3. every slab runs the corrector (Eq. 26);
   4. the ghost planes of P are exchanged;
@@ -33,7 +33,7 @@ import torch
 
 from . import grmhd as G
 
-NG = 2
+NG = G.NG
 
 
 def slab_grid(base: G.GridParams, R: int) -> G.GridParams:
@@ -281,7 +281,7 @@ class SlabRank:
 #        fix_maxsweep sweeps ran, exchange the edge rows that a sweep reads
 #        across a slab face (five primitives and the failure flags), then
 #        run one sweep on every slab;
-#     3. every slab fills its own boundaries (poles, radial), then the NG = 2
+#     3. every slab fills its own boundaries (poles, radial), then the NG = 3
 #        ghost rows of its inner sides are exchanged;
 #   the CFL minima of the predictor are reduced as for phi slabs.
 # Every value a slab reads across its faces is the one the whole grid reads

@@ -19,10 +19,12 @@ from . import build as _build
 KERR_MKS, MINK_CART = 0, 1
 BC_INFLOW, BC_POLAR, BC_PERIODIC, BC_OUTFLOW, BC_EXTERNAL = 0, 1, 2, 3, 4
 LLF, HLL = 0, 1
+PLM, PPM = 0, 1
 FP64, MIXED = 0, 1
 C2P_NR, C2P_BRENT_W, C2P_ENTROPY, C2P_ENTROPY_BETA = 0, 1, 2, 3
 C2P_FAIL, C2P_FAIL_D, C2P_FAIL_ENT, C2P_LEARNED = 8, 16, 32, 64
 NP, NU = 8, 9
+NG = 3  # ghost layers per side of the library's grids
 
 EINVAL, ECUDA, ENOMEM, ENONFINITE, EFIXUP, EITER, ESTATE = -1, -2, -3, -4, -5, -6, -7
 ERRORS = {-1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ENONFINITE", -5: "EFIXUP", -6: "EITER",
@@ -44,7 +46,7 @@ class GridParams(C.Structure):
         ("x3min", C.c_double), ("x3max", C.c_double),
         ("bc1", C.c_int), ("bc2", C.c_int), ("bc3", C.c_int), ("riemann", C.c_int),
         ("precision", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-        ("j0", C.c_int), ("n2_total", C.c_int),
+        ("j0", C.c_int), ("n2_total", C.c_int), ("recon", C.c_int),
     ]
 
 

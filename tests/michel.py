@@ -82,6 +82,7 @@ def michel_prims(og, mic: Michel, gam: float):
     MKS with r = exp(X1)); gam = 1 + 1/n."""
     n1, n2, n3 = og.shape
     tab = og.geom_table(0)
+    NG = og.ng
     P = np.zeros((8, n1, n2, n3))
     for i in range(n1):
         X1 = og.x1in + (i + 0.5) * og.dx[0]
@@ -89,7 +90,7 @@ def michel_prims(og, mic: Michel, gam: float):
         rho, T, u = mic.state(r)
         drdx = r
         for j in range(n2):
-            g = tab[i + 2, j + 2]
+            g = tab[i + NG, j + NG]
             gcov = g[:16].reshape(4, 4)
             gcon = g[16:32].reshape(4, 4)
             alpha = g[33]

@@ -3,7 +3,7 @@ global minimum for dt), run on the oracle: the host logic a multi-GPU run
 follows, checked against the undecomposed grid.
 
 Each slab r of R owns the active phi zones [r n3/R, (r+1) n3/R) and a copy of
-the (r, theta) metric; after every stage its NG = 2 X3 ghost planes on each
+the (r, theta) metric; after every stage its NG = 3 X3 ghost planes on each
 side are the neighbours' outermost active planes (periodic in phi), taken
 after the neighbours' own X1/X2 boundary fill.  The predictor's per-direction
 CFL minima are reduced over slabs and then combined by Eq. 27.
@@ -16,7 +16,7 @@ import numpy as np
 
 import oracle as O
 
-NG = 2
+NG = O.NG
 
 
 def slab_params(base: O.Params, r: int, R: int) -> O.Params:
@@ -202,7 +202,7 @@ class OracleSlab:
 # A theta-slab decomposition (the split of the paper's multi-GPU runs,
 # Section 3; here for axisymmetric grids): slab r owns the active rows
 # [r n2/R, (r+1) n2/R) and builds its own rows of the metric; after every
-# stage its NG = 2 X2 ghost rows on an inner side are the neighbour's edge
+# stage its NG = 3 X2 ghost rows on an inner side are the neighbour's edge
 # rows.  The fixups of Eq. 33 average across a slab face, so before every
 # sweep each slab receives the neighbour's current edge row (five
 # primitives and the failure flags), and the sweeps run while any slab has a

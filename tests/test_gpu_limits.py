@@ -36,7 +36,7 @@ def _stressed_state(og):
     og.init_torus(pert_amp=0.04, seed=1)
     P, U, t, dt = og.get_state()
     n1, n2 = P.shape[1], P.shape[2]
-    tab = og.geom_table(0)[2:-2, 2:-2, None, :]
+    tab = og.geom_table(0)[oracle.NG:-oracle.NG, oracle.NG:-oracle.NG, None, :]
     Bg = sum(P[5 + a] ** 2 * tab[..., 5 * a + 5] for a in range(3))
     hot = Bg > 0.2 * Bg.max()
     Pm = P.copy()
@@ -150,7 +150,7 @@ def _rotating_state(og):
     tab = og.geom_table(0)
     P = np.zeros((8, n1, n2, 1))
     P[0], P[1] = 0.3, 0.05
-    P[4, :, :, 0] = 0.4 / np.sqrt(tab[2:-2, 2:-2, 15])
+    P[4, :, :, 0] = 0.4 / np.sqrt(tab[oracle.NG:-oracle.NG, oracle.NG:-oracle.NG, 15])
     loc = np.arange(n1 * n2, dtype=np.int32)
     U = og.prim2cons(P.reshape(8, -1), loc).reshape((9,) + og.shape)
     return P, U

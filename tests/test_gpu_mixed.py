@@ -60,7 +60,7 @@ def split_monopole_state(og, B0):
     P, U, t, dt = og.get_state()
     n1, n2, n3 = P.shape[1:]
     tab = og.geom_table(0)
-    gdet = tab[2:2 + n1, 2:2 + n2, 32][:, :, None]
+    gdet = tab[og.ng:og.ng + n1, og.ng:og.ng + n2, 32][:, :, None]
     sgn = np.where(np.arange(n2) < n2 // 2, 1.0, -1.0)[None, :, None]
     P[5] += B0 * sgn / gdet
     loc = np.repeat((np.arange(n1)[:, None] * n2 + np.arange(n2)[None, :]).astype(np.int32), n3, axis=1)

@@ -160,8 +160,8 @@ def _cold_guess(G, og, U, loc):
     tab = og.geom_table(0)
     n2 = og.p.n2
     i, j = loc // n2, loc % n2
-    gdet = tab[i + 2, j + 2, 32]
-    alpha = tab[i + 2, j + 2, 33]
+    gdet = tab[i + O.NG, j + O.NG, 32]
+    alpha = tab[i + O.NG, j + O.NG, 33]
     D = alpha * U[0] / gdet
     P = np.zeros((8, U.shape[1]))
     P[0] = D
@@ -190,7 +190,7 @@ def test_trained_guess_keeps_the_root_and_cuts_newton_steps():
     th, nm = G.mlp_get(ctx)
     tab = og.geom_table(0)
     i, j = loc // og.p.n2, loc % og.p.n2
-    D = tab[i + 2, j + 2, 33] * U[0] / tab[i + 2, j + 2, 32]
+    D = tab[i + O.NG, j + O.NG, 33] * U[0] / tab[i + O.NG, j + O.NG, 32]
     wg = D * np.exp(G.mlp_forward(ctx, f).astype(np.float64))
     Po, fo, io = og.con2prim_w(U, loc, g0.copy(), wg)
     assert (fl == fo).mean() > 0.999
@@ -256,7 +256,7 @@ def _cold_restart(og, U):
     """Primitives a restart from conserved variables alone would start from:
     rho = D, u from the energy above rest mass, no velocity, the field of U."""
     n1, n2 = og.shape[0], og.shape[1]
-    tab = og.geom_table(0)[2:-2, 2:-2]
+    tab = og.geom_table(0)[O.NG:-O.NG, O.NG:-O.NG]
     gdet = tab[..., 32][..., None]
     alpha = tab[..., 33][..., None]
     D = alpha * U[0] / gdet
@@ -340,14 +340,14 @@ def test_learned_rescue_zone_by_zone_work():
     th, nm = G.mlp_get(ctx)
     tab = og.geom_table(0)
     i, j = loc // og.p.n2, loc % og.p.n2
-    D = tab[i + 2, j + 2, 33] * U[0] / tab[i + 2, j + 2, 32]
+    D = tab[i + O.NG, j + O.NG, 33] * U[0] / tab[i + O.NG, j + O.NG, 32]
     wl = D * np.exp(G.mlp_forward(ctx, f).astype(np.float64))
     # per zone: plain = set-up + Newton from the guess (fails) + Brent;
     # rescue = set-up + Newton from the guess (fails) + Newton from the
     # network's W, counted as plain - (set-up + Brent) + (set-up + learned Newton)
     plain_flops = rescue_flops = brent_part = learned_part = 0
     for a in np.flatnonzero(brent)[:200]:
-        geom = tab[i[a] + 2, j[a] + 2]
+        geom = tab[i[a] + O.NG, j[a] + O.NG]
         kw = dict(nr_maxit=8)
         A = O.count_con2prim(U[:, a], geom, g0[:, a], GAM, methods=15, **kw)[3]["flops"]
         B = O.count_con2prim(U[:, a], geom, g0[:, a], GAM, methods=10, **kw)[3]["flops"]

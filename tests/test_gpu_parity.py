@@ -18,7 +18,7 @@ def _sample(og, n, seed, n1, n2):
     tab = og.geom_table(0)
     loc = inputs.zone_locations(n, n1, n2, seed, i_h=og.i_h)
     i, j = loc // n2, loc % n2
-    gsp = tab[i + 2, j + 2, :16].reshape(n, 4, 4)[:, 1:, 1:]
+    gsp = tab[i + oracle.NG, j + oracle.NG, :16].reshape(n, 4, 4)[:, 1:, 1:]
     pp = inputs.prim_params(n, seed + 1)
     return loc, pp, inputs.place_prims(pp, gsp)
 

@@ -40,7 +40,7 @@ def _ring_state(ring):
     return P, U, parts[0][2], parts[0][3]
 
 
-@pytest.mark.parametrize("precision,R", [(0, 1), (0, 2), (0, 4), (1, 2), (1, 8)])
+@pytest.mark.parametrize("precision,R", [(0, 1), (0, 2), (0, 4), (1, 2), (1, 4)])
 def test_slab_ring_equals_the_undecomposed_step(precision, R):
     G = gpu_mod()
     from paper_2205_02484_gb300.decomp import SlabRing
@@ -99,14 +99,15 @@ def test_pack_unpack_planes():
     ring.set_state(P0, U0, t0, dt0)
     e = ring.e[0]
     buf = torch.empty(e.plane_numel, dtype=torch.float64, device="cuda")
-    for side, ks in ((0, (0, 1)), (1, (SHAPE[2] - 2, SHAPE[2] - 1))):
+    ng = G.NG
+    for side, ks in ((0, tuple(range(ng))), (1, tuple(range(SHAPE[2] - ng, SHAPE[2])))):
         e.pack(0, side, buf)
         torch.cuda.synchronize()
-        planes = buf.cpu().numpy().reshape(2, 8, SHAPE[0] + 4, SHAPE[1] + 4)
+        planes = buf.cpu().numpy().reshape(ng, 8, SHAPE[0] + 2 * ng, SHAPE[1] + 2 * ng)
         for g, k in enumerate(ks):
             # the active part of the packed plane is the state's plane k
-            assert np.array_equal(planes[g, :, 2:-2, 2:-2], P0[:, :, :, k])
-    assert G.x3_plane_bytes(e.ctx) == 2 * 8 * (SHAPE[0] + 4) * (SHAPE[1] + 4) * 8
+            assert np.array_equal(planes[g, :, G.NG:-G.NG, G.NG:-G.NG], P0[:, :, :, k])
+    assert G.x3_plane_bytes(e.ctx) == ng * 8 * (SHAPE[0] + 2 * ng) * (SHAPE[1] + 2 * ng) * 8
     with pytest.raises(G.GrmhdError):
         G.x3_pack(e.ctx, 2, 0, buf)
     with pytest.raises(G.GrmhdError):

@@ -176,15 +176,16 @@ def test_theta_pack_unpack_rows_and_errors():
     ring.set_state(P0, U0, t0, dt0)
     e0, e1 = ring.e
     n1, n2, n3 = shape[0], shape[1] // 2, shape[2]
-    assert G.x2_row_bytes(e0.ctx, 0) == 2 * 8 * (n1 + 4) * (n3 + 4) * 8
+    ng = G.NG
+    assert G.x2_row_bytes(e0.ctx, 0) == ng * 8 * (n1 + 2 * ng) * (n3 + 2 * ng) * 8
     assert G.x2_row_bytes(e0.ctx, 1) == 6 * n1 * n3 * 8
     buf = torch.empty(e0.row_numel, dtype=torch.float64, device="cuda")
-    for side, js in ((0, (0, 1)), (1, (n2 - 2, n2 - 1))):
+    for side, js in ((0, tuple(range(ng))), (1, tuple(range(n2 - ng, n2)))):
         e0.pack(0, 0, side, buf)
         torch.cuda.synchronize()
-        rows = buf.cpu().numpy().reshape(2, 8, n1 + 4, n3 + 4)
+        rows = buf.cpu().numpy().reshape(ng, 8, n1 + 2 * ng, n3 + 2 * ng)
         for g, j in enumerate(js):
-            assert np.array_equal(rows[g, :, 2:-2, 2:-2], P0[:, :, j, :])
+            assert np.array_equal(rows[g, :, ng:-ng, ng:-ng], P0[:, :, j, :])
     fb = torch.empty(e0.fix_numel, dtype=torch.float64, device="cuda")
     e1.pack(1, 0, 0, fb)
     torch.cuda.synchronize()

@@ -25,7 +25,7 @@ def setup():
     n = 6000
     loc = inputs.zone_locations(n, N1, N2, 21, i_h=G.i_h)
     i, j = loc // N2, loc % N2
-    gsp = tab[i + 2, j + 2, :16].reshape(n, 4, 4)[:, 1:, 1:]
+    gsp = tab[i + oracle.NG, j + oracle.NG, :16].reshape(n, 4, 4)[:, 1:, 1:]
     pp = inputs.prim_params(n, 22)
     P = inputs.place_prims(pp, gsp)
     U = G.prim2cons(P, loc)
@@ -131,7 +131,7 @@ def test_newton_residual_small(setup):
     tab = G.geom_table(0)
     for a in range(0, 200):
         i, j = divmod(int(loc[a]), N2)
-        row = tab[i + 2, j + 2]
+        row = tab[i + oracle.NG, j + oracle.NG]
         gcov, gcon, gdet, alpha = row[:16].reshape(4, 4), row[16:32].reshape(4, 4), row[32], row[33]
         D = alpha * U[0, a] / gdet
         Q = alpha * U[1:5, a] / gdet

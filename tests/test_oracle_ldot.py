@@ -37,7 +37,7 @@ def _grid(n2):
     P[0], P[1] = RHO, UU
     for i in range(n1):
         for j in range(n2):
-            gphph = tab[i + 2, j + 2, 15]           # g_33 = r^2 sin^2 theta (dphi/dX3 = 1)
+            gphph = tab[i + O.NG, j + O.NG, 15]           # g_33 = r^2 sin^2 theta (dphi/dX3 = 1)
             P[4, i, j, 0] = V0 / math.sqrt(gphph)
     loc = np.arange(n1 * n2, dtype=np.int32)
     U = og.prim2cons(P.reshape(8, -1), loc).reshape((9,) + og.shape)

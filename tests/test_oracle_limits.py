@@ -130,7 +130,7 @@ def _kerr_grid(n1=48, n2=48, a=0.9375, **kw):
 
 
 def _zone_metric(G, i, j):
-    row = G.geom_table(0)[i + 2, j + 2]
+    row = G.geom_table(0)[i + oracle.NG, j + oracle.NG]
     return row[:16].reshape(4, 4), row[16:32].reshape(4, 4), row[32], row[33]
 
 

@@ -54,7 +54,7 @@ def test_michel_construction_is_consistent():
     P = michel_prims(og, mic, GAM)
     tab = og.geom_table(0)
     for i in (0, 5, 17, 31):
-        g = O.geom_from(tab[i + 2, 4, :16].reshape(4, 4))
+        g = O.geom_from(tab[i + O.NG, 4 + O.NG, :16].reshape(4, 4))
         s, _ = O.state_of(P[:, i, 4, 0], g)
         r = og.r_of_x1(og.x1in + (i + 0.5) * og.dx[0])
         assert s["ucon"][1] * r == pytest.approx(-mic.state(r)[2], rel=1e-12)

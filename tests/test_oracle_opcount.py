@@ -28,7 +28,7 @@ GAM = 4.0 / 3.0
 
 def _zone(magnetised=True):
     og = oracle.Grid(oracle.default_params(n1=32, n2=32, n3=1, gam=GAM, r_out=100.0))
-    geom = og.geom_table(0)[10 + 2, 12 + 2]
+    geom = og.geom_table(0)[10 + oracle.NG, 12 + oracle.NG]
     q = np.array([0.8, 0.3, 0.12, -0.01, 0.05, 0.0, 0.0, 0.0])
     if magnetised:
         q[5:8] = [0.05, 0.004, 0.02]

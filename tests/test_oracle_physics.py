@@ -27,7 +27,7 @@ def _kerr_points(n=40, seed=3):
     geos = []
     for L in loc:
         i, j = divmod(int(L), 32)
-        row = tab[i + 2, j + 2]
+        row = tab[i + oracle.NG, j + oracle.NG]
         geos.append(oracle.geom_from(row[:16].reshape(4, 4)))
     return geos
 

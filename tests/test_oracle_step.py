@@ -168,7 +168,7 @@ def test_horizon_flux_of_split_monopole_closed_form():
     G.init_torus(pert_amp=0.0, beta0=0.0)
     P, U, t, dt = G.get_state()
     tab = G.geom_table(0)
-    gdet = tab[2:26, 2:26, 32][:, :, None]
+    gdet = tab[oracle.NG:oracle.NG + 24, oracle.NG:oracle.NG + 24, 32][:, :, None]
     sgn = np.where(np.arange(24) < 12, 1.0, -1.0)[None, :, None]
     B0 = 3e-3
     P[5] = B0 * sgn / gdet

@@ -152,7 +152,10 @@ def test_theta_slab_geometry_is_the_whole_grids():
     for kind in (0, 1, 2):
         a = whole.geom_table(kind)
         b = slab.geom_table(kind)
-        assert np.array_equal(a.reshape(a.shape[0], 28, -1)[:, 8:20], b.reshape(b.shape[0], 12, -1)), kind
+        ng = O.NG
+        # whole-grid rows j0 - ng .. j0 + n2 + ng of the ghosted table (row index + ng)
+        assert np.array_equal(a.reshape(a.shape[0], 24 + 2 * ng, -1)[:, 8:8 + 8 + 2 * ng],
+                              b.reshape(b.shape[0], 8 + 2 * ng, -1)), kind
 
 
 # ---------------------------------------------------- the library's drivers

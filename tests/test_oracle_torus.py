@@ -89,7 +89,7 @@ def test_initial_field_divergence_free_and_beta0():
     bsq = []
     for i in range(48):
         for j in range(48):
-            g = oracle.geom_from(tab[i + 2, j + 2, :16].reshape(4, 4))
+            g = oracle.geom_from(tab[i + oracle.NG, j + oracle.NG, :16].reshape(4, 4))
             s, _ = oracle.state_of(P[:, i, j, 0], g)
             bsq.append(s["bsq"])
     assert pmax / (0.5 * max(bsq)) == pytest.approx(100.0, rel=1e-10)
