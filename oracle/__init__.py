@@ -110,6 +110,7 @@ class Params(C.Structure):
         ("bu_max", C.c_double), ("gamma_max", C.c_double), ("beta_entropy", C.c_double),
         ("nr_maxit", C.c_int), ("brent_maxit", C.c_int), ("fix_maxsweep", C.c_int),
         ("j0", C.c_int), ("n2_total", C.c_int), ("recon", C.c_int),
+        ("cyl_r", C.c_double), ("cyl_dx2", C.c_double),
     ]
 
 
@@ -174,6 +175,7 @@ def lib():
                 "orc_conn_at": (None, [V, C.c_double, C.c_double, _D]),
                 "orc_r_of_x1": (C.c_double, [V, C.c_double]),
                 "orc_th_of_x2": (C.c_double, [V, C.c_double]),
+                "orc_theta_at": (C.c_double, [V, C.c_double, C.c_double, C.POINTER(C.c_double)]),
                 "orc_ks_gcov": (None, [C.c_double, C.c_double, C.c_double, _D]),
                 "orc_invert4": (C.c_int, [_D, _D, _D]),
                 "orc_mc_slope": (C.c_double, [C.c_double, C.c_double, C.c_double]),
@@ -234,7 +236,8 @@ def default_params(**kw) -> Params:
              r_br=400.0, n_x=4.0, R0=0.0, x1min=0.0, x1max=1.0, x2min=0.0, x2max=1.0,
              x3min=0.0, x3max=1.0, bc1=BC_OUTFLOW, bc2=BC_OUTFLOW, bc3=BC_PERIODIC,
              riemann=LLF, gam=13.0 / 9.0, cfl=0.45, nr_tol=1e-10, sigma_max=50.0, bu_max=2500.0,
-             gamma_max=50.0, beta_entropy=1e-2, nr_maxit=30, brent_maxit=100, fix_maxsweep=16, recon=PLM)
+             gamma_max=50.0, beta_entropy=1e-2, nr_maxit=30, brent_maxit=100, fix_maxsweep=16, recon=PLM,
+             cyl_r=0.0, cyl_dx2=0.0)
     d.update(kw)
     if d["r_in"] <= 0.0 and d["metric"] == KERR_MKS:
         d["r_in"] = 0.98 * (1.0 + (1.0 - d["a"] ** 2) ** 0.5)
@@ -429,6 +432,13 @@ class Grid:
 
     def th_of_x2(self, X2):
         return self.L.orc_th_of_x2(self.h, X2)
+
+    def theta_at(self, X1, X2):
+        """theta(X1, X2) with the polar cylindrification, and its partials
+        (d theta/dX1, d theta/dX2)."""
+        d = (C.c_double * 2)()
+        th = self.L.orc_theta_at(self.h, X1, X2, d)
+        return th, d[0], d[1]
 
     def x1_of_r(self, r):
         return self.L.orc_x1_of_r(self.h, r)

@@ -53,6 +53,68 @@ static void mks_th_c(const orc_grid *G, double complex X2, double complex *th,
     *dthdx = 0.5 * M_PI + 0.5 * (1.0 - h) * M_PI * ccos(y);
 }
 
+/* Polar cylindrification.  Section 4.1 "cylindrifies" the cells closest
+ * to the poles after Tchekhovskoy et al. 2011 and prints no formula; this
+ * is the reading used here.  Inside a band of width y_b = cyl_dx2 (in X2)
+ * next to each pole, the MKS angle is taken at a moved coordinate
+ *     X2' = pole -/+ y_b phi(s),   s = |X2 - pole| / y_b (negative beyond the pole),
+ *     phi(s) = s + (lambda - 1) s (1 - s^2)^3,
+ *     lambda(r) = (1 + (r_c / r)^4)^(1/4),   r_c = cyl_r.
+ * At the pole phi'(0) = lambda: the first rows are widened by lambda(r),
+ * which for r << r_c is r_c / r, so those rows keep a cylindrical radius
+ * R = r sin(theta) of about r_c theta_MKS instead of shrinking with r -- the
+ * cylinders of the name -- while for r >> r_c lambda -> 1 and the grid is
+ * MKS.  The rows further out in the band are narrowed to make room:
+ * phi(1) = 1, phi'(1) = 1, phi''(1) = 0 join the band to the MKS rows with
+ * a continuous metric derivative, and phi is odd in s, so the mirror image
+ * across the pole that the polar boundary uses is kept.  phi' > 0 (a
+ * monotone map) needs lambda < 1 + 49/32; the grid refuses lambda > 5/2. */
+static void cyl_lambda_c(const orc_grid *G, double complex r, double complex *lam,
+                         double complex *dlam_dr)
+{
+    double complex x = G->p.cyl_r / r;
+    double complex q = x * x * x * x;
+    *lam = cpow(1.0 + q, 0.25);
+    /* d/dr (1 + q)^(1/4) = (1/4) (1 + q)^(-3/4) dq/dr, dq/dr = -4 q / r */
+    *dlam_dr = -q * cpow(1.0 + q, -0.75) / r;
+}
+
+/* theta(X1, X2) and its two partial derivatives: Eq. 36 outside the bands,
+ * the cylindrified angle inside them */
+static void theta_c(const orc_grid *G, double complex X1, double complex X2, double complex *th,
+                    double complex *dth1, double complex *dth2)
+{
+    double yb = G->p.cyl_dx2;
+    int lower = creal(X2) < 0.0;
+    double complex s = lower ? (X2 + 1.0) / yb : (1.0 - X2) / yb;
+    if (!(G->p.cyl_r > 0.0) || fabs(creal(s)) >= 1.0) {
+        mks_th_c(G, X2, th, dth2);
+        *dth1 = 0.0;
+        return;
+    }
+    double complex r, drdx, lam, dlam;
+    mks_r_c(G, X1, &r, &drdx);
+    cyl_lambda_c(G, r, &lam, &dlam);
+    double complex w = 1.0 - s * s;
+    double complex w3 = w * w * w;
+    double complex phi = s + (lam - 1.0) * s * w3;
+    double complex dphi_ds = 1.0 + (lam - 1.0) * (w3 - 6.0 * s * s * w * w);
+    double complex dphi_dlam = s * w3;
+    /* X2' and its partials: lower pole -1 + yb phi, upper 1 - yb phi */
+    double complex X2m, dthm;
+    double complex dX2m_dX1;
+    if (lower) {
+        X2m = -1.0 + yb * phi;
+        dX2m_dX1 = yb * dphi_dlam * dlam * drdx;
+    } else {
+        X2m = 1.0 - yb * phi;
+        dX2m_dX1 = -yb * dphi_dlam * dlam * drdx;
+    }
+    mks_th_c(G, X2m, th, &dthm);
+    *dth2 = dthm * dphi_ds; /* dX2'/dX2 = dphi/ds on both sides */
+    *dth1 = dthm * dX2m_dX1;
+}
+
 double orc_r_of_x1(const orc_grid *G, double X1)
 {
     double complex r, d;
@@ -64,6 +126,15 @@ double orc_th_of_x2(const orc_grid *G, double X2)
 {
     double complex th, d;
     mks_th_c(G, X2, &th, &d);
+    return creal(th);
+}
+
+double orc_theta_at(const orc_grid *G, double X1, double X2, double dth[2])
+{
+    double complex th, d1, d2;
+    theta_c(G, X1, X2, &th, &d1, &d2);
+    dth[0] = creal(d1);
+    dth[1] = creal(d2);
     return creal(th);
 }
 
@@ -114,13 +185,32 @@ void orc_code_gcov_c(const orc_grid *G, double complex X1, double complex X2,
         g[1][1] = g[2][2] = g[3][3] = 1.0;
         return;
     }
-    double complex r, drdx, th, dthdx, gks[4][4];
+    double complex r, drdx, th, dth1, dth2, gks[4][4];
     mks_r_c(G, X1, &r, &drdx);
-    mks_th_c(G, X2, &th, &dthdx);
+    theta_c(G, X1, X2, &th, &dth1, &dth2);
     ks_gcov_c(r, th, G->p.a, gks);
-    double complex J[4] = {1.0, drdx, dthdx, 1.0};
+    if (!(G->p.cyl_r > 0.0)) { /* Eq. 36 alone: a diagonal Jacobian */
+        double complex Jd[4] = {1.0, drdx, dth2, 1.0};
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) g[m][n] = gks[m][n] * Jd[m] * Jd[n];
+        return;
+    }
+    /* g_{mn} = (dx^a/dX^m) (dx^b/dX^n) g^KS_{ab}; the Kerr-Schild
+     * coordinates (t, r, theta, phi) depend on (t, X1, X2, X3) through
+     * r(X1) and theta(X1, X2) */
+    double complex J[4][4] = {{0}}; /* J[a][m] = dx^a / dX^m */
+    J[0][0] = 1.0;
+    J[1][1] = drdx;
+    J[2][1] = dth1;
+    J[2][2] = dth2;
+    J[3][3] = 1.0;
     for (int m = 0; m < 4; m++)
-        for (int n = 0; n < 4; n++) g[m][n] = gks[m][n] * J[m] * J[n];
+        for (int n = 0; n < 4; n++) {
+            double complex s = 0.0;
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++) s += J[a][m] * J[b][n] * gks[a][b];
+            g[m][n] = s;
+        }
 }
 
 /* Gauss-Jordan inversion with partial pivoting; returns 0 if singular. */
@@ -179,10 +269,11 @@ int orc_geom_at(const orc_grid *G, double X1, double X2, orc_geom *out)
         out->alpha = 1.0;
         return 1;
     }
-    double complex rc, drc, thc, dthc;
+    double complex rc, drc, thc, dth1c, dthc;
     mks_r_c(G, X1, &rc, &drc);
-    mks_th_c(G, X2, &thc, &dthc);
+    theta_c(G, X1, X2, &thc, &dth1c, &dthc);
     double r = creal(rc), th = creal(thc), dr = creal(drc), dth = creal(dthc), a = G->p.a;
+    double dth1 = creal(dth1c);
     double s = sin(th), c = cos(th);
     double sig = r * r + a * a * c * c, del = r * r - 2.0 * r + a * a, z = 2.0 * r / sig;
     if (s == 0.0) {
@@ -196,9 +287,29 @@ int orc_geom_at(const orc_grid *G, double X1, double X2, orc_geom *out)
     gi[1][3] = gi[3][1] = a / sig;
     gi[2][2] = 1.0 / sig;
     gi[3][3] = 1.0 / (sig * s * s);
-    double J[4] = {1.0, dr, dth, 1.0};
-    for (int m = 0; m < 4; m++)
-        for (int n = 0; n < 4; n++) out->gcon[m][n] = gi[m][n] / (J[m] * J[n]);
+    if (dth1 == 0.0) {
+        double J[4] = {1.0, dr, dth, 1.0};
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) out->gcon[m][n] = gi[m][n] / (J[m] * J[n]);
+    } else {
+        /* cylindrified: g^{mn} = (dX^m/dx^a) (dX^n/dx^b) g_KS^{ab} with the
+         * inverse Jacobian dX1/dr = 1/r', dX2/dr = -theta_1 / (r' theta_2),
+         * dX2/dtheta = 1/theta_2 (theta_k = d theta / dX^k) */
+        double K[4][4] = {{0}}; /* K[m][a] = dX^m / dx^a */
+        K[0][0] = 1.0;
+        K[1][1] = 1.0 / dr;
+        K[2][1] = -dth1 / (dr * dth);
+        K[2][2] = 1.0 / dth;
+        K[3][3] = 1.0;
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) {
+                double acc = 0.0;
+                for (int p = 0; p < 4; p++)
+                    for (int q = 0; q < 4; q++) acc += K[m][p] * K[n][q] * gi[p][q];
+                out->gcon[m][n] = acc;
+            }
+    }
+    /* det(dx/dX) = r' theta_2 whether or not theta depends on X1 */
     out->gdet = sig * fabs(s) * fabs(dr * dth);
     out->alpha = 1.0 / sqrt(-out->gcon[0][0]);
     return 1;

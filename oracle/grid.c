@@ -118,6 +118,18 @@ orc_grid *orc_create(const orc_params *p)
     int n2t = p->n2_total > 0 ? p->n2_total : p->n2;
     G->dx[1] = (x2out - G->x2in) / n2t;
     G->dx[2] = (x3out - G->x3in) / p->n3;
+    if (p->cyl_r > 0.0) {
+        /* cylindrification on the Kerr grid only, bands that do not meet,
+         * and a widening lambda(r) <= 5/2 down to the innermost ghost face
+         * (lambda falls with r), which keeps the map monotone in X2 */
+        double rmin = orc_r_of_x1(G, G->x1in - ORC_NG * G->dx[0]);
+        double x = p->cyl_r / rmin;
+        if (p->metric != ORC_KERR_MKS || !(p->cyl_dx2 > 0.0 && p->cyl_dx2 <= 1.0) || !isfinite(p->cyl_r) ||
+            !(pow(1.0 + x * x * x * x, 0.25) <= 2.5)) {
+            free(G);
+            return NULL;
+        }
+    }
 
     long nm = (long)G->N1 * G->N2;
     G->gc = (orc_geom *)calloc(nm, sizeof(orc_geom));

@@ -55,6 +55,9 @@ typedef struct {
      * inside the grid, or on a periodic side, are supplied by the caller */
     int j0, n2_total;
     int recon; /* ORC_PLM (Eqs. 16-17) or ORC_PPM (the parabolic reconstruction Section 2.2 names) */
+    /* polar cylindrification (Section 4.1): radius r_c and the X2 width of
+     * the band next to each pole; cyl_r <= 0 switches it off */
+    double cyl_r, cyl_dx2;
 } orc_params;
 
 typedef struct {
@@ -97,7 +100,10 @@ typedef struct orc_grid {
 
 /* geometry.c */
 double orc_r_of_x1(const orc_grid *G, double X1);
+/* theta(X2) of Eq. 36 alone (no cylindrification) */
 double orc_th_of_x2(const orc_grid *G, double X2);
+/* theta(X1, X2) with cylindrification; dth = (d theta/dX1, d theta/dX2) */
+double orc_theta_at(const orc_grid *G, double X1, double X2, double dth[2]);
 void orc_ks_gcov(double r, double th, double a, double g[4][4]);
 #ifndef __cplusplus /* complex-step derivatives: C only (the op counter compiles physics as C++) */
 void orc_code_gcov_c(const orc_grid *G, double complex X1, double complex X2,

@@ -124,7 +124,8 @@ int orc_init_torus(orc_grid *G, const orc_torus_params *tp)
     for (int i = 0; i < n1; i++)
         for (int j = 0; j < n2; j++) {
             double X1 = G->x1in + (i + 0.5) * G->dx[0], X2 = G->x2in + (j + 0.5) * G->dx[1];
-            double r = orc_r_of_x1(G, X1), th = orc_th_of_x2(G, X2);
+            double dth[2];
+            double r = orc_r_of_x1(G, X1), th = orc_theta_at(G, X1, X2, dth);
             int in;
             double rho = fm_rho(a, l, lnh_in, r, th, tp->r_in, gam, kappa, &in);
             intorus[i * n2 + j] = (char)in;
@@ -157,8 +158,10 @@ int orc_init_torus(orc_grid *G, const orc_torus_params *tp)
         double *Aph = (double *)calloc((long)(n1 + 1) * (n2 + 1), sizeof(double));
         for (int i = 0; i <= n1; i++)
             for (int j = 0; j <= n2; j++) {
-                double r = orc_r_of_x1(G, G->x1in + i * G->dx[0]);
-                double th = orc_th_of_x2(G, G->x2in + j * G->dx[1]);
+                double dth[2];
+                double X1 = G->x1in + i * G->dx[0];
+                double r = orc_r_of_x1(G, X1);
+                double th = orc_theta_at(G, X1, G->x2in + j * G->dx[1], dth);
                 int in;
                 double rho = fm_rho(a, l, lnh_in, r, th, tp->r_in, gam, kappa, &in);
                 double v = rho / rhomax - 0.2;

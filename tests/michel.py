@@ -14,7 +14,8 @@ relation on the branch that is subsonic outside r_c and supersonic inside.
 The primitives for the step (modified Kerr-Schild, a = 0, r = exp(X1)): u^r is
 the same in Schwarzschild and Kerr-Schild coordinates (r is shared), u^t follows
 from u.u = -1 in Kerr-Schild, and the primitive velocity is
-ut^i = u^i + alpha^2 u^t g^{ti} (Eq. 11 inverted).
+ut^i = u^i + alpha^2 u^t g^{ti} (Eq. 11 inverted).  On a cylindrified grid
+theta depends on X1 too, and u^theta = 0 gives u^2 = -(d theta/dX1 / d theta/dX2) u^1.
 """
 from __future__ import annotations
 
@@ -95,13 +96,18 @@ def michel_prims(og, mic: Michel, gam: float):
             gcon = g[16:32].reshape(4, 4)
             alpha = g[33]
             u1 = -u / drdx
-            # g_tt (u^t)^2 + 2 g_t1 u^t u^1 + g_11 (u^1)^2 = -1; the future root
-            # in the form that stays finite where g_tt changes sign at r = 2
-            A, B, C = gcov[0, 0], 2.0 * gcov[0, 1] * u1, gcov[1, 1] * u1 * u1 + 1.0
+            _, th1, th2 = og.theta_at(X1, og.x2in + (og.p.j0 + j + 0.5) * og.dx[1])
+            u2 = -th1 * u1 / th2
+            # g_tt (u^t)^2 + 2 (g_t1 u^1 + g_t2 u^2) u^t + g_ij u^i u^j = -1;
+            # the future root in the form that stays finite where g_tt
+            # changes sign at r = 2
+            A = gcov[0, 0]
+            B = 2.0 * (gcov[0, 1] * u1 + gcov[0, 2] * u2)
+            C = (gcov[1, 1] * u1 * u1 + 2.0 * gcov[1, 2] * u1 * u2 + gcov[2, 2] * u2 * u2) + 1.0
             disc = B * B - 4.0 * A * C
             ut = 2.0 * C / (-B + math.sqrt(disc))
-            ut_prim = u1 + alpha * alpha * ut * gcon[0, 1]
             P[0, i, j, :] = rho
             P[1, i, j, :] = rho * T / (gam - 1.0)
-            P[2, i, j, :] = ut_prim
+            P[2, i, j, :] = u1 + alpha * alpha * ut * gcon[0, 1]
+            P[3, i, j, :] = u2 + alpha * alpha * ut * gcon[0, 2]
     return P
