@@ -113,6 +113,17 @@ typedef struct {
      * monotonicity constraints; no contact steepening or shock flattening),
      * whose face stencil reads three zones on each side. */
     int recon;
+    /* Polar cylindrification (Section 4.1, after Tchekhovskoy et al. 2011;
+     * the paper prints no formula).  cyl_r <= 0: off.  Otherwise, Kerr grids
+     * only, inside a band of X2 width cyl_dx2 (0 < cyl_dx2 <= 1) next to each
+     * pole theta(X1, X2) = theta_MKS(X2'), X2' = pole -/+ cyl_dx2 phi(s) with
+     * s = |X2 - pole| / cyl_dx2, phi(s) = s + (lambda - 1) s (1 - s^2)^3 and
+     * lambda(r) = (1 + (cyl_r / r)^4)^(1/4): the rows next to the pole are
+     * widened by lambda(r), which for r << cyl_r keeps them near cylinders
+     * of radius cyl_r theta_MKS.  grmhd_set_metric refuses (GRMHD_EINVAL)
+     * lambda > 5/2 at the innermost ghost face, where phi' would come close
+     * to changing sign, and a band on a flat-space grid. */
+    double cyl_r, cyl_dx2;
 } grmhd_grid_params;
 
 /* Physics constants; the paper's values are cfl 0.45 (Eq. 27), nr_tol 1e-10

@@ -281,8 +281,12 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
     cp.hslope = p.hslope;
     cp.n_x = p.n_x;
     cp.R0 = p.R0;
+    cp.cyl_r = p.cyl_r;
+    cp.cyl_dx2 = p.cyl_dx2;
+    if (p.cyl_r > 0.0 && kind != GRMHD_KERR_MKS)
+        return fail(ctx, GRMHD_EINVAL, "cylindrification needs the Kerr grid");
     if (kind == GRMHD_KERR_MKS) {
-        double rh = 1.0 + std::sqrt(1.0 - a * a);
+        double rh =1.0 + std::sqrt(1.0 - a * a);
         if (!(p.r_in > p.R0) || !(p.r_out > p.r_in) || !(p.r_br > p.R0))
             return fail(ctx, GRMHD_EINVAL, "need R0 < r_in < r_out and r_br > R0");
         if (g.n2 < 2) return fail(ctx, GRMHD_EINVAL, "Kerr grid needs n2 >= 2");
@@ -299,6 +303,15 @@ extern "C" int grmhd_set_metric(grmhd_ctx *ctx, double a, int kind)
         } else {
             g.x3in = 0.0;
             g.dx[2] = 2.0 * M_PI / g.n3;
+        }
+        if (p.cyl_r > 0.0) {
+            // lambda(r) falls with r: its largest value is at the innermost ghost face
+            double rmin, dr;
+            mks_radius<double>(cp, g.x1in - NG * g.dx[0], rmin, dr);
+            double x = p.cyl_r / rmin;
+            if (!(p.cyl_dx2 > 0.0 && p.cyl_dx2 <= 1.0) || !std::isfinite(p.cyl_r) ||
+                !(std::pow(1.0 + x * x * x * x, 0.25) <= 2.5))
+                return fail(ctx, GRMHD_EINVAL, "cylindrification needs 0 < cyl_dx2 <= 1 and lambda <= 5/2");
         }
         g.i_h = g.n1;
         for (int i = 0; i < g.n1; i++) {

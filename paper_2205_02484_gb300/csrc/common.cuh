@@ -177,6 +177,7 @@ __host__ __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 struct CoordParams {
     int metric;
     double a, hslope, xb, n_x, R0;
+    double cyl_r, cyl_dx2; // polar cylindrification: radius r_c and band width in X2 (cyl_r <= 0: off)
 };
 
 // r(X1) of Eq. 36 and its Jacobian, for double or Dual arguments
@@ -200,12 +201,58 @@ __host__ __device__ inline void mks_radius(const CoordParams &cp, T X1, T &r, T 
 
 // theta(X2) = pi/2 (1+X2) + (1-h)/2 sin(pi (1+X2))  (equator-refining form of Eq. 36)
 template <typename T>
-__host__ __device__ inline void mks_theta(const CoordParams &cp, T X2, T &th, T &dthdx)
+__host__ __device__ inline void mks_theta_raw(const CoordParams &cp, T X2, T &th, T &dthdx)
 {
     const double pi = 3.141592653589793238462643;
     T y = (X2 + 1.0) * pi;
     th = (X2 + 1.0) * (0.5 * pi) + dsin(y) * (0.5 * (1.0 - cp.hslope));
     dthdx = dcos(y) * (0.5 * (1.0 - cp.hslope) * pi) + 0.5 * pi;
+}
+
+// theta(X1, X2) and its partial derivatives.  Without cylindrification the
+// map of Eq. 36.  With it (Section 4.1 "cylindrifies" the cells next to the
+// poles; the formula is not printed), inside a band of X2 width y_b next to
+// each pole Eq. 36 is evaluated at a moved coordinate
+//   X2' = pole -/+ y_b phi(s),  s = |X2 - pole| / y_b (negative past the pole),
+//   phi(s) = s + (lambda - 1) s (1 - s^2)^3,  lambda(r) = (1 + (r_c / r)^4)^(1/4):
+// the rows next to the pole are widened by lambda (r_c / r for r << r_c, so
+// they keep a cylindrical radius of about r_c theta instead of shrinking
+// with r), the rest of the band is narrowed, and phi(1) = phi'(1) = 1,
+// phi''(1) = 0 join it smoothly to the MKS rows.  phi is odd, so the mirror
+// across the pole is kept; lambda <= 5/2 (checked at grid creation) keeps
+// phi' > 0.
+template <typename T>
+__host__ __device__ inline void mks_theta(const CoordParams &cp, T X1, T X2, T &th, T &dth1, T &dth2)
+{
+    if (!(cp.cyl_r > 0.0)) {
+        mks_theta_raw(cp, X2, th, dth2);
+        dth1 = X1 * 0.0;
+        return;
+    }
+    const double yb = cp.cyl_dx2;
+    const double sg = val(X2) < 0.0 ? 1.0 : -1.0; // +1 near the lower pole
+    const T s = (X2 * sg + 1.0) * (1.0 / yb);
+    if (!(fabs(val(s)) < 1.0)) {
+        mks_theta_raw(cp, X2, th, dth2);
+        dth1 = X1 * 0.0;
+        return;
+    }
+    T r, drdx;
+    mks_radius(cp, X1, r, drdx);
+    T q = cp.cyl_r / r;
+    q = q * q;
+    q = q * q;
+    const T lam = dsqrt(dsqrt(q + 1.0));
+    const T dlam = -(lam * q) / (r * (q + 1.0)); // d lambda / dr
+    const T c = 1.0 - s * s;
+    const T c3 = c * c * c;
+    const T lm1 = lam - 1.0;
+    const T phi = s + lm1 * s * c3;
+    const T dphi = 1.0 + lm1 * (c * c) * (1.0 - 7.0 * s * s); // d phi / ds
+    T dthM;
+    mks_theta_raw(cp, (phi * yb - 1.0) * sg, th, dthM);
+    dth2 = dthM * dphi;                                  // dX2'/dX2 = phi'(s) on both sides
+    dth1 = dthM * ((s * c3) * (dlam * drdx) * (yb * sg)); // via d lambda / dX1
 }
 
 // metric g_{mu nu} in code coordinates (Kerr-Schild, Eq. 35, pulled back by Eq. 36)
@@ -221,9 +268,9 @@ __host__ __device__ inline void code_gcov(const CoordParams &cp, T X1, T X2, T g
         g[3][3] = g[3][3] + 1.0;
         return;
     }
-    T r, dr, th, dth;
+    T r, dr, th, dth1, dth;
     mks_radius(cp, X1, r, dr);
-    mks_theta(cp, X2, th, dth);
+    mks_theta(cp, X1, X2, th, dth1, dth);
     const double a = cp.a;
     T s = dsin(th), c = dcos(th);
     T s2 = s * s;
@@ -241,12 +288,26 @@ __host__ __device__ inline void code_gcov(const CoordParams &cp, T X1, T X2, T g
     gk[2][2] = sig;
     gk[2][3] = z * 0.0;
     gk[3][3] = s2 * (sig + onez * s2 * (a * a));
-    T J[4] = {X1 * 0.0 + 1.0, dr, dth, X1 * 0.0 + 1.0};
+    if (!(cp.cyl_r > 0.0)) {
+        T J[4] = {X1 * 0.0 + 1.0, dr, dth, X1 * 0.0 + 1.0};
+        for (int m = 0; m < 4; m++)
+            for (int n = m; n < 4; n++) {
+                g[m][n] = gk[m][n] * J[m] * J[n];
+                g[n][m] = g[m][n];
+            }
+        return;
+    }
+    // cylindrified: theta depends on X1 too, g_{mu nu} = J^a_mu J^b_nu g^KS_{ab}
+    // with J^r_1 = dr/dX1, J^theta_1 = dtheta/dX1, J^theta_2 = dtheta/dX2
     for (int m = 0; m < 4; m++)
-        for (int n = m; n < 4; n++) {
-            g[m][n] = gk[m][n] * J[m] * J[n];
-            g[n][m] = g[m][n];
-        }
+        for (int n = m; n < 4; n++) g[m][n] = gk[m][n];
+    g[1][1] = gk[1][1] * dr * dr + gk[2][2] * dth1 * dth1;
+    g[1][2] = gk[2][2] * dth1 * dth;
+    g[2][2] = gk[2][2] * dth * dth;
+    g[0][1] = gk[0][1] * dr;
+    g[1][3] = gk[1][3] * dr;
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < m; n++) g[m][n] = g[n][m];
 }
 
 } // namespace grmhd

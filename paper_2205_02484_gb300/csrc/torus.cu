@@ -67,9 +67,9 @@ __global__ void k_torus_prims(Grid g, TorusArgs ta, double *Pd, unsigned char *i
     int i = t / g.n2, j = t % g.n2;
     long long nact = (long long)g.n1 * g.n2 * g.n3;
     double X1 = g.x1in + (i + 0.5) * g.dx[0], X2 = g.x2in + (j + 0.5) * g.dx[1];
-    double r, dr, th, dth;
+    double r, dr, th, dth1, dth;
     mks_radius<double>(ta.cp, X1, r, dr);
-    mks_theta<double>(ta.cp, X2, th, dth);
+    mks_theta<double>(ta.cp, X1, X2, th, dth1, dth);
     bool in;
     double rho = fm_rho(ta, g.gam, r, th, in);
     double q[NP] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -112,9 +112,10 @@ __global__ void k_aphi(Grid g, TorusArgs ta, const double *red, double *Aph)
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (g.n1 + 1) * (g.n2 + 1)) return;
     int i = t / (g.n2 + 1), j = t % (g.n2 + 1);
-    double r, dr, th, dth;
-    mks_radius<double>(ta.cp, g.x1in + i * g.dx[0], r, dr);
-    mks_theta<double>(ta.cp, g.x2in + j * g.dx[1], th, dth);
+    double r, dr, th, dth1, dth;
+    const double X1 = g.x1in + i * g.dx[0];
+    mks_radius<double>(ta.cp, X1, r, dr);
+    mks_theta<double>(ta.cp, X1, g.x2in + j * g.dx[1], th, dth1, dth);
     bool in;
     double rho = fm_rho(ta, g.gam, r, th, in);
     double v = rho / red[0] - 0.2;

@@ -47,6 +47,7 @@ class GridParams(C.Structure):
         ("bc1", C.c_int), ("bc2", C.c_int), ("bc3", C.c_int), ("riemann", C.c_int),
         ("precision", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
         ("j0", C.c_int), ("n2_total", C.c_int), ("recon", C.c_int),
+        ("cyl_r", C.c_double), ("cyl_dx2", C.c_double),
     ]
 
 
