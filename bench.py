@@ -761,9 +761,10 @@ def oracle_all_cores(n, n3s, steps):
     with mp.get_context("spawn").Pool(cores) as pool:
         times = pool.map(_oracle_core_worker, [(n, n3s, steps, 3 + c) for c in range(cores)])
     zc = cores * n * n * n3s * steps / max(times)
+    from oracle import NG
     desc = (f"{cores} processes, each a {n}x{n}x{n3s} phi-slab of the {n}^3 torus, {steps} RK2 steps timed "
             f"per process; the job time is the slowest process's (the ghost exchange of a decomposed run, "
-            f"{2 * 2 * 8 * (n + 4) ** 2 * 8 / 1e6:.1f} MB per slab and stage, left out)")
+            f"{2 * NG * 8 * (n + 2 * NG) ** 2 * 8 / 1e6:.1f} MB per slab and stage, left out)")
     return zc, cores, desc
 
 
