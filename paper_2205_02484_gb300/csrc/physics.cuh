@@ -197,10 +197,15 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp)
 // parabola (a_L, a, a_R) made monotone -- flat at a local extremum, else the
 // far edge moved to 3 a - 2 (near edge) where the parabola would overshoot.
 template <typename R>
+__device__ __forceinline__ R ppm_interface_s(R a0, R a1, R d0, R d1)
+{
+    return R(0.5) * (a0 + a1) - (d1 - d0) / R(6);
+}
+
+template <typename R>
 __device__ __forceinline__ R ppm_interface(R am, R a0, R a1, R a2)
 {
-    const R d0 = mc_slope(am, a0, a1), d1 = mc_slope(a0, a1, a2);
-    return R(0.5) * (a0 + a1) - (d1 - d0) / R(6);
+    return ppm_interface_s(a0, a1, mc_slope(am, a0, a1), mc_slope(a0, a1, a2));
 }
 
 template <typename R>

@@ -456,6 +456,152 @@ __device__ __forceinline__ R flux_column(const Grid &g, const R *__restrict__ P,
     return cwm;
 }
 
+// PPM faces of a column along X1 / X2: the column walk with a window of the
+// zones f, f+1, f+2, the MC slope of zone f, the interface value a_{f-1/2}
+// and the constrained upper value of zone f-1.  Each zone's slope, each
+// interface value and each zone's constrained pair are formed once per column
+// instead of once per face (flux_item_ppm forms them for every face), by the
+// same operations as ppm_face.  Box: col_box.
+template <typename R, int D>
+__device__ __forceinline__ R flux_column_ppm(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                             const Box &cb, int want_dt, long long t)
+{
+    static_assert(D == 1 || D == 2, "columns run along X1 or X2");
+    R cwm = R(0);
+    if (t >= cb.count()) return cwm;
+    int i, j, k;
+    box_decode(cb, t, i, j, k);
+    const int nf = (D == 1 ? g.n1 : g.n2) + 1;
+    const int f0 = (D == 1 ? i : j) * g.fcol, f1 = min(f0 + g.fcol, nf);
+    if (D == 1) i = f0;
+    else j = f0;
+    const long long st = D == 1 ? (long long)g.N2 * g.N3 : g.N3;
+    const long long z0 = zidx(g, i, j, k); // zone f0; face f lies between zones f-1 and f
+    R q0[NP], q1[NP], q2[NP], s0[NP], am[NP], rp[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) {
+        const R *pc = P + c * g.nz + z0;
+        const R qm3 = ldg(pc - 3 * st), qm2 = ldg(pc - 2 * st), qm1 = ldg(pc - st);
+        q0[c] = ldg(pc);
+        q1[c] = ldg(pc + st);
+        q2[c] = ldg(pc + 2 * st);
+        const R sm2 = mc_slope(qm3, qm2, qm1), sm1 = mc_slope(qm2, qm1, q0[c]);
+        s0[c] = mc_slope(qm1, q0[c], q1[c]);
+        // zone f0 - 1 between its interfaces f0 - 3/2 and f0 - 1/2
+        R L = ppm_interface_s(qm2, qm1, sm2, sm1);
+        R Rt = ppm_interface_s(qm1, q0[c], sm1, s0[c]);
+        am[c] = Rt;
+        ppm_monotone(qm1, L, Rt);
+        rp[c] = Rt;
+    }
+    for (int f = f0; f < f1; f++) {
+        const int fi = D == 1 ? f : i, fj = D == 2 ? f : j;
+        R ql[NP], qr[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const R s1 = mc_slope(q0[c], q1[c], q2[c]);
+            const R ap = ppm_interface_s(q0[c], q1[c], s0[c], s1); // a_{f+1/2}
+            R L = am[c], Rt = ap;
+            ppm_monotone(q0[c], L, Rt);
+            ql[c] = rp[c];
+            qr[c] = L;
+            rp[c] = Rt;
+            am[c] = ap;
+            s0[c] = s1;
+        }
+        if (f + 1 < f1) {
+            const int ni = D == 1 ? f + 1 : i, nj = D == 2 ? f + 1 : j;
+            const char *gp = (const char *)&face_table<R>(g, D)[midx(g, ni, nj)];
+#pragma unroll
+            for (int o = 0; o < (int)sizeof(Geo<R>); o += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(gp + o));
+#pragma unroll
+            for (int c = 0; c < NP; c++)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(P + c * g.nz + z0 + (long long)(f + 3 - f0) * st));
+        }
+        R out[NU];
+        R cw = R(0);
+        if (D == 2 && g.polar2[midx(g, fi, fj)]) {
+#pragma unroll
+            for (int c = 0; c < NU; c++) out[c] = R(0);
+        } else {
+            face_flux<R, D>(g, face_table<R>(g, D)[midx(g, fi, fj)], ql, qr, out, cw);
+        }
+        const long long zf = z0 + (long long)(f - f0) * st;
+#pragma unroll
+        for (int c = 0; c < NU; c++) F[c * g.nz + zf] = out[c];
+        if (want_dt) cwm = max(cwm, face_cw<R, D>(g, fi, fj, k, cw));
+        if (f + 1 < f1) {
+#pragma unroll
+            for (int c = 0; c < NP; c++) {
+                q0[c] = q1[c];
+                q1[c] = q2[c];
+                q2[c] = ldg(P + c * g.nz + zf + 3 * st);
+            }
+        }
+    }
+    return cwm;
+}
+
+// PPM faces of one (i, j) row by one warp: lane l holds zone k0 - 3 + l of a
+// segment, forms its slope from the neighbours' values by shuffles, its upper
+// interface value from its own and the upper neighbour's values and slopes,
+// takes its lower one from the lane below, and constrains its parabola; lanes
+// 3..29 evaluate the 27 faces k0 .. k0 + 26 between the zones of lanes l-1
+// and l.  The next segment's zones are loaded before the faces are
+// evaluated.  Box: x3_warp_box.
+constexpr int X3W_PPM_FACES = 27;
+
+template <typename R>
+__device__ __forceinline__ R flux_x3_warp_ppm(const Grid &g, const R *__restrict__ P, R *__restrict__ F,
+                                              const Box &wb, int want_dt, long long t)
+{
+    R cwm = R(0);
+    if (t >= wb.count()) return cwm;
+    int i, j, lane;
+    box_decode(wb, t, i, j, lane);
+    const long long zrow = zidx(g, i, j, 0);
+    const Geo<R> &geo = face_table<R>(g, 3)[midx(g, i, j)];
+    const int nseg = (g.n3 + 1 + X3W_PPM_FACES - 1) / X3W_PPM_FACES;
+    // this lane's zone of a segment, clamped past the last ghost on lanes no face uses
+    auto zone_of = [&](int seg) { return min(seg * X3W_PPM_FACES - 3 + lane, g.n3 + 2); };
+    R qn[NP];
+    {
+        const long long z = zrow + zone_of(0);
+#pragma unroll
+        for (int c = 0; c < NP; c++) qn[c] = ldg(P + c * g.nz + z);
+    }
+    for (int seg = 0; seg < nseg; seg++) {
+        const int k = zone_of(seg);
+        R ql[NP], qr[NP];
+#pragma unroll
+        for (int c = 0; c < NP; c++) {
+            const R q = qn[c];
+            const R qm = __shfl_up_sync(0xffffffffu, q, 1), qp = __shfl_down_sync(0xffffffffu, q, 1);
+            const R s = mc_slope(qm, q, qp);                              // lanes 1..30
+            const R sp = __shfl_down_sync(0xffffffffu, s, 1);
+            const R ap = ppm_interface_s(q, qp, s, sp);                   // a_{k+1/2}, lanes 1..29
+            R L = __shfl_up_sync(0xffffffffu, ap, 1), Rt = ap;            // a_{k-1/2}, lanes 2..29
+            ppm_monotone(q, L, Rt);
+            ql[c] = __shfl_up_sync(0xffffffffu, Rt, 1);                   // lanes 3..29
+            qr[c] = L;
+        }
+        if (seg + 1 < nseg) {
+            const long long z = zrow + zone_of(seg + 1);
+#pragma unroll
+            for (int c = 0; c < NP; c++) qn[c] = ldg(P + c * g.nz + z);
+        }
+        if (lane >= 3 && lane <= 29 && k <= g.n3) {
+            R out[NU];
+            R cw = R(0);
+            face_flux<R, 3>(g, geo, ql, qr, out, cw);
+#pragma unroll
+            for (int c = 0; c < NU; c++) F[c * g.nz + zrow + k] = out[c];
+            if (want_dt) cwm = max(cwm, face_cw<R, 3>(g, i, j, k, cw));
+        }
+    }
+    return cwm;
+}
+
 // X3 faces of one (i, j) row by one warp (the PLM stencil shared through
 // warp-level primitives, Sec. 3).  The warp walks the row in segments of 29
 // faces: lane l holds zone k0 - 2 + l of the segment, forms that zone's MC
