@@ -638,6 +638,28 @@ def run_mlp(G, torch, stream, device, fp32_peak, n_samples=10_000_000, epochs=4,
                      "frac_learned_rescue": float(((fl & 64) != 0).mean()),
                      "frac_entropy": float((fl == 2).mean()), "frac_entropy_beta": float((fl == 3).mean()),
                      "frac_fail": float(((fl & 8) != 0).mean())}
+    # the zone class Newton serves: the draws the plain order inverts by Newton
+    # (not the beta < 1e-2 entropy ones), compacted, the same two starts
+    g0 = P.clone()
+    g0[2:5] = 0.0
+    flags = torch.zeros(n, dtype=torch.int32, device=P.device)
+    iters = torch.zeros(n, dtype=torch.int32, device=P.device)
+    G.con2prim(ctx, U, loc, g0.clone(), flags, iters)
+    sel = torch.nonzero(flags == 0).flatten()
+    Us, ls, gs = U[:, sel].contiguous(), loc[sel].contiguous(), g0[:, sel].contiguous()
+    m = int(sel.numel())
+    newton_zones = {"zones": m}
+    for name, learned in (("plain_static_start", 0), ("learned_start", 1)):
+        fs = torch.zeros(m, dtype=torch.int32, device=P.device)
+        its = torch.zeros(m, dtype=torch.int32, device=P.device)
+        G.con2prim(ctx, Us, ls, gs.clone(), fs, its, use_learned_guess=learned)   # warm
+        ms = ev_time(lambda: G.con2prim(ctx, Us, ls, gs.clone(), fs, its, use_learned_guess=learned))
+        it = its.cpu().numpy()
+        newton_zones[name] = {"ms": ms, "inversions_per_s": m / (ms * 1e-3), "newton_iters_mean": float(it.mean()),
+                              "frac_newton": float(((fs & 15) == 0).float().mean().item())}
+    newton_zones["note"] = ("the inversion with the learned start first evaluates the network on the tensor cores "
+                            "(warp-level BF16 MMA, FP32 accumulation); the clone of the start is inside both times")
+    inv["newton_zone_class"] = newton_zones
     g0 = P.clone()
     flags = torch.zeros(n, dtype=torch.int32, device=P.device)
     iters = torch.zeros(n, dtype=torch.int32, device=P.device)

@@ -67,12 +67,10 @@ __device__ __forceinline__ bool finite64(double x)
 // warp slots per zone-stage against 185.3 with the invariants passed by
 // value -- the same thread-level work, better reconvergence of the divergent
 // Newton steps -- so the reference is kept.)
-static __device__ __noinline__ double c2p_learned_w(const float *buf, const C2PIn &c)
+__device__ __forceinline__ void c2p_learned_features(const C2PIn &c, float f[MLP_IN])
 {
     const float lo = -69.07755279f; // log(1e-30)
-    const float Df = (float)c.D;
-    const float lD = __logf(Df);
-    float f[MLP_IN];
+    const float lD = __logf((float)c.D);
     f[0] = fmaxf(__logf((float)(-c.nQ - c.D)) - lD, lo);
     f[1] = fmaxf(__logf((float)c.Qtsq) - 2.0f * lD, lo);
     f[2] = fmaxf(__logf((float)c.Bsq) - lD, lo);
@@ -82,9 +80,39 @@ static __device__ __noinline__ double c2p_learned_w(const float *buf, const C2PI
 #pragma unroll
     for (int k = 0; k < MLP_IN; k++)
         if (!(f[k] == f[k])) f[k] = lo; // a NaN feature (negative argument) takes the clamp
-    const float y = mlp_log_w_guess(buf, f);
-    const float w = Df * __expf(y);
+}
+
+// W = D exp(y) of a network output y, 0 where it is not a positive finite number
+__device__ __forceinline__ double c2p_w_of(double D, float y)
+{
+    const float w = (float)D * __expf(y);
     return (w > 0.0f && w < INFINITY) ? (double)w : 0.0;
+}
+
+static __device__ __noinline__ double c2p_learned_w(const float *buf, const C2PIn &c)
+{
+    float f[MLP_IN];
+    c2p_learned_features(c, f);
+    return c2p_w_of(c.D, mlp_log_w_guess(buf, f));
+}
+
+// The invariants the features need (D, n.Q, Qt^2, Bf^2, Q.Bf), formed as the
+// FP64 inversion forms them; false where D is not a positive finite number
+__device__ inline bool c2p_feature_invariants(const double U[NU], const Geo<double> &g, const double gsp[6],
+                                              C2PIn &c)
+{
+    const double f = g.aig;
+    c.D = f * U[KRHO];
+    const double Q0 = f * U[1], Q1 = f * U[2], Q2 = f * U[3], Q3 = f * U[4];
+    c.nQ = g.ialpha * Q0 - g.alpha * (g.gcon[1] * Q1 + g.gcon[2] * Q2 + g.gcon[3] * Q3);
+    const double t0 = gsp[0] * Q1 + gsp[1] * Q2 + gsp[2] * Q3;
+    const double t1 = gsp[1] * Q1 + gsp[3] * Q2 + gsp[4] * Q3;
+    const double t2 = gsp[2] * Q1 + gsp[4] * Q2 + gsp[5] * Q3;
+    c.Qtsq = t0 * Q1 + t1 * Q2 + t2 * Q3;
+    const double b0 = g.alpha * (U[KB1] * g.igdet), b1 = g.alpha * (U[KB2] * g.igdet), b2 = g.alpha * (U[KB3] * g.igdet);
+    c.QB = Q1 * b0 + Q2 * b1 + Q3 * b2;
+    c.Bsq = spatial_sq(g, b0, b1, b2);
+    return c.D > 0.0 && finite64(c.D) && finite64(c.nQ) && finite64(c.Qtsq) && finite64(c.Bsq) && finite64(c.QB);
 }
 
 __device__ __forceinline__ double c2p_pressure(const C2PIn &c, double W, double v2)
@@ -421,6 +449,8 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
 // (for callers without a good guess).  mlp_rescue: Newton from the network's
 // W is tried after Newton from the guess (and the extrapolated start) fails
 // and before Brent; a zone it converges returns C2P_NR | C2P_LEARNED.
+// w_first (> 0, with mlp_first null): a network W the caller has already
+// formed (the warp-level tensor-core inference), tried as mlp_first's.
 // FP64 path: guess = the previous FP64 primitives, Newton takes one more step
 // after the tolerance.  MIXED: guessf = the previous FP32 primitives (guess
 // unused); the starting (W, v^2) and the beta switch are formed in FP32 with
@@ -435,7 +465,7 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
                                const double *guess, const float *guessf, const C2PPar &par, int methods,
                                double P[NP], int &iters, const float *mlp_first = nullptr,
                                const Geo<float> *gf = nullptr, const float *startf = nullptr,
-                               bool have_start = false, const float *mlp_rescue = nullptr)
+                               bool have_start = false, const float *mlp_rescue = nullptr, double w_first = 0.0)
 {
     iters = 0;
     if (!MIXED) {
@@ -514,12 +544,13 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
 #pragma unroll 1
         for (int a = 0; a < 4; a++) {
             const bool learned = a == 0 || a == 3, extrap = a == 1;
-            if (a == 0 && !mlp_first) continue;
+            if (a == 0 && !mlp_first && !(w_first > 0.0)) continue;
             if (a == 3 && !mlp_rescue) continue;
             if (extrap && !(MIXED && have_start)) continue;
             double W, v2;
             if (learned) {
-                const double wl = c2p_learned_w(a == 0 ? mlp_first : mlp_rescue, c);
+                const double wl = (a == 0 && !mlp_first) ? w_first
+                                                         : c2p_learned_w(a == 0 ? mlp_first : mlp_rescue, c);
                 if (!(wl > 0.0)) continue;
                 W = wl;
                 v2 = fmin(ResidW{&c}.v2(wl), V2MAX);

@@ -287,6 +287,49 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     for (int c = 0; c < NP; c++) P[c * n + t] = q[c];
 }
 
+// The inversion with the learned start first, the network evaluated per warp
+// on the tensor cores (mlp_log_w_mma) from the invariants of each lane's
+// state; lanes without a state (past n, bad loc, D not positive) take part
+// in the warp's inference with the feature means and invert nothing.
+__global__ void __launch_bounds__(128) k_con2prim_learned(Grid g, const double *U, const int *loc, double *P,
+                                                          int *flags, int *iters, long n, const float *mlp)
+{
+    __shared__ MlpSmem s;
+    mlp_stage(mlp, s);
+    __syncthreads();
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int l = t < n ? loc[t] : -1;
+    const bool ok = l >= 0 && l < g.n1 * g.n2;
+    const int m = ok ? midx(g, l / g.n2, l % g.n2) : 0;
+    const Geo<double> geo = g.gc[m];
+    const double *gsp = g.gsp + 6LL * m;
+    double Uz[NU];
+    for (int c = 0; c < NU; c++) Uz[c] = ok ? U[c * n + t] : 0.0;
+    C2PIn c;
+    const bool have = ok && c2p_feature_invariants(Uz, geo, gsp, c);
+    float f[MLP_IN];
+    if (have) {
+        c2p_learned_features(c, f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < MLP_IN; k++) f[k] = s.norm[k];
+    }
+    const float y = mlp_log_w_mma(s, f);
+    if (t >= n) return;
+    if (!ok) {
+        flags[t] = C2P_FAIL | C2P_FAIL_D;
+        if (iters) iters[t] = 0;
+        return;
+    }
+    double q0[NP], q[NP];
+    for (int k = 0; k < NP; k++) q0[k] = P[k * n + t];
+    int it;
+    flags[t] = con2prim(Uz, geo, gsp, q0, nullptr, c2p_par(g), 15, q, it, nullptr, nullptr, nullptr, false, nullptr,
+                        have ? c2p_w_of(c.D, y) : 0.0);
+    if (iters) iters[t] = it;
+    for (int k = 0; k < NP; k++) P[k * n + t] = q[k];
+}
+
 void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U, long n, cudaStream_t s)
 {
     if (n > 0) k_prim2cons<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, P, loc, U, n);
@@ -295,7 +338,9 @@ void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U,
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
                      long n, const float *mlp, int mode, cudaStream_t s)
 {
-    if (n > 0) k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, mode);
+    if (n <= 0) return;
+    if (mode == 1) k_con2prim_learned<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp);
+    else k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, mode);
 }
 
 // ------------------------------------------------------------ state copies

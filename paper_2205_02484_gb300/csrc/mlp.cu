@@ -80,14 +80,20 @@ void launch_mlp_samples(const Grid &g, unsigned long long seed, long long first,
 
 // ----------------------------------------------------------------- forward
 
-__global__ void k_mlp_forward(const float *buf, const float *feat, long long n, float *y)
+// tensor-core inference, one warp per 32 samples; lanes past n pass the
+// feature means and write nothing
+__global__ void __launch_bounds__(128) k_mlp_forward(const float *buf, const float *feat, long long n, float *y)
 {
-    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (a >= n) return;
+    __shared__ MlpSmem s;
+    mlp_stage(buf, s);
+    __syncthreads();
+    const long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool in = a < n;
     float f[MLP_IN];
 #pragma unroll
-    for (int k = 0; k < MLP_IN; k++) f[k] = feat[k * n + a];
-    y[a] = mlp_log_w_guess(buf, f);
+    for (int k = 0; k < MLP_IN; k++) f[k] = in ? feat[k * n + a] : s.norm[k];
+    const float r = mlp_log_w_mma(s, f);
+    if (in) y[a] = r;
 }
 
 void launch_mlp_forward(const float *buf, const float *feat, long long n, float *y, cudaStream_t s)
