@@ -58,10 +58,10 @@ def test_ragged_batches_equal_the_full_batch(mode):
         assert np.array_equal(fn, ff[:n]), n
         assert np.array_equal(itn, itf[:n]), n
         assert np.array_equal(Pn, Pf[:, :n]), n
-    Ug = G.prim2cons(ctx, np.ascontiguousarray(P[:, :33]), loc[:33].copy())
-    Uo = og.prim2cons(np.ascontiguousarray(P[:, :33]), loc[:33].copy())
-    for c in range(9):
-        assert np.abs(Ug[c] - Uo[c]).max() <= 1e-13 * np.abs(Uo[c]).max(), c
+    # prim2cons of a ragged batch: the full batch's values (its parity with the
+    # oracle is tested in test_gpu_parity)
+    Ufull = G.prim2cons(ctx, P, loc)
+    assert np.array_equal(G.prim2cons(ctx, np.ascontiguousarray(P[:, :33]), loc[:33].copy()), Ufull[:, :33])
 
 
 def test_locations_outside_the_grid_fail_alone():
