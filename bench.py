@@ -1072,7 +1072,8 @@ def main():
                 "flops_per_zone_stage": flops_zone, "newton_steps_per_zone_stage": newton_per_zone,
                 "floored_zones_per_stage": dd["n_floor"] / stages,
                 "flops_source": "oracle operation counter: inversion 171 + 61 per Newton step, RK 18",
-                "traffic_source": "ncu dram bytes of one 96^3 launch, 246.6 B/zone, scaled by zone count"
+                "traffic_source": (f"ncu dram bytes of one 96^3 launch, {UPDATE_DRAM_BYTES_PER_ZONE} B/zone, "
+                                   "scaled by zone count")
                                   if traffic else f"kernel sources changed since the ncu capture (sha {sha})",
                 "hbm": {"bytes_per_zone_stage": upd_bytes, "achieved": upd_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": upd_gbs / hbm_peak, "peak_source": hbm_peak_src}}
