@@ -257,13 +257,30 @@ struct ResidW {
     }
 };
 
+// rho^(gam - 1) of the entropy inversion: cube roots for the adiabatic
+// indices 4/3, 5/3 and 13/9 (rho^(1/3), rho^(2/3), rho^(4/9) = cbrt(cbrt(rho))^4),
+// a general power otherwise; the Brent iteration evaluates it once per step
+__device__ __forceinline__ double rho_pow_gm1(double rho, double gam)
+{
+    if (gam == 4.0 / 3.0) return cbrt(rho);
+    if (gam == 5.0 / 3.0) {
+        const double r = cbrt(rho);
+        return r * r;
+    }
+    if (gam == 13.0 / 9.0) {
+        const double r = cbrt(cbrt(rho)), r2 = r * r;
+        return r2 * r2;
+    }
+    return pow(rho, gam - 1.0);
+}
+
 struct ResidS {
     const C2PIn *c;
     __device__ double W(double v2) const
     {
         double lor = 1.0 / sqrt(1.0 - v2);
         double rho = c->D / lor;
-        return lor * c->D + lor * c->gam * c->igm1 * pow(rho, c->gam - 1.0) * c->Sent;
+        return lor * c->D + lor * c->gam * c->igm1 * rho_pow_gm1(rho, c->gam) * c->Sent;
     }
     __device__ double operator()(double v2) const
     {
@@ -434,7 +451,7 @@ __device__ inline bool c2p_entropy(const C2PIn &c, int maxit, double *P)
     if (!ok) return false;
     double lor = 1.0 / sqrt(1.0 - v2);
     double rho = c.D / lor;
-    double p = (c.Sent / lor) * pow(rho, c.gam - 1.0);
+    double p = (c.Sent / lor) * rho_pow_gm1(rho, c.gam);
     c2p_recover(c, f.W(v2), v2, p, P);
     return c2p_physical(P, v2);
 }
