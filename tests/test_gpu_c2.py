@@ -27,7 +27,8 @@ pytestmark = pytest.mark.gpu
 
 N = 128
 GAM = 4.0 / 3.0
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# directory for the per-field figures as JSON (optional: nothing is written unset)
+OUT = os.environ.get("GRMHD_REPORT_DIR")
 
 
 def _c2_grid():
@@ -58,6 +59,8 @@ def c2_oracle():
 def _report(name, eP, eU, pP, pU):
     print(name, "max-norm/pointwise P:", eP, "U:", eU)
     print(name, "pointwise (Sec. 8c metric) P:", pP, "U:", pU)
+    if not OUT:
+        return
     os.makedirs(OUT, exist_ok=True)
     with open(os.path.join(OUT, f"parity_{name}.json"), "w") as f:
         json.dump(dict(field_err_P=eP.tolist(), field_err_U=eU.tolist(), pointwise_P=pP.tolist(),
