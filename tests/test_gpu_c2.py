@@ -58,7 +58,7 @@ def c2_oracle():
 
 def _report(name, eP, eU, pP, pU):
     print(name, "max-norm/pointwise P:", eP, "U:", eU)
-    print(name, "pointwise (Sec. 8c metric) P:", pP, "U:", pU)
+    print(name, "pointwise max |d| / (|x| + 1e-12 max |x|) P:", pP, "U:", pU)
     if not OUT:
         return
     os.makedirs(OUT, exist_ok=True)
