@@ -189,6 +189,25 @@ int grmhd_init_torus(grmhd_ctx *ctx, const grmhd_torus_params *torus);
 int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U, double t, double dt,
                     int on_device);
 
+/* Set the state from the conserved variables alone (U: 9 fields, FP64) with
+ * the time t and the next step dt; the primitives are re-derived on the
+ * device by the step's own inversion, floors, ceilings, Lorentz cap and
+ * fixups (Sections 2.3-2.4, Eq. 33), Newton starting from the primitives the
+ * context holds, and the ghosts refilled.  U passes through unchanged except
+ * where a floor or a fixup acts (then, as in a step, U is recomputed from
+ * the corrected primitives).  For a U that grmhd_get_state returned (P is
+ * the inversion of U after every step) the primitives come back to the
+ * inversion's tolerance (GRMHD_MIXED: the mixed Newton's acceptance, up to
+ * ~1e-5 relative in u of cold gas), so a serving loop can move half the
+ * bytes of a full state.  The inversions count in the diagnostics counters like a stage's.
+ * Needs a state already (grmhd_set_state or grmhd_init_torus: GRMHD_ESTATE
+ * otherwise) and a whole grid (a slab: GRMHD_EINVAL); t and dt finite,
+ * dt >= 0 (GRMHD_EINVAL).  A host U is copied as in grmhd_set_state; the
+ * call returns when the primitives are on the device.  A non-finite value in
+ * U returns GRMHD_ENONFINITE and leaves the context without a state;
+ * unfixable inversion failures raise GRMHD_EFIXUP at the next grmhd_sync. */
+int grmhd_set_state_u(grmhd_ctx *ctx, const double *U, double t, double dt, int on_device);
+
 /* Copy the active-zone state out (any of P, U, t, dt may be NULL); a host
  * copy is split as in grmhd_set_state.  Returns when the copy is done. */
 int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt,

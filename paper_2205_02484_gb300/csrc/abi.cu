@@ -510,6 +510,45 @@ extern "C" int grmhd_set_state(grmhd_ctx *ctx, const double *P, const double *U,
     return 0;
 }
 
+extern "C" int grmhd_set_state_u(grmhd_ctx *ctx, const double *U, double t, double dt, int on_device)
+{
+    if (!ctx || !U) return fail(ctx, GRMHD_EINVAL, "null argument");
+    if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "set_state_u needs grmhd_set_metric first");
+    if (!ctx->state_set)
+        return fail(ctx, GRMHD_ESTATE, "set_state_u needs primitives to start from (grmhd_set_state or grmhd_init_torus)");
+    if (ctx->gp.n2_total != 0 || ctx->g.bc3 == BC_EXTERNAL)
+        return fail(ctx, GRMHD_EINVAL, "set_state_u: whole grids only (a slab's ghosts come from its neighbours)");
+    if (!std::isfinite(t) || !std::isfinite(dt) || dt < 0.0)
+        return fail(ctx, GRMHD_EINVAL, "set_state_u: t and dt must be finite, dt >= 0");
+    long long na = nact_of(ctx);
+    const double *Ud = U;
+    if (!on_device) {
+        if (ensure_staging(ctx, 9 * na)) return GRMHD_ENOMEM;
+        const CopyPart part = {(char *)ctx->staging, (const char *)U, 9 * na * sizeof(double)};
+        if (int rc = copy_split(ctx, &part, 1, cudaMemcpyHostToDevice)) return rc;
+        Ud = ctx->staging;
+    }
+    (void)cudaGetLastError();
+    ctx->state_set = false;
+    CK(cudaMemsetAsync(ctx->g.status, 0, sizeof(int), ctx->stream));
+    launch_copy_state_in(ctx->g, nullptr, Ud, ctx->stream);
+    CK(cudaGetLastError());
+    if (set_scalars(ctx, t, dt)) return GRMHD_ECUDA; // synchronises the stream
+    CK(cudaMemcpyAsync(&ctx->hpin[8], ctx->g.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int st = 0;
+    std::memcpy(&st, &ctx->hpin[8], sizeof(int));
+    if (st & ST_NONFINITE) {
+        CK(cudaMemsetAsync(ctx->g.status, 0, sizeof(int), ctx->stream));
+        return fail(ctx, GRMHD_ENONFINITE, "set_state_u: U holds a non-finite value; the context has no state");
+    }
+    launch_reinvert(ctx->g, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->state_set = true;
+    return 0;
+}
+
 extern "C" int grmhd_get_state(grmhd_ctx *ctx, double *P, double *U, double *t, double *dt, int on_device)
 {
     if (!ctx) return fail(nullptr, GRMHD_EINVAL, "null context");

@@ -358,11 +358,12 @@ __global__ void k_state_in(Grid g, const double *Pa, const double *Ua)
     RS *P = (RS *)g.P[0];
     // a value is finite unless its exponent bits are all set (integer test on the high word)
     unsigned bad = 0;
-    for (int c = 0; c < NP; c++) {
-        const double v = Pa[c * nact + t];
-        bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
-        P[c * g.nz + z] = (RS)v;
-    }
+    if (Pa) // null: U alone (the primitives are re-derived afterwards)
+        for (int c = 0; c < NP; c++) {
+            const double v = Pa[c * nact + t];
+            bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+            P[c * g.nz + z] = (RS)v;
+        }
     for (int c = 0; c < NU; c++) {
         const double v = Ua[c * nact + t];
         bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;

@@ -9,6 +9,7 @@ void launch_step(const Grid &g, cudaStream_t s);
 void launch_step_profiled(const Grid &g, cudaStream_t s, cudaEvent_t *ev);
 double launch_fma_probe(int fp64, int sms, cudaStream_t s);
 void launch_bc(const Grid &g, int buf, cudaStream_t s);
+void launch_reinvert(const Grid &g, cudaStream_t s);
 // Eq. 43 sums over rows i_h.. with centre radius <= r_bar_max: out[0] = numerator, out[1] = mass
 void launch_barycentric(const Grid &g, const CoordParams &cp, double r_bar_max, double *part, double *out,
                         cudaStream_t s);

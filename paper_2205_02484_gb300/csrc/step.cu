@@ -359,6 +359,28 @@ void launch_x3_planes(const Grid &g, int which, int side, void *buf, int unpack,
     else k_x3_planes<double><<<nb, 256, 0, s>>>(g, (double *)g.P[which], (double *)buf, base, unpack);
 }
 
+// Primitives re-derived from the conserved state alone: one stage's update
+// with every face flux and edge EMF zero and a zero time-step factor, so U
+// passes through unchanged (U + 0 x finite terms) and the step's own
+// inversion, floors, ceilings, cap and fixups (Sections 2.3-2.4, Eq. 33)
+// produce P from it, Newton starting from the primitives the context holds.
+// Buffer 0 holds the result, ghosts filled.
+void launch_reinvert(const Grid &g, cudaStream_t s)
+{
+    const size_t rs = g.mixed ? sizeof(float) : sizeof(double);
+    for (int d = 0; d < 3; d++) {
+        cudaMemsetAsync(g.F[d], 0, 9 * g.nz * rs, s);
+        cudaMemsetAsync(g.E[d], 0, g.nz * rs, s);
+    }
+    const size_t bytes = (size_t)NP * g.nz * rs;
+    cudaMemcpyAsync(g.P[1], g.P[0], bytes, cudaMemcpyDeviceToDevice, s); // no history: plain Newton start
+    for (int part = 4; part < 7; part++) {
+        if (g.mixed) stage_part<float>(g, part, 0, 1, 0.0, 1, 0, s);
+        else stage_part<double>(g, part, 0, 1, 0.0, 1, 0, s);
+    }
+    cudaMemcpyAsync(g.P[0], g.P[1], bytes, cudaMemcpyDeviceToDevice, s);
+}
+
 void launch_bc(const Grid &g, int buf, cudaStream_t s)
 {
     if (g.mixed) fill_bc<float>(g, (float *)g.P[buf], s);

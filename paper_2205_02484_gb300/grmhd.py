@@ -110,6 +110,7 @@ SIGNATURES = {
     "grmhd_init_torus": (C.c_int, [_V, C.POINTER(TorusParams)]),
     "grmhd_set_state": (C.c_int, [_V, _V, _V, C.c_double, C.c_double, C.c_int]),
     "grmhd_get_state": (C.c_int, [_V, _V, _V, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
+    "grmhd_set_state_u": (C.c_int, [_V, _V, C.c_double, C.c_double, C.c_int]),
     "grmhd_step": (C.c_int, [_V, C.c_int]),
     "grmhd_con2prim": (C.c_int, [_V, _V, _V, _V, _V, _V, C.c_long, C.c_int, C.c_int]),
     "grmhd_prim2cons": (C.c_int, [_V, _V, _V, _V, C.c_long, C.c_int]),
@@ -280,6 +281,24 @@ def set_state(ctx: Context, P, U, t: float, dt: float):
     if dev != dev2:
         raise ValueError("P and U must both be host or both be device")
     ctx.check(ctx.L.grmhd_set_state(ctx.h, pp, up, t, dt, dev))
+
+
+def set_state_u(ctx: Context, U, t: float, dt: float):
+    """The state from U (9, n1, n2, n3) alone; the primitives are re-derived on
+    the device (numpy array = host, CUDA tensor = device)."""
+    up, dev = _ptr(U)
+    ctx.check(ctx.L.grmhd_set_state_u(ctx.h, up, t, dt, dev))
+
+
+def get_state_u(ctx: Context, U=None):
+    """Fills U (9, n1, n2, n3) alone (numpy or CUDA tensor; a new numpy array if
+    None) and returns (U, t, dt)."""
+    if U is None:
+        U = np.zeros((NU,) + ctx.shape)
+    up, dev = _ptr(U)
+    t, dt = C.c_double(), C.c_double()
+    ctx.check(ctx.L.grmhd_get_state(ctx.h, None, up, C.byref(t), C.byref(dt), dev))
+    return U, t.value, dt.value
 
 
 def get_state(ctx: Context, P=None, U=None):
