@@ -179,7 +179,7 @@ __device__ inline void cons_of(const double q[NP], const Geo<double> &geo, doubl
     U[KB1] = gd * q[KB1];
     U[KB2] = gd * q[KB2];
     U[KB3] = gd * q[KB3];
-    U[KENT] = gd * (p * pow(q[KRHO], 1.0 - gam)) * s.ucon[0];
+    U[KENT] = gd * (p * rho_pow_1mg(q[KRHO], gam)) * s.ucon[0];
 }
 
 } // namespace grmhd

@@ -65,6 +65,32 @@ __device__ __forceinline__ double powr<double>(double x, double y) { return pow(
 template <>
 __device__ __forceinline__ float powr<float>(float x, float y) { return powf(x, y); }
 
+// rho^(1 - gam) of the entropy density (Eq. 12): reciprocal cube roots for
+// the adiabatic indices 4/3, 5/3 and 13/9 (rho^(-1/3), rho^(-2/3),
+// rho^(-4/9) = (rho^(-1/9))^4 with rho^(-1/9) = rcbrt(cbrt(rho))), a general
+// power otherwise and for rho <= 0 (where it keeps pow's inf / NaN)
+__device__ __forceinline__ double rcbrtr(double x) { return rcbrt(x); }
+__device__ __forceinline__ float rcbrtr(float x) { return rcbrtf(x); }
+__device__ __forceinline__ double cbrtr(double x) { return cbrt(x); }
+__device__ __forceinline__ float cbrtr(float x) { return cbrtf(x); }
+
+template <typename R>
+__device__ __forceinline__ R rho_pow_1mg(R rho, R gam)
+{
+    if (rho > R(0)) {
+        if (gam == R(4.0 / 3.0)) return rcbrtr(rho);
+        if (gam == R(5.0 / 3.0)) {
+            const R r = rcbrtr(rho);
+            return r * r;
+        }
+        if (gam == R(13.0 / 9.0)) {
+            const R r = rcbrtr(cbrtr(rho)), r2 = r * r;
+            return r2 * r2;
+        }
+    }
+    return powr(rho, R(1) - gam);
+}
+
 // Row mu of T^mu_nu.
 template <typename R>
 __device__ __forceinline__ void tmunu_row(const R q[NP], const St<R> &s, R gam, int mu, R T[4])
@@ -87,7 +113,7 @@ __device__ __forceinline__ void prim_to_UF(const R q[NP], const Geo<R> &g, const
     tmunu_row(q, s, gam, d, T);
     R gd = g.gdet;
     R p = (gam - R(1)) * q[KUU];
-    R ent = p * powr(q[KRHO], R(1) - gam);
+    R ent = p * rho_pow_1mg(q[KRHO], gam);
     out[KRHO] = gd * q[KRHO] * s.ucon[d];
     if (RMS) {
         // T^d_t + rho u^d = rho u^d (1 + u_t) + (u + p + b^2) u^d u_t - b^d b_t (+ p + b^2/2 if d = t)
@@ -124,7 +150,7 @@ __device__ __forceinline__ void prim_to_UF2(const R q[NP], const Geo<R> &g, cons
     const R p = (gam - R(1)) * q[KUU];
     const R wb = q[KRHO] + q[KUU] + p + s.bsq;
     const R ptot = p + R(0.5) * s.bsq;
-    const R ent = gd * p * powr(q[KRHO], R(1) - gam);
+    const R ent = gd * p * rho_pow_1mg(q[KRHO], gam);
     const R gut = gd * s.ucon[0], gud = gd * s.ucon[d];
     const R gbt = gd * s.bcon[0], gbd = gd * s.bcon[d];
     U[KRHO] = gut * q[KRHO];
