@@ -38,15 +38,35 @@ __device__ __forceinline__ void lower4(const Geo<R> &g, const R v[4], R w[4])
                g.gcov[sym(m, 3)] * v[3];
 }
 
+// a / b: a division in FP64; in FP32 (the mixed path's face physics) the
+// hardware reciprocal times a (2 ulp, within the FP32 rounding the face
+// fluxes carry anyway; b is never near the float range's end here)
+template <typename R>
+__device__ __forceinline__ R divr(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float divr<float>(float a, float b) { return __fdividef(a, b); }
+
+// square root: correctly rounded in FP64; in FP32 the hardware approximation
+// (sqrt.approx, ~2 ulp, exact at 0) for the same reason
+template <typename R>
+__device__ __forceinline__ R sqrtr(R x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float sqrtr<float>(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <typename R>
 __device__ __forceinline__ void get_state(const R q[NP], const Geo<R> &g, St<R> &s)
 {
     R usq = spatial_sq(g, q[KU1], q[KU2], q[KU3]);
-    R gm = sqrt(R(1) + usq);
+    R gm = sqrtr(R(1) + usq);
     s.usq = usq;
     s.gamma = gm;
     s.ucon[0] = gm * g.ialpha;
-    const R iut = g.alpha / gm; // 1 / u^t
+    const R iut = divr(g.alpha, gm); // 1 / u^t
 #pragma unroll
     for (int i = 1; i <= 3; i++) s.ucon[i] = q[KU1 + i - 1] - gm * g.alpha * g.gcon[sym(0, i)];
     lower4(g, s.ucon, s.ucov);
@@ -117,7 +137,7 @@ __device__ __forceinline__ void prim_to_UF(const R q[NP], const Geo<R> &g, const
     out[KRHO] = gd * q[KRHO] * s.ucon[d];
     if (RMS) {
         // T^d_t + rho u^d = rho u^d (1 + u_t) + (u + p + b^2) u^d u_t - b^d b_t (+ p + b^2/2 if d = t)
-        R opu = g.oma - g.alpha * (s.usq / (s.gamma + R(1))) +
+        R opu = g.oma - g.alpha * divr(s.usq, s.gamma + R(1)) +
                 (g.gcov[1] * q[KU1] + g.gcov[2] * q[KU2] + g.gcov[3] * q[KU3]);
         R e = q[KRHO] * s.ucon[d] * opu + (q[KUU] + p + s.bsq) * s.ucon[d] * s.ucov[0] -
               s.bcon[d] * s.bcov[0];
@@ -164,7 +184,7 @@ __device__ __forceinline__ void prim_to_UF2(const R q[NP], const Geo<R> &g, cons
     F[1 + d] += gd * ptot;
     if (RMS) {
         // T^mu_t + rho u^mu = rho u^mu (1 + u_t) + (u + p + b^2) u^mu u_t - b^mu b_t (+ ptot for mu = t)
-        const R opu = g.oma - g.alpha * (s.usq / (s.gamma + R(1))) +
+        const R opu = g.oma - g.alpha * divr(s.usq, s.gamma + R(1)) +
                       (g.gcov[1] * q[KU1] + g.gcov[2] * q[KU2] + g.gcov[3] * q[KU3]);
         const R rest = q[KUU] + p + s.bsq;
         U[1] = gut * (q[KRHO] * opu + rest * s.ucov[0]) - gbt * s.bcov[0] + gd * ptot;
@@ -187,7 +207,7 @@ __device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, cons
     R p = (gam - R(1)) * q[KUU];
     R ef = q[KRHO] + q[KUU] + p;
     R ee = s.bsq + ef;
-    R inv = R(1) / (ee * ef);
+    R inv = divr(R(1), ee * ef);
     R va2 = s.bsq * ef * inv;   // b^2 / (b^2 + rho + u + p)
     R cs2 = gam * p * ee * inv; // gam p / (rho + u + p)
     R cms2 = va2 + cs2 * (R(1) - va2);
@@ -198,8 +218,8 @@ __device__ __forceinline__ void wave_speeds(const R q[NP], const Geo<R> &g, cons
     R C = A1 * ud * ud - cms2 * g.gcon[sym(d, d)];
     R disc = B * B - R(4) * A * C;
     disc = disc < R(0) ? R(0) : disc;
-    R sq = sqrt(disc);
-    R i2a = R(0.5) / A;
+    R sq = sqrtr(disc);
+    R i2a = divr(R(0.5), A);
     R vp = (-B + sq) * i2a;
     R vm = (-B - sq) * i2a;
     c1 = vp > vm ? vp : vm;
