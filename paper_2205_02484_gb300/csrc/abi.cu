@@ -172,7 +172,7 @@ extern "C" int grmhd_init_grid(const grmhd_grid_params *grid, const grmhd_phys_p
     g.recon = grid->recon;
     g.mixed = grid->precision == GRMHD_MIXED;
     // a row warp evaluates 29 faces per 32 lanes: worth it only for rows of >= 32 faces
-    g.x3warp = g.mixed && g.n3 + 1 >= 32;
+    g.x3warp = g.n3 + 1 >= 32;
     // an axisymmetric grid (n3 = 1, X3 ghosts copies of the one plane) computes
     // the k = 0 faces only: the k = -1 and k = 1 planes hold the same states
     g.flat3 = g.n3 == 1 && (grid->metric == GRMHD_KERR_MKS || grid->bc3 == GRMHD_BC_PERIODIC ||

@@ -73,7 +73,7 @@ struct Grid {
     int n1, n2, n3, N1, N2, N3;
     long long nz;
     int metric, bc1, bc2, bc3, riemann, mixed, i_h, nfix_cap;
-    int x3warp;                 // X3 fluxes by row warps (mixed path, rows of >= 32 faces)
+    int x3warp;                 // X3 fluxes by row warps (rows of >= 32 faces)
     int flat3;                  // one phi zone with copied X3 ghosts: the face fluxes do not vary
     int recon;                  // 0 PLM (Eqs. 16-17), 1 PPM (faces read three zones on each side)
     int j0, n2t;                // a theta slab's first row and the whole grid's rows (0, n2: whole grid)

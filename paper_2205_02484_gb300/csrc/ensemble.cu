@@ -48,7 +48,7 @@ __host__ __device__ inline long long class_count(const Grid &g, int cls)
     switch (cls) {
     case W_F1: return flux_elem_box(g, 1).count();
     case W_F2: return flux_elem_box(g, 2).count();
-    case W_F3: return g.x3warp ? x3_warp_box(g).count() : flux_elem_box(g, 3).count(); // long mixed rows: warps
+    case W_F3: return g.x3warp ? x3_warp_box(g).count() : flux_elem_box(g, 3).count(); // long rows: warps
     case W_EMF: return edge_box(g).count();
     case W_UPD: return nact_of(g);
     case W_POL: return polar_count(g);
@@ -108,10 +108,8 @@ __global__ void __launch_bounds__(ENS_THREADS) ek_sweep(EnsDev E, int src, int d
             if (CLS == W_F3) {
                 // tiles are whole warps (blockDim and items multiples of 32), as the
                 // mixed path's row-warp X3 sweep needs
-                bool warp = false;
-                if constexpr (sizeof(R) == 4) warp = sg.x3warp;
-                if (warp)
-                    cwm = max(cwm, flux_x3_warp<R>(sg, Pin, (R *)sg.F[2], x3_warp_box(sg), want_dt, t));
+                if (sg.x3warp)
+                    cwm = max(cwm, flux_x3_warp_call<R>(sg, Pin, (R *)sg.F[2], x3_warp_box(sg), want_dt, t));
                 else
                     cwm = max(cwm, flux_call<R, 3>(sg, Pin, (R *)sg.F[2], flux_elem_box(sg, 3), want_dt, t));
             }

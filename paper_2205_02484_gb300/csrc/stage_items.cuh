@@ -1099,6 +1099,21 @@ static __device__ __noinline__ double flux_item_d3(const Grid &g, const double *
 {
     return flux_item<double, 3>(g, P, F, box, w, t);
 }
+// the X3 row-warp sweep in FP64, out of line like the other FP64 items (all
+// lanes of the warp call it together)
+static __device__ __noinline__ double flux_x3_warp_d(const Grid &g, const double *P, double *F, const Box &box,
+                                                     int w, long long t)
+{
+    return flux_x3_warp<double>(g, P, F, box, w, t);
+}
+
+// X3 faces of a row by one warp (x3_warp_box), either precision
+template <typename R>
+__device__ __forceinline__ R flux_x3_warp_call(const Grid &g, const R *P, R *F, const Box &box, int w, long long t)
+{
+    if constexpr (sizeof(R) == 8) return flux_x3_warp_d(g, P, F, box, w, t);
+    else return flux_x3_warp<R>(g, P, F, box, w, t);
+}
 static __device__ __noinline__ void update_item_d(const Grid &g, const double *Pin, double *Pout, const double *F1,
                                            const double *F2, const double *F3, const double *E1,
                                            const double *E2, const double *E3, double dtfac, int corr,

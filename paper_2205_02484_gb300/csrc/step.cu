@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (D < 3 ? 4 : 5) : 1) k_f
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     R cw;
-    if constexpr (D == 3 && sizeof(R) == 4) {
-        if (g.x3warp) cw = flux_x3_warp<R>(g, P, F, box, want_dt, t);
+    if constexpr (D == 3) {
+        if (g.x3warp) cw = flux_x3_warp_call<R>(g, P, F, box, want_dt, t);
         else cw = flux_call<R, D>(g, P, F, box, want_dt, t);
     } else {
         cw = flux_call<R, D>(g, P, F, box, want_dt, t);
@@ -127,7 +127,7 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     R *Pout = (R *)g.P[dst];
     // the mixed path sweeps X3 by warps (x3_warp_box) where rows are long; else by faces
     Box b1 = flux_elem_box(g, 1), b2 = flux_elem_box(g, 2), be = edge_box(g);
-    Box b3 = (sizeof(R) == 4 && g.x3warp) ? x3_warp_box(g) : flux_elem_box(g, 3);
+    Box b3 = g.x3warp ? x3_warp_box(g) : flux_elem_box(g, 3);
     if (g.recon && part < 3) { // PPM faces: columns, row warps or single faces as for PLM
         const Box bp = part < 2 ? col_box(g, part + 1)
                                 : ((sizeof(R) == 4 && g.x3warp) ? x3_warp_box(g) : flux_box(g, 3));
