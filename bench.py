@@ -362,7 +362,8 @@ def run_theta_slabs(G, torch, device, n1=1024, n2=1024, steps=20, warmup=2, coun
 def run_slabs(G, torch, device, n, steps=10, warmup=2, counts=(2, 4, 8)):
     """The n^3 mixed torus split into R phi slabs on one GPU (decomp.SlabRing:
     stage-level launches, X3 ghost pack / unpack through device buffers, the
-    per-direction dt minima folded on the device), timed against the
+    per-direction dt minima folded on the device; one ring step captured in a
+    CUDA graph and replayed, the host-launched form timed too), timed against the
     undecomposed graph step from the same state, with a bitwise comparison
     of the final states.  A slab's time per step approximates one rank's
     compute in an R-GPU run; ghost_bytes_per_slab_step is what that rank would
@@ -418,6 +419,7 @@ def run_slabs(G, torch, device, n, steps=10, warmup=2, counts=(2, 4, 8)):
             "launches_per_step": R * (2 * 10 + 2 + 2 * 4),
         }
         del Pr, Ur
+        out["slabs"][str(R)]["ms_per_step_host_launches"] = time_it(lambda: ring.step(steps, graph=False)) / steps
         ring.close()
     return out
 

@@ -132,7 +132,12 @@ def _stream_of(engine):
 
 
 class SlabRing:
-    """All slabs of one grid on one device, in phi order, sharing one stream."""
+    """All slabs of one grid on one device, in phi order, sharing one stream.
+    A step of library slabs is a fixed sequence of device work on that stream
+    (no host read in it), so it is captured once into a CUDA graph and
+    replayed.  The graph holds every context's grid record by value: after a
+    call that changes one (set_metric, set_learned_guess) call drop_graph().
+    set_state writes into the buffers the graph reads and needs nothing."""
 
     def __init__(self, engines):
         self.e = list(engines)
@@ -140,6 +145,9 @@ class SlabRing:
         self.lo = [torch.empty(e.plane_numel, dtype=e.dtype, device=e.device) for e in self.e]
         self.hi = [torch.empty(e.plane_numel, dtype=e.dtype, device=e.device) for e in self.e]
         self.dtd_buf = torch.empty(3, dtype=torch.float64, device=e0.device)
+        self._graph = None
+        streams = {id(getattr(e, "stream", None)) for e in self.e}
+        self._capturable = all(isinstance(e, CtxSlab) for e in self.e) and len(streams) == 1
 
     @classmethod
     def create(cls, grid: G.GridParams, phys: G.PhysParams, R: int, a: float, stream=None):
@@ -164,17 +172,35 @@ class SlabRing:
             e.unpack(which, 0, self.hi[(r - 1) % R])
             e.unpack(which, 1, self.lo[(r + 1) % R])
 
-    def step(self, nsteps=1):
-        for _ in range(nsteps):
-            for r, e in enumerate(self.e):
-                e.stage(0)
-                e.dtd(self.dtd_buf, accumulate=r > 0)
-            self.exchange(1)
-            for e in self.e:
-                e.stage(1)
-            self.exchange(0)
-            for e in self.e:
-                e.finish(self.dtd_buf)
+    def _step_once(self):
+        for r, e in enumerate(self.e):
+            e.stage(0)
+            e.dtd(self.dtd_buf, accumulate=r > 0)
+        self.exchange(1)
+        for e in self.e:
+            e.stage(1)
+        self.exchange(0)
+        for e in self.e:
+            e.finish(self.dtd_buf)
+
+    def step(self, nsteps=1, graph=True):
+        """nsteps RK2 steps of the whole grid; graph=False launches every
+        kernel from the host (the form the engines' tests drive)."""
+        if not (graph and self._capturable):
+            for _ in range(nsteps):
+                self._step_once()
+            return
+        s = self.e[0].stream
+        if self._graph is None:
+            self._graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self._graph, stream=s):
+                self._step_once()
+        with torch.cuda.stream(s):
+            for _ in range(nsteps):
+                self._graph.replay()
+
+    def drop_graph(self):
+        self._graph = None
 
     def diagnostics(self, r_bar_max=80.0):
         return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[0]

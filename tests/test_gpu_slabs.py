@@ -87,6 +87,35 @@ def test_slab_ring_matches_the_oracle_per_step():
     ring.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_host_launches(precision):
+    """A ring step replayed from its CUDA graph equals the same step launched
+    kernel by kernel, and a state set after the capture is the one the
+    replay steps."""
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import SlabRing
+    grid, phys, full, (P0, U0, t0, dt0) = _start(G, precision)
+    full.close()
+    a = SlabRing.create(grid, phys, 4, A)
+    b = SlabRing.create(grid, phys, 4, A)
+    a.set_state(P0, U0, t0, dt0)
+    b.set_state(P0, U0, t0, dt0)
+    a.step(3, graph=False)
+    b.step(3)
+    assert b._graph is not None
+    Pa, Ua, ta, dta = _ring_state(a)
+    Pb, Ub, tb, dtb = _ring_state(b)
+    assert (ta, dta) == (tb, dtb)
+    assert np.array_equal(Pa, Pb) and np.array_equal(Ua, Ub)
+    b.set_state(P0, U0, t0, dt0)
+    b.step(3)
+    Pc, Uc, tc, dtc = _ring_state(b)
+    assert (tc, dtc) == (ta, dta)
+    assert np.array_equal(Pc, Pa) and np.array_equal(Uc, Ua)
+    a.close()
+    b.close()
+
+
 def test_pack_unpack_planes():
     """pack copies the two outermost active planes of a side; unpack writes
     the ghost planes the step reads (checked through a one-slab ring, whose
