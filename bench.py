@@ -298,10 +298,12 @@ def run_ensemble(G, torch, stream, device, steps=10, n=24, shapes=None, workload
 
 def run_theta_slabs(G, torch, device, n1=1024, n2=1024, steps=20, warmup=2, counts=(2, 4, 8)):
     """An n1 x n2 axisymmetric mixed torus split into R theta slabs on one GPU
-    (decomp.ThetaRing: stage parts, X2 ghost rows and fixup edge rows through
-    device buffers, the failed-zone count read on the host once per stage and
-    once per fixup sweep), timed against the undecomposed graph step from the
-    same state, with a bitwise comparison of the final states."""
+    (decomp.ThetaRing: stage parts, X2 ghost rows through device buffers, the
+    fixup loop of every stage on the device, one ring step captured in a CUDA
+    graph and replayed), timed against the undecomposed graph step from the
+    same state, with a bitwise comparison of the final states; the ring with
+    the fixup loop run from the host (the failed-zone count read there once
+    per stage and once per sweep, no graph) is timed too."""
     from paper_2205_02484_gb300.decomp import ThetaRing
     phys = G.default_phys(gam=13.0 / 9.0)
     gp = G.default_grid(n1, n2, 1, a=0.9375, r_out=1000.0, precision=G.MIXED, device=device)
@@ -354,6 +356,11 @@ def run_theta_slabs(G, torch, device, n1=1024, n2=1024, steps=20, warmup=2, coun
         }
         del Pr, Ur
         ring.close()
+        host = ThetaRing.create(gp, phys, R, 0.9375, stream=s, device_fix=False)
+        host.set_state(P0, U0, t0, dt0)
+        host.step(warmup)
+        out["slabs"][str(R)]["ms_per_step_host_loop"] = time_it(lambda: host.step(steps)) / steps
+        host.close()
     return out
 
 
@@ -1210,6 +1217,8 @@ def main():
     if world == 1 and not args.no_slabs:
         slabs = run_slabs(G, torch, local, n)
         theta_slabs = run_theta_slabs(G, torch, local)
+        # a grid whose step is short enough that launches and host reads count
+        theta_slabs["small_grid"] = run_theta_slabs(G, torch, local, n1=256, n2=256, steps=40, counts=(2, 4))
     # ---- the 256^3 workload's (gamma, beta_0) grid, and its FP64-vs-mixed window
     variants = window256 = None
     if world == 1 and not args.no_window:

@@ -554,7 +554,9 @@ int grmhd_x3_unpack(grmhd_ctx *ctx, int which, int side, const void *buf_dev);
  * unpacks its low neighbour's side-1 pack into its side 0 and its high
  * neighbour's side-0 pack into its side 1 (no neighbour across a pole).
  * Every call is asynchronous on the context stream; reading `left` on the
- * host is the caller's synchronisation.
+ * host is the caller's synchronisation.  When all slabs sit on one device,
+ * grmhd_theta_ring_fix runs the whole fixup loop there instead (no host
+ * read), so that a ring step can be captured in a CUDA graph.
  * ------------------------------------------------------------------- */
 
 /* Fluxes, flux-CT, update and inversion of stage st (a stage up to its
@@ -574,6 +576,19 @@ int grmhd_fix_sweep(grmhd_ctx *ctx, int st, long long *acc_dev);
  * grmhd_sync) if a zone stays failed, clear the failure list. */
 int grmhd_fix_end(grmhd_ctx *ctx, int st, int nsweeps);
 
+/* The fixups (Eq. 33) of stage st of the nslab (1..16) theta slabs of one
+ * grid (the decomposition of Sec. 3), all on one device and one stream,
+ * given in theta order (ctxs[r]->j0 = the rows before it; together they hold
+ * every row): the loop above from the fail counts through grmhd_fix_end --
+ * kind-1 row exchanges between neighbouring slabs (across the periodic edge
+ * of a periodic flat box too), Jacobi sweeps, the close of every slab -- run
+ * by one kernel on ctxs[0]'s stream, bit for bit the host loop's result.
+ * nsweeps_dev (one int of device memory, or null) receives the sweep count.
+ * Errors are reported on ctxs[0] (GRMHD_EINVAL for slabs that are not such
+ * a split, on another device or stream; GRMHD_ESTATE for a slab without a
+ * state), and nothing is launched then. */
+int grmhd_theta_ring_fix(grmhd_ctx *const *ctxs, int nslab, int st, int *nsweeps_dev);
+
 /* Boundary fill of stage st's output (poles, X1, X3; the external X2 sides
  * are left to the exchange). */
 int grmhd_stage_bc(grmhd_ctx *ctx, int st);
@@ -588,13 +603,13 @@ int grmhd_stage_bc(grmhd_ctx *ctx, int st);
 int grmhd_x2_row_bytes(grmhd_ctx *ctx, int kind, unsigned long long *bytes);
 
 /* Pack the outermost active rows of buffer `which` (0 = P, 1 = P-hat) on
- * `side` (0: j = 0, 1 for kind 0, j = 0 for kind 1; 1: j = n2-2, n2-1, or
- * j = n2-1) into the caller's device buffer. */
+ * `side` (0: j = 0 .. NG-1 for kind 0, j = 0 for kind 1; 1: j = n2-NG ..
+ * n2-1, or j = n2-1) into the caller's device buffer. */
 int grmhd_x2_pack(grmhd_ctx *ctx, int kind, int which, int side, void *buf_dev);
 
-/* Write a neighbour's packed rows into the ghost rows on `side` (0: j = -2,
- * -1, or j = -1; 1: j = n2, n2+1, or j = n2) of buffer `which` (kind 1
- * writes the ghost rows' failure flags too). */
+/* Write a neighbour's packed rows into the ghost rows on `side` (0: j = -NG
+ * .. -1, or j = -1; 1: j = n2 .. n2+NG-1, or j = n2) of buffer `which`
+ * (kind 1 writes the ghost rows' failure flags too). */
 int grmhd_x2_unpack(grmhd_ctx *ctx, int kind, int which, int side, const void *buf_dev);
 
 /* Barycentric radius of the disk (Sec. 4.2, Eq. 43):

@@ -1425,6 +1425,34 @@ extern "C" int grmhd_fix_end(grmhd_ctx *ctx, int st, int nsweeps)
     return 0;
 }
 
+extern "C" int grmhd_theta_ring_fix(grmhd_ctx *const *ctxs, int nslab, int st, int *nsweeps_dev)
+{
+    if (!ctxs || !ctxs[0]) return fail(nullptr, GRMHD_EINVAL, "null argument");
+    grmhd_ctx *c0 = ctxs[0];
+    if (nslab < 1 || nslab > RING_MAX) return fail(c0, GRMHD_EINVAL, "a ring holds 1 to 16 theta slabs");
+    Grid gs[RING_MAX];
+    for (int r = 0; r < nslab; r++) {
+        grmhd_ctx *c = ctxs[r];
+        if (!c) return fail(c0, GRMHD_EINVAL, "null slab " + std::to_string(r));
+        if (int rc = theta_check(c, st)) return fail(c0, rc, "slab " + std::to_string(r) + ": " + c->err);
+        const int j0 = r == 0 ? 0 : ctxs[r - 1]->g.j0 + ctxs[r - 1]->g.n2;
+        if (c->g.j0 != j0 || c->g.n2t != c0->g.n2t || c->g.n1 != c0->g.n1 || c->g.n3 != c0->g.n3 ||
+            c->g.mixed != c0->g.mixed || c->g.metric != c0->g.metric || c->g.bc2 != c0->g.bc2 ||
+            c->g.fix_maxsweep != c0->g.fix_maxsweep || c->gp.device != c0->gp.device ||
+            c->stream != c0->stream)
+            return fail(c0, GRMHD_EINVAL, "slab " + std::to_string(r) +
+                                              ": the slabs of a ring split one grid in theta order, on one device "
+                                              "and one stream");
+        gs[r] = c->g;
+    }
+    if (ctxs[nslab - 1]->g.j0 + ctxs[nslab - 1]->g.n2 != c0->g.n2t)
+        return fail(c0, GRMHD_EINVAL, "the slabs of a ring cover every row of the grid");
+    grmhd_ctx *ctx = c0;
+    launch_fix_ring(gs, nslab, st, nsweeps_dev, ctx->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
 extern "C" int grmhd_stage_bc(grmhd_ctx *ctx, int st)
 {
     if (int rc = theta_check(ctx, st)) return rc;

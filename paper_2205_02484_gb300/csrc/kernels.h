@@ -22,6 +22,10 @@ void launch_stage_update(const Grid &g, int st, cudaStream_t s);
 void launch_fail_count(const Grid &g, long long *acc, cudaStream_t s);
 void launch_fix_sweep(const Grid &g, int st, long long *acc, cudaStream_t s);
 void launch_fix_end(const Grid &g, int nsweeps, cudaStream_t s);
+// the fixup loop of stage st over the theta slabs gs[0..nslab) of one grid on
+// one device, in theta order; nsweeps (device, may be null) <- the sweeps run
+constexpr int RING_MAX = 16;
+void launch_fix_ring(const Grid *gs, int nslab, int st, int *nsweeps, cudaStream_t s);
 long long x2_row_elems(const Grid &g, int kind);
 void launch_x2_rows(const Grid &g, int kind, int which, int side, void *buf, int unpack, cudaStream_t s);
 void launch_fluxes_dt(const Grid &g, int set_dt, cudaStream_t s);

@@ -302,6 +302,92 @@ __global__ void __launch_bounds__(256) k_fix_end(Grid g, int nsweeps)
 
 void launch_fix_end(const Grid &g, int nsweeps, cudaStream_t s) { k_fix_end<<<1, 256, 0, s>>>(g, nsweeps); }
 
+// The fixups of stage st of all theta slabs of one grid held on one device,
+// in one block: the loop of fail counts, kind-1 row exchanges, Jacobi sweeps
+// and closes that a host runs over the per-slab calls, with nothing read on
+// the host.  A round copies every slab's neighbours' edge rows (the five
+// averaged primitives and the flags) into its ghost rows before any slab
+// sweeps, and a sweep reads across a slab face only those ghost rows, so
+// the slabs' sweeps of a round see the same start state as the host loop's.
+struct RingGrids {
+    Grid g[RING_MAX];
+};
+static_assert(sizeof(RingGrids) < 32000, "kernel parameter block");
+
+template <typename R>
+__device__ void ring_edge_copy(const Grid &g, const Grid &gs, int jd, int js, int dst)
+{
+    R *P = (R *)g.P[dst];
+    const R *Ps = (const R *)gs.P[dst];
+    const long long plane = (long long)g.n1 * g.n3;
+    for (long long t = threadIdx.x; t < 6 * plane; t += blockDim.x) {
+        const int c = (int)(t / plane);
+        const long long e = t % plane;
+        const int i = (int)(e / g.n3), k = (int)(e % g.n3);
+        const long long zd = zidx(g, i, jd, k), zs = zidx(gs, i, js, k);
+        if (c < 5) P[c * g.nz + zd] = Ps[c * gs.nz + zs];
+        else g.flag[zd] = gs.flag[zs] ? 1 : 0;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_fix_ring(RingGrids rg, int nslab, int st, int *nsweeps)
+{
+    __shared__ int s_left;
+    const int dst = st == 0 ? 1 : 0;
+    long long left = 0;
+    for (int r = 0; r < nslab; r++) left += *rg.g[r].nfail;
+    int n = 0;
+    while (left > 0 && n < rg.g[0].fix_maxsweep) {
+        for (int r = 0; r < nslab; r++) {
+            const Grid &g = rg.g[r];
+            if (x2_external(g, 0)) {
+                const Grid &gs = rg.g[(r + nslab - 1) % nslab];
+                ring_edge_copy<R>(g, gs, -1, gs.n2 - 1, dst);
+            }
+            if (x2_external(g, 1)) ring_edge_copy<R>(g, rg.g[(r + 1) % nslab], g.n2, 0, dst);
+        }
+        __syncthreads();
+        left = 0;
+        for (int r = 0; r < nslab; r++) {
+            const Grid &g = rg.g[r];
+            const int nlist = min(*g.nfail, g.nfix_cap);
+            if (nlist > 0) left += fixup_sweep<R>(g, (R *)g.P[dst], st, nlist);
+        }
+        n++;
+    }
+    // close every slab as grmhd_fix_end does, with the common round count
+    for (int r = 0; r < nslab; r++) {
+        const Grid &g = rg.g[r];
+        if (threadIdx.x == 0) s_left = 0;
+        __syncthreads();
+        const int nlist = min(*g.nfail, g.nfix_cap);
+        int still = 0;
+        for (int a = threadIdx.x; a < nlist; a += blockDim.x) {
+            int t = g.faillist[a];
+            int k = t % g.n3, q = t / g.n3, j = q % g.n2, i = q / g.n2;
+            still += g.flag[zidx(g, i, j, k)] != 0;
+        }
+        if (still) atomicAdd(&s_left, still);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(&g.cnt[C_SWEEPS], (unsigned long long)n);
+            if (s_left > 0 || *g.nfail > g.nfix_cap) atomicOr(g.status, ST_FIXUP);
+            *g.nfail = 0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && nsweeps) *nsweeps = n;
+}
+
+void launch_fix_ring(const Grid *gs, int nslab, int st, int *nsweeps, cudaStream_t s)
+{
+    RingGrids rg;
+    for (int r = 0; r < nslab; r++) rg.g[r] = gs[r];
+    if (gs[0].mixed) k_fix_ring<float><<<1, 1024, 0, s>>>(rg, nslab, st, nsweeps);
+    else k_fix_ring<double><<<1, 1024, 0, s>>>(rg, nslab, st, nsweeps);
+}
+
 __host__ __device__ inline long long x2_row_count(const Grid &g, int kind)
 {
     return kind == 0 ? (long long)NG * NP * g.N1 * g.N3 : 6LL * g.n1 * g.n3;

@@ -416,11 +416,18 @@ def _theta_sides(R: int, r: int, periodic: bool):
 class ThetaRing:
     """All theta slabs of one grid on one device, in theta order, sharing one
     stream.  `periodic`: the whole grid is periodic in X2 (a flat box), so
-    the first and last slabs are neighbours."""
+    the first and last slabs are neighbours.
+
+    Library slabs (CtxTheta) run each stage's fixup loop on the device
+    (grmhd_theta_ring_fix: nothing read on the host), so a step is a fixed
+    sequence of device work, captured once in a CUDA graph and replayed (as
+    SlabRing's, drop_graph() after a change of a context's grid record).
+    device_fix=False, or other engines, run the loop from the host over the
+    per-slab calls (fail counts read on the host, kind-1 row exchanges)."""
 
     ROWS, FIX = 0, 1  # the two exchanges: NG ghost rows, a fixup sweep's edge row
 
-    def __init__(self, engines, periodic: bool = False):
+    def __init__(self, engines, periodic: bool = False, device_fix: bool = True):
         self.e = list(engines)
         self.periodic = periodic
         e0 = self.e[0]
@@ -432,12 +439,26 @@ class ThetaRing:
         self.dtd_buf = torch.empty(3, dtype=torch.float64, device=e0.device)
         self.count = torch.zeros(1, dtype=torch.int64, device=e0.device)
         self.fix_maxsweep = e0.fix_maxsweep
-        self.sweeps = []  # fixup sweeps of each stage of the last step
+        streams = {id(getattr(e, "stream", None)) for e in self.e}
+        self.device_fix = device_fix and all(isinstance(e, CtxTheta) for e in self.e) and len(streams) == 1
+        self._nsw = torch.zeros(2, dtype=torch.int32, device=e0.device) if self.device_fix else None
+        self._sweeps = []  # host loop: fixup sweeps of each stage of the last step
+        self._graph = None
 
     @classmethod
-    def create(cls, grid: G.GridParams, phys: G.PhysParams, R: int, a: float, stream=None, periodic=False):
+    def create(cls, grid: G.GridParams, phys: G.PhysParams, R: int, a: float, stream=None, periodic=False,
+               device_fix=True):
         stream = stream or torch.cuda.Stream(device=grid.device)
-        return cls([CtxTheta.create(theta_grid(grid, R, r), phys, a, stream) for r in range(R)], periodic)
+        return cls([CtxTheta.create(theta_grid(grid, R, r), phys, a, stream) for r in range(R)], periodic,
+                   device_fix)
+
+    @property
+    def sweeps(self):
+        """Fixup sweeps of each stage of the last step."""
+        if self.device_fix:
+            with _stream_of(self.e[0]):
+                return [int(v) for v in self._nsw.cpu()]
+        return list(self._sweeps)
 
     def set_state(self, P, U, t, dt):
         R = len(self.e)
@@ -466,29 +487,55 @@ class ThetaRing:
             fn(e)
         return int(self.count.item())
 
-    def step(self, nsteps=1):
-        with _stream_of(self.e[0]):
+    def _fixups(self, st, out):
+        if self.device_fix:
+            G.theta_ring_fix([e.ctx for e in self.e], st, self._nsw[st:st + 1])
+            for e in self.e:
+                e.stage_bc(st)
+            return
+        left = self._count(lambda e: e.fail_count(self.count))
+        n = 0
+        while left > 0 and n < self.fix_maxsweep:
+            self.exchange(self.FIX, out)
+            left = self._count(lambda e: e.fix_sweep(st, self.count))
+            n += 1
+        self._sweeps.append(n)
+        for e in self.e:
+            e.fix_end(st, n)
+            e.stage_bc(st)
+
+    def _step_once(self):
+        self._sweeps = []
+        for st in (0, 1):
+            out = 1 if st == 0 else 0  # the stage's output buffer
+            for r, e in enumerate(self.e):
+                e.stage_update(st)
+                if st == 0:
+                    e.dtd(self.dtd_buf, accumulate=r > 0)
+            self._fixups(st, out)
+            self.exchange(self.ROWS, out)
+        for e in self.e:
+            e.finish(self.dtd_buf)
+
+    def step(self, nsteps=1, graph=True):
+        """nsteps RK2 steps of the whole grid; graph=False launches every
+        kernel from the host."""
+        s = self.e[0].stream if hasattr(self.e[0], "stream") else None
+        if not (graph and self.device_fix):
+            with _stream_of(self.e[0]):
+                for _ in range(nsteps):
+                    self._step_once()
+            return
+        if self._graph is None:
+            self._graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self._graph, stream=s):
+                self._step_once()
+        with torch.cuda.stream(s):
             for _ in range(nsteps):
-                self.sweeps = []
-                for st in (0, 1):
-                    out = 1 if st == 0 else 0  # the stage's output buffer
-                    for r, e in enumerate(self.e):
-                        e.stage_update(st)
-                        if st == 0:
-                            e.dtd(self.dtd_buf, accumulate=r > 0)
-                    left = self._count(lambda e: e.fail_count(self.count))
-                    n = 0
-                    while left > 0 and n < self.fix_maxsweep:
-                        self.exchange(self.FIX, out)
-                        left = self._count(lambda e: e.fix_sweep(st, self.count))
-                        n += 1
-                    self.sweeps.append(n)
-                    for e in self.e:
-                        e.fix_end(st, n)
-                        e.stage_bc(st)
-                    self.exchange(self.ROWS, out)
-                for e in self.e:
-                    e.finish(self.dtd_buf)
+                self._graph.replay()
+
+    def drop_graph(self):
+        self._graph = None
 
     def diagnostics(self, r_bar_max=80.0):
         return _combine(self.e[0], [e.diag_partials(r_bar_max) for e in self.e])[0]

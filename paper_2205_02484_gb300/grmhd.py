@@ -154,6 +154,7 @@ SIGNATURES = {
     "grmhd_fail_count": (C.c_int, [_V, _V]),
     "grmhd_fix_sweep": (C.c_int, [_V, C.c_int, _V]),
     "grmhd_fix_end": (C.c_int, [_V, C.c_int, C.c_int]),
+    "grmhd_theta_ring_fix": (C.c_int, [C.POINTER(_V), C.c_int, C.c_int, _V]),
     "grmhd_stage_bc": (C.c_int, [_V, C.c_int]),
     "grmhd_x2_row_bytes": (C.c_int, [_V, C.c_int, C.POINTER(C.c_ulonglong)]),
     "grmhd_x2_pack": (C.c_int, [_V, C.c_int, C.c_int, C.c_int, _V]),
@@ -392,6 +393,17 @@ def fix_sweep(ctx: Context, st: int, acc):
 
 def fix_end(ctx: Context, st: int, nsweeps: int):
     ctx.check(ctx.L.grmhd_fix_end(ctx.h, st, nsweeps))
+
+
+def theta_ring_fix(ctxs, st: int, nsweeps=None):
+    """The fixup loop of stage st over the theta slabs `ctxs` of one grid on
+    one device (theta order), run on the device; nsweeps: an int32 device
+    tensor that receives the sweep count, or None."""
+    import torch
+    if nsweeps is not None and (nsweeps.dtype != torch.int32 or nsweeps.numel() < 1):
+        raise ValueError("nsweeps must be an int32 device tensor")
+    hs = (_V * len(ctxs))(*[c.h for c in ctxs])
+    ctxs[0].check(ctxs[0].L.grmhd_theta_ring_fix(hs, len(ctxs), st, None if nsweeps is None else _dev_ptr(nsweeps)))
 
 
 def stage_bc(ctx: Context, st: int):

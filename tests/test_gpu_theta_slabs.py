@@ -1,12 +1,14 @@
 """The theta-slab decomposition through the C ABI (grmhd_stage_update,
 grmhd_fail_count, grmhd_fix_sweep, grmhd_fix_end, grmhd_stage_bc,
-grmhd_x2_pack / unpack) on one GPU: R slab contexts exchanging their X2
-ghost rows, and before every fixup sweep the edge rows a sweep reads across a
-slab face, reproduce the undecomposed GPU step bit for bit in FP64 and in the
-mixed path; the slab state stays within the per-step parity bound of the
-undecomposed oracle.  A block of zones made to fail (negative conserved
-density) straddles a slab face, so the fixups of Eq. 33 run several sweeps
-across it in both stages."""
+grmhd_x2_pack / unpack, and grmhd_theta_ring_fix, the same fixup loop on the
+device) on one GPU: R slab contexts exchanging their X2 ghost rows, and
+before every fixup sweep the edge rows a sweep reads across a slab face,
+reproduce the undecomposed GPU step bit for bit in FP64 and in the mixed
+path, with the fixup loop run from the host or on the device, stepped kernel
+by kernel or replayed from a CUDA graph; the slab state stays within the
+per-step parity bound of the undecomposed oracle.  A block of zones made to
+fail (negative conserved density) straddles a slab face, so the fixups of
+Eq. 33 run several sweeps across it in both stages."""
 import numpy as np
 import pytest
 
@@ -52,19 +54,23 @@ def _ring_state(ring):
     return P, U, parts[0][2], parts[0][3]
 
 
-@pytest.mark.parametrize("precision,R,riemann", [(0, 2, 0), (0, 3, 0), (0, 4, 0), (1, 2, 0), (1, 4, 0), (1, 3, 1)])
-def test_theta_ring_equals_the_undecomposed_step(precision, R, riemann):
+@pytest.mark.parametrize("precision,R,riemann,device_fix,graph",
+                         [(0, 2, 0, True, True), (0, 3, 0, True, True), (0, 4, 0, True, True),
+                          (1, 2, 0, True, True), (1, 4, 0, True, True), (1, 3, 1, True, True),
+                          (0, 4, 0, False, False), (1, 3, 1, False, False), (0, 3, 0, True, False)])
+def test_theta_ring_equals_the_undecomposed_step(precision, R, riemann, device_fix, graph):
     G = gpu_mod()
     from paper_2205_02484_gb300.decomp import ThetaRing
     grid, phys, full, (P0, U0, t0, dt0) = _start(G, precision, R, riemann=riemann)
-    ring = ThetaRing.create(grid, phys, R, A)
+    ring = ThetaRing.create(grid, phys, R, A, device_fix=device_fix)
+    assert ring.device_fix == device_fix
     ring.set_state(P0, U0, t0, dt0)
     nsteps = 4
     G.step(full, 1)
-    ring.step(1)
+    ring.step(1, graph=graph)
     assert ring.sweeps[0] >= 2 and ring.sweeps[1] >= 2  # the block, across the face, both stages
     G.step(full, nsteps - 1)
-    ring.step(nsteps - 1)
+    ring.step(nsteps - 1, graph=graph)
     Pf, Uf, tf, dtf = G.get_state(full)
     Pr, Ur, tr, dtr = _ring_state(ring)
     assert tr == tf and dtr == dtf
@@ -121,8 +127,8 @@ def test_theta_slabs_of_a_3d_grid():
     full.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_periodic_flat_box_theta_slabs(precision):
+@pytest.mark.parametrize("precision,device_fix", [(0, True), (1, True), (0, False)])
+def test_periodic_flat_box_theta_slabs(precision, device_fix):
     """A flat periodic box split in X2: the first and last slabs are
     neighbours, and a failed block across the periodic edge is fixed from
     both sides."""
@@ -153,7 +159,7 @@ def test_periodic_flat_box_theta_slabs(precision):
     U = _spoil(U, [n2 - 2, n2 - 1, 0, 1], range(4, 8))
     dt = 2e-3
     G.set_state(full, P, U, 0.0, dt)
-    ring = ThetaRing.create(grid, phys, 2, 0.0, periodic=True)
+    ring = ThetaRing.create(grid, phys, 2, 0.0, periodic=True, device_fix=device_fix)
     ring.set_state(P, U, 0.0, dt)
     G.step(full, 3)
     ring.step(3)
@@ -216,6 +222,55 @@ def test_theta_pack_unpack_rows_and_errors():
     with pytest.raises(G.GrmhdError):
         G.x2_pack(whole, 0, 0, 0, buf)
     whole.close()
+    ring.close()
+
+
+def test_graph_replay_after_set_state():
+    """A state set after the ring's graph was captured is the one replayed:
+    the same steps from the same start give the same bits and sweep counts."""
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import ThetaRing
+    grid, phys, full, state = _start(G, 1, 4)
+    full.close()
+    ring = ThetaRing.create(grid, phys, 4, A)
+    ring.set_state(*state)
+    ring.step(2)
+    P1, U1, t1, dt1 = _ring_state(ring)
+    sw1 = ring.sweeps
+    ring.set_state(*state)
+    ring.step(2)
+    P2, U2, t2, dt2 = _ring_state(ring)
+    assert (t1, dt1) == (t2, dt2) and ring.sweeps == sw1
+    assert np.array_equal(P1, P2) and np.array_equal(U1, U2)
+    ring.close()
+
+
+def test_ring_fix_refusals():
+    """grmhd_theta_ring_fix takes the slabs of one grid, in theta order,
+    covering every row, on one stream; a refusal launches nothing."""
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import ThetaRing
+    grid, phys, full, state = _start(G, 0, 4)
+    full.close()
+    ring = ThetaRing.create(grid, phys, 4, A)
+    ring.set_state(*state)
+    c = [e.ctx for e in ring.e]
+    nsw = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for bad in (c[1:], c[:3], [c[0], c[2], c[1], c[3]], [c[0], c[0], c[2], c[3]]):
+        with pytest.raises(G.GrmhdError) as e:
+            G.theta_ring_fix(bad, 0, nsw)
+        assert e.value.code == G.EINVAL
+    with pytest.raises(G.GrmhdError):
+        G.theta_ring_fix(c, 2, nsw)
+    other = ThetaRing.create(grid, phys, 4, A)     # its own stream
+    other.set_state(*state)
+    with pytest.raises(G.GrmhdError):
+        G.theta_ring_fix([c[0], c[1], other.e[2].ctx, c[3]], 0, nsw)
+    with pytest.raises(ValueError):
+        G.theta_ring_fix(c, 0, torch.zeros(1, dtype=torch.int64, device="cuda"))
+    G.theta_ring_fix(c, 0, nsw)                    # nothing failed before a stage: no sweep
+    assert int(nsw.cpu()[0]) == 0
+    other.close()
     ring.close()
 
 
