@@ -242,10 +242,16 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp)
 // (a_0 + a_1)/2 - (d_1 - d_0)/6 from the MC-limited slopes, then each zone's
 // parabola (a_L, a, a_R) made monotone -- flat at a local extremum, else the
 // far edge moved to 3 a - 2 (near edge) where the parabola would overshoot.
+// x / 6: a correctly rounded division in FP64; in FP32 (the mixed path's
+// faces) a product with the rounded 1/6, within an ulp of it and without
+// the division's instruction sequence (three per variable and zone)
+__device__ __forceinline__ double sixth(double x) { return x / 6.0; }
+__device__ __forceinline__ float sixth(float x) { return x * (1.0f / 6.0f); }
+
 template <typename R>
 __device__ __forceinline__ R ppm_interface_s(R a0, R a1, R d0, R d1)
 {
-    return R(0.5) * (a0 + a1) - (d1 - d0) / R(6);
+    return R(0.5) * (a0 + a1) - sixth(d1 - d0);
 }
 
 template <typename R>
@@ -262,8 +268,9 @@ __device__ __forceinline__ void ppm_monotone(R a, R &L, R &Rt)
         Rt = a;
     } else {
         const R d = Rt - L, m = a - R(0.5) * (L + Rt);
-        if (d * m > d * d / R(6)) L = R(3) * a - R(2) * Rt;
-        else if (-d * d / R(6) > d * m) Rt = R(3) * a - R(2) * L;
+        const R d26 = sixth(d * d);
+        if (d * m > d26) L = R(3) * a - R(2) * Rt;
+        else if (-d26 > d * m) Rt = R(3) * a - R(2) * L;
     }
 }
 

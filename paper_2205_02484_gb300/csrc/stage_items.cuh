@@ -269,7 +269,7 @@ __device__ __forceinline__ void face_flux(const Grid &g, const Geo<R> &geo, cons
     cw = fmax(cmax, cmin);
     R wlF, wlU, wrF, wrU;
     if (g.riemann == 1 && cmax + cmin > R(0)) {
-        R inv = R(1) / (cmax + cmin);
+        R inv = divr(R(1), cmax + cmin);
         wlF = cmax * inv;
         wrF = cmin * inv;
         wlU = cmax * cmin * inv;
