@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # UPDATE_SOURCES_SHA (else the bench reports traffic null)
 UPDATE_DRAM_BYTES_PER_ZONE = 257.5
 UPDATE_SOURCES = ("stage_items.cuh", "con2prim.cuh", "fixes.cuh", "physics.cuh", "common.cuh", "step.cu")
-UPDATE_SOURCES_SHA = "c49131a147c9de6b"
+UPDATE_SOURCES_SHA = "5786ed57bad265d1"
 
 
 def update_sources_sha():

@@ -5,7 +5,8 @@ columns, X3 row warps with a ragged last segment), on sampled outputs the
 oracle computes one at a time:
   * Riemann fluxes of 6000 sampled faces against the oracle's single-face
     flux from the same four zone states (the oracle's (r, theta) metric
-    records of a 256 x 256 grid: the metric does not depend on phi);
+    records of a 256 x 256 grid: the metric does not depend on phi); with
+    PPM faces (the bench's PPM step) from the same six zone states;
   * the inversion at 20000 sampled zones: the oracle's con2prim of the GPU's
     conserved variables, started from the GPU's primitives, returns them;
   * a property that holds at any size: the corner divergence of B (Eq. 24)
@@ -28,8 +29,8 @@ A, GAM, R_OUT = 0.9375, 4.0 / 3.0, 1000.0
 NOT_B = [0, 1, 2, 3, 4, 8]
 
 
-def _bench_torus(G, precision, steps):
-    gp = G.default_grid(N, N, N, a=A, r_out=R_OUT, precision=precision)
+def _bench_torus(G, precision, steps, recon=0):
+    gp = G.default_grid(N, N, N, a=A, r_out=R_OUT, precision=precision, recon=recon)
     ctx = G.init_grid(gp, G.default_phys(gam=GAM))
     G.set_metric(ctx, A, G.KERR_MKS)
     G.init_torus(ctx, r_in=6.0, r_max=12.0, beta0=100.0, pert_amp=0.04, seed=3)
@@ -38,18 +39,18 @@ def _bench_torus(G, precision, steps):
     return ctx
 
 
-def _oracle_records():
-    return O.Grid(O.default_params(n1=N, n2=N, n3=1, a=A, r_out=R_OUT, gam=GAM))
+def _oracle_records(recon=0):
+    return O.Grid(O.default_params(n1=N, n2=N, n3=1, a=A, r_out=R_OUT, gam=GAM, recon=recon))
 
 
-def _sample_faces(rng, d, n):
-    """face indices (i, j, k) of direction d whose four-zone stencil lies in
-    the active zones (X3 wraps periodically), with the ends of the ranges
-    always included"""
+def _sample_faces(rng, d, n, w=2):
+    """face indices (i, j, k) of direction d whose stencil of 2 w zones
+    (w = 2: PLM, 3: PPM) lies in the active zones (X3 wraps periodically),
+    with the ends of the ranges always included"""
     lo = [0, 0, 0]
     hi = [N - 1, N - 1, N - 1]
     if d < 2:
-        lo[d], hi[d] = 2, N - 2
+        lo[d], hi[d] = w, N - w
     else:
         hi[2] = N  # faces 0 .. n3, stencils wrap in phi
     idx = np.stack([rng.integers(lo[e], hi[e] + 1, n) for e in range(3)], axis=1)
@@ -66,32 +67,33 @@ def _loc(faces, d, o):
     return (z[:, 0] * N + z[:, 1]).astype(np.int32)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_fullsize_face_fluxes(precision):
+@pytest.mark.parametrize("precision,recon", [(0, O.PLM), (1, O.PLM), (0, O.PPM), (1, O.PPM)])
+def test_fullsize_face_fluxes(precision, recon):
     G = gpu_mod()
-    ctx = _bench_torus(G, precision, 3)
+    w = 3 if recon == O.PPM else 2
+    ctx = _bench_torus(G, precision, 3, recon)
     Pd = torch.empty((8, N, N, N), dtype=torch.float64, device="cuda")
     Ud = torch.empty((9, N, N, N), dtype=torch.float64, device="cuda")
     G.get_state(ctx, Pd, Ud)
     del Ud
     Fd = torch.zeros((3, 9, N + 1, N + 1, N + 1), dtype=torch.float64, device="cuda")
     G.fluxes(ctx, Fd)
-    og = _oracle_records()
+    og = _oracle_records(recon)
     rng = np.random.default_rng(20260)
     for d in range(3):
-        faces = _sample_faces(rng, d, 2000)
+        faces = _sample_faces(rng, d, 2000, w)
         fi = torch.as_tensor(faces, device="cuda")
         Fg = Fd[d][:, fi[:, 0], fi[:, 1], fi[:, 2]].cpu().numpy().T  # (n, 9)
         # the zone states of every stencil, gathered on the device
         sten = []
-        for o in (-2, -1, 0, 1):
+        for o in range(-w, w):
             z = faces.copy()
             z[:, d] += o
             if d == 2:
                 z[:, 2] %= N
             zt = torch.as_tensor(z, device="cuda")
             sten.append(Pd[:, zt[:, 0], zt[:, 1], zt[:, 2]].cpu().numpy().T)  # (n, 8)
-        sten = np.stack(sten, axis=1)  # (n, 4, 8)
+        sten = np.stack(sten, axis=1)  # (n, 2 w, 8)
         Fo, cw = [], []
         for m, f in enumerate(faces):
             F1, c1 = og.face_flux_at(d, f[0], f[1], sten[m])
@@ -104,8 +106,8 @@ def test_fullsize_face_fluxes(precision):
             # FP32 error of a face is eps_32 x (|F| + c_w |U|) times the depth of
             # the dependent arithmetic; U of the two zones next to the face (the
             # oracle's conserved variables at their centres) sets the scale
-            Ul = og.prim2cons(np.ascontiguousarray(sten[:, 1].T), _loc(faces, d, -1))
-            Ur = og.prim2cons(np.ascontiguousarray(sten[:, 2].T), _loc(faces, d, 0))
+            Ul = og.prim2cons(np.ascontiguousarray(sten[:, w - 1].T), _loc(faces, d, -1))
+            Ur = og.prim2cons(np.ascontiguousarray(sten[:, w].T), _loc(faces, d, 0))
             Ul[1] += Ul[0]
             Ur[1] += Ur[0]
             # (max-norm over the samples: where a component cancels to ~0, e.g.
