@@ -62,11 +62,20 @@ template <typename R>
 __device__ __forceinline__ void get_state(const R q[NP], const Geo<R> &g, St<R> &s)
 {
     R usq = spatial_sq(g, q[KU1], q[KU2], q[KU3]);
-    R gm = sqrtr(R(1) + usq);
+    R gm, iut; // Gamma and 1 / u^t = alpha / Gamma
+    if constexpr (sizeof(R) == 8) {
+        // FP64: both from one reciprocal square root (a division and a square
+        // root are each an FP64 instruction sequence), to an ulp or two
+        const R ig = rsqrt(R(1) + usq);
+        gm = (R(1) + usq) * ig;
+        iut = g.alpha * ig;
+    } else {
+        gm = sqrtr(R(1) + usq);
+        iut = divr(g.alpha, gm);
+    }
     s.usq = usq;
     s.gamma = gm;
     s.ucon[0] = gm * g.ialpha;
-    const R iut = divr(g.alpha, gm); // 1 / u^t
 #pragma unroll
     for (int i = 1; i <= 3; i++) s.ucon[i] = q[KU1 + i - 1] - gm * g.alpha * g.gcon[sym(0, i)];
     lower4(g, s.ucon, s.ucov);
@@ -235,6 +244,30 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp)
     if (fabs(dm) < fabs(dp) && R(2) * fabs(dm) < R(0.5) * fabs(dc)) return R(2) * dm;
     if (R(2) * fabs(dp) < R(0.5) * fabs(dc)) return R(2) * dp;
     return R(0.5) * dc;
+}
+
+// The same slope in FP64 with its three decisions taken on the bit patterns
+// of the differences (integer operations: GB300 runs FP64 multiplies and
+// compares at the FP64 rate, 1/64 of FP32's).  For finite differences whose
+// magnitudes are zero or at least 2^-1020 (so that doubling and halving them
+// is exact) they are the comparisons above:
+// dm dp < 0 is opposite sign bits with both nonzero; |x| < |y| orders the
+// magnitudes' bit patterns as unsigned integers; 2|x| < |dc|/2 is 4|x| < |dc|,
+// the magnitude with its exponent raised by 2.  The values returned are the
+// same products.
+template <>
+__device__ __forceinline__ double mc_slope<double>(double qm, double q0, double qp)
+{
+    const double dm = q0 - qm, dp = qp - q0, dc = qp - qm;
+    const unsigned long long mag = 0x7fffffffffffffffULL, four = 2ULL << 52;
+    const unsigned long long bm = (unsigned long long)__double_as_longlong(dm);
+    const unsigned long long bp = (unsigned long long)__double_as_longlong(dp);
+    const unsigned long long am = bm & mag, ap = bp & mag;
+    const unsigned long long ac = (unsigned long long)__double_as_longlong(dc) & mag;
+    if (((bm ^ bp) >> 63) && am != 0 && ap != 0) return 0.0;
+    if (am < ap && am + four < ac) return 2.0 * dm;
+    if (ap + four < ac) return 2.0 * dp;
+    return 0.5 * dc;
 }
 
 // Piecewise parabolic faces (Colella & Woodward 1984 on uniform code-coordinate
