@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (D < 3 ? 4 : 5) : 1) k_f
 }
 
 // PPM faces: X1 / X2 as columns (col_box), X3 as row warps where rows are
-// long in the mixed path (x3_warp_box), else one face per thread (flux_box)
+// long (x3_warp_box), else one face per thread (flux_box)
 template <typename R, int D>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux_ppm(Grid g, const R *__restrict__ P,
                                                                           R *__restrict__ F, Box box, int want_dt)
@@ -61,11 +61,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux_ppm(Grid g
     R cw;
     if constexpr (D < 3) {
         cw = flux_column_ppm<R, D>(g, P, F, box, want_dt, t);
-    } else if constexpr (sizeof(R) == 4) {
+    } else {
         if (g.x3warp) cw = flux_x3_warp_ppm<R>(g, P, F, box, want_dt, t);
         else cw = flux_item_ppm<R, D>(g, P, F, box, want_dt, t);
-    } else {
-        cw = flux_item_ppm<R, D>(g, P, F, box, want_dt, t);
     }
     if (want_dt) block_cfl_into(&g.dtmin[D - 1], cw, g.cfl * g.dx[D - 1]);
 }
@@ -129,8 +127,7 @@ static void stage_part(const Grid &g, int part, int src, int dst, double dtfac, 
     Box b1 = flux_elem_box(g, 1), b2 = flux_elem_box(g, 2), be = edge_box(g);
     Box b3 = g.x3warp ? x3_warp_box(g) : flux_elem_box(g, 3);
     if (g.recon && part < 3) { // PPM faces: columns, row warps or single faces as for PLM
-        const Box bp = part < 2 ? col_box(g, part + 1)
-                                : ((sizeof(R) == 4 && g.x3warp) ? x3_warp_box(g) : flux_box(g, 3));
+        const Box bp = part < 2 ? col_box(g, part + 1) : (g.x3warp ? x3_warp_box(g) : flux_box(g, 3));
         const unsigned nb = nblk(bp.count(), T);
         if (part == 0) k_flux_ppm<R, 1><<<nb, T, 0, s>>>(g, Pin, (R *)g.F[0], bp, want_dt);
         else if (part == 1) k_flux_ppm<R, 2><<<nb, T, 0, s>>>(g, Pin, (R *)g.F[1], bp, want_dt);

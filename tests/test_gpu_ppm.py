@@ -130,8 +130,8 @@ def test_ensemble_refuses_a_ppm_member():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_ppm_columns_and_row_warps_96cubed(precision):
-    """At 96^3 the X1 / X2 sweeps walk columns of 4 faces and the mixed X3
-    sweep runs one warp per row: face fluxes and one step against the
+    """At 96^3 the X1 / X2 sweeps walk columns of 4 faces and the X3 sweep
+    runs one warp per row (both paths): face fluxes and one step against the
     oracle (FP64: 1e-13 of the LLF scale per face, 1e-10 per field after
     the step, u of the cold atmosphere at r_out = 1000 M measured against
     rho + u, the precision its inversion from E - D gives it; mixed: the
