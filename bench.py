@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # UPDATE_SOURCES_SHA (else the bench reports traffic null)
 UPDATE_DRAM_BYTES_PER_ZONE = 257.4
 UPDATE_SOURCES = ("stage_items.cuh", "con2prim.cuh", "fixes.cuh", "physics.cuh", "common.cuh", "step.cu")
-UPDATE_SOURCES_SHA = "19ebe4dd228c5047"
+UPDATE_SOURCES_SHA = "1ceef2a96dada0df"
 
 
 def update_sources_sha():
