@@ -19,9 +19,9 @@ MEMBERS = [  # (n1, n2, n3, spin, gamma, beta0, seed)
 ]
 
 
-def _member(G, torch, spec, precision):
+def _member(G, torch, spec, precision, **kw):
     n1, n2, n3, a, gam, b0, seed = spec
-    gp = G.default_grid(n1, n2, n3, a=a, r_out=60.0, precision=precision)
+    gp = G.default_grid(n1, n2, n3, a=a, r_out=60.0, precision=precision, **kw)
     gp.stream = torch.cuda.current_stream().cuda_stream
     ctx = G.init_grid(gp, G.default_phys(gam=gam))
     G.set_metric(ctx, a, G.KERR_MKS)
@@ -56,6 +56,30 @@ def test_members_evolve_as_alone(precision):
         da, db = G.diagnostics(a), G.diagnostics(b)
         for k in ("n_nr", "nr_iters", "n_floor", "n_fail", "n_steps"):
             assert da[k] == db[k], k
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cylindrified_and_hll_members_evolve_as_alone(precision):
+    """Members with the polar cylindrification (their band rows' metric) and
+    one with the HLL flux, batched beside plain ones, step bit for bit as
+    alone."""
+    torch = pytest.importorskip("torch")
+    G = gpu_mod()
+    kws = [dict(cyl_r=1.8, cyl_dx2=0.3), dict(riemann=G.HLL), dict(cyl_r=1.6, cyl_dx2=0.25, riemann=G.HLL), {}]
+    specs = MEMBERS[:4]
+    mem = [_member(G, torch, s, precision, **k) for s, k in zip(specs, kws)]
+    solo = [_member(G, torch, s, precision, **k) for s, k in zip(specs, kws)]
+    ens = G.ensemble_create(mem)
+    G.ensemble_step(ens, 3)
+    G.ensemble_sync(ens)
+    for c in solo:
+        G.step(c, 3)
+    for a, b in zip(mem, solo):
+        Pa, Ua, ta, dta = G.get_state(a)
+        Pb, Ub, tb, dtb = G.get_state(b)
+        assert np.array_equal(Pa, Pb) and np.array_equal(Ua, Ub)
+        assert ta == tb and dta == dtb
     ens.close()
 
 
