@@ -32,8 +32,8 @@ def _spoil(U, rows, cols):
     return U
 
 
-def _torus_start(n3=1, R=2):
-    g = O.Grid(_base(n3))
+def _torus_start(n3=1, R=2, **kw):
+    g = O.Grid(_base(n3, **kw))
     g.init_torus(pert_amp=0.04, seed=5)
     P0, U0, t0, dt0 = g.get_state()
     b = 24 // R  # the first inner slab face
@@ -56,6 +56,23 @@ def _check_combined(dr, df, exact_sweeps=True):
     if exact_sweeps:
         assert dr["fix_sweeps"] == df["fix_sweeps"]
     assert dr["divb_max"] <= df["divb_max"]
+
+
+def test_theta_slabs_with_ppm_and_cylindrification():
+    """PPM faces (six-zone stencils: all NG = 3 exchanged rows read) on a
+    cylindrified grid (each slab's band rows built from their global X2),
+    with the failed block across the slab face: bit for bit."""
+    kw = dict(recon=O.PPM, cyl_r=1.8, cyl_dx2=0.3)
+    state = _torus_start(1, 3, **kw)
+    ref = _undecomposed(_base(**kw), state, 2)
+    slabs = S.make_theta_slabs(_base(**kw), *state, 3)
+    for _ in range(2):
+        assert S.step_theta_slabs(slabs)[0] == 0
+    P, U, t, dt = S.gather_theta(slabs)
+    Pr, Ur, tr, dtr = ref.get_state()
+    assert (t, dt) == (tr, dtr)
+    assert np.array_equal(P, Pr) and np.array_equal(U, Ur)
+    assert ref.diagnostics()["n_fixed"] > 0
 
 
 @pytest.mark.parametrize("R", [2, 3, 4])
