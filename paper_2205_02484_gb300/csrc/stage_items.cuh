@@ -156,6 +156,22 @@ __device__ inline void zero_radial_velocity(const Geo<double> &geo, double q[NP]
     q[KU1] = gm * c;
 }
 
+// Mixed path: whether the radial ghost (id, j) of side `side` flows into the
+// grid, from the FP32 state of the stored primitives of its source zone zs
+// on the FP32 record (out of line, so that the single-grid and ensemble
+// kernels take the same decision).
+static __device__ __noinline__ bool ghost_inflow_f(const Grid &g, const float *P, long long zs, int id, int j,
+                                                   int side)
+{
+    float qf[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) qf[c] = P[c * g.nz + zs];
+    const Geo<float> gf = g.gcF[midx(g, id, j)];
+    St<float> sf;
+    get_state(qf, gf, sf);
+    return (side == 0 && sf.ucon[1] > 0.0f) || (side == 1 && sf.ucon[1] < 0.0f);
+}
+
 template <typename RS>
 __device__ inline void bc1_item(const Grid &g, RS *P, long long t)
 {
@@ -171,7 +187,15 @@ __device__ inline void bc1_item(const Grid &g, RS *P, long long t)
     if (bc == BC_PERIODIC) is = wrapi(id, g.n1);
     else is = side == 0 ? 0 : g.n1 - 1;
     long long zs = zidx(g, is, j, k), zd = zidx(g, id, j, k);
-    if (bc != BC_INFLOW) {
+    bool copy = bc != BC_INFLOW;
+    if constexpr (sizeof(RS) == 4) {
+        // mixed path: the sign of u^r from the FP32 state of the stored
+        // primitives on the FP32 record (the FP64 correction only where the
+        // ghost flows into the grid; a sign within FP32 rounding of zero
+        // moves u^r by that rounding either way)
+        if (!copy) copy = !ghost_inflow_f(g, (const float *)P, zs, id, j, side);
+    }
+    if (copy) {
 #pragma unroll
         for (int c = 0; c < NP; c++) P[c * g.nz + zd] = P[c * g.nz + zs];
         return;
@@ -180,9 +204,13 @@ __device__ inline void bc1_item(const Grid &g, RS *P, long long t)
 #pragma unroll
     for (int c = 0; c < NP; c++) q[c] = (double)P[c * g.nz + zs];
     Geo<double> geo = g.gc[midx(g, id, j)];
-    St<double> s;
-    get_state(q, geo, s);
-    if ((side == 0 && s.ucon[1] > 0.0) || (side == 1 && s.ucon[1] < 0.0)) zero_radial_velocity(geo, q);
+    if constexpr (sizeof(RS) == 4) {
+        zero_radial_velocity(geo, q);
+    } else {
+        St<double> s;
+        get_state(q, geo, s);
+        if ((side == 0 && s.ucon[1] > 0.0) || (side == 1 && s.ucon[1] < 0.0)) zero_radial_velocity(geo, q);
+    }
 #pragma unroll
     for (int c = 0; c < NP; c++) P[c * g.nz + zd] = (RS)q[c];
 }
