@@ -476,6 +476,28 @@ def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
         best = ms if best is None else min(best, ms)
     fl = flags.cpu().numpy()
     it = iters.cpu().numpy()
+    # the Newton branch alone, the inversions the torus step runs: the draws
+    # that took it above, inverted again as one batch from the same guesses
+    idx = torch.nonzero(flags == 0).squeeze(1)
+    m = int(idx.numel())
+    Un, ln, gn = U[:, idx].contiguous(), loc[idx].contiguous(), g0[:, idx].contiguous()
+    fl2 = torch.zeros(m, dtype=torch.int32, device=P.device)
+    it2 = torch.zeros(m, dtype=torch.int32, device=P.device)
+    G.con2prim(ctx, Un, ln, gn.clone(), fl2, it2)
+    best2 = None
+    for _ in range(3):
+        work = gn.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.con2prim(ctx, Un, ln, work, fl2, it2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1)
+        best2 = ms2 if best2 is None else min(best2, ms2)
+    f2 = fl2.cpu().numpy()
+    i2 = it2.cpu().numpy()
     ctx.close()
     out = {"workload": f"{n} inversions (FP64 path), states of the seeded sample distribution at the 256x192 "
                        f"grid's metric, guess = exact primitives x (1 + {rel} U[-1,1])",
@@ -492,6 +514,13 @@ def run_con2prim(G, torch, stream, device, n=1_000_000, rel=1e-4):
                 "tflops_fp64_algorithmic": tf, "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS,
                 "fp64_peak_tflops": FP64_PEAK_TFLOPS,
                 "flops_source": "oracle operation counter (oracle/opcount.cpp), Newton inversions only"})
+    flops2 = float(((C2P_FIXED_FLOPS + C2P_BETA_FLOPS) + C2P_NEWTON_FLOPS * i2[f2 == 0]).sum())
+    tf2 = flops2 / (best2 * 1e-3) / 1e12
+    out["newton_branch"] = {
+        "workload": f"the {m} draws above that Newton inverts, as one batch from the same guesses",
+        "ms": best2, "inversions_per_s": m / (best2 * 1e-3), "all_newton": bool((f2 == 0).all()),
+        "newton_iters_mean": float(i2[f2 == 0].mean()) if m else 0.0,
+        "tflops_fp64_algorithmic": tf2, "frac_of_fp64_peak": tf2 / FP64_PEAK_TFLOPS}
     return out
 
 

@@ -237,7 +237,11 @@ int grmhd_step(grmhd_ctx *ctx, int nsteps);
  * it does not converge, from the MLP's W before Brent (the step's order, see
  * grmhd_set_learned_guess; such zones are flagged GRMHD_C2P_NR |
  * GRMHD_C2P_LEARNED).  iters counts every Newton run.  Same method order
- * and tolerances as the step otherwise (Section 2.3). */
+ * and tolerances as the step otherwise (Section 2.3).  The zones that leave
+ * Newton (Brent, the entropy inversion) finish in a second pass over a
+ * compacted list, with the same results; n < 2^31 - 1 (GRMHD_EINVAL
+ * otherwise); the context keeps n + 1 ints of device scratch for the list,
+ * allocated on the first call that needs more. */
 int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, double *P_inout,
                    int *flags, int *iters, long n, int use_learned_guess, int on_device);
 

@@ -5,6 +5,7 @@
 // first grmhd_step call and replayed afterwards; the time step lives on the
 // device, so replays need no host round trip.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,6 +36,8 @@ struct grmhd_ctx {
     long long scratch_len = 0;
     double *staging = nullptr;
     long long staging_len = 0;
+    int *c2p_list = nullptr; // the stand-alone inversion's deferred zones (count, then indices)
+    long long c2p_list_len = 0;
     unsigned char *intorus = nullptr;
     double *hpin = nullptr; // pinned host scratch (64 doubles)
     double disk_mass = 0.0, disk_eb = 0.0;
@@ -749,6 +752,7 @@ extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, d
     if (!ctx || (n > 0 && (!P || !loc || !U || !flags))) return fail(ctx, GRMHD_EINVAL, "null argument");
     if (!ctx->metric_set) return fail(ctx, GRMHD_ESTATE, "needs grmhd_set_metric first");
     if (n < 0) return fail(ctx, GRMHD_EINVAL, "n < 0");
+    if (n >= INT_MAX) return fail(ctx, GRMHD_EINVAL, "n must be below 2^31 - 1");
     if (use_learned_guess < 0 || use_learned_guess > 2) return fail(ctx, GRMHD_EINVAL, "use_learned_guess must be 0, 1 or 2");
     if (use_learned_guess && !ctx->mlp_loaded) return fail(ctx, GRMHD_ESTATE, "no MLP loaded");
     if (n == 0) return 0;
@@ -767,9 +771,15 @@ extern "C" int grmhd_con2prim(grmhd_ctx *ctx, const double *U, const int *loc, d
         CK(cudaMemcpyAsync(sl, loc, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
         Ud = su; Pd = sp; ld = sl; fd = sf; id = iters ? si : nullptr;
     }
+    if (ctx->c2p_list_len < n + 1) {
+        int *p;
+        if (int rc = dalloc(ctx, &p, (size_t)n + 1)) return rc;
+        ctx->c2p_list = p;
+        ctx->c2p_list_len = n + 1;
+    }
     (void)cudaGetLastError();
     launch_con2prim(ctx->g, Ud, ld, Pd, fd, id, n, use_learned_guess ? ctx->mlp : nullptr, use_learned_guess,
-                    ctx->stream);
+                    ctx->c2p_list, ctx->stream);
     CK(cudaGetLastError());
     if (!on_device) {
         CK(cudaMemcpyAsync(P, Pd, 8LL * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

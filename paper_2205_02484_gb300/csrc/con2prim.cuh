@@ -28,6 +28,13 @@ namespace grmhd {
 constexpr int C2P_NR = 0, C2P_BRENT_W = 1, C2P_ENTROPY = 2, C2P_ENTROPY_BETA = 3;
 constexpr int C2P_FAIL = 8, C2P_FAIL_D = 16, C2P_FAIL_ENT = 32;
 constexpr int C2P_LEARNED = 64; // with C2P_NR: Newton converged from the learned start
+// internal: a first pass (pass = 1) stops where the chain would leave Newton
+// and returns C2P_DEFER with the step to resume at (pass = 2, resume = that
+// value): the entropy inversion of a low-beta zone, the entropy inversion
+// after an unphysical Newton root (P then holds that root's primitives, as
+// the whole chain leaves them), or Brent in W followed by the entropy
+// inversion
+constexpr int C2P_DEFER = 256, C2P_DEFER_BETA = 512, C2P_DEFER_ENT = 1024, C2P_DEFER_TAIL = 2048;
 constexpr double V2MAX = 1.0 - 1.0e-16;
 
 struct C2PIn {
@@ -482,7 +489,8 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
                                const double *guess, const float *guessf, const C2PPar &par, int methods,
                                double P[NP], int &iters, const float *mlp_first = nullptr,
                                const Geo<float> *gf = nullptr, const float *startf = nullptr,
-                               bool have_start = false, const float *mlp_rescue = nullptr, double w_first = 0.0)
+                               bool have_start = false, const float *mlp_rescue = nullptr, double w_first = 0.0,
+                               int pass = 0, int resume = 0)
 {
     iters = 0;
     if (!MIXED) {
@@ -536,6 +544,16 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
     bool fin = finite64(c.D) && finite64(c.Qtsq) && finite64(c.nQ) && finite64(c.Bsq);
     // a finite D is > 0 exactly when its signed bit pattern is (integer test)
     if (!fin || __double_as_longlong(c.D) <= 0) return fail(C2P_FAIL | C2P_FAIL_D);
+    if (!MIXED && pass == 2) {
+        // the rest of the chain from the step a first pass deferred
+        if (resume & C2P_DEFER_TAIL) {
+            if ((methods & 2) && c2p_brent_w(c, par.brent_maxit, P)) return C2P_BRENT_W;
+            if ((methods & 4) && entropy()) return C2P_ENTROPY;
+            return fail(C2P_FAIL | C2P_FAIL_ENT);
+        }
+        if (entropy()) return (resume & C2P_DEFER_BETA) ? C2P_ENTROPY_BETA : C2P_ENTROPY;
+        return fail(C2P_FAIL | C2P_FAIL_ENT);
+    }
 
     if (methods & 8) {
         bool low_beta;
@@ -551,7 +569,10 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
             low_beta = s.bsq > 0.0 && pg < par.beta_ent * 0.5 * s.bsq;
         }
         if (low_beta) {
-            if ((methods & 4) && entropy()) return C2P_ENTROPY_BETA;
+            if (methods & 4) {
+                if (!MIXED && pass == 1) return C2P_DEFER | C2P_DEFER_BETA;
+                if (entropy()) return C2P_ENTROPY_BETA;
+            }
             return fail(C2P_FAIL | C2P_FAIL_ENT);
         }
     }
@@ -596,11 +617,15 @@ __device__ inline int con2prim(const double U[NU], const Geo<double> &g, const d
                 if (MIXED) c2p_recover_mixed(c, W, v2, par.ig, P);
                 else c2p_recover_w(c, W, v2, P);
                 if (c2p_physical(P, v2)) return a == 3 ? (C2P_NR | C2P_LEARNED) : C2P_NR;
-                if ((methods & 4) && entropy()) return C2P_ENTROPY;
+                if (methods & 4) {
+                    if (!MIXED && pass == 1) return C2P_DEFER | C2P_DEFER_ENT;
+                    if (entropy()) return C2P_ENTROPY;
+                }
                 return fail(C2P_FAIL | C2P_FAIL_ENT);
             }
         }
     }
+    if (!MIXED && pass == 1 && (methods & 6)) return C2P_DEFER | C2P_DEFER_TAIL;
     if ((methods & 2) && c2p_brent_w(c, par.brent_maxit, P)) return C2P_BRENT_W;
     if ((methods & 4) && entropy()) return C2P_ENTROPY;
     return fail(C2P_FAIL | C2P_FAIL_ENT);

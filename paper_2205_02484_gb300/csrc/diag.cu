@@ -265,8 +265,42 @@ __global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, 
 
 // mode 0: plain start from P; 1: the network's W first, then P; 2: P, then the
 // network's W as a rescue before Brent (the step's use)
-__global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                           long n, const float *mlp, int mode)
+// The stand-alone inversion runs in two passes so that the zones leaving
+// Newton (the low-beta entropy inversions, Brent in W, the entropy inversion
+// after an unphysical Newton root: loops of their own length) do not hold
+// the lanes of Newton zones: the first pass (pass 1 of con2prim) finishes
+// every zone Newton settles and appends the others to a compacted list; the
+// second resumes each listed zone at its deferred step, 32 such zones to a
+// warp.  The results are those of the whole chain in one pass.
+//
+// list: [0] the count, then the deferred indices.  On deferral the flag
+// holds the step to resume at, P the input primitives (after an unphysical
+// Newton root, that root's primitives, where the whole chain leaves them).
+__device__ __forceinline__ void c2p_defer(int *list, long t, bool defer)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, defer);
+    if (!defer) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(list, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    list[1 + base + __popc(m & ((1u << lane) - 1))] = (int)t;
+}
+
+__device__ __forceinline__ void c2p_store(const int fl, const double q[NP], double *P, int *flags, long n, long t,
+                                          int *list)
+{
+    flags[t] = fl;
+    const bool defer = (fl & C2P_DEFER) != 0;
+    if (!defer || (fl & C2P_DEFER_ENT)) {
+        for (int c = 0; c < (defer ? 5 : NP); c++) P[c * n + t] = q[c];
+    }
+    c2p_defer(list, t, defer);
+}
+
+__global__ void __launch_bounds__(128) k_con2prim(Grid g, const double *U, const int *loc, double *P, int *flags,
+                                                  int *iters, long n, const float *mlp, int mode, int *list)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -274,6 +308,7 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     if (l < 0 || l >= g.n1 * g.n2) {
         flags[t] = C2P_FAIL | C2P_FAIL_D;
         if (iters) iters[t] = 0;
+        c2p_defer(list, t, false);
         return;
     }
     const Geo<double> geo = g.gc[midx(g, l / g.n2, l % g.n2)];
@@ -281,9 +316,29 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
     for (int c = 0; c < NU; c++) Uz[c] = U[c * n + t];
     for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
     int it;
-    flags[t] = con2prim(Uz, geo, g.gsp + 6LL * midx(g, l / g.n2, l % g.n2), q0, nullptr, c2p_par(g), 15, q, it,
-                        mode == 1 ? mlp : nullptr, nullptr, nullptr, false, mode == 2 ? mlp : nullptr);
+    const int fl = con2prim(Uz, geo, g.gsp + 6LL * midx(g, l / g.n2, l % g.n2), q0, nullptr, c2p_par(g), 15, q,
+                            it, mode == 1 ? mlp : nullptr, nullptr, nullptr, false, mode == 2 ? mlp : nullptr, 0.0,
+                            1);
     if (iters) iters[t] = it;
+    c2p_store(fl, q, P, flags, n, t, list);
+}
+
+// the second pass: the listed zones resumed at their deferred steps
+__global__ void __launch_bounds__(128) k_con2prim_rest(Grid g, const double *U, const int *loc, double *P,
+                                                       int *flags, long n, const int *list)
+{
+    const long a = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (a >= list[0]) return;
+    const long t = list[1 + a];
+    const int l = loc[t];
+    const int m = midx(g, l / g.n2, l % g.n2);
+    const Geo<double> geo = g.gc[m];
+    double Uz[NU], q0[NP], q[NP];
+    for (int c = 0; c < NU; c++) Uz[c] = U[c * n + t];
+    for (int c = 0; c < NP; c++) q0[c] = P[c * n + t];
+    int it;
+    flags[t] = con2prim(Uz, geo, g.gsp + 6LL * m, q0, nullptr, c2p_par(g), 15, q, it, nullptr, nullptr, nullptr,
+                        false, nullptr, 0.0, 2, flags[t]);
     for (int c = 0; c < NP; c++) P[c * n + t] = q[c];
 }
 
@@ -292,7 +347,8 @@ __global__ void k_con2prim(Grid g, const double *U, const int *loc, double *P, i
 // state; lanes without a state (past n, bad loc, D not positive) take part
 // in the warp's inference with the feature means and invert nothing.
 __global__ void __launch_bounds__(128) k_con2prim_learned(Grid g, const double *U, const int *loc, double *P,
-                                                          int *flags, int *iters, long n, const float *mlp)
+                                                          int *flags, int *iters, long n, const float *mlp,
+                                                          int *list)
 {
     __shared__ MlpSmem s;
     mlp_stage(mlp, s);
@@ -319,15 +375,16 @@ __global__ void __launch_bounds__(128) k_con2prim_learned(Grid g, const double *
     if (!ok) {
         flags[t] = C2P_FAIL | C2P_FAIL_D;
         if (iters) iters[t] = 0;
+        c2p_defer(list, t, false);
         return;
     }
     double q0[NP], q[NP];
     for (int k = 0; k < NP; k++) q0[k] = P[k * n + t];
     int it;
-    flags[t] = con2prim(Uz, geo, gsp, q0, nullptr, c2p_par(g), 15, q, it, nullptr, nullptr, nullptr, false, nullptr,
-                        have ? c2p_w_of(c.D, y) : 0.0);
+    const int fl = con2prim(Uz, geo, gsp, q0, nullptr, c2p_par(g), 15, q, it, nullptr, nullptr, nullptr, false,
+                            nullptr, have ? c2p_w_of(c.D, y) : 0.0, 1);
     if (iters) iters[t] = it;
-    for (int k = 0; k < NP; k++) P[k * n + t] = q[k];
+    c2p_store(fl, q, P, flags, n, t, list);
 }
 
 void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U, long n, cudaStream_t s)
@@ -336,11 +393,14 @@ void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U,
 }
 
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                     long n, const float *mlp, int mode, cudaStream_t s)
+                     long n, const float *mlp, int mode, int *list, cudaStream_t s)
 {
     if (n <= 0) return;
-    if (mode == 1) k_con2prim_learned<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp);
-    else k_con2prim<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, mode);
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    cudaMemsetAsync(list, 0, sizeof(int), s);
+    if (mode == 1) k_con2prim_learned<<<nb, 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, list);
+    else k_con2prim<<<nb, 128, 0, s>>>(g, U, loc, P, flags, iters, n, mlp, mode, list);
+    k_con2prim_rest<<<nb, 128, 0, s>>>(g, U, loc, P, flags, n, list);
 }
 
 // ------------------------------------------------------------ state copies

@@ -58,8 +58,9 @@ void launch_torus(const Grid &g, const TorusArgs &ta, double *scratch, unsigned 
 
 // points.cu
 void launch_prim2cons(const Grid &g, const double *P, const int *loc, double *U, long n, cudaStream_t s);
+// list: n + 1 ints of device scratch (the deferred zones of the first pass)
 void launch_con2prim(const Grid &g, const double *U, const int *loc, double *P, int *flags, int *iters,
-                     long n, const float *mlp, int mode, cudaStream_t s);
+                     long n, const float *mlp, int mode, int *list, cudaStream_t s);
 
 // mlp.cu (learned Newton start)
 struct MlpHyper {
