@@ -270,6 +270,30 @@ def test_graph_replay_after_set_state():
     ring.close()
 
 
+def test_sixteen_slab_ring_and_the_limit():
+    """16 slabs of 4 rows (the most one ring kernel takes: their grid records
+    travel as one parameter block) equal the undecomposed step, failed block
+    included; 17 are refused by grmhd_theta_ring_fix."""
+    G = gpu_mod()
+    from paper_2205_02484_gb300.decomp import ThetaRing
+    grid, phys, full, state = _start(G, 0, 16, shape=(24, 64, 1))
+    ring = ThetaRing.create(grid, phys, 16, A)
+    ring.set_state(*state)
+    G.step(full, 2)
+    ring.step(2)
+    Pf, Uf, tf, dtf = G.get_state(full)
+    Pr, Ur, tr, dtr = _ring_state(ring)
+    assert (tr, dtr) == (tf, dtf)
+    assert np.array_equal(Pr, Pf) and np.array_equal(Ur, Uf)
+    assert G.diagnostics(full)["n_fixed"] > 0
+    nsw = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(G.GrmhdError) as e:
+        G.theta_ring_fix([e_.ctx for e_ in ring.e] + [ring.e[0].ctx], 0, nsw)
+    assert e.value.code == G.EINVAL
+    ring.close()
+    full.close()
+
+
 def test_ring_fix_refusals():
     """grmhd_theta_ring_fix takes the slabs of one grid, in theta order,
     covering every row, on one stream; a refusal launches nothing."""
