@@ -81,6 +81,25 @@ def test_slabs_with_ppm_and_cylindrification():
     assert np.array_equal(P, Pr) and np.array_equal(U, Ur)
 
 
+@pytest.mark.parametrize("R", [2, 4])
+def test_slab_ring_over_oracle_slabs(R):
+    """SlabRing (the single-device driver) with the oracle as its engines:
+    they have no CUDA stream, so the ring steps them by host calls (the graph
+    form is for library slabs) and reproduces the undecomposed oracle."""
+    pytest.importorskip("torch")
+    from paper_2205_02484_gb300.decomp import SlabRing
+    (P0, U0, t0, dt0), (Pr, Ur, tr, dtr) = _reference(3)
+    ring = SlabRing([S.OracleSlab(S.slab_params(_base(), r, R)) for r in range(R)])
+    assert not ring._capturable
+    ring.set_state(P0, U0, t0, dt0)
+    ring.step(3)
+    P = np.concatenate([e.get_state()[0] for e in ring.e], axis=3)
+    U = np.concatenate([e.get_state()[1] for e in ring.e], axis=3)
+    assert ring.e[0].get_state()[2:] == (tr, dtr)
+    assert np.array_equal(P, Pr) and np.array_equal(U, Ur)
+    _check_combined(ring.diagnostics(), _reference_grid(3).diagnostics())
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))

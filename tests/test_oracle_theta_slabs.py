@@ -183,8 +183,11 @@ def test_theta_ring_over_oracle_slabs():
     state = _torus_start(1, 3)
     ref = _undecomposed(_base(), state, 2)
     ring = ThetaRing([S.OracleThetaSlab(S.theta_params(_base(), r, 3)) for r in range(3)])
+    assert not ring.device_fix  # oracle engines: the fixup loop runs from the host
     ring.set_state(*state)
-    ring.step(2)
+    ring.step(1)
+    assert ring.sweeps[0] >= 2 and ring.sweeps[1] >= 2  # the block, across the face, both stages
+    ring.step(1)
     P = np.concatenate([e.get_state()[0] for e in ring.e], axis=2)
     U = np.concatenate([e.get_state()[1] for e in ring.e], axis=2)
     Pr, Ur, tr, dtr = ref.get_state()
