@@ -263,8 +263,6 @@ __global__ void k_prim2cons(Grid g, const double *P, const int *loc, double *U, 
     for (int c = 0; c < NU; c++) U[c * n + t] = Uz[c];
 }
 
-// mode 0: plain start from P; 1: the network's W first, then P; 2: P, then the
-// network's W as a rescue before Brent (the step's use)
 // The stand-alone inversion runs in two passes so that the zones leaving
 // Newton (the low-beta entropy inversions, Brent in W, the entropy inversion
 // after an unphysical Newton root: loops of their own length) do not hold
@@ -299,6 +297,8 @@ __device__ __forceinline__ void c2p_store(const int fl, const double q[NP], doub
     c2p_defer(list, t, defer);
 }
 
+// the first pass; mode 0: plain start from P; 1: the network's W first, then
+// P; 2: P, then the network's W as a rescue before Brent (the step's use)
 __global__ void __launch_bounds__(128) k_con2prim(Grid g, const double *U, const int *loc, double *P, int *flags,
                                                   int *iters, long n, const float *mlp, int mode, int *list)
 {
